@@ -1,0 +1,329 @@
+"""Seeded synthetic frontal matrices: the inputs of the solver, and nothing of its method.
+
+The paper applies its solver to the dense frontal matrices of a multifrontal
+elimination of 3D finite-element stiffness matrices (Section 6, Table 3).  Those
+matrices are not public, so the workloads here are their closest synthetic
+stand-in with the same structure: the exact Schur complement of a 3D
+variable-coefficient 7-point diffusion operator onto the separator plane in the
+middle of a box, i.e. a dense SPD front whose rows are the vertices of a 2D grid.
+
+Everything in this module is input preparation, shared by the CPU oracle, the
+CUDA path, the tests and the benchmark:
+
+* a counter-based normal generator (SplitMix64 finaliser + Box-Muller), so that
+  every coefficient and right-hand side is a pure function of (seed, index);
+* the coefficient fields (lognormal and checkerboard);
+* the exact FP64 plane-by-plane block-tridiagonal elimination of the box onto
+  its middle plane;
+* the recursive-bisection ordering of the plane (every HODLR node is then a
+  rectangle of the plane and a contiguous index range), the plane's 5-point
+  adjacency graph in that order (the sparse graph the BDLR row/column selection
+  of Section 5.3 walks), and the leaf boundaries of the resulting tree.
+
+No HODLR compression, factorisation, preconditioning or Krylov arithmetic is here.
+The elimination runs in PyTorch FP64 on whatever device it is given (CPU for the
+small cases, a GPU to make the large fronts quickly); the solver only ever sees the
+finished matrix.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "splitmix64", "uniform01", "normal", "coefficient_lognormal",
+    "coefficient_checkerboard", "face_coefficients", "plane_front",
+    "bisection_order", "plane_graph", "Front", "make_front", "rhs",
+    "WORKLOADS", "octree_boxes",
+]
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (Steele, Lea, Flood 2014) applied to counters x.
+
+    z = x + 0x9E3779B97F4A7C15; z = (z ^ z>>30) * 0xBF58476D1CE4E5B9;
+    z = (z ^ z>>27) * 0x94D049BB133111EB; return z ^ z>>31   (all mod 2^64).
+    """
+    z = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = z + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, counter: np.ndarray) -> np.ndarray:
+    """U(0,1) doubles from the counter-based stream (seed, counter).
+
+    The 64-bit counter word is seed * 2^40 + counter; the top 53 bits of its
+    SplitMix64 image give a double in [0, 1)."""
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        word = np.uint64(seed) * np.uint64(1 << 40) + c
+    bits = splitmix64(word) >> np.uint64(11)
+    return bits.astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, index: np.ndarray) -> np.ndarray:
+    """N(0,1) doubles: Box-Muller on the uniforms at counters 2g and 2g+1."""
+    g = np.asarray(index, dtype=np.uint64)
+    u1 = uniform01(seed, np.uint64(2) * g)
+    u2 = uniform01(seed, np.uint64(2) * g + np.uint64(1))
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# --------------------------------------------------------------------------- fields
+def coefficient_lognormal(nx: int, ny: int, nz: int, sigma: float, seed: int = 0,
+                          origin=(0, 0, 0), full_shape=None) -> np.ndarray:
+    """Node coefficients a = exp(sigma * z), z ~ N(0,1) from the global node index.
+
+    The field is defined on a (possibly larger) grid `full_shape` with x-fastest
+    global index g = i + X*(j + Y*k); the returned array is the box of size
+    nx*ny*nz starting at `origin`, indexed [k, j, i]."""
+    X, Y, _ = full_shape if full_shape is not None else (nx, ny, nz)
+    i = np.arange(nx) + origin[0]
+    j = np.arange(ny) + origin[1]
+    k = np.arange(nz) + origin[2]
+    g = i[None, None, :] + X * (j[None, :, None] + Y * k[:, None, None])
+    return np.exp(sigma * normal(seed, g.astype(np.uint64)))
+
+
+def coefficient_checkerboard(nx: int, ny: int, nz: int, cell: int = 8,
+                             contrast: float = 1e6) -> np.ndarray:
+    """a = 1 where (i//cell + j//cell + k//cell) is even, `contrast` where odd."""
+    i = np.arange(nx) // cell
+    j = np.arange(ny) // cell
+    k = np.arange(nz) // cell
+    par = (i[None, None, :] + j[None, :, None] + k[:, None, None]) % 2
+    return np.where(par == 1, contrast, 1.0)
+
+
+def face_coefficients(a: np.ndarray):
+    """Face coefficients of the 7-point finite-volume operator, h = 1.
+
+    Interior faces take the harmonic mean 2ab/(a+b) of the two nodes; a face to
+    the outside of the box (Dirichlet) takes the node's own coefficient.
+    Returns (fx, fy, fz) of shapes (nz,ny,nx+1), (nz,ny+1,nx), (nz+1,ny,nx)."""
+    nz, ny, nx = a.shape
+
+    def faces(axis):
+        lo = np.take(a, range(0, a.shape[axis] - 1), axis=axis)
+        hi = np.take(a, range(1, a.shape[axis]), axis=axis)
+        inner = 2.0 * lo * hi / (lo + hi)
+        first = np.take(a, [0], axis=axis)
+        last = np.take(a, [a.shape[axis] - 1], axis=axis)
+        return np.concatenate([first, inner, last], axis=axis)
+
+    return faces(2), faces(1), faces(0)
+
+
+# --------------------------------------------------------------------------- front
+def plane_front(a: np.ndarray, n_below: int, device="cpu") -> np.ndarray:
+    """Exact FP64 Schur complement of the box operator onto plane k = n_below.
+
+    Planes 0..n_below-1 and n_below+1..nz-1 are eliminated one plane at a time:
+    S_0 = T_0, S_{k+1} = T_{k+1} - C_k S_k^{-1} C_k, where T_k is the 2D block of
+    plane k (its diagonal carries all six face coefficients) and C_k is the
+    diagonal matrix of z-face coefficients between planes k and k+1.  The front is
+    T_m - C_below S_below^{-1} C_below - C_above S_above^{-1} C_above, returned in
+    the plane's natural x-fastest order, symmetrised exactly."""
+    import torch
+
+    nz, ny, nx = a.shape
+    n = nx * ny
+    m = n_below
+    fx, fy, fz = face_coefficients(a)
+    dev = torch.device(device)
+    f64 = torch.float64
+
+    def T(k):
+        diag = (fx[k, :, :-1] + fx[k, :, 1:] + fy[k, :-1, :] + fy[k, 1:, :]
+                + fz[k] + fz[k + 1]).reshape(-1)
+        t = torch.diag(torch.as_tensor(diag, dtype=f64, device=dev))
+        idx = np.arange(n).reshape(ny, nx)
+        # x-neighbours
+        r = torch.as_tensor(idx[:, :-1].reshape(-1), device=dev)
+        c = torch.as_tensor(idx[:, 1:].reshape(-1), device=dev)
+        v = torch.as_tensor(fx[k, :, 1:-1].reshape(-1), dtype=f64, device=dev)
+        t[r, c] = -v
+        t[c, r] = -v
+        # y-neighbours
+        r = torch.as_tensor(idx[:-1, :].reshape(-1), device=dev)
+        c = torch.as_tensor(idx[1:, :].reshape(-1), device=dev)
+        v = torch.as_tensor(fy[k, 1:-1, :].reshape(-1), dtype=f64, device=dev)
+        t[r, c] = -v
+        t[c, r] = -v
+        return t
+
+    def cz(k):  # z-faces between plane k and k+1
+        return torch.as_tensor(fz[k + 1].reshape(-1), dtype=f64, device=dev)
+
+    def eliminate(planes, links):
+        s = None
+        for step, k in enumerate(planes):
+            t = T(k)
+            if s is not None:
+                c = links[step - 1]
+                sinv = torch.cholesky_inverse(torch.linalg.cholesky(s))
+                t -= c[:, None] * sinv * c[None, :]
+                del sinv
+            s = t
+        return s
+
+    front = T(m)
+    if m > 0:
+        below = list(range(0, m))
+        s = eliminate(below, [cz(k) for k in below[:-1]])
+        c = cz(m - 1)
+        front -= c[:, None] * torch.cholesky_inverse(torch.linalg.cholesky(s)) * c[None, :]
+        del s
+    if m < nz - 1:
+        above = list(range(nz - 1, m, -1))
+        s = eliminate(above, [cz(k - 1) for k in above[:-1]])
+        c = cz(m)
+        front -= c[:, None] * torch.cholesky_inverse(torch.linalg.cholesky(s)) * c[None, :]
+        del s
+    front = 0.5 * (front + front.T)
+    return front.cpu().numpy() if dev.type == "cpu" else front
+
+
+# --------------------------------------------------------------------------- ordering
+def bisection_order(nx: int, ny: int, leaf: int):
+    """Recursive bisection of the nx-by-ny plane rectangle.
+
+    Each node is split across its longer side (x on ties) into a lower half of
+    floor(len/2) lines and an upper half; all nodes of a level are split together
+    until every node holds at most `leaf` vertices, giving a complete binary tree
+    of depth L.  Inside a leaf the order is lexicographic (x fastest).
+
+    Returns (perm, bounds, L, rects): perm[new] = natural index x + nx*y,
+    bounds = the 2^L + 1 leaf boundary offsets, rects = per-level rectangles."""
+    rects = [[(0, nx, 0, ny)]]
+    while max((x1 - x0) * (y1 - y0) for x0, x1, y0, y1 in rects[-1]) > leaf:
+        nxt = []
+        for x0, x1, y0, y1 in rects[-1]:
+            if (x1 - x0) >= (y1 - y0):
+                xm = x0 + (x1 - x0) // 2
+                nxt += [(x0, xm, y0, y1), (xm, x1, y0, y1)]
+            else:
+                ym = y0 + (y1 - y0) // 2
+                nxt += [(x0, x1, y0, ym), (x0, x1, ym, y1)]
+        rects.append(nxt)
+    perm = []
+    bounds = [0]
+    for x0, x1, y0, y1 in rects[-1]:
+        for y in range(y0, y1):
+            for x in range(x0, x1):
+                perm.append(x + nx * y)
+        bounds.append(len(perm))
+    return np.asarray(perm, dtype=np.int64), np.asarray(bounds, dtype=np.int64), len(rects) - 1, rects
+
+
+def plane_graph(nx: int, ny: int, perm: np.ndarray):
+    """5-point adjacency of the plane (the sparsity of the front's own block of the
+    3D operator) in the permuted order, as CSR (rowptr, colind) int32, columns
+    sorted ascending within each row."""
+    n = nx * ny
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    rows = [[] for _ in range(n)]
+    for new, old in enumerate(perm):
+        x, y = old % nx, old // nx
+        for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+            xx, yy = x + dx, y + dy
+            if 0 <= xx < nx and 0 <= yy < ny:
+                rows[new].append(int(inv[xx + nx * yy]))
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    colind = np.asarray([c for r in rows for c in sorted(r)], dtype=np.int32)
+    return rowptr, colind
+
+
+# --------------------------------------------------------------------------- workloads
+@dataclass
+class Front:
+    """A dense front in tree order plus everything a solver needs about it."""
+    A: object                 # n x n FP64 (numpy, or torch tensor when built on a GPU)
+    n: int
+    nx: int
+    ny: int
+    perm: np.ndarray          # tree order -> natural plane index
+    bounds: np.ndarray        # leaf boundaries (2^L + 1)
+    levels: int
+    rowptr: np.ndarray        # plane graph, CSR, tree order
+    colind: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+
+def _finish(A_nat, nx, ny, leaf, meta):
+    perm, bounds, L, _ = bisection_order(nx, ny, leaf)
+    if isinstance(A_nat, np.ndarray):
+        A = np.ascontiguousarray(A_nat[np.ix_(perm, perm)])
+    else:
+        import torch
+        p = torch.as_tensor(perm, device=A_nat.device)
+        A = A_nat.index_select(0, p).index_select(1, p).contiguous()
+    rowptr, colind = plane_graph(nx, ny, perm)
+    return Front(A, nx * ny, nx, ny, perm, bounds, L, rowptr, colind, meta)
+
+
+# The five synthetic workloads: grid (nx, ny, planes below, planes above), field, leaf.
+WORKLOADS = {
+    "plane576":  dict(nx=24, ny=24, below=8, above=8, field="lognormal", sigma=0.5, leaf=64),
+    "plane4096": dict(nx=64, ny=64, below=32, above=32, field="lognormal", sigma=0.5, leaf=128),
+    "checker16384": dict(nx=128, ny=128, below=16, above=16, field="checkerboard", leaf=256),
+    "plane32768": dict(nx=128, ny=256, below=4, above=4, field="lognormal", sigma=0.5, leaf=256),
+}
+
+
+def make_front(nx, ny, below, above, field="lognormal", sigma=0.5, leaf=64, seed=0,
+               device="cpu", cell=8, contrast=1e6):
+    """Build one plane front on an nx x ny x (below+1+above) box, in tree order."""
+    nz = below + 1 + above
+    if field == "lognormal":
+        a = coefficient_lognormal(nx, ny, nz, sigma, seed)
+    elif field == "checkerboard":
+        a = coefficient_checkerboard(nx, ny, nz, cell, contrast)
+    elif field == "constant":
+        a = np.ones((nz, ny, nx))
+    else:
+        raise ValueError(field)
+    A_nat = plane_front(a, below, device=device)
+    return _finish(A_nat, nx, ny, leaf, dict(nz=nz, below=below, above=above,
+                                             field=field, sigma=sigma, seed=seed))
+
+
+def octree_boxes(side: int = 64, min_side: int = 8):
+    """Octree reading of a nested-dissection tree of a side^3 grid: every box of
+    side s = side, side/2, ..., min_side contributes the front of its middle z-plane
+    (s/2 planes below it, s/2 - 1 above).  Returns [(s, (x0, y0, z0))] root first:
+    1 + 8 + 64 + 512 = 585 boxes for 64 -> 8."""
+    out = []
+    s = side
+    while s >= min_side:
+        m = side // s
+        for kz in range(m):
+            for jy in range(m):
+                for ix in range(m):
+                    out.append((s, (ix * s, jy * s, kz * s)))
+        s //= 2
+    return out
+
+
+def make_octree_front(s, origin, leaf, sigma=1.0, seed=0, side=64, device="cpu"):
+    """Front of one octree box of side s inside a side^3 lognormal field."""
+    a = coefficient_lognormal(s, s, s, sigma, seed, origin=origin, full_shape=(side, side, side))
+    A_nat = plane_front(a, s // 2, device=device)
+    return _finish(A_nat, s, s, leaf, dict(box=s, origin=origin, sigma=sigma, seed=seed))
+
+
+def rhs(n: int, s: int, seed: int = 1) -> np.ndarray:
+    """Right-hand sides B (n x s, column-major values) with B[i, c] ~ N(0,1) at
+    counter i + n*c of stream `seed`; returned as a C-contiguous n x s array."""
+    i = np.arange(n, dtype=np.uint64)[:, None]
+    c = np.arange(s, dtype=np.uint64)[None, :]
+    return np.ascontiguousarray(normal(seed, i + np.uint64(n) * c))

@@ -1,0 +1,419 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+hand-derived worked examples, closed forms, identities, brute force on tiny inputs.
+CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import frontgen as fg
+from oracle import hodlr_oracle as O
+
+
+# --------------------------------------------------------------------------- inputs
+def _dense_3d_operator(a):
+    """Assemble the 7-point operator of the whole box as a dense matrix, straight
+    from its stencil definition (x-fastest natural order)."""
+    nz, ny, nx = a.shape
+    fx, fy, fz = fg.face_coefficients(a)
+    N = nx * ny * nz
+    M = np.zeros((N, N))
+    idx = lambda i, j, k: i + nx * (j + ny * k)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                p = idx(i, j, k)
+                faces = [(fx[k, j, i], (i - 1, j, k)), (fx[k, j, i + 1], (i + 1, j, k)),
+                         (fy[k, j, i], (i, j - 1, k)), (fy[k, j + 1, i], (i, j + 1, k)),
+                         (fz[k, j, i], (i, j, k - 1)), (fz[k + 1, j, i], (i, j, k + 1))]
+                for c, (ii, jj, kk) in faces:
+                    M[p, p] += c
+                    if 0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz:
+                        M[p, idx(ii, jj, kk)] -= c
+    return M
+
+
+@pytest.mark.parametrize("field", ["lognormal", "checkerboard"])
+def test_front_is_brute_force_schur_complement(field):
+    nx, ny, nz, below = 4, 4, 5, 2
+    a = (fg.coefficient_lognormal(nx, ny, nz, 0.7, seed=3) if field == "lognormal"
+         else fg.coefficient_checkerboard(nx, ny, nz, cell=2, contrast=1e3))
+    M = _dense_3d_operator(a)
+    s = np.arange(nx * ny) + nx * ny * below
+    i = np.setdiff1d(np.arange(M.shape[0]), s)
+    S = M[np.ix_(s, s)] - M[np.ix_(s, i)] @ np.linalg.solve(M[np.ix_(i, i)], M[np.ix_(i, s)])
+    F = fg.plane_front(a, below)
+    assert np.allclose(F, S, rtol=1e-12, atol=1e-12 * np.abs(S).max())
+
+
+def test_front_invariants():
+    F = fg.make_front(8, 6, 3, 2, "lognormal", 0.5, leaf=8, seed=0)
+    A = F.A
+    assert np.array_equal(A, A.T)
+    np.linalg.cholesky(A)                                   # SPD
+    off = A - np.diag(np.diag(A))
+    assert off.max() <= 0.0                                 # M-matrix signs
+    assert A.sum(axis=1).min() >= -1e-12 * np.abs(A).max()  # row sums >= 0
+    # tree order: every leaf is a rectangle of the plane, sizes add up to n
+    assert F.bounds[-1] == F.n and np.all(np.diff(F.bounds) > 0)
+    assert sorted(F.perm.tolist()) == list(range(F.n))
+
+
+def test_constant_coefficient_stencil_is_translation_invariant():
+    a = np.ones((7, 10, 10))
+    F = fg.plane_front(a, 3)                                # natural order, 10x10 plane
+    idx = lambda x, y: x + 10 * y
+    # interior couplings depend only on the offset (away from the Dirichlet edges)
+    ref = F[idx(4, 4), idx(5, 6)]
+    assert math.isclose(F[idx(5, 5), idx(6, 7)], ref, rel_tol=1e-2)
+
+
+def test_rng_is_counter_based_and_normal():
+    z = fg.normal(7, np.arange(200000))
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    assert np.array_equal(fg.normal(7, np.arange(10, 20)), z[10:20])
+    # SplitMix64 reference value for input 0 (published test vector of the mixer)
+    assert int(fg.splitmix64(np.uint64(0))) == 0xE220A8397B1DCDAF
+
+
+def test_bisection_tree_geometry():
+    perm, bounds, L, rects = fg.bisection_order(24, 24, 64)
+    assert L == 4 and np.all(np.diff(bounds) == 36)
+    perm, bounds, L, rects = fg.bisection_order(64, 64, 128)
+    assert L == 5 and np.all(np.diff(bounds) == 128)
+    perm, bounds, L, rects = fg.bisection_order(256, 128, 256)
+    assert L == 7 and np.all(np.diff(bounds) == 256)
+    perm, bounds, L, rects = fg.bisection_order(64, 64, 128)
+    # the first split of a 64x64 plane is x < 32 | x >= 32
+    x = perm % 64
+    assert x[:2048].max() == 31 and x[2048:].min() == 32 and len(perm) == 4096
+
+
+def test_octree_count():
+    boxes = fg.octree_boxes(64, 8)
+    assert len(boxes) == 585
+    assert sorted({s for s, _ in boxes}) == [8, 16, 32, 64]
+
+
+# --------------------------------------------------------------------------- dense LU
+def test_lu_partial_textbook_example():
+    # Hand elimination of [[1,2,3],[4,5,6],[7,8,10]]: pivot 7 (row 3), then 6/7
+    # (original row 1) -> perm [2,0,1], L = [[1],[1/7,1],[4/7,1/2,1]],
+    # U = [[7,8,10],[0,6/7,11/7],[0,0,-1/2]].
+    A = np.array([[1.0, 2, 3], [4, 5, 6], [7, 8, 10]])
+    LU, perm = O.lu_partial(A)
+    assert perm.tolist() == [2, 0, 1]
+    L = np.tril(LU, -1) + np.eye(3)
+    U = np.triu(LU)
+    assert np.allclose(L, [[1, 0, 0], [1 / 7, 1, 0], [4 / 7, 0.5, 1]], atol=1e-15)
+    assert np.allclose(U, [[7, 8, 10], [0, 6 / 7, 11 / 7], [0, 0, -0.5]], atol=1e-15)
+    x = O.lu_solve(LU, perm, np.array([6.0, 15, 25]))
+    assert np.allclose(x, [1, 1, 1], atol=1e-14)
+
+
+def test_lu_partial_matches_lapack_pivots_and_residual():
+    import scipy.linalg as sla
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((60, 60))
+    LU, perm = O.lu_partial(A)
+    P, L, U = sla.lu(A)                    # A = P L U
+    assert np.array_equal(np.argmax(P, axis=0), perm)
+    assert np.allclose(np.tril(LU, -1) + np.eye(60), L, atol=1e-12)
+    b = rng.standard_normal(60)
+    x = O.lu_solve(LU, perm, b)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-14 * np.linalg.cond(A)
+
+
+def test_lu_partial_zero_pivot_raises():
+    with pytest.raises(np.linalg.LinAlgError):
+        O.lu_partial(np.array([[0.0, 1.0], [0.0, 2.0]]))
+
+
+# --------------------------------------------------------------------------- ACA
+def _aca_matrix(M, tol, cap=1 << 30):
+    return O.aca(lambda i: M[i], lambda j: M[:, j], M.shape[0], M.shape[1], tol, cap)
+
+
+def test_aca_hand_example():
+    # Hand run of partial-pivoting ACA on [[1,3,2],[2,1,0],[0,0,5]]:
+    # row 0 -> |3| at col 1, v1 = [1/3,1,2/3], u1 = [3,1,0]; next row = 1 (|u1|);
+    # residual row 1 = [5/3,0,-2/3] -> col 0, v2 = [1,0,-2/5], u2 = [0,5/3,0];
+    # row 2 residual [0,0,5] -> col 2, v3 = [0,0,1], u3 = [0,0,5].
+    M = np.array([[1.0, 3, 2], [2, 1, 0], [0, 0, 5]])
+    r = _aca_matrix(M, 1e-15)
+    assert r.rows == [0, 1, 2] and r.cols == [1, 0, 2]
+    assert np.allclose(r.V[:, 0], [1 / 3, 1, 2 / 3], atol=1e-15)
+    assert np.allclose(r.U[:, 1], [0, 5 / 3, 0], atol=1e-15)
+    assert np.allclose(r.V[:, 1], [1, 0, -0.4], atol=1e-15)
+    assert np.allclose(r.U @ r.V.T, M, atol=1e-14)
+
+
+def test_aca_tie_break_and_zero_row():
+    # equal magnitudes in the first row -> lowest column; a zero first row is
+    # skipped (marked used) and the lowest unused row is tried next.
+    M = np.array([[2.0, -2.0, 1.0], [1.0, 1.0, 1.0]])
+    r = _aca_matrix(M, 1e-15)
+    assert r.cols[0] == 0
+    Z = np.array([[0.0, 0.0, 0.0], [0.0, 4.0, 1.0], [0.0, 2.0, 3.0]])
+    r = _aca_matrix(Z, 1e-15)
+    assert r.rows[0] == 1 and r.cols[0] == 1
+    assert np.allclose(r.U @ r.V.T, Z, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [1, 4, 9])
+def test_aca_recovers_exact_rank_k(k):
+    rng = np.random.default_rng(k)
+    M = rng.standard_normal((70, k)) @ rng.standard_normal((k, 55))
+    r = _aca_matrix(M, 1e-10)
+    assert r.U.shape[1] in (k, k + 1)
+    assert np.linalg.norm(M - r.U @ r.V.T) / np.linalg.norm(M) < 1e-13
+
+
+def test_aca_norm_recurrence_is_frobenius_norm():
+    rng = np.random.default_rng(5)
+    x = np.linspace(0, 1, 80)
+    M = 1.0 / (1.0 + np.abs(x[:, None] - (x[None, :] + 1.5)))   # smooth kernel
+    r = _aca_matrix(M, 1e-9)
+    exact = np.linalg.norm(r.U @ r.V.T) ** 2
+    assert math.isclose(r.norm2, exact, rel_tol=1e-12)
+    assert np.linalg.norm(M - r.U @ r.V.T) / np.linalg.norm(M) < 1e-7
+
+
+def test_aca_rank_cap():
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((30, 30))
+    r = _aca_matrix(M, 1e-12, cap=5)
+    assert r.U.shape[1] == 5 and r.cap_hit
+
+
+def test_aca_zero_block():
+    r = _aca_matrix(np.zeros((4, 6)), 1e-6)
+    assert r.U.shape == (4, 0) and r.V.shape == (6, 0)
+
+
+# --------------------------------------------------------------------------- BDLR
+def test_boundary_distance_on_grid():
+    # 4x4 plane, natural order; rows = left half (x in {0,1}) is not contiguous in
+    # natural order, so use the tree order of bisection_order(4,4,8): first half x<2.
+    perm, bounds, L, _ = fg.bisection_order(4, 4, 8)
+    rowptr, colind = fg.plane_graph(4, 4, perm)
+    sel, dist = O.boundary_distance(rowptr, colind, range(0, 8), range(8, 16), depth=5)
+    xs = perm[:8] % 4
+    assert np.array_equal(dist, np.where(xs == 1, 0, 1))       # x=1 column is d=0
+    assert [int(perm[v] % 4) for v in sel[:4]] == [1, 1, 1, 1]
+    sel0, _ = O.boundary_distance(rowptr, colind, range(0, 8), range(8, 16), depth=0)
+    assert len(sel0) == 4
+
+
+def test_full_pivot_lu_hand_example():
+    # [[1,4],[2,3]]: largest |4| at (0,1) -> swap columns; l = 3/4; 2 - 3/4 = 5/4.
+    LU, prow, pcol, r = O.full_pivot_lu(np.array([[1.0, 4.0], [2.0, 3.0]]), 0.0)
+    assert r == 2 and prow.tolist() == [0, 1] and pcol.tolist() == [1, 0]
+    assert np.allclose(np.diag(LU), [4.0, 1.25])
+    # truncation: keep while |p_k| >= eps |p_1|
+    _, _, _, r = O.full_pivot_lu(np.array([[1.0, 4.0], [2.0, 3.0]]), 0.5)
+    assert r == 1
+
+
+def test_full_pivot_lu_reconstructs():
+    rng = np.random.default_rng(2)
+    Ah = rng.standard_normal((12, 9))
+    LU, prow, pcol, r = O.full_pivot_lu(Ah, 0.0)
+    assert r == 9
+    L = np.tril(LU, -1)[:, :9] + np.eye(12, 9)
+    U = np.triu(LU[:9, :9])
+    assert np.allclose(Ah[prow][:, pcol], L @ U, atol=1e-13)
+
+
+def _front_small(leaf=16):
+    return fg.make_front(12, 12, 4, 4, "lognormal", 0.5, leaf=leaf, seed=0)
+
+
+def test_bdlr_closed_form_skeleton():
+    F = _front_small()
+    A = F.A
+    tree = O.make_tree(F.n, 16, F.bounds)
+    a0, a1 = tree.range(1, 0)
+    b0, b1 = tree.range(1, 1)
+    res = O.bdlr(A, F.rowptr, F.colind, range(a0, a1), range(b0, b1), 1e-6, 3)
+    r = len(res.Ir)
+    assert r > 0 and len(set(res.Ir)) == r and set(res.Ir) <= set(res.I)
+    C = A[a0:a1][:, res.Jr]
+    R = A[res.Ir][:, b0:b1]
+    closed = C @ np.linalg.solve(A[np.ix_(res.Ir, res.Jr)], R)
+    assert np.allclose(res.U @ res.V.T, closed, rtol=1e-10, atol=1e-12 * np.abs(closed).max())
+
+
+def test_bdlr_exact_when_skeleton_has_full_rank():
+    rng = np.random.default_rng(9)
+    n = 32
+    k = 3
+    A = np.eye(n) * 10
+    A[:16, 16:] = rng.standard_normal((16, k)) @ rng.standard_normal((k, 16))
+    A[16:, :16] = A[:16, 16:].T
+    # chain graph 0-1-...-31: the boundary of [0,16) is vertex 15
+    rows = [[1]] + [[i - 1, i + 1] for i in range(1, n - 1)] + [[n - 2]]
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    colind = np.asarray([c for r in rows for c in r], dtype=np.int32)
+    res = O.bdlr(A, rowptr, colind, range(0, 16), range(16, 32), 1e-10, 6)
+    assert len(res.Ir) == k
+    blk = A[:16, 16:]
+    assert np.linalg.norm(res.U @ res.V.T - blk) / np.linalg.norm(blk) < 1e-12
+
+
+# --------------------------------------------------------------------------- HODLR
+def test_make_tree_halving():
+    t = O.make_tree(576, 64)
+    assert t.L == 4 and t.range(4, 0) == (0, 36) and t.range(0, 0) == (0, 576)
+    t = O.make_tree(100, 30)
+    assert t.L == 2 and t.bounds.tolist() == [0, 25, 50, 75, 100]
+
+
+def test_assemble_exact_hodlr_matrix():
+    # A matrix that is exactly HODLR (rank-2 off-diagonal blocks) is reproduced.
+    rng = np.random.default_rng(4)
+    n = 64
+    tree = O.make_tree(n, 16)
+    A = np.diag(rng.uniform(5, 6, n))
+    for l in range(tree.L):
+        for i in range(1 << l):
+            a0, a1 = tree.range(l + 1, 2 * i)
+            b0, b1 = tree.range(l + 1, 2 * i + 1)
+            A[a0:a1, b0:b1] = rng.standard_normal((a1 - a0, 2)) @ rng.standard_normal((2, b1 - b0)) * 0.1
+            A[b0:b1, a0:a1] = rng.standard_normal((b1 - b0, 2)) @ rng.standard_normal((2, a1 - a0)) * 0.1
+    for l in range(tree.L + 1):          # leaf blocks random
+        pass
+    blocks = O.build(A, tree, "aca", 1e-12)
+    K = O.assemble(A, tree, blocks)
+    assert np.linalg.norm(K - A) / np.linalg.norm(A) < 1e-13
+
+
+def test_one_level_woodbury_by_hand():
+    # One level: K~ = diag(K1,K2) + [[0, U1 V12^T],[U2 V21^T, 0]] = D + U C V^T with
+    # U = blkdiag(U1,U2), V^T = [[0, V12^T],[V21^T, 0]]; Woodbury:
+    # K~^-1 = D^-1 - D^-1 U (I + V^T D^-1 U)^-1 V^T D^-1.
+    rng = np.random.default_rng(8)
+    F = fg.make_front(8, 8, 3, 3, "lognormal", 0.5, leaf=32, seed=1)
+    A = F.A
+    tree = O.make_tree(F.n, 32, F.bounds)
+    assert tree.L == 1
+    blocks = O.build(A, tree, "aca", 1e-3)
+    blk = blocks[(0, 0)]
+    K = O.assemble(A, tree, blocks)
+    D = np.zeros_like(A)
+    D[:32, :32] = A[:32, :32]
+    D[32:, 32:] = A[32:, 32:]
+    ra, rb = blk.Ua.shape[1], blk.Ub.shape[1]
+    Ublk = np.zeros((64, ra + rb))
+    Ublk[:32, :ra] = blk.Ua
+    Ublk[32:, ra:] = blk.Ub
+    Vt = np.zeros((ra + rb, 64))
+    Vt[:ra, 32:] = blk.Vab.T
+    Vt[ra:, :32] = blk.Vba.T
+    assert np.allclose(D + Ublk @ Vt, K, atol=1e-13)
+    Dinv = np.linalg.inv(D)
+    Kinv = Dinv - Dinv @ Ublk @ np.linalg.solve(np.eye(ra + rb) + Vt @ Dinv @ Ublk, Vt @ Dinv)
+    Fac = O.factor(A, tree, blocks)
+    b = rng.standard_normal((64, 3))
+    assert np.allclose(O.solve(Fac, b), Kinv @ b, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("method", ["aca", "bdlr"])
+def test_solve_equals_dense_inverse_of_assembled(method):
+    F = fg.make_front(16, 16, 4, 4, "lognormal", 0.5, leaf=16, seed=0)
+    A = F.A
+    tree = O.make_tree(F.n, 16, F.bounds)
+    blocks = O.build(A, tree, method, 1e-4, graph=(F.rowptr, F.colind), depth=4)
+    K = O.assemble(A, tree, blocks)
+    Fac = O.factor(A, tree, blocks)
+    b = fg.rhs(F.n, 3, seed=1)
+    x = O.solve(Fac, b)
+    ref = np.linalg.solve(K, b)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-12 * np.linalg.cond(K)
+    # the approximation error of K~ is small at this tolerance
+    assert np.linalg.norm(K - A) / np.linalg.norm(A) < 1e-3
+
+
+def test_factor_d_is_inverse_times_u():
+    F = _front_small()
+    A = F.A
+    tree = O.make_tree(F.n, 16, F.bounds)
+    blocks = O.build(A, tree, "aca", 1e-6)
+    K = O.assemble(A, tree, blocks)
+    Fac = O.factor(A, tree, blocks)
+    # d_i^(l) = (K~ restricted to node (l,i))^-1 U_i^(l)
+    for (l, i), d in Fac.d.items():
+        s, e = tree.range(l, i)
+        par = blocks[(l - 1, i // 2)]
+        U = par.Ua if i % 2 == 0 else par.Ub
+        ref = np.linalg.solve(K[s:e, s:e], U)
+        assert np.allclose(d, ref, rtol=1e-10, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+# --------------------------------------------------------------------------- GMRES
+def test_gmres_diagonal_distinct_eigenvalues():
+    vals = np.repeat([1.0, 2.0, 5.0, 7.0], 10)
+    A = np.diag(vals)
+    b = np.random.default_rng(0).standard_normal(40)
+    r = O.gmres(A, b, tol=1e-12, max_iter=50)
+    assert r.iters <= 4 and r.true_relres <= 1e-12
+
+
+def test_gmres_exact_preconditioner_one_step():
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((30, 30)) + 30 * np.eye(30)
+    b = rng.standard_normal(30)
+    r = O.gmres(A, b, prec=lambda v: np.linalg.solve(A, v), tol=1e-12)
+    assert r.iters == 1 and r.true_relres < 1e-13
+
+
+def test_gmres_iterate_is_krylov_least_squares():
+    rng = np.random.default_rng(2)
+    n = 24
+    A = rng.standard_normal((n, n)) + 6 * np.eye(n)
+    M = np.diag(rng.uniform(0.5, 2.0, n))               # right preconditioner M^-1
+    b = rng.standard_normal(n)
+    for k in (1, 3, 6):
+        r = O.gmres(A, b, prec=lambda v: M @ v, tol=1e-30, max_iter=k)
+        # brute force: x in M K_k(A M, b), minimise ||b - A x||
+        Kry = [b]
+        for _ in range(k - 1):
+            Kry.append(A @ (M @ Kry[-1]))
+        Kmat = M @ np.stack(Kry, axis=1)
+        c, *_ = np.linalg.lstsq(A @ Kmat, b, rcond=None)
+        assert np.allclose(r.x, Kmat @ c, rtol=1e-8, atol=1e-10)
+        assert math.isclose(r.est_relres, np.linalg.norm(b - A @ (Kmat @ c)) / np.linalg.norm(b),
+                            rel_tol=1e-6)
+
+
+def test_gmres_zero_rhs_and_max_iter():
+    A = np.eye(5) * 2
+    r = O.gmres(A, np.zeros(5))
+    assert r.iters == 0 and r.converged
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((40, 40)) + 2 * np.eye(40)
+    r = O.gmres(A, rng.standard_normal(40), tol=1e-14, max_iter=3)
+    assert r.iters == 3 and not r.converged
+
+
+def test_hodlr_preconditioned_gmres_on_front():
+    F = fg.make_front(24, 24, 8, 8, "lognormal", 0.5, leaf=64, seed=0)
+    A = F.A
+    tree = O.make_tree(F.n, 64, F.bounds)
+    blocks, Fac, P = O.hodlr_precond(A, tree, "aca", 1e-6)
+    b = fg.rhs(F.n, 1, seed=1)[:, 0]
+    r = O.gmres(A, b, prec=P, tol=1e-12)
+    assert r.converged and r.true_relres <= 1e-12
+    plain = O.gmres(A, b, tol=1e-12)
+    assert r.iters < plain.iters
+    assert O.dense_floor(A, b) < 1e-14
+
+
+def test_precond_error_limits():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((20, 20)) + 20 * np.eye(20)
+    Om = rng.standard_normal((20, 4))
+    assert O.precond_error(A, lambda v: np.linalg.solve(A, v), Om) < 1e-14
+    e = O.precond_error(A, lambda v: v, Om)
+    assert math.isclose(e, np.linalg.norm(Om - A @ Om) / np.linalg.norm(Om))
