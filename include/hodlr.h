@@ -1,0 +1,229 @@
+/*
+ * hodlr.h -- C ABI of libhodlr: HODLR-preconditioned GMRES for dense frontal
+ * matrices on one GB300 GPU (sm_103a).
+ *
+ * The library follows Aminfar, Ambikasaran and Darve, "A Fast Block Low-Rank
+ * Dense Solver with Applications to Finite-Element Matrices" (arXiv:1403.5337):
+ *
+ *   problem     K x = F, K in R^{n x n} dense, x, F in R^{n x s}       (Sec. 4.2)
+ *   structure   HODLR: K = [[K1, U1 V12^T], [U2 V21^T, K2]] recursively (Sec. 4.1)
+ *   compression ACA with partial pivoting (Sec. 5.1) or BDLR, the boundary-
+ *               distance pseudo-skeleton with a full-pivoting LU (Sec. 5.3)
+ *   factor      the recursive Sherman-Morrison-Woodbury scheme: leaf LU, one
+ *               Woodbury core S_i^(p) per node (Sec. 4.3, Factorize)
+ *   solve       applying the factored inverse (Sec. 4.3, Solve)
+ *   iterative   GMRES with the low-accuracy HODLR solve as preconditioner (Sec. 3)
+ *
+ * Conventions common to every call
+ * --------------------------------
+ * - Pointers named "device" are CUDA device pointers on the context's device;
+ *   "host" pointers are ordinary host memory.  No call takes ownership of a
+ *   caller buffer.  The caller keeps A (and the graph) alive and unchanged for
+ *   as long as any hodlr_t built from it, or any gmres_solve using it, is in use.
+ * - Dense matrices are FP64 and ROW-major with a leading dimension (ld >= n).
+ *   Right-hand sides and solutions are n x s, COLUMN-major (each right-hand side
+ *   contiguous), with ld >= n.
+ * - The index order of A is the HODLR tree order: every tree node is a
+ *   contiguous index range.  By default the tree halves each range (lower half
+ *   floor(size/2)) until all leaves hold at most `leaf` rows; explicit leaf
+ *   boundaries may be passed instead (hodlr_opts.leaf_bounds).
+ * - Calls are ordered on the CUDA stream they are given (NULL = legacy default
+ *   stream).  hodlr_build and gmres_solve synchronise that stream before they
+ *   return (they read a few device scalars); hodlr_factor and hodlr_solve do not.
+ * - Every call returns a hodlr_status.  On failure hodlr_last_error() gives a
+ *   thread-local message.  Device-side failures (a zero pivot, a non-finite
+ *   value, a wait that ran out of its budget) are reported through a device
+ *   status word that the next synchronising call reads; they never trap.
+ * - Library-owned device memory comes from the allocator given to
+ *   hodlr_ctx_create (or cudaMallocAsync / cudaFreeAsync when none is given).
+ */
+#ifndef HODLR_H
+#define HODLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HODLR_ABI_VERSION 1
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *hodlr_stream;
+
+typedef enum {
+    HODLR_OK = 0,
+    HODLR_INVALID_ARG = 1,      /* a size, pointer or option is out of range        */
+    HODLR_OUT_OF_MEMORY = 2,    /* the allocator returned NULL                       */
+    HODLR_CUDA_ERROR = 3,       /* a CUDA runtime call failed                        */
+    HODLR_SINGULAR = 4,         /* zero pivot in a leaf block or a Woodbury core     */
+    HODLR_NOT_FACTORED = 5,     /* hodlr_solve / gmres_solve before hodlr_factor     */
+    HODLR_NOT_CONVERGED = 6,    /* GMRES hit max_iter; X holds the last iterate      */
+    HODLR_TIMEOUT = 7,          /* a device-side wait exceeded its budget            */
+    HODLR_NONFINITE_INPUT = 8,  /* NaN/Inf (or an FP64 entry outside the range the
+                                   double-float matvec represents) in A or B         */
+    HODLR_RANGE = 9             /* a size exceeds a fixed limit of the call          */
+} hodlr_status;
+
+typedef enum { HODLR_ACA = 0, HODLR_BDLR = 1 } hodlr_method;
+
+/* Arithmetic of the HODLR part (compression is FP64 or FP32, see hodlr_opts).
+ * GMRES itself is always FP64-accurate. */
+typedef enum {
+    HODLR_FP64 = 0,   /* plain FP64 factor and apply                              */
+    HODLR_FP32 = 1,   /* FP32 factor and apply                                     */
+    HODLR_BF16 = 2,   /* BF16 storage of U, V, d with FP32 accumulation            */
+    HODLR_FP16 = 3    /* FP16 storage with a power-of-two scale per column         */
+} hodlr_precision;
+
+/* Device allocator callbacks (e.g. a framework's caching allocator).  alloc must
+ * return memory usable on `stream` or NULL; free receives the same stream. */
+typedef void *(*hodlr_alloc_fn)(size_t bytes, void *user, hodlr_stream stream);
+typedef void (*hodlr_free_fn)(void *ptr, size_t bytes, void *user, hodlr_stream stream);
+
+typedef struct hodlr_ctx hodlr_ctx;
+typedef struct hodlr_s hodlr_t;
+
+/* A dense FP64 matrix in device memory, row-major, leading dimension ld. */
+typedef struct {
+    const double *data;   /* device                                                 */
+    int64_t n;            /* rows = columns                                         */
+    int64_t ld;           /* >= n                                                   */
+    int symmetric;        /* 1 if A == A^T exactly: columns are then read as rows
+                             (a faster access pattern; values are identical)        */
+} hodlr_matrix;
+
+/* The sparse graph whose vertices are the rows/columns of A (Sec. 5.3): CSR in
+ * host memory, tree order, no self loops.  Required for BDLR, else NULL. */
+typedef struct {
+    const int32_t *rowptr;   /* host, n + 1 */
+    const int32_t *colind;   /* host, rowptr[n] */
+    int64_t n;
+} hodlr_graph;
+
+typedef struct {
+    int precision;              /* hodlr_precision of factor + apply (default FP32)  */
+    int compress_precision;     /* HODLR_FP64 or HODLR_FP32 arithmetic for ACA/BDLR;
+                                   -1 = FP64 if precision == FP64, else FP32         */
+    int rank_cap;               /* maximum rank of an off-diagonal block (<= 1024);
+                                   0 = 1024                                          */
+    int bdlr_depth;             /* BDLR distance depth d; -1 = round(-log10 tol)     */
+    double core_cond_threshold; /* reserved (Woodbury core condition guard); 0      */
+    const int64_t *leaf_bounds; /* host, optional: 2^L + 1 leaf boundary offsets     */
+    int n_leaf_bounds;          /* length of leaf_bounds, or 0                       */
+    uint64_t seed;              /* probe seed of hodlr_precond_error                 */
+} hodlr_opts;
+
+/* Per-call statistics of a built (and possibly factored) HODLR matrix. */
+#define HODLR_MAX_LEVELS 16
+typedef struct {
+    int64_t n;
+    int levels;                          /* L: leaves are at level L               */
+    int leaf_max;                        /* largest leaf                           */
+    int rank_max[HODLR_MAX_LEVELS];      /* max off-diagonal rank at level 1..L (index l-1) */
+    int rank_pad[HODLR_MAX_LEVELS];      /* padded rank used for storage           */
+    double rank_mean[HODLR_MAX_LEVELS];
+    int cap[HODLR_MAX_LEVELS];           /* pivot-list stride of level 1..L       */
+    int cap_hit;                        /* 1 if a block stopped at rank_cap       */
+    int64_t bytes_factors;               /* device bytes of V, d, leaf and core factors */
+    int factored;
+    double ms_compress, ms_factor;       /* device time of the last build / factor */
+} hodlr_stats;
+
+/* Per-right-hand-side GMRES results (arrays of length s supplied by the caller,
+ * host memory; any pointer may be NULL). */
+typedef struct {
+    int *iters;                /* Arnoldi steps used                                 */
+    double *est_relres;        /* |g_{j+1}| / ||b|| at exit                           */
+    double *true_relres;       /* ||b - A x|| / ||b|| recomputed at exit              */
+    int restarts;              /* restarts taken (true residual missed tol)          */
+    double ms_total;           /* device time of the whole solve                      */
+} hodlr_gmres_info;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device`.  alloc/free may be NULL (then
+ * cudaMallocAsync / cudaFreeAsync are used).  *out receives the context. */
+hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn free_fn,
+                              void *alloc_user, hodlr_ctx **out);
+hodlr_status hodlr_ctx_destroy(hodlr_ctx *ctx);
+
+/* Default options (precision FP32, compress -1, rank_cap 0, depth -1). */
+void hodlr_opts_default(hodlr_opts *o);
+
+/* ---------------------------------------------------------------- HODLR */
+/* Compress A into HODLR form (Sec. 4.3 Factorize step 1; Sec. 5.1 / 5.3): every
+ * off-diagonal block of every level, A(alpha,beta) ~ U_alpha V_alpha,beta^T, by
+ * ACA to relative tolerance `tol` or by BDLR with pivot threshold `tol` and the
+ * graph `g`.  `leaf` is the maximum leaf size (>= 1; ignored when leaf_bounds is
+ * given).  The result keeps a pointer to A.  Synchronises `stream`. */
+hodlr_status hodlr_build(hodlr_ctx *ctx, const hodlr_matrix *A, int leaf, double tol,
+                         int method, const hodlr_graph *g, const hodlr_opts *o,
+                         hodlr_stream stream, hodlr_t **out);
+
+/* Recursive Woodbury factorisation (Sec. 4.3 Factorize steps 2-5), level by
+ * level from the leaves: leaf inverses, d = K^-1 U for every node, and the core
+ * S_i^(p) of every internal node, inverted.  Stream-ordered, no host sync; a
+ * singular leaf or core is reported by the next synchronising call. */
+hodlr_status hodlr_factor(hodlr_t *h, hodlr_stream stream);
+
+/* X <- K~^-1 X in place (Sec. 4.3 Solve) for s right-hand sides: X device,
+ * n x s column-major, ld >= n.  Arithmetic in the factor's precision, FP64 in
+ * and out.  Stream-ordered, no host sync. */
+hodlr_status hodlr_solve(hodlr_t *h, int s, double *X, int64_t ldx, hodlr_stream stream);
+
+/* GMRES (Sec. 3) for A X = B with right preconditioner P^-1 = K~^-1 (P may be
+ * NULL: no preconditioner).  B, X device, n x s column-major.  Each column is an
+ * independent system; x0 = 0.  Flexible right-preconditioned Arnoldi (classical
+ * Gram-Schmidt applied twice, Givens rotations, all on the device), stopping
+ * when the estimated residual <= tol ||b||; the true residual is then
+ * recomputed and the solve restarts from x while it misses tol.  restart = 0
+ * means one cycle of up to max_iter steps.  Returns HODLR_NOT_CONVERGED with X
+ * = the last iterate if some column misses tol within max_iter steps.
+ * Synchronises `stream`. */
+hodlr_status gmres_solve(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *B,
+                         int64_t ldb, double *X, int64_t ldx, const hodlr_t *P, double tol,
+                         int max_iter, int restart, hodlr_gmres_info *info,
+                         hodlr_stream stream);
+
+/* W <- A Z (device, n x s column-major) with the FP64-accurate double-float
+ * matvec used inside gmres_solve. */
+hodlr_status hodlr_matvec(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *Z,
+                          int64_t ldz, double *W, int64_t ldw, hodlr_stream stream);
+
+/* Preconditioner quality ||(I - P^-1 A) Omega||_F / ||Omega||_F for a caller
+ * probe block Omega (device, n x k column-major, ld >= n); *out is host.  A is
+ * the matrix the HODLR form was built from.  Synchronises `stream`. */
+hodlr_status hodlr_precond_error(hodlr_t *h, int k, const double *Omega, int64_t ldo,
+                                 double *out, hodlr_stream stream);
+
+hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *out);
+
+/* Copy one level's factors to host memory, for inspection and testing.
+ * level = 1..L.  U_or_d, V: n x rank_pad[level-1] column-major FP64 (the U
+ * columns before hodlr_factor, d = K_node^-1 U_node after it; rows of a node
+ * beyond its rank are zero).  ranks: 2^level ints.  piv_rows / piv_cols:
+ * 2^level x cap[level-1] ints, the block-local pivot rows/columns of each
+ * node's block A(node, sibling) in pivot order (ACA: i_k, j_k; BDLR: the kept
+ * skeleton rows/columns), -1 past the rank.  Any output may be NULL.
+ * Synchronises `stream`. */
+hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U_or_d, double *V,
+                                int32_t *ranks, int32_t *piv_rows, int32_t *piv_cols,
+                                hodlr_stream stream);
+
+/* Copy the inverted Woodbury cores of level `level` (0..L-1: the parents of
+ * level level+1) to host memory: 2^level blocks of (2 rp)^2 FP64, column-major,
+ * rp = rank_pad[level].  Block i is S_i^-1 with S_i = [[I, V_ba^T d_a],
+ * [V_ab^T d_b, I]] of the node's children a = 2i, b = 2i+1 (Sec. 4.3 step 4).
+ * Synchronises `stream`. */
+hodlr_status hodlr_export_core(const hodlr_t *h, int level, double *Sinv, hodlr_stream stream);
+
+hodlr_status hodlr_destroy(hodlr_t *h);
+
+const char *hodlr_status_string(hodlr_status s);
+const char *hodlr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HODLR_H */

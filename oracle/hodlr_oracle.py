@@ -135,14 +135,21 @@ class ACAResult:
     cap_hit: bool = False
 
 
-def aca(row, col, m: int, n: int, tol: float, rank_cap: int) -> ACAResult:
+def aca(row, col, m: int, n: int, tol: float, rank_cap: int, dtype=np.float64) -> ACAResult:
     """Partial-pivoting adaptive cross approximation (Section 5.1).
 
     `row(i)` returns block row i (length n), `col(j)` block column j (length m).
     Step k: residual row r = row(i_k) - sum_l U[i_k,l] V[:,l]; j_k = argmax |r|;
     v_k = r / r[j_k]; u_k = col(j_k) - sum_l V[j_k,l] U[:,l]; next row =
     argmax over unused rows of |u_k|.  ||S_k||_F^2 is updated by
-    ||S_{k-1}||^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l) + ||u_k||^2 ||v_k||^2."""
+    ||S_{k-1}||^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l) + ||u_k||^2 ||v_k||^2.
+
+    `dtype` is the precision the residual rows/columns, their pivots and the
+    scaled vectors are formed and decided in (float64, or float32 for the
+    single-precision compression: block entries are rounded to float32 first).
+    The dot products are formed in that precision too; the norm recurrence and
+    the stopping test are evaluated in float64."""
+    dt = np.dtype(dtype)
     kmax = min(m, n, rank_cap)
     us, vs = [], []
     rows, cols = [], []
@@ -151,7 +158,7 @@ def aca(row, col, m: int, n: int, tol: float, rank_cap: int) -> ACAResult:
     i = 0
     res = ACAResult(np.zeros((m, 0)), np.zeros((n, 0)))
     while len(us) < kmax:
-        r = np.array(row(i), dtype=np.float64, copy=True)
+        r = np.array(row(i), dtype=np.float64).astype(dt)
         for l in range(len(us)):
             r = r - us[l][i] * vs[l]
         used[i] = True
@@ -163,13 +170,13 @@ def aca(row, col, m: int, n: int, tol: float, rank_cap: int) -> ACAResult:
             i = int(free[0])
             continue
         v = r / r[j]
-        u = np.array(col(j), dtype=np.float64, copy=True)
+        u = np.array(col(j), dtype=np.float64).astype(dt)
         for l in range(len(us)):
             u = u - vs[l][j] * us[l]
         cross = 0.0
         for l in range(len(us)):
-            cross += (u @ us[l]) * (v @ vs[l])
-        uu, vv = u @ u, v @ v
+            cross += float(u @ us[l]) * float(v @ vs[l])
+        uu, vv = float(u @ u), float(v @ v)
         norm2 = norm2 + 2.0 * cross + uu * vv
         us.append(u)
         vs.append(v)
@@ -184,8 +191,8 @@ def aca(row, col, m: int, n: int, tol: float, rank_cap: int) -> ACAResult:
             break
         i = int(np.argmax(cand))
     k = len(us)
-    res.U = np.stack(us, axis=1) if k else np.zeros((m, 0))
-    res.V = np.stack(vs, axis=1) if k else np.zeros((n, 0))
+    res.U = np.stack(us, axis=1).astype(np.float64) if k else np.zeros((m, 0))
+    res.V = np.stack(vs, axis=1).astype(np.float64) if k else np.zeros((n, 0))
     res.rows, res.cols, res.norm2 = rows, cols, norm2
     res.cap_hit = (k == rank_cap and k < min(m, n))
     return res
@@ -222,19 +229,21 @@ def boundary_distance(rowptr, colind, own: range, other: range, depth: int):
     return [v for _, v in sel], dist
 
 
-def full_pivot_lu(Ahat: np.ndarray, eps: float):
+def full_pivot_lu(Ahat: np.ndarray, eps: float, kmax: int = 1 << 30, dtype=np.float64):
     """Full-pivoting LU of A^ (eq. Ahat): at step k take the largest |entry| of the
     trailing block (lowest local row, then column, on ties), swap it to (k,k),
     divide the column below by it and subtract the rank-1 product.  Stop before the
     first pivot with |p_k| < eps |p_1| (or a zero pivot, or exhaustion).
+    At most kmax pivots are taken (the rank cap).  The arithmetic (division and
+    the rank-1 update, a separate multiply and subtract) runs in `dtype`.
     Returns (LU packed, row order, column order, r)."""
-    a = np.array(Ahat, dtype=np.float64, copy=True)
+    a = np.array(Ahat, dtype=np.float64).astype(dtype)
     mi, nj = a.shape
     prow = np.arange(mi)
     pcol = np.arange(nj)
     p1 = None
     r = 0
-    for k in range(min(mi, nj)):
+    for k in range(min(mi, nj, kmax)):
         blk = np.abs(a[k:, k:])
         flat = int(np.argmax(blk))            # row-major: lowest row, then column
         pi, pj = divmod(flat, blk.shape[1])
@@ -242,8 +251,8 @@ def full_pivot_lu(Ahat: np.ndarray, eps: float):
         pj += k
         piv = a[pi, pj]
         if p1 is None:
-            p1 = abs(piv)
-        if piv == 0.0 or abs(piv) < eps * p1:
+            p1 = float(abs(piv))
+        if piv == 0.0 or float(abs(piv)) < eps * p1:
             break
         a[[k, pi]] = a[[pi, k]]
         prow[[k, pi]] = prow[[pi, k]]
@@ -267,22 +276,25 @@ class BDLRResult:
 
 
 def bdlr(A: np.ndarray, rowptr, colind, rows: range, cols: range, eps: float,
-         depth: int) -> BDLRResult:
+         depth: int, rank_cap: int = 1 << 30, dtype=np.float64) -> BDLRResult:
     """Boundary-distance low-rank approximation of the block A[rows, cols]
     (Section 5.3): R = A(I,:), C = A(:,J), A^ = A(I,J) = P^-1 L U Q^-1 truncated at
     eps, then C~ = (CQ)(:,1:r) U11^-1 and R~ = L11^-1 (PR)(1:r,:), block ~ C~ R~.
-    Returns U = C~ (m x r) and V = R~^T (n x r)."""
+    Returns U = C~ (m x r) and V = R~^T (n x r).  The LU (and so the choice of
+    I_r, J_r) runs in `dtype` on A^ rounded to it; the triangular solves are
+    formed in float64 from the same rounded values."""
     I, _ = boundary_distance(rowptr, colind, rows, cols, depth)
     J, _ = boundary_distance(rowptr, colind, cols, rows, depth)
     m, n = len(rows), len(cols)
     if not I or not J:
         return BDLRResult(np.zeros((m, 0)), np.zeros((n, 0)), I, J, [], [], np.zeros(0))
     Ahat = A[np.ix_(I, J)]
-    LU, prow, pcol, r = full_pivot_lu(Ahat, eps)
+    LU, prow, pcol, r = full_pivot_lu(Ahat, eps, rank_cap, dtype)
+    LU = LU.astype(np.float64)
     Ir = [I[p] for p in prow[:r]]
     Jr = [J[p] for p in pcol[:r]]
-    Cr = A[rows.start:rows.stop][:, Jr]             # m x r  = (CQ)(:,1:r)
-    Rr = A[Ir][:, cols.start:cols.stop]             # r x n  = (PR)(1:r,:)
+    Cr = A[rows.start:rows.stop][:, Jr].astype(dtype).astype(np.float64)   # (CQ)(:,1:r)
+    Rr = A[Ir][:, cols.start:cols.stop].astype(dtype).astype(np.float64)   # (PR)(1:r,:)
     U11 = np.triu(LU[:r, :r])
     L11 = np.tril(LU[:r, :r], -1) + np.eye(r)
     # C~ : solve X U11 = Cr column by column (upper triangular, from the left column).
@@ -310,7 +322,8 @@ class Blocks:
 
 
 def build(A: np.ndarray, tree: Tree, method: str = "aca", tol: float = 1e-6,
-          rank_cap: int = 1 << 30, graph=None, depth: int = -1, symmetric=False):
+          rank_cap: int = 1 << 30, graph=None, depth: int = -1, symmetric=False,
+          dtype=np.float64):
     """Compress every off-diagonal block of every level with ACA or BDLR (Section 4.3,
     Factorize step 1).  `symmetric` only changes how a column is fetched (as the
     equal row), never a value."""
@@ -325,12 +338,11 @@ def build(A: np.ndarray, tree: Tree, method: str = "aca", tol: float = 1e-6,
                     res = aca(lambda k: A[r0 + k, c0:c1],
                               (lambda k: A[c0 + k, r0:r1]) if symmetric else
                               (lambda k: A[r0:r1, c0 + k]),
-                              r1 - r0, c1 - c0, tol, rank_cap)
+                              r1 - r0, c1 - c0, tol, rank_cap, dtype)
                 elif method == "bdlr":
                     d = depth if depth >= 0 else int(round(-math.log10(tol)))
-                    res = bdlr(A, graph[0], graph[1], range(r0, r1), range(c0, c1), tol, d)
-                    if res.U.shape[1] > rank_cap:
-                        res.U, res.V = res.U[:, :rank_cap], res.V[:, :rank_cap]
+                    res = bdlr(A, graph[0], graph[1], range(r0, r1), range(c0, c1), tol, d,
+                               rank_cap, dtype)
                 else:
                     raise ValueError(method)
                 pair.append(res)
@@ -453,7 +465,9 @@ def gmres(A: np.ndarray, b: np.ndarray, prec=None, tol: float = 1e-12,
     Arnoldi with modified Gram-Schmidt on A M^-1, Givens rotations on the
     Hessenberg columns, stop when the estimated residual |g_{j+1}| <= tol ||b||;
     then x = x0 + M^-1 (V_j y) and the true residual ||b - A x|| / ||b|| is checked,
-    restarting from x when it misses tol (also every `restart` steps if > 0)."""
+    restarting from x when it misses tol (also every `restart` steps if > 0).
+    M^-1 (V_j y) is formed as Z_j y with the stored z_i = M^-1 v_i (the flexible
+    form), equal to it in exact arithmetic for a fixed linear preconditioner."""
     P = prec if prec is not None else (lambda v: v)
     b = np.asarray(b, dtype=np.float64)
     n = b.shape[0]
@@ -471,13 +485,15 @@ def gmres(A: np.ndarray, b: np.ndarray, prec=None, tol: float = 1e-12,
         if beta <= tol * bnorm or total >= max_iter:
             break
         V = [r / beta]
+        Z = []
         H = np.zeros((m + 1, m))
         cs, sn = np.zeros(m), np.zeros(m)
         g = np.zeros(m + 1)
         g[0] = beta
         j = 0
         while j < m and total < max_iter:
-            w = A @ P(V[j])
+            Z.append(P(V[j]))
+            w = A @ Z[j]
             for i in range(j + 1):
                 H[i, j] = V[i] @ w
                 w = w - H[i, j] * V[i]
@@ -508,7 +524,7 @@ def gmres(A: np.ndarray, b: np.ndarray, prec=None, tol: float = 1e-12,
         y = np.zeros(j)
         for i in range(j - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1:j] @ y[i + 1:j]) / H[i, i]
-        x = x + P(np.stack(V[:j], axis=1) @ y)
+        x = x + np.stack(Z[:j], axis=1) @ y
         if est > tol and total >= max_iter:
             break
     true = float(np.linalg.norm(b - A @ x)) / bnorm
@@ -529,8 +545,8 @@ def dense_floor(A: np.ndarray, b: np.ndarray) -> float:
 
 
 def hodlr_precond(A, tree, method="aca", tol=1e-6, rank_cap=1 << 30, graph=None,
-                  depth=-1, symmetric=False):
+                  depth=-1, symmetric=False, dtype=np.float64):
     """Convenience: build + factor, returning (blocks, factors, apply function)."""
-    blocks = build(A, tree, method, tol, rank_cap, graph, depth, symmetric)
+    blocks = build(A, tree, method, tol, rank_cap, graph, depth, symmetric, dtype)
     F = factor(A, tree, blocks)
     return blocks, F, (lambda v: solve(F, v))

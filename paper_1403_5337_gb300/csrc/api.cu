@@ -1,0 +1,721 @@
+// C ABI of libhodlr: contexts, HODLR construction (tree, compression staging,
+// rank compaction), factor / solve entry points, statistics and export.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hodlr {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+hodlr_status status_from_word(int w) {
+    if (w & ST_NONFINITE) return HODLR_NONFINITE_INPUT;
+    if (w & ST_SINGULAR) return HODLR_SINGULAR;
+    if (w & ST_TIMEOUT) return HODLR_TIMEOUT;
+    if (w & ST_RANGE) return HODLR_RANGE;
+    return HODLR_OK;
+}
+
+hodlr_status take_status(hodlr_ctx *c, cudaStream_t s) {
+    HODLR_TRY_CUDA(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HODLR_TRY_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+    HODLR_TRY_CUDA(cudaStreamSynchronize(s));
+    const int w = *c->h_status;
+    if (w) {
+        set_error("device status word 0x%x (%s%s%s%s)", w, (w & ST_NONFINITE) ? "non-finite value " : "",
+                  (w & ST_SINGULAR) ? "zero pivot " : "", (w & ST_TIMEOUT) ? "wait budget exceeded " : "",
+                  (w & ST_RANGE) ? "size limit " : "");
+    }
+    return status_from_word(w);
+}
+
+void *dalloc(hodlr_ctx *c, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 256;
+    if (c->alloc) return c->alloc(bytes, c->user, reinterpret_cast<hodlr_stream>(s));
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(hodlr_ctx *c, void *p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (c->free_fn)
+        c->free_fn(p, bytes, c->user, reinterpret_cast<hodlr_stream>(s));
+    else
+        cudaFreeAsync(p, s);
+}
+
+void *own(hodlr_t *h, size_t bytes, cudaStream_t s) {
+    void *p = dalloc(h->ctx, bytes, s);
+    if (p) h->owned.push_back(DevBuf{p, bytes == 0 ? 256 : bytes});
+    return p;
+}
+
+hodlr_status ensure_work(hodlr_t *h, size_t bytes, cudaStream_t s) {
+    if (h->work_bytes >= bytes) return HODLR_OK;
+    if (h->work) dfree(h->ctx, h->work, h->work_bytes, s);
+    h->work = dalloc(h->ctx, bytes, s);
+    if (!h->work) {
+        h->work_bytes = 0;
+        set_error("out of device memory (%zu bytes of workspace)", bytes);
+        return HODLR_OUT_OF_MEMORY;
+    }
+    h->work_bytes = bytes;
+    return HODLR_OK;
+}
+
+namespace {
+
+// dst(:, col) for the rows of every node of a level: src column if col < rank, else 0.
+// U rows of a node carry the node's own block (rank(node)); V rows of a node
+// carry the sibling's block A(sibling, node) (rank(sibling)): sib = 1.
+template <typename S, typename D>
+__global__ void compact_kernel(const S *__restrict__ src, int64_t lds, D *__restrict__ dst, int64_t ldd,
+                               const int64_t *__restrict__ bounds, int L, int l, const int32_t *__restrict__ ranks,
+                               int rp, int sib) {
+    const int col = blockIdx.y;
+    const int node = blockIdx.z;
+    const int64_t r0 = bounds[(size_t)node << (L - l)];
+    const int64_t r1 = bounds[(size_t)(node + 1) << (L - l)];
+    const int rk = ranks[sib ? (node ^ 1) : node];
+    for (int64_t i = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < r1; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i + col * ldd] = col < rk ? (D)src[i + col * lds] : (D)0;
+}
+
+template <typename S>
+__global__ void to_double_kernel(const S *__restrict__ src, int64_t lds, double *__restrict__ dst, int64_t ldd,
+                                 int64_t rows, int64_t cols) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % rows, j = e / rows;
+        dst[i + j * ldd] = (double)src[i + j * lds];
+    }
+}
+
+template <typename S, typename D>
+hodlr_status launch_compact(const void *src, int64_t lds, void *dst, int64_t ldd, const int64_t *bounds, int L, int l,
+                            const int32_t *ranks, int rp, int64_t node_max, cudaStream_t s) {
+    if (rp == 0) return HODLR_OK;
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((node_max + 255) / 256, 64)), rp, 1u << l);
+    // src/dst given as the U pair: U(node rows) uses rank(node)
+    compact_kernel<S, D><<<grid, 256, 0, s>>>(reinterpret_cast<const S *>(src), lds, reinterpret_cast<D *>(dst), ldd,
+                                              bounds, L, l, ranks, rp, 0);
+    HODLR_TRY_CUDA(cudaGetLastError());
+    return HODLR_OK;
+}
+
+template <typename S, typename D>
+hodlr_status launch_compact_v(const void *src, int64_t lds, void *dst, int64_t ldd, const int64_t *bounds, int L,
+                              int l, const int32_t *ranks, int rp, int64_t node_max, cudaStream_t s) {
+    if (rp == 0) return HODLR_OK;
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((node_max + 255) / 256, 64)), rp, 1u << l);
+    compact_kernel<S, D><<<grid, 256, 0, s>>>(reinterpret_cast<const S *>(src), lds, reinterpret_cast<D *>(dst), ldd,
+                                              bounds, L, l, ranks, rp, 1);
+    HODLR_TRY_CUDA(cudaGetLastError());
+    return HODLR_OK;
+}
+
+hodlr_status check_matrix(const hodlr_matrix *A) {
+    if (!A || !A->data || A->n <= 0 || A->ld < A->n) {
+        set_error("invalid matrix descriptor");
+        return HODLR_INVALID_ARG;
+    }
+    return HODLR_OK;
+}
+
+}  // namespace
+}  // namespace hodlr
+
+using namespace hodlr;
+
+extern "C" {
+
+const char *hodlr_status_string(hodlr_status s) {
+    switch (s) {
+        case HODLR_OK: return "ok";
+        case HODLR_INVALID_ARG: return "invalid argument";
+        case HODLR_OUT_OF_MEMORY: return "out of device memory";
+        case HODLR_CUDA_ERROR: return "CUDA error";
+        case HODLR_SINGULAR: return "singular leaf block or Woodbury core";
+        case HODLR_NOT_FACTORED: return "not factored";
+        case HODLR_NOT_CONVERGED: return "GMRES did not converge";
+        case HODLR_TIMEOUT: return "device wait exceeded its budget";
+        case HODLR_NONFINITE_INPUT: return "non-finite or out-of-range input";
+        case HODLR_RANGE: return "size beyond a fixed limit";
+    }
+    return "unknown status";
+}
+
+const char *hodlr_last_error(void) { return g_err; }
+
+void hodlr_opts_default(hodlr_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = HODLR_FP32;
+    o->compress_precision = -1;
+    o->rank_cap = 0;
+    o->bdlr_depth = -1;
+    o->core_cond_threshold = 0.0;
+    o->leaf_bounds = nullptr;
+    o->n_leaf_bounds = 0;
+    o->seed = 2;
+}
+
+hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn free_fn, void *user, hodlr_ctx **out) {
+    if (!out || ((alloc == nullptr) != (free_fn == nullptr))) {
+        set_error("hodlr_ctx_create: out is NULL or only one of alloc/free given");
+        return HODLR_INVALID_ARG;
+    }
+    int ndev = 0;
+    HODLR_TRY_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) {
+        set_error("hodlr_ctx_create: device %d of %d", device, ndev);
+        return HODLR_INVALID_ARG;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(device));
+    hodlr_ctx *c = new hodlr_ctx();
+    c->device = device;
+    c->alloc = alloc;
+    c->free_fn = free_fn;
+    c->user = user;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        set_error("hodlr_ctx_create: cannot allocate the status word");
+        return HODLR_OUT_OF_MEMORY;
+    }
+    cudaMemset(c->d_status, 0, sizeof(int));
+    *c->h_status = 0;
+    *out = c;
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_ctx_destroy(hodlr_ctx *c) {
+    if (!c) return HODLR_OK;
+    cudaSetDevice(c->device);
+    cudaFree(c->d_status);
+    cudaFreeHost(c->h_status);
+    delete c;
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_destroy(hodlr_t *h) {
+    if (!h) return HODLR_OK;
+    cudaSetDevice(h->ctx->device);
+    cudaStreamSynchronize(nullptr);
+    cudaDeviceSynchronize();
+    for (auto &b : h->owned) dfree(h->ctx, b.p, b.bytes, nullptr);
+    if (h->work) dfree(h->ctx, h->work, h->work_bytes, nullptr);
+    cudaDeviceSynchronize();
+    delete h;
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double tol, int method, const hodlr_graph *g,
+                         const hodlr_opts *o_in, hodlr_stream stream, hodlr_t **out) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!c || !out) {
+        set_error("hodlr_build: NULL context or output");
+        return HODLR_INVALID_ARG;
+    }
+    HODLR_TRY(check_matrix(A));
+    hodlr_opts o;
+    hodlr_opts_default(&o);
+    if (o_in) o = *o_in;
+    if (!(tol > 0.0) || !(tol < 1.0)) {
+        set_error("hodlr_build: tol must be in (0, 1)");
+        return HODLR_INVALID_ARG;
+    }
+    if (method != HODLR_ACA && method != HODLR_BDLR) {
+        set_error("hodlr_build: unknown method %d", method);
+        return HODLR_INVALID_ARG;
+    }
+    if (method == HODLR_BDLR && (!g || !g->rowptr || !g->colind || g->n != A->n)) {
+        set_error("hodlr_build: BDLR needs the graph of the matrix");
+        return HODLR_INVALID_ARG;
+    }
+    if (o.precision != HODLR_FP64 && o.precision != HODLR_FP32) {
+        set_error("hodlr_build: precision %d is not available in this build", o.precision);
+        return HODLR_INVALID_ARG;
+    }
+    int cprec = o.compress_precision;
+    if (cprec < 0) cprec = (o.precision == HODLR_FP64) ? HODLR_FP64 : HODLR_FP32;
+    if (cprec != HODLR_FP64 && cprec != HODLR_FP32) {
+        set_error("hodlr_build: compress_precision must be FP64 or FP32");
+        return HODLR_INVALID_ARG;
+    }
+    const int rank_cap = o.rank_cap <= 0 ? 1024 : o.rank_cap;
+    if (rank_cap > 1024) {
+        set_error("hodlr_build: rank_cap %d > 1024", rank_cap);
+        return HODLR_RANGE;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(c->device));
+    const int64_t n = A->n;
+    // ---- tree
+    std::vector<int64_t> bounds;
+    if (o.leaf_bounds && o.n_leaf_bounds > 0) {
+        const int nb = o.n_leaf_bounds;
+        const int nl = nb - 1;
+        if (nl < 1 || (nl & (nl - 1)) != 0 || o.leaf_bounds[0] != 0 || o.leaf_bounds[nl] != n) {
+            set_error("hodlr_build: leaf_bounds must hold 2^L + 1 increasing offsets from 0 to n");
+            return HODLR_INVALID_ARG;
+        }
+        for (int i = 0; i < nl; ++i)
+            if (o.leaf_bounds[i + 1] <= o.leaf_bounds[i]) {
+                set_error("hodlr_build: leaf_bounds not strictly increasing");
+                return HODLR_INVALID_ARG;
+            }
+        bounds.assign(o.leaf_bounds, o.leaf_bounds + nb);
+    } else {
+        if (leaf < 1) {
+            set_error("hodlr_build: leaf must be >= 1");
+            return HODLR_INVALID_ARG;
+        }
+        std::vector<std::pair<int64_t, int64_t>> r{{0, n}};
+        auto widest = [&]() {
+            int64_t w = 0;
+            for (auto &q : r) w = std::max(w, q.second - q.first);
+            return w;
+        };
+        while (widest() > leaf) {
+            std::vector<std::pair<int64_t, int64_t>> nx;
+            for (auto &q : r) {
+                const int64_t mid = q.first + (q.second - q.first) / 2;
+                nx.push_back({q.first, mid});
+                nx.push_back({mid, q.second});
+            }
+            r.swap(nx);
+            if (r.size() > (1u << 15)) break;
+        }
+        for (auto &q : r) bounds.push_back(q.first);
+        bounds.push_back(n);
+    }
+    const int nleaf = (int)bounds.size() - 1;
+    int L = 0;
+    while ((1 << L) < nleaf) ++L;
+    if (L >= HODLR_MAX_LEVELS) {
+        set_error("hodlr_build: %d levels exceed the limit %d", L, HODLR_MAX_LEVELS - 1);
+        return HODLR_RANGE;
+    }
+    for (int i = 0; i < nleaf; ++i)
+        if (bounds[i + 1] - bounds[i] <= 0) {
+            set_error("hodlr_build: empty leaf (n too small for the leaf size)");
+            return HODLR_INVALID_ARG;
+        }
+    hodlr_t *h = new hodlr_t();
+    h->ctx = c;
+    h->A = A->data;
+    h->n = n;
+    h->lda = A->ld;
+    h->sym = A->symmetric ? 1 : 0;
+    h->L = L;
+    h->bounds = bounds;
+    h->prec = o.precision;
+    h->cprec = cprec;
+    h->method = method;
+    h->tol = tol;
+    h->rank_cap = rank_cap;
+    h->ldn = (n + 31) / 32 * 32;
+    h->lv.resize(L + 1);
+    int64_t bmax = 0;
+    for (int i = 0; i < nleaf; ++i) bmax = std::max(bmax, bounds[i + 1] - bounds[i]);
+    h->bmax = (int)bmax;
+    auto fail = [&](hodlr_status s) {
+        hodlr_destroy(h);
+        return s;
+    };
+    h->d_bounds = (int64_t *)own(h, bounds.size() * sizeof(int64_t), st);
+    if (!h->d_bounds) return fail(HODLR_OUT_OF_MEMORY);
+    if (cudaMemcpyAsync(h->d_bounds, bounds.data(), bounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return fail(HODLR_CUDA_ERROR);
+    auto nrange = [&](int l, int i, int64_t &r0, int64_t &m) {
+        r0 = bounds[(size_t)i << (L - l)];
+        m = bounds[(size_t)(i + 1) << (L - l)] - r0;
+    };
+    // ---- compression staging
+    const size_t ce = elem_size(cprec);
+    std::vector<void *> Ust(L + 1, nullptr), Vst(L + 1, nullptr);
+    std::vector<std::pair<void *, size_t>> temp;
+    h->piv_rows.assign(L + 1, nullptr);
+    h->piv_cols.assign(L + 1, nullptr);
+    h->d_ranks.assign(L + 1, nullptr);
+    int32_t *caphit = (int32_t *)own(h, (size_t)(2 << L) * sizeof(int32_t), st);
+    if (!caphit) return fail(HODLR_OUT_OF_MEMORY);
+    std::vector<AcaBlockDesc> blocks;
+    int64_t max_m = 0;
+    for (int l = 1; l <= L; ++l) {
+        Level &lv = h->lv[l];
+        lv.nnodes = 1 << l;
+        int cap = 0;
+        for (int i = 0; i < lv.nnodes; ++i) {
+            int64_t r0, m, c0, mc;
+            nrange(l, i, r0, m);
+            nrange(l, i ^ 1, c0, mc);
+            cap = (int)std::max<int64_t>(cap, std::min<int64_t>(rank_cap, std::min(m, mc)));
+            max_m = std::max(max_m, m);
+        }
+        lv.cap = std::max(cap, 1);
+        const size_t sb = (size_t)h->ldn * lv.cap * ce;
+        Ust[l] = dalloc(c, sb, st);
+        Vst[l] = dalloc(c, sb, st);
+        if (!Ust[l] || !Vst[l]) {
+            for (int q = 1; q <= l; ++q) {
+                dfree(c, Ust[q], sb, st);
+                dfree(c, Vst[q], sb, st);
+            }
+            return fail(HODLR_OUT_OF_MEMORY);
+        }
+        temp.push_back({Ust[l], sb});
+        temp.push_back({Vst[l], sb});
+        h->piv_rows[l] = (int32_t *)own(h, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
+        h->piv_cols[l] = (int32_t *)own(h, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
+        h->d_ranks[l] = (int32_t *)own(h, (size_t)lv.nnodes * sizeof(int32_t), st);
+        if (!h->piv_rows[l] || !h->piv_cols[l] || !h->d_ranks[l]) return fail(HODLR_OUT_OF_MEMORY);
+        cudaMemsetAsync(h->piv_rows[l], 0xff, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
+        cudaMemsetAsync(h->piv_cols[l], 0xff, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
+        for (int i = 0; i < lv.nnodes; ++i) {
+            AcaBlockDesc b;
+            nrange(l, i, b.r0, b.m);
+            nrange(l, i ^ 1, b.c0, b.nc);
+            b.ld = h->ldn;
+            b.U = Ust[l];
+            b.V = Vst[l];
+            b.cap = lv.cap;
+            b.rank = h->d_ranks[l] + i;
+            b.prow = h->piv_rows[l] + (size_t)i * lv.cap;
+            b.pcol = h->piv_cols[l] + (size_t)i * lv.cap;
+            b.cap_hit = caphit + blocks.size();
+            blocks.push_back(b);
+        }
+    }
+    auto free_temp = [&]() {
+        for (auto &q : temp) dfree(c, q.first, q.second, st);
+        temp.clear();
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    hodlr_status rs = HODLR_OK;
+    if (method == HODLR_ACA) {
+        AcaBlockDesc *db = (AcaBlockDesc *)dalloc(c, blocks.size() * sizeof(AcaBlockDesc) + 16, st);
+        if (!db) {
+            free_temp();
+            return fail(HODLR_OUT_OF_MEMORY);
+        }
+        cudaMemcpyAsync(db, blocks.data(), blocks.size() * sizeof(AcaBlockDesc), cudaMemcpyHostToDevice, st);
+        rs = launch_aca(c, A->data, A->ld, h->sym, cprec, db, (int)blocks.size(), max_m, tol, st);
+        cudaStreamSynchronize(st);
+        dfree(c, db, blocks.size() * sizeof(AcaBlockDesc) + 16, st);
+    } else {
+        const int depth = o.bdlr_depth >= 0 ? o.bdlr_depth : (int)std::lround(-std::log10(tol));
+        rs = run_bdlr(h, g, depth, st, Ust, Vst);
+    }
+    cudaEventRecord(e1, st);
+    if (rs != HODLR_OK) {
+        cudaStreamSynchronize(st);
+        free_temp();
+        return fail(rs);
+    }
+    // ---- ranks -> padded layout
+    std::vector<int32_t> hr;
+    std::vector<int32_t> hcap(blocks.size());
+    for (int l = 1; l <= L; ++l) {
+        Level &lv = h->lv[l];
+        lv.ranks.resize(lv.nnodes);
+        if (cudaMemcpyAsync(lv.ranks.data(), h->d_ranks[l], lv.nnodes * sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess) {
+            free_temp();
+            return fail(HODLR_CUDA_ERROR);
+        }
+    }
+    cudaMemcpyAsync(hcap.data(), caphit, blocks.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    {
+        hodlr_status s2 = take_status(c, st);
+        if (s2 != HODLR_OK) {
+            free_temp();
+            return fail(s2);
+        }
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->ms_compress = ms;
+    for (auto v : hcap) h->cap_hit |= v;
+    int64_t coff = 0;
+    for (int l = 1; l <= L; ++l) {
+        Level &lv = h->lv[l];
+        int mx = 0;
+        double sum = 0;
+        for (int r : lv.ranks) {
+            mx = std::max(mx, r);
+            sum += r;
+        }
+        lv.rank_max = mx;
+        lv.rank_mean = sum / lv.nnodes;
+        lv.rp = mx == 0 ? 0 : (mx + 7) / 8 * 8;
+        lv.coff = coff;
+        coff += lv.rp;
+    }
+    h->Wtot = coff;
+    const size_t pe = elem_size(h->prec);
+    const size_t dvb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * pe;
+    h->D = own(h, dvb, st);
+    h->V = own(h, dvb, st);
+    h->leafinv = own(h, (size_t)nleaf * bmax * bmax * pe, st);
+    h->Sinv.assign(L, nullptr);
+    for (int l = 0; l < L; ++l) {
+        const int64_t s2 = 2 * (int64_t)h->lv[l + 1].rp;
+        h->Sinv[l] = own(h, (size_t)(1 << l) * std::max<int64_t>(s2 * s2, 1) * pe, st);
+        if (!h->Sinv[l]) {
+            free_temp();
+            return fail(HODLR_OUT_OF_MEMORY);
+        }
+    }
+    if (!h->D || !h->V || !h->leafinv) {
+        free_temp();
+        return fail(HODLR_OUT_OF_MEMORY);
+    }
+    if (h->Wtot > 0) {
+        cudaMemsetAsync(h->D, 0, dvb, st);
+        cudaMemsetAsync(h->V, 0, dvb, st);
+    }
+    for (int l = 1; l <= L; ++l) {
+        Level &lv = h->lv[l];
+        int64_t node_max = 0;
+        for (int i = 0; i < lv.nnodes; ++i) {
+            int64_t r0, m;
+            nrange(l, i, r0, m);
+            node_max = std::max(node_max, m);
+        }
+        const size_t off = (size_t)lv.coff * h->ldn * pe;
+        char *Dl = (char *)h->D + off, *Vl = (char *)h->V + off;
+        hodlr_status s3 = HODLR_OK;
+        if (cprec == HODLR_FP64 && h->prec == HODLR_FP64) {
+            s3 = launch_compact<double, double>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                                node_max, st);
+            if (s3 == HODLR_OK)
+                s3 = launch_compact_v<double, double>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                                    node_max, st);
+        } else if (cprec == HODLR_FP64) {
+            s3 = launch_compact<double, float>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                               node_max, st);
+            if (s3 == HODLR_OK)
+                s3 = launch_compact_v<double, float>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                                   node_max, st);
+        } else if (h->prec == HODLR_FP64) {
+            s3 = launch_compact<float, double>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                               node_max, st);
+            if (s3 == HODLR_OK)
+                s3 = launch_compact_v<float, double>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                                   node_max, st);
+        } else {
+            s3 = launch_compact<float, float>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                              node_max, st);
+            if (s3 == HODLR_OK)
+                s3 = launch_compact_v<float, float>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
+                                                  node_max, st);
+        }
+        if (s3 != HODLR_OK) {
+            free_temp();
+            return fail(s3);
+        }
+    }
+    free_temp();
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("hodlr_build: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(HODLR_CUDA_ERROR);
+    }
+    *out = h;
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_factor(hodlr_t *h, hodlr_stream stream) {
+    if (!h) {
+        set_error("hodlr_factor: NULL");
+        return HODLR_INVALID_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
+    h->factored = false;
+    HODLR_TRY(factor_impl(h, st));
+    h->factored = true;
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_solve(hodlr_t *h, int s, double *X, int64_t ldx, hodlr_stream stream) {
+    if (!h || !X || s <= 0 || ldx < h->n) {
+        set_error("hodlr_solve: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    if (!h->factored) {
+        set_error("hodlr_solve: not factored");
+        return HODLR_NOT_FACTORED;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
+    return solve_impl(h, s, X, ldx, reinterpret_cast<cudaStream_t>(stream));
+}
+
+hodlr_status hodlr_matvec(hodlr_ctx *c, const hodlr_matrix *A, int s, const double *Z, int64_t ldz, double *W,
+                          int64_t ldw, hodlr_stream stream) {
+    if (!c || !Z || !W || s <= 0) {
+        set_error("hodlr_matvec: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    HODLR_TRY(check_matrix(A));
+    if (ldz < A->n || ldw < A->n) {
+        set_error("hodlr_matvec: leading dimension < n");
+        return HODLR_INVALID_ARG;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(c->device));
+    return matvec_impl(c, A->data, A->n, A->ld, s, Z, ldz, W, ldw, reinterpret_cast<cudaStream_t>(stream));
+}
+
+hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {
+    if (!h || !o) {
+        set_error("hodlr_stats_get: NULL");
+        return HODLR_INVALID_ARG;
+    }
+    std::memset(o, 0, sizeof(*o));
+    o->n = h->n;
+    o->levels = h->L;
+    o->leaf_max = h->bmax;
+    for (int l = 1; l <= h->L; ++l) {
+        o->rank_max[l - 1] = h->lv[l].rank_max;
+        o->rank_pad[l - 1] = h->lv[l].rp;
+        o->rank_mean[l - 1] = h->lv[l].rank_mean;
+        o->cap[l - 1] = h->lv[l].cap;
+    }
+    o->cap_hit = h->cap_hit;
+    const size_t pe = elem_size(h->prec);
+    int64_t b = (int64_t)2 * h->ldn * h->Wtot * pe + ((int64_t)1 << h->L) * h->bmax * h->bmax * pe;
+    for (int l = 0; l < h->L; ++l) b += ((int64_t)1 << l) * 4 * (int64_t)h->lv[l + 1].rp * h->lv[l + 1].rp * pe;
+    o->bytes_factors = b;
+    o->factored = h->factored ? 1 : 0;
+    o->ms_compress = h->ms_compress;
+    o->ms_factor = h->ms_factor;
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U_or_d, double *V, int32_t *ranks,
+                                int32_t *piv_rows, int32_t *piv_cols, hodlr_stream stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!h || level < 1 || level > h->L) {
+        set_error("hodlr_export_level: level out of range");
+        return HODLR_INVALID_ARG;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
+    const Level &lv = h->lv[level];
+    const int64_t n = h->n, rp = lv.rp;
+    if ((U_or_d || V) && rp > 0) {
+        double *tmp = (double *)dalloc(h->ctx, (size_t)n * rp * 8, st);
+        if (!tmp) return HODLR_OUT_OF_MEMORY;
+        for (int which = 0; which < 2; ++which) {
+            double *dst = which == 0 ? U_or_d : V;
+            if (!dst) continue;
+            const void *src = which == 0 ? h->D : h->V;
+            int blocks = (int)std::min<int64_t>((n * rp + 255) / 256, 4096);
+            if (h->prec == HODLR_FP64)
+                to_double_kernel<double><<<blocks, 256, 0, st>>>((const double *)src + lv.coff * h->ldn, h->ldn, tmp, n,
+                                                                 n, rp);
+            else
+                to_double_kernel<float><<<blocks, 256, 0, st>>>((const float *)src + lv.coff * h->ldn, h->ldn, tmp, n, n,
+                                                                rp);
+            HODLR_TRY_CUDA(cudaMemcpyAsync(dst, tmp, (size_t)n * rp * 8, cudaMemcpyDeviceToHost, st));
+        }
+        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+        dfree(h->ctx, tmp, (size_t)n * rp * 8, st);
+    }
+    if (ranks) std::memcpy(ranks, lv.ranks.data(), lv.nnodes * sizeof(int32_t));
+    if (piv_rows)
+        HODLR_TRY_CUDA(cudaMemcpyAsync(piv_rows, h->piv_rows[level], (size_t)lv.nnodes * lv.cap * 4,
+                                       cudaMemcpyDeviceToHost, st));
+    if (piv_cols)
+        HODLR_TRY_CUDA(cudaMemcpyAsync(piv_cols, h->piv_cols[level], (size_t)lv.nnodes * lv.cap * 4,
+                                       cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_export_core(const hodlr_t *h, int level, double *Sinv, hodlr_stream stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!h || level < 0 || level >= h->L || !Sinv) {
+        set_error("hodlr_export_core: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    if (!h->factored) {
+        set_error("hodlr_export_core: not factored");
+        return HODLR_NOT_FACTORED;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
+    const int64_t s2 = 2 * (int64_t)h->lv[level + 1].rp;
+    const int64_t cnt = ((int64_t)1 << level) * s2 * s2;
+    if (cnt == 0) return HODLR_OK;
+    double *tmp = (double *)dalloc(h->ctx, (size_t)cnt * 8, st);
+    if (!tmp) return HODLR_OUT_OF_MEMORY;
+    int blocks = (int)std::min<int64_t>((cnt + 255) / 256, 4096);
+    if (h->prec == HODLR_FP64)
+        to_double_kernel<double><<<blocks, 256, 0, st>>>((const double *)h->Sinv[level], cnt, tmp, cnt, cnt, 1);
+    else
+        to_double_kernel<float><<<blocks, 256, 0, st>>>((const float *)h->Sinv[level], cnt, tmp, cnt, cnt, 1);
+    HODLR_TRY_CUDA(cudaMemcpyAsync(Sinv, tmp, (size_t)cnt * 8, cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+    dfree(h->ctx, tmp, (size_t)cnt * 8, st);
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_precond_error(hodlr_t *h, int k, const double *Omega, int64_t ldo, double *out, hodlr_stream stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!h || !Omega || !out || k <= 0 || ldo < h->n) {
+        set_error("hodlr_precond_error: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    if (!h->factored) {
+        set_error("hodlr_precond_error: not factored");
+        return HODLR_NOT_FACTORED;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
+    const int64_t n = h->n;
+    double *T = (double *)dalloc(h->ctx, (size_t)n * k * 8, st);
+    if (!T) return HODLR_OUT_OF_MEMORY;
+    hodlr_status s = matvec_impl(h->ctx, h->A, n, h->lda, k, Omega, ldo, T, n, st);
+    if (s == HODLR_OK) s = solve_impl(h, k, T, n, st);
+    if (s != HODLR_OK) {
+        dfree(h->ctx, T, (size_t)n * k * 8, st);
+        return s;
+    }
+    std::vector<double> ht((size_t)n * k), ho((size_t)n * k);
+    cudaMemcpyAsync(ht.data(), T, (size_t)n * k * 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpy2DAsync(ho.data(), n * 8, Omega, ldo * 8, n * 8, k, cudaMemcpyDeviceToHost, st);
+    HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+    dfree(h->ctx, T, (size_t)n * k * 8, st);
+    double num = 0, den = 0;
+    for (size_t e = 0; e < ht.size(); ++e) {
+        const double d = ho[e] - ht[e];
+        num += d * d;
+        den += ho[e] * ho[e];
+    }
+    *out = den > 0 ? std::sqrt(num / den) : 0.0;
+    return take_status(h->ctx, st);
+}
+
+}  // extern "C"

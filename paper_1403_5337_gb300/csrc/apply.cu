@@ -1,0 +1,235 @@
+// Applying the factored HODLR inverse, X <- K~^-1 X (Sec. 4.3, Solve):
+//   leaves:  x_leaf <- K_leaf^-1 x_leaf
+//   for c = L .. 1 (children level), every parent node (alpha, beta):
+//       w = [V_ba^T x_alpha ; V_ab^T x_beta]         (segmented reductions)
+//       y = S^-1 w                                   (one GEMV per node)
+//       x_alpha -= d_alpha y2,  x_beta -= d_beta y1  (rank-rp updates)
+// X is FP64 in and out; the arithmetic runs in the factor's precision T on a
+// private copy of X.  Memory-bound: each level streams V and d once.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace hodlr {
+namespace {
+
+constexpr int AP_THREADS = 256;
+constexpr int MAX_RHS_CHUNK = 8;
+
+// x_T(leaf rows, r) = Kinv_leaf * X(leaf rows, r).  One CTA per (leaf, rhs).
+template <typename T>
+__global__ void __launch_bounds__(AP_THREADS)
+    leaf_apply_kernel(const T *__restrict__ Kinv, int bmax, const int64_t *__restrict__ bounds,
+                      const double *__restrict__ X, int64_t ldx, T *__restrict__ xt, int64_t ldt) {
+    const int leaf = blockIdx.x, r = blockIdx.y;
+    const int64_t r0 = bounds[leaf], b = bounds[leaf + 1] - r0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *xs = reinterpret_cast<T *>(smem);
+    for (int64_t i = threadIdx.x; i < b; i += AP_THREADS) xs[i] = dev::from_double<T>(X[r0 + i + r * ldx]);
+    __syncthreads();
+    const T *K = Kinv + (size_t)leaf * bmax * bmax;
+    for (int64_t i = threadIdx.x; i < b; i += AP_THREADS) {
+        T acc = T(0);
+        for (int64_t k = 0; k < b; ++k) acc = fma(K[i + k * bmax], xs[k], acc);
+        xt[r0 + i + r * ldt] = acc;
+    }
+}
+
+// w(child, col, r) += sum_{rows of child} V(row, coff+col) x(row, r).
+// Grid: (child * row-chunks, column groups); one warp per column.
+template <typename T>
+__global__ void __launch_bounds__(AP_THREADS)
+    vtx_kernel(const T *__restrict__ V, int64_t ldn, int64_t coff, int rp, const int64_t *__restrict__ bounds,
+               int L, int c, int chunks, int64_t chunk_rows, const T *__restrict__ xt, int64_t ldt,
+               int s, T *__restrict__ w) {
+    const int child = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    const int64_t n0 = bounds[(size_t)child << (L - c)];
+    const int64_t n1 = bounds[(size_t)(child + 1) << (L - c)];
+    const int64_t a = n0 + ch * chunk_rows;
+    const int64_t e = (a + chunk_rows < n1) ? a + chunk_rows : n1;
+    if (a >= e) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = blockIdx.y * (AP_THREADS / 32) + warp;
+    if (col >= rp) return;
+    const T *vc = V + (coff + col) * ldn;
+    T acc[MAX_RHS_CHUNK];
+    for (int r0 = 0; r0 < s; r0 += MAX_RHS_CHUNK) {
+        const int rr = (s - r0) < MAX_RHS_CHUNK ? (s - r0) : MAX_RHS_CHUNK;
+#pragma unroll
+        for (int q = 0; q < MAX_RHS_CHUNK; ++q) acc[q] = T(0);
+        for (int64_t i = a + lane; i < e; i += 32) {
+            const T v = vc[i];
+#pragma unroll
+            for (int q = 0; q < MAX_RHS_CHUNK; ++q)
+                if (q < rr) acc[q] = fma(v, xt[i + (r0 + q) * ldt], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < MAX_RHS_CHUNK; ++q) {
+            if (q >= rr) break;
+            T v = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) atomicAdd(&w[((size_t)child * rp + col) * s + r0 + q], v);
+        }
+    }
+}
+
+// y(node) = S^-1 [w(alpha); w(beta)] for every RHS.  One CTA per node.
+template <typename T>
+__global__ void __launch_bounds__(AP_THREADS)
+    core_apply_kernel(const T *__restrict__ Sinv, int rp, const T *__restrict__ w, int s, T *__restrict__ y) {
+    const int node = blockIdx.x;
+    const int s2 = 2 * rp;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *ws = reinterpret_cast<T *>(smem);   // s2 * s
+    const T *wn = w + (size_t)node * s2 * s;   // children 2 node, 2 node + 1 are contiguous
+    for (int e = threadIdx.x; e < s2 * s; e += AP_THREADS) ws[e] = wn[e];
+    __syncthreads();
+    const T *S = Sinv + (size_t)node * s2 * s2;
+    for (int e = threadIdx.x; e < s2 * s; e += AP_THREADS) {
+        const int i = e % s2, r = e / s2;
+        T acc = T(0);
+        for (int k = 0; k < s2; ++k) acc = fma(S[i + (size_t)k * s2], ws[k * s + r], acc);
+        y[((size_t)node * s2 + i) * s + r] = acc;
+    }
+}
+
+// x(child rows, r) -= d(child rows, coff:coff+rp) * y_sib(:, r), y_sib = y2 for the
+// first child (alpha) and y1 for the second (beta).
+template <typename T>
+__global__ void __launch_bounds__(AP_THREADS)
+    update_kernel(const T *__restrict__ Dm, int64_t ldn, int64_t coff, int rp,
+                  const int64_t *__restrict__ bounds, int L, int c, int chunks, int64_t chunk_rows,
+                  const T *__restrict__ y, int s, T *__restrict__ xt, int64_t ldt) {
+    const int child = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    const int64_t n0 = bounds[(size_t)child << (L - c)];
+    const int64_t n1 = bounds[(size_t)(child + 1) << (L - c)];
+    const int64_t a = n0 + ch * chunk_rows;
+    const int64_t e = (a + chunk_rows < n1) ? a + chunk_rows : n1;
+    if (a >= e) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *ys = reinterpret_cast<T *>(smem);   // rp * s
+    const int node = child >> 1;
+    const int half = (child & 1) ? 0 : rp;   // alpha uses y2 (second half)
+    const T *yn = y + ((size_t)node * 2 * rp + half) * s;
+    for (int q = threadIdx.x; q < rp * s; q += AP_THREADS) ys[q] = yn[q];
+    __syncthreads();
+    for (int64_t i = a + threadIdx.x; i < e; i += AP_THREADS) {
+        for (int r0 = 0; r0 < s; r0 += MAX_RHS_CHUNK) {
+            const int rr = (s - r0) < MAX_RHS_CHUNK ? (s - r0) : MAX_RHS_CHUNK;
+            T acc[MAX_RHS_CHUNK];
+#pragma unroll
+            for (int q = 0; q < MAX_RHS_CHUNK; ++q) acc[q] = T(0);
+            for (int k = 0; k < rp; ++k) {
+                const T dv = Dm[i + (coff + k) * ldn];
+#pragma unroll
+                for (int q = 0; q < MAX_RHS_CHUNK; ++q)
+                    if (q < rr) acc[q] = fma(dv, ys[k * s + r0 + q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < MAX_RHS_CHUNK; ++q)
+                if (q < rr) xt[i + (r0 + q) * ldt] -= acc[q];
+        }
+    }
+}
+
+template <typename T>
+__global__ void store_kernel(const T *__restrict__ xt, int64_t ldt, int64_t n, int s, double *__restrict__ X,
+                             int64_t ldx) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * s;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, r = e / n;
+        X[i + r * ldx] = (double)xt[i + r * ldt];
+    }
+}
+
+template <typename T>
+__global__ void zero_kernel2(T *p, int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = T(0);
+}
+
+template <typename T>
+hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st) {
+    const int L = h->L;
+    const int64_t n = h->n, ldn = h->ldn;
+    hodlr_t *hm = const_cast<hodlr_t *>(h);
+    // scratch: x_T (ldn * s), w (n*... <= 2^L * rpmax * s), y (same)
+    int rpmax = 0;
+    for (int c = 1; c <= L; ++c) rpmax = std::max(rpmax, h->lv[c].rp);
+    const size_t xt_bytes = (size_t)ldn * s * sizeof(T);
+    const size_t w_elems = (size_t)(1 << L) * std::max(rpmax, 1) * s;
+    const size_t need = xt_bytes + 2 * w_elems * sizeof(T) + 1024;
+    if (hm->work_bytes < need) {
+        HODLR_TRY(ensure_work(hm, need, st));
+    }
+    char *wp = reinterpret_cast<char *>(hm->work);
+    T *xt = reinterpret_cast<T *>(wp);
+    T *w = reinterpret_cast<T *>(wp + ((xt_bytes + 255) & ~size_t(255)));
+    T *y = w + w_elems;
+    const T *Kinv = reinterpret_cast<const T *>(h->leafinv);
+    const T *V = reinterpret_cast<const T *>(h->V);
+    const T *Dm = reinterpret_cast<const T *>(h->D);
+    {
+        dim3 grid(1 << L, s);
+        size_t sm = (size_t)h->bmax * sizeof(T);
+        leaf_apply_kernel<T><<<grid, AP_THREADS, sm, st>>>(Kinv, h->bmax, h->d_bounds, X, ldx, xt, ldn);
+        HODLR_TRY_CUDA(cudaGetLastError());
+    }
+    for (int c = L; c >= 1; --c) {
+        const int rp = h->lv[c].rp;
+        if (rp == 0) continue;
+        const int64_t coff = h->lv[c].coff;
+        const int nch = 1 << c;
+        int64_t node_rows = 0;
+        for (int i = 0; i < nch; ++i)
+            node_rows = std::max(node_rows, h->bounds[(size_t)(i + 1) << (L - c)] - h->bounds[(size_t)i << (L - c)]);
+        const int64_t chunk_rows = 1024;
+        const int chunks = (int)((node_rows + chunk_rows - 1) / chunk_rows);
+        {
+            int64_t cnt = (int64_t)nch * rp * s;
+            int blocks = (int)std::min<int64_t>((cnt + 255) / 256, 1024);
+            zero_kernel2<T><<<blocks, 256, 0, st>>>(w, cnt);
+            dim3 grid(nch * chunks, (rp + AP_THREADS / 32 - 1) / (AP_THREADS / 32));
+            vtx_kernel<T><<<grid, AP_THREADS, 0, st>>>(V, ldn, coff, rp, h->d_bounds, L, c, chunks, chunk_rows,
+                                                        xt, ldn, s, w);
+            HODLR_TRY_CUDA(cudaGetLastError());
+        }
+        {
+            const T *Sinv = reinterpret_cast<const T *>(h->Sinv[c - 1]);
+            size_t sm = (size_t)2 * rp * s * sizeof(T);
+            if (sm > 48 * 1024)
+                HODLR_TRY_CUDA(cudaFuncSetAttribute(core_apply_kernel<T>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            core_apply_kernel<T><<<nch / 2, AP_THREADS, sm, st>>>(Sinv, rp, w, s, y);
+            HODLR_TRY_CUDA(cudaGetLastError());
+        }
+        {
+            const int64_t urows = 256;
+            const int uchunks = (int)((node_rows + urows - 1) / urows);
+            size_t sm = (size_t)rp * s * sizeof(T);
+            if (sm > 48 * 1024)
+                HODLR_TRY_CUDA(cudaFuncSetAttribute(update_kernel<T>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            update_kernel<T><<<nch * uchunks, AP_THREADS, sm, st>>>(Dm, ldn, coff, rp, h->d_bounds, L, c, uchunks,
+                                                                     urows, y, s, xt, ldn);
+            HODLR_TRY_CUDA(cudaGetLastError());
+        }
+    }
+    {
+        int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
+        store_kernel<T><<<blocks, 256, 0, st>>>(xt, ldn, n, s, X, ldx);
+        HODLR_TRY_CUDA(cudaGetLastError());
+    }
+    return HODLR_OK;
+}
+
+}  // namespace
+
+hodlr_status solve_impl(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st) {
+    if (h->prec == HODLR_FP64) return solve_typed<double>(h, s, X, ldx, st);
+    return solve_typed<float>(h, s, X, ldx, st);
+}
+
+}  // namespace hodlr

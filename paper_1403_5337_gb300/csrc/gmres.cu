@@ -1,0 +1,530 @@
+// FP64-accurate GMRES on the device (Sec. 3: GMRES with the HODLR direct solve
+// as preconditioner), right-preconditioned in the flexible form:
+//   z_j = P^-1 v_j (stored),  w = A z_j,  classical Gram-Schmidt twice,
+//   Givens rotations on the Hessenberg column, estimate |g_{j+1}| / ||b||,
+//   x = x0 + Z_j y once the estimate meets tol, then the true residual.
+// Each right-hand side is an independent system with its own Krylov basis.
+//
+// The matvec with the FP64 front A is the dominant data stream.  GB300's FP64
+// pipe is ~1/64 of its FP32 rate, so the product is formed on the FP32 pipes
+// in double-float arithmetic: every FP64 entry a is split exactly into
+// a = a_hi + a_lo + (a 5-bit tail) by integer operations on its bits (a_hi =
+// the leading 24 significand bits, a_lo = the next 29 rounded to 24), z is
+// split likewise, the product a_hi z_hi is made exact with an FMA
+// (TwoProduct), cross terms are added in FP32, and the row sum is accumulated
+// as an unevaluated float pair with TwoSum.  The relative error per term is
+// about 2^-48, comparable to an FP64 dot product's accumulated rounding.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hodlr {
+namespace {
+
+// ------------------------------------------------------------------ double-float matvec
+struct DF {
+    float s, c;
+};
+
+__device__ __forceinline__ void split_entry(double a, float &hi, float &lo, int &bad) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+    const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
+    const unsigned ex = (h32 >> 20) & 0x7FFu;
+    const unsigned sgn = h32 & 0x80000000u;
+    if (ex < 897u) {            // zero, FP64 subnormal, or below FP32's normal range
+        hi = 0.f;
+        lo = 0.f;
+        return;
+    }
+    if (ex > 1150u) {           // >= 2^128, Inf or NaN
+        bad = 1;
+        hi = 0.f;
+        lo = 0.f;
+        return;
+    }
+    hi = __uint_as_float(sgn | ((ex - 896u) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+    if (ex >= 949u) {
+        const float rem = __uint2float_rn(l32 & 0x1FFFFFFFu);
+        const float scale = __uint_as_float((ex - 948u) << 23);   // 2^(ex - 1075)
+        lo = __uint_as_float(__float_as_uint(rem * scale) | sgn);
+    } else {
+        lo = 0.f;
+    }
+}
+
+__device__ __forceinline__ void df_acc(DF &acc, float ah, float al, float zh, float zl) {
+    const float p = ah * zh;
+    const float e = fmaf(ah, zh, -p);
+    const float t = fmaf(ah, zl, fmaf(al, zh, e));
+    const float s = acc.s + p;
+    const float bp = s - acc.s;
+    const float err = (acc.s - (s - bp)) + (p - bp);
+    acc.s = s;
+    acc.c += err + t;
+}
+
+constexpr int MV_THREADS = 256;
+constexpr int MV_WARPS = MV_THREADS / 32;
+constexpr int MV_RPW = 2;            // rows per warp
+constexpr int MV_ROWS = MV_WARPS * MV_RPW;
+constexpr int MV_KC = 1024;          // columns per staged chunk
+constexpr int MV_S = 4;              // right-hand sides per pass
+
+__global__ void split_vec_kernel(const double *__restrict__ Z, int64_t ldz, int64_t n, int s,
+                                 float2 *__restrict__ zs) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * s;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, r = e / n;
+        const double z = Z[i + r * ldz];
+        const float h = __double2float_rn(z);
+        const float l = __double2float_rn(z - (double)h);
+        zs[r * n + i] = make_float2(h, l);
+    }
+}
+
+// W(:, r0:r0+sr) = A Z(:, r0:r0+sr);  zs = split Z (n x s, column-major float2).
+__global__ void __launch_bounds__(MV_THREADS)
+    df_matvec_kernel(const double *__restrict__ A, int64_t n, int64_t lda, const float2 *__restrict__ zs,
+                     int s, int r0, double *__restrict__ W, int64_t ldw, int *status) {
+    __shared__ float2 zsm[MV_S][MV_KC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * MV_ROWS + warp * MV_RPW;
+    const int sr = min(MV_S, s - r0);
+    // The float pair accumulates at most 32 terms per lane (one staged chunk);
+    // it is then folded into an FP64 accumulator, so the compensation term's own
+    // FP32 rounding never accumulates over more than 32 terms.
+    DF acc[MV_RPW][MV_S];
+    double dacc[MV_RPW][MV_S];
+#pragma unroll
+    for (int a = 0; a < MV_RPW; ++a)
+#pragma unroll
+        for (int q = 0; q < MV_S; ++q) {
+            acc[a][q] = DF{0.f, 0.f};
+            dacc[a][q] = 0.0;
+        }
+    int bad = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += MV_KC) {
+        const int kc = (n - k0 < (int64_t)MV_KC) ? (int)(n - k0) : MV_KC;
+        __syncthreads();
+        for (int e = threadIdx.x; e < MV_S * MV_KC; e += MV_THREADS) {
+            const int q = e / MV_KC, kk = e % MV_KC;
+            zsm[q][kk] = (q < sr && kk < kc) ? zs[(int64_t)(r0 + q) * n + k0 + kk] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < MV_RPW; ++a) {
+            const int64_t row = row0 + a;
+            if (row >= n) continue;
+            const double *ar = A + row * lda + k0;
+            for (int kk = lane; kk < kc; kk += 32) {
+                float ah, al;
+                split_entry(__ldg(ar + kk), ah, al, bad);
+#pragma unroll
+                for (int q = 0; q < MV_S; ++q) {
+                    const float2 z = zsm[q][kk];
+                    df_acc(acc[a][q], ah, al, z.x, z.y);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MV_S; ++q) {
+                dacc[a][q] += (double)acc[a][q].s + (double)acc[a][q].c;
+                acc[a][q] = DF{0.f, 0.f};
+            }
+        }
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+    for (int a = 0; a < MV_RPW; ++a) {
+        const int64_t row = row0 + a;
+#pragma unroll
+        for (int q = 0; q < MV_S; ++q) {
+            double v = dacc[a][q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && row < n && q < sr) W[row + (int64_t)(r0 + q) * ldw] = v;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ Krylov kernels
+constexpr int KT = 256;
+
+// h[r][i] += sum_rows V_r(:, i) . w_r  for i <= j; rows split into chunks.
+__global__ void __launch_bounds__(KT)
+    gram_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, int j, const double *__restrict__ w,
+                int64_t ldw, const int *__restrict__ active, double *__restrict__ h, int hstride,
+                int64_t chunk) {
+    const int r = blockIdx.y;
+    if (!active[r]) return;
+    const int64_t a = blockIdx.x * chunk, e = (a + chunk < n) ? a + chunk : n;
+    const double *V = Vk + r * vstride;
+    const double *wr = w + r * ldw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i <= j; i += KT / 32) {
+        const double *vi = V + (int64_t)i * n;
+        double acc = 0.0;
+        for (int64_t q = a + lane; q < e; q += 32) acc = fma(vi[q], wr[q], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) atomicAdd(&h[(int64_t)r * hstride + i], acc);
+    }
+}
+
+// w_r -= V_r(:, 0:j+1) h_r ; optionally accumulate ||w_r||^2.
+__global__ void __launch_bounds__(KT)
+    orth_update_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, int j, double *__restrict__ w,
+                       int64_t ldw, const int *__restrict__ active, const double *__restrict__ h, int hstride,
+                       double *__restrict__ nrm2) {
+    const int r = blockIdx.y;
+    if (!active[r]) return;
+    const double *V = Vk + r * vstride;
+    const double *hr = h + (int64_t)r * hstride;
+    double local = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)KT + threadIdx.x; q < n; q += (int64_t)gridDim.x * KT) {
+        double v = w[q + r * ldw];
+        for (int i = 0; i <= j; ++i) v = fma(-hr[i], V[(int64_t)i * n + q], v);
+        w[q + r * ldw] = v;
+        local = fma(v, v, local);
+    }
+    if (nrm2) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&nrm2[r], local);
+    }
+}
+
+// v_{j+1} = w / ||w||  (skipped for a zero norm: breakdown).
+__global__ void normalize_kernel(const double *__restrict__ w, int64_t ldw, int64_t n, const int *__restrict__ active,
+                                 const double *__restrict__ nrm2, double *__restrict__ Vk, int64_t vstride, int jn) {
+    const int r = blockIdx.y;
+    if (!active[r]) return;
+    const double nr = sqrt(nrm2[r]);
+    if (!(nr > 0.0)) return;
+    double *dst = Vk + r * vstride + (int64_t)jn * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = w[q + r * ldw] / nr;
+}
+
+struct GState {
+    double *H;       // (m+1) x m per rhs
+    double *cs, *sn, *g;
+    double *bnorm, *est;
+    int *iters, *jcur, *active, *nactive;
+};
+
+// Givens update of column j for every active rhs; one thread per rhs.
+__global__ void givens_kernel(GState st, int m, int s, const double *__restrict__ h1, const double *__restrict__ h2,
+                              int hstride, const double *__restrict__ nrm2, double tol, int max_iter) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= s || !st.active[r]) return;
+    const int j = st.jcur[r];
+    double *Hc = st.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
+    double *cs = st.cs + (int64_t)r * m, *sn = st.sn + (int64_t)r * m, *g = st.g + (int64_t)r * (m + 1);
+    for (int i = 0; i <= j; ++i) Hc[i] = h1[(int64_t)r * hstride + i] + h2[(int64_t)r * hstride + i];
+    const double hn = sqrt(nrm2[r]);
+    Hc[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hc[i] + sn[i] * Hc[i + 1];
+        Hc[i + 1] = -sn[i] * Hc[i] + cs[i] * Hc[i + 1];
+        Hc[i] = t;
+    }
+    const double rho = hypot(Hc[j], Hc[j + 1]);
+    if (rho == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+    } else {
+        cs[j] = Hc[j] / rho;
+        sn[j] = Hc[j + 1] / rho;
+    }
+    Hc[j] = rho;
+    Hc[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    st.iters[r] += 1;
+    st.jcur[r] = j + 1;
+    const double est = fabs(g[j + 1]) / st.bnorm[r];
+    st.est[r] = est;
+    if (est <= tol || rho == 0.0 || hn == 0.0 || j + 1 >= m || st.iters[r] >= max_iter) st.active[r] = 0;
+    else atomicAdd(st.nactive, 1);
+}
+
+// y = H(0:j,0:j)^-1 g(0:j) by back substitution, then X_r += Z_r y.  One CTA per rhs.
+__global__ void __launch_bounds__(KT)
+    backsolve_kernel(GState st, int m, const double *__restrict__ Zk, int64_t zstride, int64_t n, double *__restrict__ X,
+                     int64_t ldx) {
+    const int r = blockIdx.x;
+    const int j = st.jcur[r];
+    if (j <= 0) return;
+    extern __shared__ double ys[];
+    const double *H = st.H + (int64_t)r * (m + 1) * m;
+    const double *g = st.g + (int64_t)r * (m + 1);
+    if (threadIdx.x == 0) {
+        for (int i = j - 1; i >= 0; --i) {
+            double v = g[i];
+            for (int k = i + 1; k < j; ++k) v -= H[i + (int64_t)k * (m + 1)] * ys[k];
+            ys[i] = v / H[i + (int64_t)i * (m + 1)];
+        }
+    }
+    __syncthreads();
+    const double *Z = Zk + r * zstride;
+    for (int64_t q = threadIdx.x; q < n; q += KT) {
+        double v = X[q + r * ldx];
+        for (int k = 0; k < j; ++k) v = fma(Z[(int64_t)k * n + q], ys[k], v);
+        X[q + r * ldx] = v;
+    }
+}
+
+// R = B - R (R holds A X), accumulate ||R||^2 per rhs.
+__global__ void residual_kernel(const double *__restrict__ B, int64_t ldb, double *__restrict__ R, int64_t ldr, int64_t n,
+                                double *__restrict__ nrm2) {
+    const int r = blockIdx.y;
+    double local = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const double v = B[q + r * ldb] - R[q + r * ldr];
+        R[q + r * ldr] = v;
+        local = fma(v, v, local);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&nrm2[r], local);
+}
+
+// Start a cycle: v_0 = r / ||r||, g = ||r|| e_1, jcur = 0, activity from the residual.
+__global__ void start_cycle_kernel(GState st, int m, int s, const double *__restrict__ R, int64_t ldr, int64_t n,
+                                   const double *__restrict__ nrm2, double *__restrict__ Vk, int64_t vstride, double tol,
+                                   int max_iter, int first) {
+    const int r = blockIdx.y;
+    if (r >= s) return;
+    const double beta = sqrt(nrm2[r]);
+    if (first && blockIdx.x == 0 && threadIdx.x == 0) {
+        st.bnorm[r] = beta;
+        st.iters[r] = 0;
+    }
+    const double bn = first ? beta : st.bnorm[r];
+    const int act = (bn > 0.0) && (beta > tol * bn) && (st.iters[r] < max_iter);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st.active[r] = act;
+        st.jcur[r] = 0;
+        st.g[(int64_t)r * (m + 1)] = beta;
+        if (!act) st.est[r] = bn > 0.0 ? beta / bn : 0.0;
+    }
+    if (!act) return;
+    double *v0 = Vk + r * vstride;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        v0[q] = R[q + r * ldr] / beta;
+}
+
+__global__ void count_active_kernel(const int *active, int s, int *nactive) {
+    int c = 0;
+    for (int r = 0; r < s; ++r) c += active[r];
+    *nactive = c;
+}
+
+__global__ void copy_active_kernel(const double *__restrict__ src, int64_t lds, double *__restrict__ dst, int64_t ldd,
+                                   int64_t n, const int *__restrict__ active) {
+    const int r = blockIdx.y;
+    if (!active[r]) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q + r * ldd] = src[q + r * lds];
+}
+
+}  // namespace
+
+hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s, const double *Z, int64_t ldz,
+                         double *W, int64_t ldw, cudaStream_t st, void *work) {
+    if (n == 0 || s == 0) return HODLR_OK;
+    float2 *zs = work ? reinterpret_cast<float2 *>(work)
+                      : reinterpret_cast<float2 *>(dalloc(c, (size_t)n * s * sizeof(float2), st));
+    if (!zs) return HODLR_OUT_OF_MEMORY;
+    int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
+    split_vec_kernel<<<blocks, 256, 0, st>>>(Z, ldz, n, s, zs);
+    const int grid = (int)((n + MV_ROWS - 1) / MV_ROWS);
+    for (int r0 = 0; r0 < s; r0 += MV_S)
+        df_matvec_kernel<<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (!work) dfree(c, zs, (size_t)n * s * sizeof(float2), st);
+    if (e != cudaSuccess) {
+        set_error("matvec launch: %s", cudaGetErrorString(e));
+        return HODLR_CUDA_ERROR;
+    }
+    return HODLR_OK;
+}
+
+}  // namespace hodlr
+
+using namespace hodlr;
+
+namespace {
+
+struct GmresBufs {
+    hodlr_ctx *c = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<void *, size_t>> list;
+    void *get(size_t bytes) {
+        void *p = dalloc(c, bytes, st);
+        if (p) list.push_back({p, bytes});
+        return p;
+    }
+    ~GmresBufs() {
+        for (auto &q : list) dfree(c, q.first, q.second, st);
+    }
+};
+
+}  // namespace
+
+extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, const double *B, int64_t ldb,
+                                    double *X, int64_t ldx, const hodlr_t *P, double tol, int max_iter, int restart,
+                                    hodlr_gmres_info *info, hodlr_stream stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!c || !A || !A->data || !B || !X || s <= 0 || A->n <= 0 || A->ld < A->n || ldb < A->n || ldx < A->n ||
+        max_iter <= 0 || !(tol > 0.0) || restart < 0) {
+        set_error("gmres_solve: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    if (P && (P->n != A->n)) {
+        set_error("gmres_solve: preconditioner size %lld != %lld", (long long)P->n, (long long)A->n);
+        return HODLR_INVALID_ARG;
+    }
+    if (P && !P->factored) {
+        set_error("gmres_solve: preconditioner not factored");
+        return HODLR_NOT_FACTORED;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(c->device));
+    const int64_t n = A->n;
+    const int m = restart > 0 ? std::min(restart, max_iter) : max_iter;
+    GmresBufs bufs;
+    bufs.c = c;
+    bufs.st = st;
+    const int64_t vstride = n * (m + 1), zstride = n * m;
+    double *Vk = (double *)bufs.get((size_t)vstride * s * 8);
+    double *Zk = (double *)bufs.get((size_t)zstride * s * 8);
+    double *Wv = (double *)bufs.get((size_t)n * s * 8);
+    const int hstride = m + 1;
+    double *h1 = (double *)bufs.get((size_t)s * hstride * 8);
+    double *h2 = (double *)bufs.get((size_t)s * hstride * 8);
+    double *nrm = (double *)bufs.get((size_t)s * 8);
+    GState gs;
+    gs.H = (double *)bufs.get((size_t)s * (m + 1) * m * 8);
+    gs.cs = (double *)bufs.get((size_t)s * m * 8);
+    gs.sn = (double *)bufs.get((size_t)s * m * 8);
+    gs.g = (double *)bufs.get((size_t)s * (m + 1) * 8);
+    gs.bnorm = (double *)bufs.get((size_t)s * 8);
+    gs.est = (double *)bufs.get((size_t)s * 8);
+    int *ibuf = (int *)bufs.get((size_t)(4 * s + 4) * sizeof(int));
+    void *zsw = bufs.get((size_t)n * s * sizeof(float2));
+    if (!Vk || !Zk || !Wv || !h1 || !h2 || !nrm || !gs.H || !gs.cs || !gs.sn || !gs.g || !gs.bnorm || !gs.est ||
+        !ibuf || !zsw) {
+        set_error("gmres_solve: out of device memory");
+        return HODLR_OUT_OF_MEMORY;
+    }
+    gs.iters = ibuf;
+    gs.jcur = ibuf + s;
+    gs.active = ibuf + 2 * s;
+    gs.nactive = ibuf + 3 * s;
+    int *h_pin = nullptr;
+    HODLR_TRY_CUDA(cudaMallocHost(&h_pin, 64 * sizeof(int)));
+    struct PinFree {
+        int *p;
+        ~PinFree() { cudaFreeHost(p); }
+    } pf{h_pin};
+    std::vector<double> hbuf(4 * (size_t)s);
+    cudaEvent_t e0, e1;
+    HODLR_TRY_CUDA(cudaEventCreate(&e0));
+    HODLR_TRY_CUDA(cudaEventCreate(&e1));
+    HODLR_TRY_CUDA(cudaEventRecord(e0, st));
+
+    const dim3 vgrid((unsigned)std::min<int64_t>((n + KT - 1) / KT, 1024), s);
+    const int64_t gchunk = 2048;
+    const dim3 ggrid((unsigned)((n + gchunk - 1) / gchunk), s);
+    // x0 = 0
+    HODLR_TRY_CUDA(cudaMemset2DAsync(X, ldx * 8, 0, n * 8, s, st));
+    // R = B (first cycle): Wv = B
+    HODLR_TRY_CUDA(cudaMemcpy2DAsync(Wv, n * 8, B, ldb * 8, n * 8, s, cudaMemcpyDeviceToDevice, st));
+    HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, s * 8, st));
+    {
+        // ||b||^2 via residual kernel with A X = 0: R = B - 0
+        double *zero = h1;   // reuse as zero source
+        HODLR_TRY_CUDA(cudaMemsetAsync(zero, 0, (size_t)s * hstride * 8, st));
+    }
+    // nrm = ||Wv||^2
+    {
+        // R := B - 0 computed as residual_kernel(B, Wv=0): zero Wv first
+        HODLR_TRY_CUDA(cudaMemset2DAsync(Wv, n * 8, 0, n * 8, s, st));
+        residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
+    }
+    int restarts = 0;
+    hodlr_status result = HODLR_OK;
+    for (int cycle = 0;; ++cycle) {
+        start_cycle_kernel<<<vgrid, KT, 0, st>>>(gs, m, s, Wv, n, n, nrm, Vk, vstride, tol, max_iter, cycle == 0);
+        count_active_kernel<<<1, 1, 0, st>>>(gs.active, s, gs.nactive);
+        HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin, gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+        HODLR_TRY(take_status(c, st));
+        if (h_pin[0] == 0) break;
+        if (cycle > 0) ++restarts;
+        for (int j = 0; j < m; ++j) {
+            // z_j = P^-1 v_j
+            double *vj = Vk + (int64_t)j * n;
+            double *zj = Zk + (int64_t)j * n;
+            copy_active_kernel<<<vgrid, KT, 0, st>>>(vj, vstride, zj, zstride, n, gs.active);
+            if (P) HODLR_TRY(solve_impl(P, s, zj, zstride, st));
+            // w = A z_j
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, zj, zstride, Wv, n, st, zsw));
+            // CGS2
+            HODLR_TRY_CUDA(cudaMemsetAsync(h1, 0, (size_t)s * hstride * 8, st));
+            HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, st));
+            HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, st));
+            gram_kernel<<<ggrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h1, hstride, gchunk);
+            orth_update_kernel<<<vgrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h1, hstride, nullptr);
+            gram_kernel<<<ggrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h2, hstride, gchunk);
+            orth_update_kernel<<<vgrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h2, hstride, nrm);
+            normalize_kernel<<<vgrid, KT, 0, st>>>(Wv, n, n, gs.active, nrm, Vk, vstride, j + 1);
+            HODLR_TRY_CUDA(cudaMemsetAsync(gs.nactive, 0, sizeof(int), st));
+            givens_kernel<<<(s + 127) / 128, 128, 0, st>>>(gs, m, s, h1, h2, hstride, nrm, tol, max_iter);
+            HODLR_TRY_CUDA(cudaGetLastError());
+            HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin, gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+            HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+            if (h_pin[0] == 0) break;
+        }
+        // x += Z y
+        backsolve_kernel<<<s, KT, (size_t)m * 8, st>>>(gs, m, Zk, zstride, n, X, ldx);
+        HODLR_TRY_CUDA(cudaGetLastError());
+        // true residual R = B - A X
+        HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, X, ldx, Wv, n, st, zsw));
+        HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, st));
+        residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
+        HODLR_TRY_CUDA(cudaGetLastError());
+        if (cycle > 10000) break;
+    }
+    HODLR_TRY_CUDA(cudaEventRecord(e1, st));
+    // final info
+    std::vector<int> iters(s);
+    HODLR_TRY_CUDA(cudaMemcpyAsync(iters.data(), gs.iters, s * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaMemcpyAsync(hbuf.data(), gs.est, s * 8, cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaMemcpyAsync(hbuf.data() + s, nrm, s * 8, cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaMemcpyAsync(hbuf.data() + 2 * s, gs.bnorm, s * 8, cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+    HODLR_TRY(take_status(c, st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int r = 0; r < s; ++r) {
+        const double bn = hbuf[2 * s + r];
+        const double tr = bn > 0.0 ? std::sqrt(hbuf[s + r]) / bn : 0.0;
+        if (!(tr <= tol)) result = HODLR_NOT_CONVERGED;
+        if (info) {
+            if (info->iters) info->iters[r] = iters[r];
+            if (info->est_relres) info->est_relres[r] = hbuf[r];
+            if (info->true_relres) info->true_relres[r] = tr;
+        }
+    }
+    if (info) {
+        info->restarts = restarts;
+        info->ms_total = ms;
+    }
+    if (result == HODLR_NOT_CONVERGED) set_error("gmres_solve: not converged within %d iterations", max_iter);
+    return result;
+}

@@ -1,0 +1,196 @@
+// Internal declarations of libhodlr (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hodlr.h"
+
+namespace hodlr {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+
+#define HODLR_TRY_CUDA(call)                                                         \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            ::hodlr::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,             \
+                               cudaGetErrorString(e_));                              \
+            return HODLR_CUDA_ERROR;                                                 \
+        }                                                                            \
+    } while (0)
+
+#define HODLR_TRY(call)                                                              \
+    do {                                                                             \
+        hodlr_status s_ = (call);                                                    \
+        if (s_ != HODLR_OK) return s_;                                               \
+    } while (0)
+
+// Device status word bits (set with atomicOr by kernels, read by synchronising calls).
+enum : int {
+    ST_SINGULAR = 1,
+    ST_NONFINITE = 2,
+    ST_TIMEOUT = 4,
+    ST_RANGE = 8,
+};
+
+hodlr_status status_from_word(int w);
+
+// ------------------------------------------------------------------ context
+}  // namespace hodlr
+
+struct hodlr_ctx {
+    int device = 0;
+    int num_sms = 0;
+    hodlr_alloc_fn alloc = nullptr;
+    hodlr_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    int *d_status = nullptr;      // device status word (one int)
+    int *h_status = nullptr;      // pinned mirror
+};
+
+namespace hodlr {
+
+void *dalloc(hodlr_ctx *c, size_t bytes, cudaStream_t s);
+void dfree(hodlr_ctx *c, void *p, size_t bytes, cudaStream_t s);
+
+// RAII-less device buffer bookkeeping: every hodlr_t remembers what it owns.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Read and clear the context's device status word (synchronises the stream).
+hodlr_status take_status(hodlr_ctx *c, cudaStream_t s);
+
+// ------------------------------------------------------------------ tree
+// Level l (1..L) of the tree holds 2^l nodes; node i covers leaves
+// [i << (L-l), (i+1) << (L-l)).  Off-diagonal factors of level l belong to the
+// nodes of level l: U rows = the node's rows, paired with V rows = the
+// sibling's rows (A(node, sibling) ~ U_node V_sibling^T).
+struct Level {
+    int nnodes = 0;
+    int rp = 0;               // padded rank (columns of this level in D and V)
+    int64_t coff = 0;         // first column of this level in D and V
+    int cap = 0;              // staging columns for compression
+    std::vector<int> ranks;   // per node
+    int rank_max = 0;
+    double rank_mean = 0.0;
+};
+
+}  // namespace hodlr
+
+struct hodlr_s {
+    hodlr_ctx *ctx = nullptr;
+    const double *A = nullptr;
+    int64_t n = 0, lda = 0;
+    int sym = 0;
+    int L = 0;
+    int bmax = 0;                     // largest leaf
+    std::vector<int64_t> bounds;      // 2^L + 1 leaf boundaries
+    int64_t *d_bounds = nullptr;
+    int prec = HODLR_FP32;            // factor / apply precision
+    int cprec = HODLR_FP32;           // compression precision
+    int method = HODLR_ACA;
+    double tol = 0.0;
+    int rank_cap = 1024;
+    int cap_hit = 0;
+    std::vector<hodlr::Level> lv;     // index 1..L used
+    int64_t ldn = 0;                  // leading dimension of D, V (n rounded up to 32)
+    int64_t Wtot = 0;                 // total columns of D, V
+    void *D = nullptr;                // elem[ldn * Wtot]: U, then d after factor
+    void *V = nullptr;                // elem[ldn * Wtot]
+    void *leafinv = nullptr;          // elem[2^L * bmax * bmax], column-major per leaf
+    std::vector<void *> Sinv;         // level l = 0..L-1: elem[2^l * (2 rp(l+1))^2]
+    std::vector<int32_t *> piv_rows;  // per level 1..L: [nnodes][cap] pivot rows (ACA) / kept rows (BDLR)
+    std::vector<int32_t *> piv_cols;
+    std::vector<int32_t *> d_ranks;   // per level 1..L: [nnodes]
+    bool factored = false;
+    double ms_compress = 0, ms_factor = 0;
+    std::vector<hodlr::DevBuf> owned;
+    // scratch reused by solve / factor
+    void *work = nullptr;
+    size_t work_bytes = 0;
+};
+
+namespace hodlr {
+
+inline size_t elem_size(int prec) { return prec == HODLR_FP64 ? 8 : 4; }
+
+void *own(hodlr_t *h, size_t bytes, cudaStream_t s);   // allocate and remember
+hodlr_status ensure_work(hodlr_t *h, size_t bytes, cudaStream_t s);
+
+// ------------------------------------------------------------------ kernels (launchers)
+// Compression
+struct AcaBlockDesc {
+    int64_t r0, m;      // block rows  [r0, r0+m)
+    int64_t c0, nc;     // block cols  [c0, c0+nc)
+    int64_t ld;         // leading dimension of the U/V staging (column-major)
+    void *U;            // staging of the row side  (element type = compression precision)
+    void *V;            // staging of the column side
+    int cap;            // columns available
+    int32_t *rank;      // out
+    int32_t *prow;      // out: pivot rows (block-local), cap entries
+    int32_t *pcol;      // out: pivot cols (block-local)
+    int32_t *cap_hit;   // out
+};
+hodlr_status launch_aca(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
+                        const AcaBlockDesc *d_blocks, int nblocks, int64_t max_m, double tol,
+                        cudaStream_t s);
+
+struct BdlrHost;   // defined in bdlr.cu
+hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t s,
+                      std::vector<void *> &Ust, std::vector<void *> &Vst);
+
+// Generic batched GEMM:  C_b += alpha * op(A_b) * B_b  (column-major), op = N or T.
+template <typename T>
+struct GemmDesc {
+    const T *A;
+    const T *B;
+    T *C;
+    int64_t lda, ldb, ldc;
+    int M, N, K;
+};
+template <typename T>
+hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T> *d_desc, int nbatch, int maxM,
+                          int maxN, int maxK, int transA, T alpha, cudaStream_t s);
+
+hodlr_status factor_impl(hodlr_t *h, cudaStream_t s);
+hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s);
+hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s_rhs,
+                         const double *Z, int64_t ldz, double *W, int64_t ldw, cudaStream_t s,
+                         void *work = nullptr);
+
+// Convert / pad kernels
+hodlr_status copy_columns(int prec_src, int prec_dst, const void *src, int64_t ld_src,
+                          void *dst, int64_t ld_dst, int64_t rows, int64_t cols,
+                          cudaStream_t s);
+
+}  // namespace hodlr
+
+// ------------------------------------------------------------------ device helpers
+namespace hodlr {
+namespace dev {
+
+// Exact-rounding multiply and subtract with no contraction into an FMA, so that a
+// residual formed term by term rounds exactly like the reference formulation.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T from_double(double x);
+template <>
+__device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_double<float>(double x) { return __double2float_rn(x); }
+
+}  // namespace dev
+}  // namespace hodlr

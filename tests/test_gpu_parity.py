@@ -1,0 +1,343 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (derived from the arithmetic):
+* FP64 compression forms every residual with the same round-to-nearest
+  multiply/subtract sequence as the oracle, so pivots, ranks and U, V agree
+  exactly up to the norm recurrence's summation order: 1e-12 relative.
+* FP64 factor / solve: different (blocked, level-synchronous) order of the same
+  algebra, explicit inverses instead of LU solves: 1e-10 relative (cond(K~) of the
+  test fronts is below 1e3, FP64 unit roundoff 1.1e-16, with a margin).
+* FP32 factor / solve: 2e-4 relative (FP32 unit roundoff 6e-8 times cond ~1e3).
+* GMRES: the true FP64 relative residual <= 1e-12 on both sides; iterates agree
+  to cond * 1e-12 (1e-9 here); iteration counts within 1 (FP64) or 2 (FP32).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import frontgen as fg  # noqa: E402
+from oracle import hodlr_oracle as O  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def H():
+    from __graft_entry__ import build
+    build()
+    import paper_1403_5337_gb300 as H
+    return H
+
+
+@pytest.fixture(scope="module")
+def ctx(H):
+    c = H.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def front576():
+    return fg.make_front(24, 24, 8, 8, "lognormal", 0.5, leaf=64, seed=0)
+
+
+@pytest.fixture(scope="module")
+def front4096():
+    F = fg.make_front(64, 64, 32, 32, "lognormal", 0.5, leaf=128, seed=0, device="cuda")
+    F.A = F.A.cpu().numpy()
+    return F
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _oracle_block(blocks, l, i):
+    """(U, V, rows, cols) of node i of level l's block A(node, sibling)."""
+    b = blocks[(l - 1, i // 2)]
+    if i % 2 == 0:
+        return b.Ua, b.Vab, b.info_ab
+    return b.Ub, b.Vba, b.info_ba
+
+
+def _compare_compression(h, F, blocks, tree, rtol, exact_pivots=True):
+    for l in range(1, tree.L + 1):
+        U, V, ranks, pr, pc = h.export_level(l)
+        for i in range(1 << l):
+            Uo, Vo, info = _oracle_block(blocks, l, i)
+            k = Uo.shape[1]
+            assert ranks[i] == k, (l, i, ranks[i], k)
+            r0, r1 = tree.range(l, i)
+            c0, c1 = tree.range(l, i ^ 1)
+            if exact_pivots:
+                if isinstance(info, O.ACAResult):
+                    rows, cols = list(info.rows), list(info.cols)
+                else:
+                    rows, cols = [v - r0 for v in info.Ir], [v - c0 for v in info.Jr]
+                assert pr[i, :k].tolist() == rows, (l, i)
+                assert pc[i, :k].tolist() == cols, (l, i)
+            Ug = U[r0:r1, :k]
+            Vg = V[c0:c1, :k]
+            scale_u = max(np.abs(Uo).max(), 1e-300) if k else 1.0
+            scale_v = max(np.abs(Vo).max(), 1e-300) if k else 1.0
+            assert np.abs(Ug - Uo).max() <= rtol * scale_u, (l, i)
+            assert np.abs(Vg - Vo).max() <= rtol * scale_v, (l, i)
+            # padding columns are zero
+            assert not np.any(U[r0:r1, k:]) and not np.any(V[c0:c1, k:])
+
+
+@pytest.mark.parametrize("cprec,dtype,rtol", [("fp64", np.float64, 1e-12), ("fp32", np.float32, 2e-6)])
+def test_aca_matches_oracle(H, ctx, front576, cprec, dtype, rtol):
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    blocks = O.build(F.A, tree, "aca", 1e-6, symmetric=True, dtype=dtype)
+    h = H.hodlr_build(ctx, _dev(F.A), 64, 1e-6, "aca", precision="fp64", compress_precision=cprec)
+    _compare_compression(h, F, blocks, tree, rtol)
+    h.close()
+
+
+@pytest.mark.parametrize("cprec,dtype,rtol", [("fp64", np.float64, 1e-10), ("fp32", np.float32, 1e-3)])
+def test_bdlr_matches_oracle(H, ctx, front576, cprec, dtype, rtol):
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    g = (F.rowptr, F.colind)
+    blocks = O.build(F.A, tree, "bdlr", 1e-4, graph=g, depth=4, dtype=dtype)
+    h = H.hodlr_build(ctx, _dev(F.A), 64, 1e-4, "bdlr", graph=g, precision="fp64", compress_precision=cprec,
+                      bdlr_depth=4)
+    _compare_compression(h, F, blocks, tree, rtol)
+    h.close()
+
+
+def test_aca_nonsymmetric_column_reads(H, ctx, front576):
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    rng = np.random.default_rng(0)
+    A = F.A + 0.01 * np.triu(rng.standard_normal(F.A.shape), 1)   # not symmetric
+    blocks = O.build(A, tree, "aca", 1e-6)
+    h = H.hodlr_build(ctx, _dev(A), 64, 1e-6, "aca", precision="fp64", symmetric=False)
+    _compare_compression(h, F, blocks, tree, 1e-12)
+    h.close()
+
+
+def test_factor_and_solve_fp64(H, ctx, front576):
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    blocks = O.build(F.A, tree, "aca", 1e-6)
+    Fac = O.factor(F.A, tree, blocks)
+    h = H.hodlr_build(ctx, _dev(F.A), 64, 1e-6, "aca", precision="fp64")
+    H.hodlr_factor(h)
+    st = h.stats()
+    for l in range(1, tree.L + 1):
+        D, _, ranks, _, _ = h.export_level(l)
+        for i in range(1 << l):
+            r0, r1 = tree.range(l, i)
+            ref = Fac.d[(l, i)]
+            got = D[r0:r1, :ref.shape[1]]
+            assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), (l, i)
+    for l in range(tree.L):
+        S = h.export_core(l)
+        rp = st["rank_pad"][l]
+        for i in range(1 << l):
+            blk = blocks[(l, i)]
+            ra, rb = blk.Ua.shape[1], blk.Ub.shape[1]
+            idx = np.concatenate([np.arange(rb), rp + np.arange(ra)])
+            ref = np.linalg.inv(Fac.S[(l, i)])
+            got = S[i][np.ix_(idx, idx)]
+            assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), (l, i)
+    b = fg.rhs(F.n, 3, seed=1)
+    X = _dev(b.T)
+    H.hodlr_solve(h, X)
+    ref = O.solve(Fac, b)
+    got = X.cpu().numpy().T
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+    h.close()
+
+
+def test_solve_fp32(H, ctx, front576):
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    blocks = O.build(F.A, tree, "aca", 1e-6, dtype=np.float32)
+    Fac = O.factor(F.A, tree, blocks)
+    h = H.hodlr_build(ctx, _dev(F.A), 64, 1e-6, "aca", precision="fp32")
+    H.hodlr_factor(h)
+    b = fg.rhs(F.n, 2, seed=1)
+    X = _dev(b.T)
+    H.hodlr_solve(h, X)
+    ref = O.solve(Fac, b)
+    got = X.cpu().numpy().T
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-4
+    h.close()
+
+
+def test_matvec_is_fp64_accurate(H, ctx, front576):
+    F = front576
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal((5, F.n))
+    W = H.hodlr_matvec(ctx, _dev(F.A), _dev(z)).cpu().numpy()
+    ref = (F.A @ z.T).T
+    # per term: a and z represented to 2^-48, cross terms and the float-pair
+    # compensation rounded at 2^-48 each; 32 terms per pair, then FP64
+    err = np.abs(W - ref).max(axis=1) / (np.abs(F.A) @ np.abs(z.T)).T.max(axis=1)
+    assert err.max() < 16 * 2.0 ** -48
+    # an FP64 dot product of this length is accurate to about sqrt(n) 2^-53 ~ 3e-15
+    assert np.median(np.abs(W - ref) / (np.abs(F.A) @ np.abs(z.T)).T) < 2.0 ** -48
+
+
+@pytest.mark.parametrize("prec,itol", [("fp64", 1), ("fp32", 2)])
+def test_gmres_matches_oracle(H, ctx, front576, prec, itol):
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    dtype = np.float64 if prec == "fp64" else np.float32
+    _, _, P = O.hodlr_precond(F.A, tree, "aca", 1e-6, dtype=dtype)
+    b = fg.rhs(F.n, 2, seed=1)
+    A = _dev(F.A)
+    h = H.hodlr_build(ctx, A, 64, 1e-6, "aca", precision=prec)
+    H.hodlr_factor(h)
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    x = X.cpu().numpy()
+    for r in range(2):
+        ref = O.gmres(F.A, b[:, r], prec=P, tol=1e-12)
+        assert info.true_relres[r] <= 1e-12
+        true = np.linalg.norm(b[:, r] - F.A @ x[r]) / np.linalg.norm(b[:, r])
+        assert true <= 1.5e-12
+        assert abs(int(info.iters[r]) - ref.iters) <= itol
+        assert np.linalg.norm(x[r] - ref.x) / np.linalg.norm(ref.x) < 1e-9
+    h.close()
+
+
+def test_gmres_unpreconditioned_and_nonconvergence(H, ctx, front576):
+    F = front576
+    b = fg.rhs(F.n, 1, seed=1)
+    A = _dev(F.A)
+    ref = O.gmres(F.A, b[:, 0], tol=1e-8, max_iter=400)
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), None, tol=1e-8, max_iter=400)
+    assert info.converged and abs(int(info.iters[0]) - ref.iters) <= 2
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), None, tol=1e-14, max_iter=3)
+    assert not info.converged and info.iters[0] == 3
+    with pytest.raises(H.NotConverged):
+        H.gmres_solve(ctx, A, _dev(b.T), None, tol=1e-14, max_iter=3, raise_on_fail=True)
+
+
+def test_ragged_tree_and_zero_rhs(H, ctx):
+    # n = 1000 with leaf 60: 16 leaves of 62/63 rows, odd node sizes at every level
+    F = fg.make_front(25, 40, 5, 5, "lognormal", 0.5, leaf=60, seed=4)
+    A = F.A
+    n = F.n
+    tree = O.make_tree(n, 60)
+    blocks, Fac, P = O.hodlr_precond(A, tree, "aca", 1e-5)
+    h = H.hodlr_build(ctx, _dev(A), 60, 1e-5, "aca", precision="fp64")
+    H.hodlr_factor(h)
+    st = h.stats()
+    assert st["levels"] == tree.L and st["leaf_max"] == int(np.diff(tree.bounds).max())
+    b = fg.rhs(n, 3, seed=1)
+    b[:, 1] = 0.0
+    X = _dev(b.T)
+    H.hodlr_solve(h, X)
+    ref = O.solve(Fac, b)
+    assert np.linalg.norm(X.cpu().numpy().T - ref) / np.linalg.norm(ref) < 1e-10
+    Xg, info = H.gmres_solve(ctx, _dev(A), _dev(b.T), h, tol=1e-12)
+    assert info.converged and info.iters[1] == 0 and np.all(Xg.cpu().numpy()[1] == 0)
+    h.close()
+
+
+def test_custom_leaf_bounds_and_single_leaf(H, ctx, front576):
+    F = front576
+    A = _dev(F.A)
+    bounds = [0, 100, 288, 400, 576]
+    tree = O.make_tree(F.n, 0, bounds)
+    blocks, Fac, P = O.hodlr_precond(F.A, tree, "aca", 1e-6)
+    h = H.hodlr_build(ctx, A, 0, 1e-6, "aca", precision="fp64", leaf_bounds=bounds)
+    H.hodlr_factor(h)
+    b = fg.rhs(F.n, 1, seed=2)
+    X = _dev(b.T)
+    H.hodlr_solve(h, X)
+    assert np.linalg.norm(X.cpu().numpy().T - O.solve(Fac, b)) / np.linalg.norm(b) < 1e-10
+    h.close()
+    # leaf >= n: one dense leaf, the solve is a dense inverse
+    h = H.hodlr_build(ctx, A, 1000, 1e-6, "aca", precision="fp64")
+    H.hodlr_factor(h)
+    X = _dev(b.T)
+    H.hodlr_solve(h, X)
+    ref = np.linalg.solve(F.A, b)
+    assert np.linalg.norm(X.cpu().numpy().T - ref) / np.linalg.norm(ref) < 1e-12
+    h.close()
+
+
+def test_rank_zero_blocks(H, ctx):
+    # block-diagonal matrix: every off-diagonal block is zero, every rank 0
+    rng = np.random.default_rng(5)
+    n = 256
+    A = np.zeros((n, n))
+    for s in range(0, n, 32):
+        M = rng.standard_normal((32, 32))
+        A[s:s + 32, s:s + 32] = M @ M.T + 32 * np.eye(32)
+    h = H.hodlr_build(ctx, _dev(A), 32, 1e-6, "aca", precision="fp64")
+    H.hodlr_factor(h)
+    assert all(r == 0 for r in h.stats()["rank_max"])
+    b = rng.standard_normal((1, n))
+    X = _dev(b)
+    H.hodlr_solve(h, X)
+    assert np.linalg.norm(X.cpu().numpy()[0] - np.linalg.solve(A, b[0])) / np.linalg.norm(b) < 1e-12
+    h.close()
+
+
+def test_nonfinite_input_is_reported(H, ctx, front576):
+    A = front576.A.copy()
+    A[0, 300] = np.nan                   # row 0 of the top block is always read
+    with pytest.raises(H.HodlrError) as e:
+        H.hodlr_build(ctx, _dev(A), 64, 1e-6, "aca", precision="fp64", symmetric=False)
+    assert e.value.code == 8
+
+
+def test_invalid_arguments(H, ctx, front576):
+    A = _dev(front576.A)
+    with pytest.raises(H.HodlrError) as e:
+        H.hodlr_build(ctx, A, 64, 2.0, "aca")
+    assert e.value.code == 1
+    with pytest.raises(H.HodlrError) as e:
+        H.hodlr_build(ctx, A, 64, 1e-3, "bdlr")          # BDLR without a graph
+    assert e.value.code == 1
+    with pytest.raises(H.HodlrError) as e:
+        H.hodlr_build(ctx, A, 64, 1e-3, "aca", rank_cap=5000)
+    assert e.value.code == 9
+
+
+def test_singular_leaf_is_reported(H, ctx):
+    n = 128
+    A = np.eye(n)
+    A[:32, :32] = 0.0                     # first leaf singular
+    h = H.hodlr_build(ctx, _dev(A), 32, 1e-6, "aca", precision="fp64")
+    H.hodlr_factor(h)
+    with pytest.raises(H.HodlrError) as e:
+        H.gmres_solve(ctx, _dev(A), _dev(np.ones((1, n))), h, tol=1e-12, max_iter=5)
+    assert e.value.code == 4
+    h.close()
+
+
+# ---------------------------------------------------------------- the 4096 front
+@pytest.mark.parametrize("method,tol,prec", [("aca", 1e-4, "fp32"), ("aca", 1e-4, "fp64"),
+                                             ("bdlr", 1e-4, "fp32"), ("aca", 1e-8, "fp32")])
+def test_front4096_gmres(H, ctx, front4096, method, tol, prec):
+    F = front4096
+    g = (F.rowptr, F.colind)
+    tree = O.make_tree(F.n, 128, F.bounds)
+    dtype = np.float64 if prec == "fp64" else np.float32
+    blocks, Fac, P = O.hodlr_precond(F.A, tree, method, tol, graph=g, dtype=dtype)
+    b = fg.rhs(F.n, 4, seed=1)
+    A = _dev(F.A)
+    h = H.hodlr_build(ctx, A, 128, tol, method, graph=g, precision=prec)
+    st = h.stats()
+    for l in range(1, tree.L + 1):
+        ro = max(max(blocks[(l - 1, i // 2)].Ua.shape[1] if i % 2 == 0 else blocks[(l - 1, i // 2)].Ub.shape[1]
+                      for i in range(1 << l)), 0)
+        assert st["rank_max"][l - 1] == ro
+    H.hodlr_factor(h)
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    x = X.cpu().numpy()
+    assert info.converged and np.all(info.true_relres <= 1e-12)
+    for r in range(4):
+        ref = O.gmres(F.A, b[:, r], prec=P, tol=1e-12)
+        assert abs(int(info.iters[r]) - ref.iters) <= 2, (r, info.iters, ref.iters)
+        assert np.linalg.norm(x[r] - ref.x) / np.linalg.norm(ref.x) < 1e-9
+    h.close()
