@@ -101,7 +101,7 @@ def make_inputs(wl, device):
     import frontgen as fg
     w = dict(WORKLOADS[wl])
     nrhs = w.pop("nrhs")
-    F = fg.make_front(**w, device=device)
+    F = fg.make_front(**w, device=device, cache=True)
     B = fg.rhs(F.n, nrhs, seed=1)
     return F, B
 
@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--nvtx", action="store_true", help="wrap every timed step in an NVTX range 'bench_step'")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -241,7 +242,11 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
+            if args.nvtx:
+                torch.cuda.nvtx.range_push("bench_step")
             X, info, st = step(prec)
+            if args.nvtx:
+                torch.cuda.nvtx.range_pop()
             e1.record()
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)

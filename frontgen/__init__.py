@@ -28,6 +28,7 @@ finished matrix.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -280,9 +281,32 @@ WORKLOADS = {
 }
 
 
+def default_cache_dir() -> str:
+    """Directory for generated fronts: $HODLR_FRONT_CACHE or <tmp>/hodlr_fronts."""
+    import tempfile
+    return os.environ.get("HODLR_FRONT_CACHE", os.path.join(tempfile.gettempdir(), "hodlr_fronts"))
+
+
 def make_front(nx, ny, below, above, field="lognormal", sigma=0.5, leaf=64, seed=0,
-               device="cpu", cell=8, contrast=1e6):
-    """Build one plane front on an nx x ny x (below+1+above) box, in tree order."""
+               device="cpu", cell=8, contrast=1e6, cache=False):
+    """Build one plane front on an nx x ny x (below+1+above) box, in tree order.
+
+    With cache=True the natural-order front is stored in default_cache_dir() and
+    reloaded on the next call with the same parameters (the elimination is the
+    slow part; the ordering and graph are recomputed)."""
+    path = None
+    if cache:
+        key = f"front_{nx}x{ny}_{below}_{above}_{field}_{sigma}_{seed}_{cell}_{contrast}.npy"
+        d = default_cache_dir()
+        os.makedirs(d, exist_ok=True)
+        path = os.path.join(d, key)
+        if os.path.exists(path):
+            A_nat = np.load(path)
+            if device != "cpu":
+                import torch
+                A_nat = torch.as_tensor(A_nat, device=device)
+            return _finish(A_nat, nx, ny, leaf, dict(nz=below + 1 + above, below=below, above=above,
+                                                     field=field, sigma=sigma, seed=seed))
     nz = below + 1 + above
     if field == "lognormal":
         a = coefficient_lognormal(nx, ny, nz, sigma, seed)
@@ -293,6 +317,10 @@ def make_front(nx, ny, below, above, field="lognormal", sigma=0.5, leaf=64, seed
     else:
         raise ValueError(field)
     A_nat = plane_front(a, below, device=device)
+    if path is not None:
+        tmp = path + f".{os.getpid()}.tmp.npy"
+        np.save(tmp, A_nat if isinstance(A_nat, np.ndarray) else A_nat.cpu().numpy())
+        os.replace(tmp, path)
     return _finish(A_nat, nx, ny, leaf, dict(nz=nz, below=below, above=above,
                                              field=field, sigma=sigma, seed=seed))
 

@@ -203,6 +203,16 @@ hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn fr
     }
     cudaMemset(c->d_status, 0, sizeof(int));
     *c->h_status = 0;
+    for (int i = 0; i < HODLR_SIDE_STREAMS; ++i)
+        if (cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (int q = 0; q < i; ++q) cudaStreamDestroy(c->side[q]);
+            cudaFree(c->d_status);
+            cudaFreeHost(c->h_status);
+            delete c;
+            set_error("hodlr_ctx_create: cannot create streams");
+            return HODLR_CUDA_ERROR;
+        }
     *out = c;
     return HODLR_OK;
 }
@@ -210,6 +220,8 @@ hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn fr
 hodlr_status hodlr_ctx_destroy(hodlr_ctx *c) {
     if (!c) return HODLR_OK;
     cudaSetDevice(c->device);
+    for (int i = 0; i < HODLR_SIDE_STREAMS; ++i)
+        if (c->side[i]) cudaStreamDestroy(c->side[i]);
     cudaFree(c->d_status);
     cudaFreeHost(c->h_status);
     delete c;
@@ -221,6 +233,7 @@ hodlr_status hodlr_destroy(hodlr_t *h) {
     cudaSetDevice(h->ctx->device);
     cudaStreamSynchronize(nullptr);
     cudaDeviceSynchronize();
+    free_plan(h, nullptr);
     for (auto &b : h->owned) dfree(h->ctx, b.p, b.bytes, nullptr);
     if (h->work) dfree(h->ctx, h->work, h->work_bytes, nullptr);
     cudaDeviceSynchronize();
@@ -422,7 +435,18 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             return fail(HODLR_OUT_OF_MEMORY);
         }
         cudaMemcpyAsync(db, blocks.data(), blocks.size() * sizeof(AcaBlockDesc), cudaMemcpyHostToDevice, st);
-        rs = launch_aca(c, A->data, A->ld, h->sym, cprec, db, (int)blocks.size(), max_m, tol, st);
+        std::vector<int> first;
+        std::vector<int64_t> maxdim;
+        int b0 = 0;
+        for (int l = 1; l <= L; ++l) {
+            first.push_back(b0);
+            int64_t md = 0;
+            for (int i = 0; i < (1 << l); ++i) md = std::max(md, std::max(blocks[b0 + i].m, blocks[b0 + i].nc));
+            maxdim.push_back(md);
+            b0 += 1 << l;
+        }
+        first.push_back(b0);
+        rs = launch_aca_levels(c, A->data, A->ld, h->sym, cprec, db, first, maxdim, tol, st);
         cudaStreamSynchronize(st);
         dfree(c, db, blocks.size() * sizeof(AcaBlockDesc) + 16, st);
     } else {
@@ -541,6 +565,10 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         }
     }
     free_temp();
+    {
+        hodlr_status sp = plan_factor(h, st);
+        if (sp != HODLR_OK) return fail(sp);
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("hodlr_build: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(HODLR_CUDA_ERROR);

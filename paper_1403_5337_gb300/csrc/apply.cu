@@ -74,28 +74,58 @@ __global__ void __launch_bounds__(AP_THREADS)
     }
 }
 
-// y(node) = S^-1 [w(alpha); w(beta)] for every RHS.  One CTA per node.
+// y(node) = S^-1 [w(alpha); w(beta)] for every RHS.  Grid (node, 32-row tiles of
+// S^-1): lane = output row, the 8 warps split the inner dimension, partial sums
+// are reduced in shared memory.
+constexpr int TR = 32;   // rows per CTA in the row-tiled apply kernels
+
 template <typename T>
 __global__ void __launch_bounds__(AP_THREADS)
     core_apply_kernel(const T *__restrict__ Sinv, int rp, const T *__restrict__ w, int s, T *__restrict__ y) {
     const int node = blockIdx.x;
     const int s2 = 2 * rp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.y * TR + lane;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *ws = reinterpret_cast<T *>(smem);   // s2 * s
-    const T *wn = w + (size_t)node * s2 * s;   // children 2 node, 2 node + 1 are contiguous
+    T *ws = reinterpret_cast<T *>(smem);          // s2 * s
+    T *part = ws + (size_t)s2 * s;                // 8 warps * TR * MAX_RHS_CHUNK
+    const T *wn = w + (size_t)node * s2 * s;      // children 2 node, 2 node + 1 are contiguous
     for (int e = threadIdx.x; e < s2 * s; e += AP_THREADS) ws[e] = wn[e];
     __syncthreads();
     const T *S = Sinv + (size_t)node * s2 * s2;
-    for (int e = threadIdx.x; e < s2 * s; e += AP_THREADS) {
-        const int i = e % s2, r = e / s2;
-        T acc = T(0);
-        for (int k = 0; k < s2; ++k) acc = fma(S[i + (size_t)k * s2], ws[k * s + r], acc);
-        y[((size_t)node * s2 + i) * s + r] = acc;
+    const int kper = (s2 + 7) / 8, kb = warp * kper, ke = min(s2, kb + kper);
+    for (int r0 = 0; r0 < s; r0 += MAX_RHS_CHUNK) {
+        const int rr = (s - r0) < MAX_RHS_CHUNK ? (s - r0) : MAX_RHS_CHUNK;
+        T acc[MAX_RHS_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MAX_RHS_CHUNK; ++q) acc[q] = T(0);
+        if (i < s2) {
+#pragma unroll 4
+            for (int k = kb; k < ke; ++k) {
+                const T sv = S[i + (size_t)k * s2];
+#pragma unroll
+                for (int q = 0; q < MAX_RHS_CHUNK; ++q)
+                    if (q < rr) acc[q] = fma(sv, ws[k * s + r0 + q], acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MAX_RHS_CHUNK; ++q) part[(warp * TR + lane) * MAX_RHS_CHUNK + q] = acc[q];
+        __syncthreads();
+        for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
+            const int li = e % TR, q = e / TR;
+            T v = T(0);
+            for (int wv = 0; wv < AP_THREADS / 32; ++wv) v += part[(wv * TR + li) * MAX_RHS_CHUNK + q];
+            const int ii = blockIdx.y * TR + li;
+            if (ii < s2) y[((size_t)node * s2 + ii) * s + r0 + q] = v;
+        }
+        __syncthreads();
     }
 }
 
 // x(child rows, r) -= d(child rows, coff:coff+rp) * y_sib(:, r), y_sib = y2 for the
 // first child (alpha) and y1 for the second (beta).
+// Rows are tiled by TR = 32 per CTA (lane = row); the 8 warps split the rp
+// columns of d and the partial sums are reduced in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(AP_THREADS)
     update_kernel(const T *__restrict__ Dm, int64_t ldn, int64_t coff, int rp,
@@ -107,29 +137,43 @@ __global__ void __launch_bounds__(AP_THREADS)
     const int64_t a = n0 + ch * chunk_rows;
     const int64_t e = (a + chunk_rows < n1) ? a + chunk_rows : n1;
     if (a >= e) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *ys = reinterpret_cast<T *>(smem);   // rp * s
+    T *ys = reinterpret_cast<T *>(smem);     // rp * s
+    T *part = ys + (size_t)rp * s;           // 8 warps * TR * MAX_RHS_CHUNK
     const int node = child >> 1;
     const int half = (child & 1) ? 0 : rp;   // alpha uses y2 (second half)
     const T *yn = y + ((size_t)node * 2 * rp + half) * s;
     for (int q = threadIdx.x; q < rp * s; q += AP_THREADS) ys[q] = yn[q];
     __syncthreads();
-    for (int64_t i = a + threadIdx.x; i < e; i += AP_THREADS) {
-        for (int r0 = 0; r0 < s; r0 += MAX_RHS_CHUNK) {
-            const int rr = (s - r0) < MAX_RHS_CHUNK ? (s - r0) : MAX_RHS_CHUNK;
-            T acc[MAX_RHS_CHUNK];
+    const int kper = (rp + 7) / 8, kb = warp * kper, ke = min(rp, kb + kper);
+    const int64_t i = a + lane;
+    for (int r0 = 0; r0 < s; r0 += MAX_RHS_CHUNK) {
+        const int rr = (s - r0) < MAX_RHS_CHUNK ? (s - r0) : MAX_RHS_CHUNK;
+        T acc[MAX_RHS_CHUNK];
 #pragma unroll
-            for (int q = 0; q < MAX_RHS_CHUNK; ++q) acc[q] = T(0);
-            for (int k = 0; k < rp; ++k) {
+        for (int q = 0; q < MAX_RHS_CHUNK; ++q) acc[q] = T(0);
+        if (i < e) {
+#pragma unroll 4
+            for (int k = kb; k < ke; ++k) {
                 const T dv = Dm[i + (coff + k) * ldn];
 #pragma unroll
                 for (int q = 0; q < MAX_RHS_CHUNK; ++q)
                     if (q < rr) acc[q] = fma(dv, ys[k * s + r0 + q], acc[q]);
             }
-#pragma unroll
-            for (int q = 0; q < MAX_RHS_CHUNK; ++q)
-                if (q < rr) xt[i + (r0 + q) * ldt] -= acc[q];
         }
+#pragma unroll
+        for (int q = 0; q < MAX_RHS_CHUNK; ++q) part[(warp * TR + lane) * MAX_RHS_CHUNK + q] = acc[q];
+        __syncthreads();
+        for (int t = threadIdx.x; t < TR * rr; t += AP_THREADS) {
+            const int li = t % TR, q = t / TR;
+            const int64_t ii = a + li;
+            if (ii >= e) continue;
+            T v = T(0);
+            for (int wv = 0; wv < AP_THREADS / 32; ++wv) v += part[(wv * TR + li) * MAX_RHS_CHUNK + q];
+            xt[ii + (r0 + q) * ldt] -= v;
+        }
+        __syncthreads();
     }
 }
 
@@ -185,7 +229,7 @@ hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
         int64_t node_rows = 0;
         for (int i = 0; i < nch; ++i)
             node_rows = std::max(node_rows, h->bounds[(size_t)(i + 1) << (L - c)] - h->bounds[(size_t)i << (L - c)]);
-        const int64_t chunk_rows = 1024;
+        const int64_t chunk_rows = 256;
         const int chunks = (int)((node_rows + chunk_rows - 1) / chunk_rows);
         {
             int64_t cnt = (int64_t)nch * rp * s;
@@ -196,19 +240,21 @@ hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
                                                         xt, ldn, s, w);
             HODLR_TRY_CUDA(cudaGetLastError());
         }
+        const size_t part_bytes = (size_t)(AP_THREADS / 32) * TR * MAX_RHS_CHUNK * sizeof(T);
         {
             const T *Sinv = reinterpret_cast<const T *>(h->Sinv[c - 1]);
-            size_t sm = (size_t)2 * rp * s * sizeof(T);
+            const size_t sm = (size_t)2 * rp * s * sizeof(T) + part_bytes;
             if (sm > 48 * 1024)
                 HODLR_TRY_CUDA(cudaFuncSetAttribute(core_apply_kernel<T>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            core_apply_kernel<T><<<nch / 2, AP_THREADS, sm, st>>>(Sinv, rp, w, s, y);
+            dim3 grid(nch / 2, (2 * rp + TR - 1) / TR);
+            core_apply_kernel<T><<<grid, AP_THREADS, sm, st>>>(Sinv, rp, w, s, y);
             HODLR_TRY_CUDA(cudaGetLastError());
         }
         {
-            const int64_t urows = 256;
+            const int64_t urows = TR;
             const int uchunks = (int)((node_rows + urows - 1) / urows);
-            size_t sm = (size_t)rp * s * sizeof(T);
+            const size_t sm = (size_t)rp * s * sizeof(T) + part_bytes;
             if (sm > 48 * 1024)
                 HODLR_TRY_CUDA(cudaFuncSetAttribute(update_kernel<T>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

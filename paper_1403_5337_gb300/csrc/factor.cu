@@ -18,6 +18,8 @@
 // S; it halves the size of the dense inversion.
 #include <algorithm>
 #include <climits>
+#include <cstring>
+#include <functional>
 
 #include "internal.cuh"
 
@@ -240,55 +242,217 @@ hodlr_status zero(T *p, int64_t count, cudaStream_t s) {
     return HODLR_OK;
 }
 
+// Gauss-Jordan inversion in place in shared memory (ld = b + 1, conflict-free
+// row and column access), same pivot rule as above (argmax_{i>=k} |a(i,k)|,
+// lowest row on ties).  Step k: swap rows k and p, d = 1/a(k,k), scale row k,
+// eliminate column k from every other row, storing -a(i,k) d in column k.  The
+// result is (PA)^-1; A^-1 = (PA)^-1 P, i.e. column j of A^-1 is column pos(j) of
+// the work matrix, pos(j) = final position of the original row j.
+constexpr int GJS_THREADS = 512;
+
 template <typename T>
-hodlr_status run_gj(hodlr_ctx *c, const std::vector<GJDesc<T>> &hd, cudaStream_t s, void *scratch) {
-    if (hd.empty()) return HODLR_OK;
-    int bmax = 0;
-    for (auto &g : hd) bmax = std::max(bmax, g.b);
-    GJDesc<T> *dd = reinterpret_cast<GJDesc<T> *>(scratch);
-    HODLR_TRY_CUDA(cudaMemcpyAsync(dd, hd.data(), hd.size() * sizeof(GJDesc<T>),
-                                   cudaMemcpyHostToDevice, s));
+__global__ void __launch_bounds__(GJS_THREADS) gj_inverse_smem_kernel(const GJDesc<T> *__restrict__ descs,
+                                                                      int *status) {
+    const GJDesc<T> g = descs[blockIdx.x];
+    const int b = g.b, tid = threadIdx.x;
+    if (b <= 0) return;
+    const int ldb = b + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *a = reinterpret_cast<T *>(smem);            // ldb * b
+    T *rowk = a + (size_t)ldb * b;                 // b
+    T *colk = rowk + b;                            // b
+    int *orig = reinterpret_cast<int *>(colk + b); // b: original row at each position
+    __shared__ int s_p, s_fail;
+    for (int e = tid; e < b * b; e += GJS_THREADS) {
+        const int j = e / b, i = e % b;
+        a[i + j * ldb] = g.srcA ? dev::from_double<T>(g.srcA[(int64_t)i * g.lda + j]) : g.srcM[i + (int64_t)j * g.ldm];
+    }
+    for (int i = tid; i < b; i += GJS_THREADS) orig[i] = i;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int k = 0; k < b; ++k) {
+        if (warp == 0) {
+            T bv = T(-1);
+            int bi = INT_MAX;
+            for (int i = k + lane; i < b; i += 32) {
+                const T v = fabs(a[i + k * ldb]);
+                if (v > bv) {
+                    bv = v;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                s_p = bi;
+                if (!(bv > T(0))) s_fail = 1;
+                else if (bi != k) {
+                    const int t = orig[k];
+                    orig[k] = orig[bi];
+                    orig[bi] = t;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < b; j += GJS_THREADS) {
+                const T t = a[k + j * ldb];
+                a[k + j * ldb] = a[p + j * ldb];
+                a[p + j * ldb] = t;
+            }
+        __syncthreads();
+        const T d = T(1) / a[k + k * ldb];
+        for (int j = tid; j < b; j += GJS_THREADS) rowk[j] = (j == k) ? d : a[k + j * ldb] * d;
+        for (int i = tid; i < b; i += GJS_THREADS) colk[i] = (i == k) ? T(0) : a[i + k * ldb];
+        __syncthreads();
+        for (int e = tid; e < b * b; e += GJS_THREADS) {
+            const int j = e / b, i = e % b;
+            T v;
+            if (i == k)
+                v = rowk[j];
+            else if (j == k)
+                v = -colk[i] * d;
+            else
+                v = a[i + j * ldb] - colk[i] * rowk[j];
+            a[i + j * ldb] = v;
+        }
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, ST_SINGULAR);
+        return;
+    }
+    // pos(orig[q]) = q
+    for (int q = tid; q < b; q += GJS_THREADS) colk[orig[q]] = (T)q;
+    __syncthreads();
+    for (int e = tid; e < b * b; e += GJS_THREADS) {
+        const int j = e / b, i = e % b;
+        const int pj = (int)colk[j];
+        g.out[i + (int64_t)j * g.ldo] = a[i + pj * ldb];
+    }
+}
+
+constexpr size_t GJS_SMEM_MAX = 200 * 1024;
+
+template <typename T>
+size_t gjs_smem(int b) {
+    return ((size_t)(b + 1) * b + 2 * (size_t)b) * sizeof(T) + (size_t)b * sizeof(int) + 16;
+}
+
+template <typename T>
+hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, cudaStream_t s) {
+    if (gjs_smem<T>(bmax) <= GJS_SMEM_MAX) {
+        const size_t sm = gjs_smem<T>(bmax);
+        HODLR_TRY_CUDA(cudaFuncSetAttribute(gj_inverse_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sm));
+        gj_inverse_smem_kernel<T><<<count, GJS_THREADS, sm, s>>>(dd, c->d_status);
+        HODLR_TRY_CUDA(cudaGetLastError());
+        return HODLR_OK;
+    }
     size_t sm = 3 * (size_t)bmax * sizeof(T);
     HODLR_TRY_CUDA(cudaFuncSetAttribute(gj_inverse_kernel<T>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    gj_inverse_kernel<T><<<(int)hd.size(), GJ_THREADS, sm, s>>>(dd, c->d_status);
+    gj_inverse_kernel<T><<<count, GJ_THREADS, sm, s>>>(dd, c->d_status);
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
 }
 
-// Upload a vector of GEMM descriptors into `scratch` and launch.
-template <typename T>
-hodlr_status run_gemm(hodlr_ctx *c, const std::vector<GemmDesc<T>> &hd, int transA, T alpha,
-                      cudaStream_t s, void *scratch) {
-    if (hd.empty()) return HODLR_OK;
-    int maxM = 0, maxN = 0, maxK = 0;
-    for (auto &g : hd) {
-        maxM = std::max(maxM, g.M);
-        maxN = std::max(maxN, g.N);
-        maxK = std::max(maxK, g.K);
-    }
-    if (maxM == 0 || maxN == 0 || maxK == 0) return HODLR_OK;
-    GemmDesc<T> *dd = reinterpret_cast<GemmDesc<T> *>(scratch);
-    HODLR_TRY_CUDA(cudaMemcpyAsync(dd, hd.data(), hd.size() * sizeof(GemmDesc<T>),
-                                   cudaMemcpyHostToDevice, s));
-    return gemm_batched<T>(c, dd, (int)hd.size(), maxM, maxN, maxK, transA, alpha, s);
-}
+}  // namespace
 
-// A descriptor upload area per step; several steps are enqueued before any sync,
-// so each uses its own slice of the scratch.
-struct Scratch {
-    char *base = nullptr;
-    size_t used = 0, cap = 0;
-    void *take(size_t bytes) {
-        size_t off = (used + 255) & ~size_t(255);
-        if (off + bytes > cap) return nullptr;
-        used = off + bytes;
-        return base + off;
+// The factorisation is planned once, when the HODLR matrix is built: every
+// launch of the level-synchronous sweep is recorded with its arguments, and all
+// batched-GEMM and inversion descriptors are laid out in one blob that is
+// uploaded in a single copy.  hodlr_factor then only replays the launches, with
+// no host-device transfer on the stream.
+struct FactorPlan {
+    std::vector<std::function<hodlr_status(cudaStream_t)>> ops;
+    std::vector<char> blob;
+    char *dblob = nullptr;
+    size_t dbytes = 0;
+    void *work = nullptr;
+    size_t work_bytes = 0;
+
+    size_t put(const void *p, size_t bytes) {
+        const size_t off = (blob.size() + 255) & ~size_t(255);
+        blob.resize(off + bytes);
+        std::memcpy(blob.data() + off, p, bytes);
+        return off;
+    }
+};
+
+namespace {
+
+template <typename T>
+struct Rec {
+    hodlr_ctx *c;
+    FactorPlan *P;
+    void gj(const std::vector<GJDesc<T>> &hd) {
+        if (hd.empty()) return;
+        int bmax = 0;
+        for (auto &g : hd) bmax = std::max(bmax, g.b);
+        const size_t off = P->put(hd.data(), hd.size() * sizeof(GJDesc<T>));
+        const int cnt = (int)hd.size();
+        hodlr_ctx *cc = c;
+        FactorPlan *PP = P;
+        P->ops.push_back([=](cudaStream_t s) {
+            return launch_gj<T>(cc, reinterpret_cast<const GJDesc<T> *>(PP->dblob + off), cnt, bmax, s);
+        });
+    }
+    void gemm(const std::vector<GemmDesc<T>> &hd, int transA, T alpha) {
+        if (hd.empty()) return;
+        int maxM = 0, maxN = 0, maxK = 0;
+        for (auto &g : hd) {
+            maxM = std::max(maxM, g.M);
+            maxN = std::max(maxN, g.N);
+            maxK = std::max(maxK, g.K);
+        }
+        if (maxM == 0 || maxN == 0 || maxK == 0) return;
+        const size_t off = P->put(hd.data(), hd.size() * sizeof(GemmDesc<T>));
+        const int cnt = (int)hd.size();
+        hodlr_ctx *cc = c;
+        FactorPlan *PP = P;
+        P->ops.push_back([=](cudaStream_t s) {
+            return gemm_batched<T>(cc, reinterpret_cast<const GemmDesc<T> *>(PP->dblob + off), cnt, maxM, maxN,
+                                   maxK, transA, alpha, s);
+        });
+    }
+    void zero_(T *p, int64_t count) {
+        P->ops.push_back([=](cudaStream_t s) { return zero<T>(p, count, s); });
+    }
+    void identity(T *M, int64_t ld, int n, int count, int64_t stride) {
+        P->ops.push_back([=](cudaStream_t s) {
+            dim3 grid(std::max(1, std::min(64, (n * n + 255) / 256)), count);
+            set_identity_kernel<T><<<grid, 256, 0, s>>>(M, ld, n, count, stride);
+            HODLR_TRY_CUDA(cudaGetLastError());
+            return HODLR_OK;
+        });
+    }
+    void memset2d(T *p, int64_t pitch_elems, int64_t width_elems, int64_t height) {
+        P->ops.push_back([=](cudaStream_t s) {
+            HODLR_TRY_CUDA(cudaMemset2DAsync(p, pitch_elems * sizeof(T), 0, width_elems * sizeof(T), height, s));
+            return HODLR_OK;
+        });
+    }
+    void copy(T *dst, const T *src, int64_t count) {
+        P->ops.push_back([=](cudaStream_t s) {
+            HODLR_TRY_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToDevice, s));
+            return HODLR_OK;
+        });
     }
 };
 
 template <typename T>
-hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
+hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
     hodlr_ctx *c = h->ctx;
     const int L = h->L;
     const int64_t ldn = h->ldn, W = h->Wtot;
@@ -316,11 +480,14 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
         size_t gw = (size_t)nn * 2 * rp * rp;                    // GJ work per node
         lvl_max = std::max(lvl_max, (y + yv + mm + gw) * sizeof(T) + 4096);
     }
-    need += lvl_max;
-    const size_t desc_bytes = (size_t)64 << 20;
-    need += desc_bytes;
-    HODLR_TRY(ensure_work(h, need, s));
-    char *wp = reinterpret_cast<char *>(h->work);
+    need += lvl_max + 4096;
+    Pl->work = dalloc(c, need, s);
+    if (!Pl->work) {
+        set_error("factor plan: out of device memory (%zu bytes)", need);
+        return HODLR_OUT_OF_MEMORY;
+    }
+    Pl->work_bytes = need;
+    char *wp = reinterpret_cast<char *>(Pl->work);
     auto carve = [&](size_t bytes) {
         char *p = wp;
         wp += (bytes + 255) & ~size_t(255);
@@ -329,9 +496,7 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
     T *gjw = reinterpret_cast<T *>(carve((size_t)nleaf * 2 * bmax * bmax * sizeof(T)));
     T *D2 = reinterpret_cast<T *>(carve((size_t)ldn * W * sizeof(T)));
     char *lvl = carve(lvl_max);
-    Scratch sc;
-    sc.base = carve(desc_bytes);
-    sc.cap = desc_bytes;
+    Rec<T> rec{c, Pl};
 
     // ---- 1. leaf inverses
     T *Kinv = reinterpret_cast<T *>(h->leafinv);
@@ -344,13 +509,11 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
                               gjw + (size_t)i * 2 * bmax * bmax, Kinv + (size_t)i * bmax * bmax,
                               bmax, (int)m};
         }
-        void *dd = sc.take(gd.size() * sizeof(GJDesc<T>));
-        if (!dd) return HODLR_OUT_OF_MEMORY;
-        HODLR_TRY(run_gj<T>(c, gd, s, dd));
+        rec.gj(gd);
     }
-    // ---- 2. leaf stack: D2 = Kinv_leaf * D (all columns), then swap
+    // ---- 2. leaf stack: D2 = Kinv_leaf * D (all columns), then copy back
     if (W > 0) {
-        HODLR_TRY(zero<T>(D2, ldn * W, s));
+        rec.zero_(D2, ldn * W);
         std::vector<GemmDesc<T>> gd(nleaf);
         for (int i = 0; i < nleaf; ++i) {
             int64_t r0, m;
@@ -358,10 +521,8 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
             gd[i] = GemmDesc<T>{Kinv + (size_t)i * bmax * bmax, D + r0, D2 + r0, bmax, ldn, ldn,
                                 (int)m, (int)W, (int)m};
         }
-        void *dd = sc.take(gd.size() * sizeof(GemmDesc<T>));
-        if (!dd) return HODLR_OUT_OF_MEMORY;
-        HODLR_TRY(run_gemm<T>(c, gd, 0, T(1), s, dd));
-        HODLR_TRY_CUDA(cudaMemcpyAsync(D, D2, (size_t)ldn * W * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        rec.gemm(gd, 0, T(1));
+        rec.copy(D, D2, ldn * W);
     }
     // ---- 3. levels, bottom-up
     for (int l = L - 1; l >= 0; --l) {
@@ -385,7 +546,7 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
         T *M = reinterpret_cast<T *>(lcarve((size_t)nn * rp * rp * sizeof(T)));
         T *gw = reinterpret_cast<T *>(lcarve((size_t)nn * 2 * rp * rp * sizeof(T)));
         // (a) Y_child = V(child, blk c)^T D(child, 0:Wc)
-        HODLR_TRY(zero<T>(Y, (int64_t)nch * rp * Wc, s));
+        rec.zero_(Y, (int64_t)nch * rp * Wc);
         {
             std::vector<GemmDesc<T>> gd(nch);
             for (int i = 0; i < nch; ++i) {
@@ -394,24 +555,18 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
                 gd[i] = GemmDesc<T>{V + coffc * ldn + r0, D + r0, Y + (size_t)i * rp * Wc, ldn, ldn,
                                     rp, rp, (int)Wc, (int)m};
             }
-            void *dd = sc.take(gd.size() * sizeof(GemmDesc<T>));
-            if (!dd) return HODLR_OUT_OF_MEMORY;
-            HODLR_TRY(run_gemm<T>(c, gd, 1, T(1), s, dd));
+            rec.gemm(gd, 1, T(1));
         }
         // (b) M = I - P Q per node
         {
-            dim3 grid(std::max(1, std::min(64, (rp * rp + 255) / 256)), nn);
-            set_identity_kernel<T><<<grid, 256, 0, s>>>(M, rp, rp, nn, (int64_t)rp * rp);
-            HODLR_TRY_CUDA(cudaGetLastError());
+            rec.identity(M, rp, rp, nn, (int64_t)rp * rp);
             std::vector<GemmDesc<T>> gd(nn);
             for (int i = 0; i < nn; ++i) {
                 const T *P = Y + (size_t)(2 * i) * rp * Wc + coffc * rp;
                 const T *Q = Y + (size_t)(2 * i + 1) * rp * Wc + coffc * rp;
                 gd[i] = GemmDesc<T>{P, Q, M + (size_t)i * rp * rp, rp, rp, rp, rp, rp, rp};
             }
-            void *dd = sc.take(gd.size() * sizeof(GemmDesc<T>));
-            if (!dd) return HODLR_OUT_OF_MEMORY;
-            HODLR_TRY(run_gemm<T>(c, gd, 0, T(-1), s, dd));
+            rec.gemm(gd, 0, T(-1));
         }
         // (c) M^-1 into the top-left block of S^-1
         {
@@ -419,24 +574,17 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
             for (int i = 0; i < nn; ++i)
                 gd[i] = GJDesc<T>{nullptr, 0, M + (size_t)i * rp * rp, rp, gw + (size_t)i * 2 * rp * rp,
                                   Sinv + (size_t)i * s2 * s2, s2, rp};
-            void *dd = sc.take(gd.size() * sizeof(GJDesc<T>));
-            if (!dd) return HODLR_OUT_OF_MEMORY;
-            HODLR_TRY(run_gj<T>(c, gd, s, dd));
+            rec.gj(gd);
         }
         // (d) the other three blocks of S^-1
         {
             // TR = -M^-1 P ; BL = -Q M^-1 (zeroed first), BR = I - Q TR
             for (int i = 0; i < nn; ++i) {
                 T *S = Sinv + (size_t)i * s2 * s2;
-                // zero TR and BL, identity BR: handled by kernels below via cudaMemset2D
-                HODLR_TRY_CUDA(cudaMemset2DAsync(S + rp * s2, s2 * sizeof(T), 0, rp * sizeof(T), rp, s));
-                HODLR_TRY_CUDA(cudaMemset2DAsync(S + rp, s2 * sizeof(T), 0, rp * sizeof(T), rp, s));
+                rec.memset2d(S + rp * s2, s2, rp, rp);
+                rec.memset2d(S + rp, s2, rp, rp);
             }
-            {
-                dim3 grid(std::max(1, std::min(64, (rp * rp + 255) / 256)), nn);
-                set_identity_kernel<T><<<grid, 256, 0, s>>>(Sinv + rp + rp * s2, s2, rp, nn, s2 * s2);
-                HODLR_TRY_CUDA(cudaGetLastError());
-            }
+            rec.identity(Sinv + rp + rp * s2, s2, rp, nn, s2 * s2);
             std::vector<GemmDesc<T>> g1(nn), g2(nn), g3(nn);
             for (int i = 0; i < nn; ++i) {
                 T *S = Sinv + (size_t)i * s2 * s2;
@@ -446,17 +594,13 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
                 g2[i] = GemmDesc<T>{Q, S, S + rp, rp, s2, s2, rp, rp, rp};              // BL -= Q Minv
                 g3[i] = GemmDesc<T>{Q, S + rp * s2, S + rp + rp * s2, rp, s2, s2, rp, rp, rp};  // BR -= Q TR
             }
-            void *d1 = sc.take(nn * sizeof(GemmDesc<T>));
-            void *d2 = sc.take(nn * sizeof(GemmDesc<T>));
-            void *d3 = sc.take(nn * sizeof(GemmDesc<T>));
-            if (!d1 || !d2 || !d3) return HODLR_OUT_OF_MEMORY;
-            HODLR_TRY(run_gemm<T>(c, g1, 0, T(-1), s, d1));
-            HODLR_TRY(run_gemm<T>(c, g2, 0, T(-1), s, d2));
-            HODLR_TRY(run_gemm<T>(c, g3, 0, T(-1), s, d3));
+            rec.gemm(g1, 0, T(-1));
+            rec.gemm(g2, 0, T(-1));
+            rec.gemm(g3, 0, T(-1));
         }
         // (e) update the ancestor columns (levels 1..l) for l >= 1
         if (l >= 1 && coffc > 0) {
-            HODLR_TRY(zero<T>(Yv, (int64_t)nn * s2 * coffc, s));
+            rec.zero_(Yv, (int64_t)nn * s2 * coffc);
             std::vector<GemmDesc<T>> ga(2 * nn);
             for (int i = 0; i < nn; ++i) {
                 T *S = Sinv + (size_t)i * s2 * s2;
@@ -472,11 +616,8 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
                 gA[i] = ga[2 * i];
                 gB[i] = ga[2 * i + 1];
             }
-            void *da = sc.take(nn * sizeof(GemmDesc<T>));
-            void *db = sc.take(nn * sizeof(GemmDesc<T>));
-            if (!da || !db) return HODLR_OUT_OF_MEMORY;
-            HODLR_TRY(run_gemm<T>(c, gA, 0, T(1), s, da));
-            HODLR_TRY(run_gemm<T>(c, gB, 0, T(1), s, db));
+            rec.gemm(gA, 0, T(1));
+            rec.gemm(gB, 0, T(1));
             std::vector<GemmDesc<T>> gu(nch);
             for (int i = 0; i < nn; ++i) {
                 int64_t ra, ma, rb, mb;
@@ -489,11 +630,18 @@ hodlr_status factor_typed(hodlr_t *h, cudaStream_t s) {
                 gu[2 * i + 1] = GemmDesc<T>{D + coffc * ldn + rb, yv, D + rb, ldn, s2, ldn,
                                             (int)mb, (int)coffc, rp};
             }
-            void *du = sc.take(gu.size() * sizeof(GemmDesc<T>));
-            if (!du) return HODLR_OUT_OF_MEMORY;
-            HODLR_TRY(run_gemm<T>(c, gu, 0, T(-1), s, du));
+            rec.gemm(gu, 0, T(-1));
         }
     }
+    // one upload of every descriptor (the caller synchronises before factor runs)
+    Pl->dbytes = std::max<size_t>(Pl->blob.size(), 256);
+    Pl->dblob = reinterpret_cast<char *>(dalloc(c, Pl->dbytes, s));
+    if (!Pl->dblob) {
+        set_error("factor plan: out of device memory for descriptors");
+        return HODLR_OUT_OF_MEMORY;
+    }
+    if (!Pl->blob.empty())
+        HODLR_TRY_CUDA(cudaMemcpyAsync(Pl->dblob, Pl->blob.data(), Pl->blob.size(), cudaMemcpyHostToDevice, s));
     return HODLR_OK;
 }
 
@@ -524,9 +672,26 @@ template hodlr_status gemm_batched<float>(hodlr_ctx *, const GemmDesc<float> *, 
 template hodlr_status gemm_batched<double>(hodlr_ctx *, const GemmDesc<double> *, int, int, int, int, int,
                                            double, cudaStream_t);
 
+hodlr_status plan_factor(hodlr_t *h, cudaStream_t s) {
+    if (h->plan) return HODLR_OK;
+    FactorPlan *P = new FactorPlan();
+    hodlr_status st = (h->prec == HODLR_FP64) ? plan_typed<double>(h, P, s) : plan_typed<float>(h, P, s);
+    h->plan = P;   // owned even on failure, released by free_plan
+    return st;
+}
+
+void free_plan(hodlr_t *h, cudaStream_t s) {
+    if (!h->plan) return;
+    if (h->plan->work) dfree(h->ctx, h->plan->work, h->plan->work_bytes, s);
+    if (h->plan->dblob) dfree(h->ctx, h->plan->dblob, h->plan->dbytes, s);
+    delete h->plan;
+    h->plan = nullptr;
+}
+
 hodlr_status factor_impl(hodlr_t *h, cudaStream_t s) {
-    if (h->prec == HODLR_FP64) return factor_typed<double>(h, s);
-    return factor_typed<float>(h, s);
+    HODLR_TRY(plan_factor(h, s));
+    for (auto &op : h->plan->ops) HODLR_TRY(op(s));
+    return HODLR_OK;
 }
 
 }  // namespace hodlr

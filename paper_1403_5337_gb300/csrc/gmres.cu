@@ -69,8 +69,9 @@ constexpr int MV_THREADS = 256;
 constexpr int MV_WARPS = MV_THREADS / 32;
 constexpr int MV_RPW = 2;            // rows per warp
 constexpr int MV_ROWS = MV_WARPS * MV_RPW;
-constexpr int MV_KC = 1024;          // columns per staged chunk
+constexpr int MV_KC = 1024;          // columns per CTA (one column split)
 constexpr int MV_S = 4;              // right-hand sides per pass
+constexpr int MV_U = 4;              // 16-byte loads in flight per lane and row
 
 __global__ void split_vec_kernel(const double *__restrict__ Z, int64_t ldz, int64_t n, int s,
                                  float2 *__restrict__ zs) {
@@ -84,53 +85,100 @@ __global__ void split_vec_kernel(const double *__restrict__ Z, int64_t ldz, int6
     }
 }
 
-// W(:, r0:r0+sr) = A Z(:, r0:r0+sr);  zs = split Z (n x s, column-major float2).
+// W(:, r0:r0+sr) += A(:, k0:k0+KC) Z(k0:k0+KC, r0:r0+sr) for the column split
+// k0 = blockIdx.y * KC; zs = split Z (n x s, column-major float2); W zeroed
+// beforehand, the splits are combined with FP64 atomics.  Each lane sums at
+// most 32 terms per row in the float pair before it is converted to FP64, so
+// the compensation term's own FP32 rounding never accumulates further.
+// VEC: A rows are 16-byte aligned (even lda, aligned base) -> double2 loads.
+template <bool VEC>
 __global__ void __launch_bounds__(MV_THREADS)
     df_matvec_kernel(const double *__restrict__ A, int64_t n, int64_t lda, const float2 *__restrict__ zs,
                      int s, int r0, double *__restrict__ W, int64_t ldw, int *status) {
-    __shared__ float2 zsm[MV_S][MV_KC];
+    __shared__ __align__(16) float2 zsm[MV_S][MV_KC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * MV_ROWS + warp * MV_RPW;
+    const int64_t k0 = (int64_t)blockIdx.y * MV_KC;
+    const int kc = (n - k0 < (int64_t)MV_KC) ? (int)(n - k0) : MV_KC;
     const int sr = min(MV_S, s - r0);
-    // The float pair accumulates at most 32 terms per lane (one staged chunk);
-    // it is then folded into an FP64 accumulator, so the compensation term's own
-    // FP32 rounding never accumulates over more than 32 terms.
+    for (int e = threadIdx.x; e < MV_S * MV_KC; e += MV_THREADS) {
+        const int q = e / MV_KC, kk = e % MV_KC;
+        zsm[q][kk] = (q < sr && kk < kc) ? zs[(int64_t)(r0 + q) * n + k0 + kk] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int64_t row0 = (int64_t)blockIdx.x * MV_ROWS + warp * MV_RPW;
     DF acc[MV_RPW][MV_S];
-    double dacc[MV_RPW][MV_S];
 #pragma unroll
     for (int a = 0; a < MV_RPW; ++a)
 #pragma unroll
-        for (int q = 0; q < MV_S; ++q) {
-            acc[a][q] = DF{0.f, 0.f};
-            dacc[a][q] = 0.0;
-        }
+        for (int q = 0; q < MV_S; ++q) acc[a][q] = DF{0.f, 0.f};
     int bad = 0;
-    for (int64_t k0 = 0; k0 < n; k0 += MV_KC) {
-        const int kc = (n - k0 < (int64_t)MV_KC) ? (int)(n - k0) : MV_KC;
-        __syncthreads();
-        for (int e = threadIdx.x; e < MV_S * MV_KC; e += MV_THREADS) {
-            const int q = e / MV_KC, kk = e % MV_KC;
-            zsm[q][kk] = (q < sr && kk < kc) ? zs[(int64_t)(r0 + q) * n + k0 + kk] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
+    if (VEC) {
+        const int np = kc >> 1;   // column pairs
+        for (int p0 = lane; p0 < np; p0 += 32 * MV_U) {
+            double2 av[MV_RPW][MV_U];
 #pragma unroll
-        for (int a = 0; a < MV_RPW; ++a) {
-            const int64_t row = row0 + a;
-            if (row >= n) continue;
-            const double *ar = A + row * lda + k0;
-            for (int kk = lane; kk < kc; kk += 32) {
-                float ah, al;
-                split_entry(__ldg(ar + kk), ah, al, bad);
+            for (int u = 0; u < MV_U; ++u) {
+                const int p = p0 + 32 * u;
 #pragma unroll
-                for (int q = 0; q < MV_S; ++q) {
-                    const float2 z = zsm[q][kk];
-                    df_acc(acc[a][q], ah, al, z.x, z.y);
+                for (int a = 0; a < MV_RPW; ++a) {
+                    const int64_t row = row0 + a;
+                    av[a][u] = (p < np && row < n)
+                                   ? __ldg(reinterpret_cast<const double2 *>(A + row * lda + k0) + p)
+                                   : make_double2(0.0, 0.0);
                 }
             }
 #pragma unroll
-            for (int q = 0; q < MV_S; ++q) {
-                dacc[a][q] += (double)acc[a][q].s + (double)acc[a][q].c;
-                acc[a][q] = DF{0.f, 0.f};
+            for (int u = 0; u < MV_U; ++u) {
+                const int p = p0 + 32 * u;
+                if (p >= np) break;
+#pragma unroll
+                for (int a = 0; a < MV_RPW; ++a) {
+                    float h0, l0, h1, l1;
+                    split_entry(av[a][u].x, h0, l0, bad);
+                    split_entry(av[a][u].y, h1, l1, bad);
+#pragma unroll
+                    for (int q = 0; q < MV_S; ++q) {
+                        const float4 z = reinterpret_cast<const float4 *>(zsm[q])[p];
+                        df_acc(acc[a][q], h0, l0, z.x, z.y);
+                        df_acc(acc[a][q], h1, l1, z.z, z.w);
+                    }
+                }
+            }
+        }
+        if ((kc & 1) && lane == 0) {   // odd tail column
+            const int kk = kc - 1;
+#pragma unroll
+            for (int a = 0; a < MV_RPW; ++a) {
+                const int64_t row = row0 + a;
+                if (row >= n) continue;
+                float h0, l0;
+                split_entry(A[row * lda + k0 + kk], h0, l0, bad);
+#pragma unroll
+                for (int q = 0; q < MV_S; ++q) df_acc(acc[a][q], h0, l0, zsm[q][kk].x, zsm[q][kk].y);
+            }
+        }
+    } else {
+        for (int kk0 = lane; kk0 < kc; kk0 += 32 * MV_U) {
+            double av[MV_RPW][MV_U];
+#pragma unroll
+            for (int u = 0; u < MV_U; ++u)
+#pragma unroll
+                for (int a = 0; a < MV_RPW; ++a) {
+                    const int kk = kk0 + 32 * u;
+                    const int64_t row = row0 + a;
+                    av[a][u] = (kk < kc && row < n) ? __ldg(A + row * lda + k0 + kk) : 0.0;
+                }
+#pragma unroll
+            for (int u = 0; u < MV_U; ++u) {
+                const int kk = kk0 + 32 * u;
+                if (kk >= kc) break;
+#pragma unroll
+                for (int a = 0; a < MV_RPW; ++a) {
+                    float h0, l0;
+                    split_entry(av[a][u], h0, l0, bad);
+#pragma unroll
+                    for (int q = 0; q < MV_S; ++q) df_acc(acc[a][q], h0, l0, zsm[q][kk].x, zsm[q][kk].y);
+                }
             }
         }
     }
@@ -140,10 +188,10 @@ __global__ void __launch_bounds__(MV_THREADS)
         const int64_t row = row0 + a;
 #pragma unroll
         for (int q = 0; q < MV_S; ++q) {
-            double v = dacc[a][q];
+            double v = (double)acc[a][q].s + (double)acc[a][q].c;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && row < n && q < sr) W[row + (int64_t)(r0 + q) * ldw] = v;
+            if (lane == 0 && row < n && q < sr) atomicAdd(&W[row + (int64_t)(r0 + q) * ldw], v);
         }
     }
 }
@@ -295,13 +343,13 @@ __global__ void residual_kernel(const double *__restrict__ B, int64_t ldb, doubl
 __global__ void start_cycle_kernel(GState st, int m, int s, const double *__restrict__ R, int64_t ldr, int64_t n,
                                    const double *__restrict__ nrm2, double *__restrict__ Vk, int64_t vstride, double tol,
                                    int max_iter, int first) {
+    // Every block decides activity from values no block of this launch writes:
+    // iters was zeroed before the first cycle, and bnorm is only written (by
+    // block 0) on the first cycle, when every block uses beta instead.
     const int r = blockIdx.y;
     if (r >= s) return;
     const double beta = sqrt(nrm2[r]);
-    if (first && blockIdx.x == 0 && threadIdx.x == 0) {
-        st.bnorm[r] = beta;
-        st.iters[r] = 0;
-    }
+    if (first && blockIdx.x == 0 && threadIdx.x == 0) st.bnorm[r] = beta;
     const double bn = first ? beta : st.bnorm[r];
     const int act = (bn > 0.0) && (beta > tol * bn) && (st.iters[r] < max_iter);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -340,10 +388,17 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
     if (!zs) return HODLR_OUT_OF_MEMORY;
     int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
     split_vec_kernel<<<blocks, 256, 0, st>>>(Z, ldz, n, s, zs);
-    const int grid = (int)((n + MV_ROWS - 1) / MV_ROWS);
-    for (int r0 = 0; r0 < s; r0 += MV_S)
-        df_matvec_kernel<<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemset2DAsync(W, ldw * sizeof(double), 0, n * sizeof(double), s, st);
+    const dim3 grid((unsigned)((n + MV_ROWS - 1) / MV_ROWS), (unsigned)((n + MV_KC - 1) / MV_KC));
+    const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    for (int r0 = 0; r0 < s && e == cudaSuccess; r0 += MV_S) {
+        if (vec)
+            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
+        else
+            df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (!work) dfree(c, zs, (size_t)n * s * sizeof(float2), st);
     if (e != cudaSuccess) {
         set_error("matvec launch: %s", cudaGetErrorString(e));
@@ -436,10 +491,11 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     HODLR_TRY_CUDA(cudaEventRecord(e0, st));
 
     const dim3 vgrid((unsigned)std::min<int64_t>((n + KT - 1) / KT, 1024), s);
-    const int64_t gchunk = 2048;
+    const int64_t gchunk = 256;
     const dim3 ggrid((unsigned)((n + gchunk - 1) / gchunk), s);
-    // x0 = 0
+    // x0 = 0; iteration counters and per-rhs state start at zero
     HODLR_TRY_CUDA(cudaMemset2DAsync(X, ldx * 8, 0, n * 8, s, st));
+    HODLR_TRY_CUDA(cudaMemsetAsync(ibuf, 0, (size_t)(4 * s + 4) * sizeof(int), st));
     // R = B (first cycle): Wv = B
     HODLR_TRY_CUDA(cudaMemcpy2DAsync(Wv, n * 8, B, ldb * 8, n * 8, s, cudaMemcpyDeviceToDevice, st));
     HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, s * 8, st));

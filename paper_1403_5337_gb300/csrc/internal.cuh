@@ -43,9 +43,12 @@ hodlr_status status_from_word(int w);
 // ------------------------------------------------------------------ context
 }  // namespace hodlr
 
+#define HODLR_SIDE_STREAMS 8
+
 struct hodlr_ctx {
     int device = 0;
     int num_sms = 0;
+    cudaStream_t side[HODLR_SIDE_STREAMS] = {};   // forked from the caller's stream per level
     hodlr_alloc_fn alloc = nullptr;
     hodlr_free_fn free_fn = nullptr;
     void *user = nullptr;
@@ -82,6 +85,8 @@ struct Level {
     double rank_mean = 0.0;
 };
 
+struct FactorPlan;   // factor.cu
+
 }  // namespace hodlr
 
 struct hodlr_s {
@@ -112,9 +117,11 @@ struct hodlr_s {
     bool factored = false;
     double ms_compress = 0, ms_factor = 0;
     std::vector<hodlr::DevBuf> owned;
-    // scratch reused by solve / factor
+    // scratch of the apply
     void *work = nullptr;
     size_t work_bytes = 0;
+    // the recorded factorisation (workspace, descriptors, launches)
+    hodlr::FactorPlan *plan = nullptr;
 };
 
 namespace hodlr {
@@ -141,6 +148,12 @@ struct AcaBlockDesc {
 hodlr_status launch_aca(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
                         const AcaBlockDesc *d_blocks, int nblocks, int64_t max_m, double tol,
                         cudaStream_t s);
+// One thread-block cluster per block, one launch per level on the context's side
+// streams (forked from and joined back into s).  level_first: first block of each
+// level in d_blocks (size nlev + 1); level_maxdim: largest block side per level.
+hodlr_status launch_aca_levels(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
+                               const AcaBlockDesc *d_blocks, const std::vector<int> &level_first,
+                               const std::vector<int64_t> &level_maxdim, double tol, cudaStream_t s);
 
 struct BdlrHost;   // defined in bdlr.cu
 hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t s,
@@ -160,6 +173,10 @@ hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T> *d_desc, int nbatch, i
                           int maxN, int maxK, int transA, T alpha, cudaStream_t s);
 
 hodlr_status factor_impl(hodlr_t *h, cudaStream_t s);
+// Record the factorisation's launches and upload its descriptors (stream-ordered
+// on s; the caller synchronises before the first factor_impl).
+hodlr_status plan_factor(hodlr_t *h, cudaStream_t s);
+void free_plan(hodlr_t *h, cudaStream_t s);
 hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s);
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s_rhs,
                          const double *Z, int64_t ldz, double *W, int64_t ldw, cudaStream_t s,

@@ -44,7 +44,7 @@ def front576():
 
 @pytest.fixture(scope="module")
 def front4096():
-    F = fg.make_front(64, 64, 32, 32, "lognormal", 0.5, leaf=128, seed=0, device="cuda")
+    F = fg.make_front(64, 64, 32, 32, "lognormal", 0.5, leaf=128, seed=0, device="cuda", cache=True)
     F.A = F.A.cpu().numpy()
     return F
 
@@ -203,6 +203,28 @@ def test_gmres_matches_oracle(H, ctx, front576, prec, itol):
         assert true <= 1.5e-12
         assert abs(int(info.iters[r]) - ref.iters) <= itol
         assert np.linalg.norm(x[r] - ref.x) / np.linalg.norm(ref.x) < 1e-9
+    h.close()
+
+
+def test_gmres_multi_rhs_on_dirty_memory(H, ctx, front576):
+    """Library buffers come from torch's caching allocator: fill its cache with
+    garbage first, so that any read of a not-yet-written buffer shows."""
+    F = front576
+    A = _dev(F.A)
+    h = H.hodlr_build(ctx, A, 64, 1e-6, "aca", precision="fp32")
+    H.hodlr_factor(h)
+    b = fg.rhs(F.n, 6, seed=3)
+    B = _dev(b.T)
+    iters = None
+    for trial in range(6):
+        junk = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+        junk.fill_(0x7F if trial % 2 else 0xFF)
+        del junk
+        X, info = H.gmres_solve(ctx, A, B, h, tol=1e-12, max_iter=100)
+        assert info.converged and np.all(info.true_relres <= 1e-12), (trial, info.iters)
+        if iters is None:
+            iters = info.iters.copy()
+        assert np.abs(info.iters - iters).max() <= 1
     h.close()
 
 
