@@ -191,6 +191,28 @@ hodlr_status gmres_solve(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const dou
 hodlr_status hodlr_matvec(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *Z,
                           int64_t ldz, double *W, int64_t ldw, hodlr_stream stream);
 
+/* W <- A Z like hodlr_matvec, but without allocating any device memory.
+ *
+ * There is no counterpart of this call in the paper.  It exists for callers
+ * that may not allocate: an application whose memory manager has already
+ * claimed all device memory and forbids other allocations, a loop under a
+ * fixed memory budget that must not touch the allocator while it runs, or code
+ * that cannot pass a context (hodlr_ctx_create allocates).  Such callers pass
+ * the inputs and outputs only; the scratch this product needs (the FP32 split
+ * of Z) lives in a fixed array inside the library, n * s <= 524288 entries
+ * (4 MiB), which every GPU that loads the library holds until the process
+ * exits.  Larger sizes return HODLR_RANGE without launching anything.
+ *
+ * A: device, row-major FP64; Z, W: device, n x s column-major (ld >= n).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (different streams or
+ * host threads at the same time) race and give wrong results.  The call
+ * synchronises `stream` (it reads back the non-finite-input flag) and never
+ * calls cudaMalloc, cudaFree or an allocating library routine. */
+hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const double *Z, int64_t ldz,
+                                  double *W, int64_t ldw, hodlr_stream stream);
+
 /* Preconditioner quality ||(I - P^-1 A) Omega||_F / ||Omega||_F for a caller
  * probe block Omega (device, n x k column-major, ld >= n); *out is host.  A is
  * the matrix the HODLR form was built from.  Synchronises `stream`. */

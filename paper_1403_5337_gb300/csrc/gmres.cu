@@ -16,6 +16,7 @@
 // about 2^-48, comparable to an FP64 dot product's accumulated rounding.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -407,9 +408,98 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
     return HODLR_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free matvec
+// Scratch of hodlr_matvec_noalloc: the FP32 (hi, lo) split of Z lives in a
+// file-scope device array instead of memory obtained from an allocator.  The
+// array exists on every GPU that loads this library, for the life of the
+// process.  Its device address is looked up once per device (host code may not
+// use the symbol itself: on the host it only names a stand-in object).
+namespace {
+
+constexpr int64_t NOALLOC_MAX_ELEMS = int64_t(1) << 19;   // n * s <= 524288 (4 MiB of float2)
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) float2 g_noalloc_split[NOALLOC_MAX_ELEMS];
+static __device__ __align__(256) int g_noalloc_status[64];
+
+struct NoallocSlot {
+    float2 *split = nullptr;
+    int *status = nullptr;
+    bool ready = false;
+};
+NoallocSlot g_noalloc_slots[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
 }  // namespace hodlr
 
 using namespace hodlr;
+
+// W = A Z without allocating device memory: the same double-float kernels as
+// hodlr_matvec, with the split of Z in the static array above.  Sizes with
+// n * s above NOALLOC_MAX_ELEMS are refused with HODLR_RANGE.  The first call on
+// a device resolves the array's device address (cudaGetSymbolAddress) with that
+// device current.  Concurrent calls share the array and must not overlap on the
+// GPU.  The call synchronises `stream` to report non-finite entries of A.
+extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const double *Z, int64_t ldz, double *W,
+                                             int64_t ldw, hodlr_stream stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!A || !A->data || A->n <= 0 || A->ld < A->n || !Z || !W || s <= 0 || ldz < A->n || ldw < A->n) {
+        set_error("hodlr_matvec_noalloc: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    const int64_t n = A->n;
+    if (n * s > NOALLOC_MAX_ELEMS) {
+        set_error("hodlr_matvec_noalloc: n * s = %lld exceeds the static scratch limit %lld",
+                  (long long)(n * s), (long long)NOALLOC_MAX_ELEMS);
+        return HODLR_RANGE;
+    }
+    int dev = 0;
+    HODLR_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_error("hodlr_matvec_noalloc: device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+        return HODLR_RANGE;
+    }
+    NoallocSlot slot;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        NoallocSlot &sl = g_noalloc_slots[dev];
+        if (!sl.ready) {
+            void *p = nullptr, *q = nullptr;
+            HODLR_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_split));
+            HODLR_TRY_CUDA(cudaGetSymbolAddress(&q, g_noalloc_status));
+            sl.split = reinterpret_cast<float2 *>(p);
+            sl.status = reinterpret_cast<int *>(q);
+            sl.ready = true;
+        }
+        slot = sl;
+    }
+    // the array keeps the previous call's contents: the status word and W start
+    // at zero, the split is rewritten in full before it is read
+    HODLR_TRY_CUDA(cudaMemsetAsync(slot.status, 0, sizeof(int), st));
+    HODLR_TRY_CUDA(cudaMemset2DAsync(W, ldw * sizeof(double), 0, n * sizeof(double), s, st));
+    const int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
+    split_vec_kernel<<<blocks, 256, 0, st>>>(Z, ldz, n, s, slot.split);
+    const dim3 grid((unsigned)((n + MV_ROWS - 1) / MV_ROWS), (unsigned)((n + MV_KC - 1) / MV_KC));
+    const bool vec = (A->ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(A->data) & 15) == 0);
+    for (int r0 = 0; r0 < s; r0 += MV_S) {
+        if (vec)
+            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw, slot.status);
+        else
+            df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw,
+                                                                 slot.status);
+    }
+    HODLR_TRY_CUDA(cudaGetLastError());
+    int hstat = 0;
+    HODLR_TRY_CUDA(cudaMemcpyAsync(&hstat, slot.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+    if (hstat) {
+        set_error("hodlr_matvec_noalloc: non-finite or out-of-range entry in A");
+        return status_from_word(hstat);
+    }
+    return HODLR_OK;
+}
 
 namespace {
 

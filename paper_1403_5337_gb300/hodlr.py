@@ -73,7 +73,8 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 # every exported symbol of include/hodlr.h
 SYMBOLS = ["hodlr_ctx_create", "hodlr_ctx_destroy", "hodlr_opts_default", "hodlr_build", "hodlr_factor",
-           "hodlr_solve", "gmres_solve", "hodlr_matvec", "hodlr_precond_error", "hodlr_stats_get",
+           "hodlr_solve", "gmres_solve", "hodlr_matvec", "hodlr_matvec_noalloc", "hodlr_precond_error",
+           "hodlr_stats_get",
            "hodlr_export_level", "hodlr_export_core", "hodlr_destroy", "hodlr_status_string",
            "hodlr_last_error"]
 
@@ -119,6 +120,7 @@ def load_library(path: str = _LIBPATH):
     lib.hodlr_solve.argtypes = [vp, ci, vp, i64, vp]
     lib.gmres_solve.argtypes = [vp, C.POINTER(_Matrix), ci, vp, i64, vp, i64, vp, cd, ci, ci, C.POINTER(_Info), vp]
     lib.hodlr_matvec.argtypes = [vp, C.POINTER(_Matrix), ci, vp, i64, vp, i64, vp]
+    lib.hodlr_matvec_noalloc.argtypes = [C.POINTER(_Matrix), ci, vp, i64, vp, i64, vp]
     lib.hodlr_precond_error.argtypes = [vp, ci, vp, i64, C.POINTER(cd), vp]
     lib.hodlr_stats_get.argtypes = [vp, C.POINTER(_Stats)]
     lib.hodlr_export_level.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp]
@@ -342,6 +344,21 @@ def hodlr_matvec(ctx: Context, A: torch.Tensor, Z: torch.Tensor, symmetric: bool
     W = torch.empty_like(Z, memory_format=torch.contiguous_format)
     _check(_lib.hodlr_matvec(ctx.handle, C.byref(mat), s, C.c_void_p(ptr), ld, C.c_void_p(W.data_ptr()),
                              A.shape[0], _stream(stream)))
+    return W
+
+
+def hodlr_matvec_noalloc(A: torch.Tensor, Z: torch.Tensor, W: torch.Tensor, symmetric: bool = True,
+                         stream=None) -> torch.Tensor:
+    """W = A Z into a caller-provided W, allocating nothing on the device (the
+    library's fixed scratch holds n * s <= 524288 entries); Z, W are (s, n)."""
+    lib = load_library()
+    mat = _mat(A, symmetric)
+    ptr, s, ld = _rhs(Z, A.shape[0])
+    wptr, s2, ldw = _rhs(W, A.shape[0])
+    if s2 != s:
+        raise ValueError("W and Z differ in the number of columns")
+    _check(lib.hodlr_matvec_noalloc(C.byref(mat), s, C.c_void_p(ptr), ld, C.c_void_p(wptr), ldw,
+                                    _stream(stream)))
     return W
 
 
