@@ -279,3 +279,21 @@ hodlr_status solve_impl(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStr
 }
 
 }  // namespace hodlr
+
+namespace hodlr {
+
+// Allocate the apply's workspace for s right-hand sides ahead of time (the
+// same sizing as solve_typed), so that later solves allocate nothing -- e.g.
+// while they are being recorded into a graph.
+hodlr_status solve_prepare(const hodlr_t *h, int s, cudaStream_t st) {
+    const size_t es = elem_size(h->prec);
+    int rpmax = 0;
+    for (int c = 1; c <= h->L; ++c) rpmax = std::max(rpmax, h->lv[c].rp);
+    const size_t xt_bytes = (size_t)h->ldn * s * es;
+    const size_t w_elems = (size_t)(1 << h->L) * std::max(rpmax, 1) * s;
+    const size_t need = xt_bytes + 2 * w_elems * es + 1024;
+    if (h->work_bytes < need) return ensure_work(const_cast<hodlr_t *>(h), need, st);
+    return HODLR_OK;
+}
+
+}  // namespace hodlr

@@ -344,6 +344,183 @@ __global__ void __launch_bounds__(GJS_THREADS) gj_inverse_smem_kernel(const GJDe
 
 constexpr size_t GJS_SMEM_MAX = 200 * 1024;
 
+// Gauss-Jordan inversion with the matrix held in registers: 512 threads as a
+// 16 x 32 grid, thread (ty, tx) owns rows ty + 16 p (p < MR) and columns
+// tx + 32 q (q < MC).  Per step only pivot column k and pivot row k pass
+// through shared memory (the row swap too), so each step costs MR + MC shared
+// loads and MR * MC FMAs per thread.  Same pivot rule and the same in-place
+// update as gj_inverse_smem_kernel.  Register slots are selected with unrolled
+// predicated loops, never by a run-time index.
+constexpr int GJR_TY = 16, GJR_TX = 32, GJR_THREADS = GJR_TY * GJR_TX;
+
+template <typename T, int MR, int MC>
+__global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJDesc<T> *__restrict__ descs,
+                                                                       int *status) {
+    const GJDesc<T> g = descs[blockIdx.x];
+    const int b = g.b;
+    if (b <= 0) return;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    __shared__ T colk[MR * GJR_TY];
+    __shared__ T rowk[MC * GJR_TX];
+    __shared__ T rowa[MC * GJR_TX];
+    __shared__ T rowb[MC * GJR_TX];
+    __shared__ int orig[MR * GJR_TY];
+    __shared__ int s_p, s_fail;
+    T a[MR][MC];
+#pragma unroll
+    for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int i = ty + GJR_TY * p, j = tx + GJR_TX * q;
+            T v = T(0);
+            if (i < b && j < b)
+                v = g.srcA ? dev::from_double<T>(g.srcA[(int64_t)i * g.lda + j]) : g.srcM[i + (int64_t)j * g.ldm];
+            a[p][q] = v;
+        }
+    for (int i = tid; i < b; i += GJR_THREADS) orig[i] = i;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int k = 0; k < b; ++k) {
+        const int kq = k / GJR_TX, kx = k % GJR_TX;
+        // 1. column k to shared memory
+        if (tx == kx) {
+#pragma unroll
+            for (int q = 0; q < MC; ++q)
+                if (q == kq) {
+#pragma unroll
+                    for (int p = 0; p < MR; ++p) {
+                        const int i = ty + GJR_TY * p;
+                        if (i < b) colk[i] = a[p][q];
+                    }
+                }
+        }
+        __syncthreads();
+        // 2. pivot row: argmax_{i >= k} |colk[i]|, lowest row on ties
+        if (ty == 0) {
+            T bv = T(-1);
+            int bi = INT_MAX;
+            for (int i = k + tx; i < b; i += 32) {
+                const T v = fabs(colk[i]);
+                if (v > bv) {
+                    bv = v;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (tx == 0) {
+                s_p = bi;
+                if (!(bv > T(0))) s_fail = 1;
+                else if (bi != k) {
+                    const int t = orig[k];
+                    orig[k] = orig[bi];
+                    orig[bi] = t;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const int pr = s_p;
+        // 3. swap rows k and pr through shared memory
+        if (pr != k) {
+            const int ky = k % GJR_TY, kp = k / GJR_TY, py = pr % GJR_TY, pp = pr / GJR_TY;
+            if (ty == ky)
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == kp)
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) rowa[tx + GJR_TX * q] = a[p][q];
+            if (ty == py)
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == pp)
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) rowb[tx + GJR_TX * q] = a[p][q];
+            __syncthreads();
+            if (ty == ky)
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == kp)
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) a[p][q] = rowb[tx + GJR_TX * q];
+            if (ty == py)
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == pp)
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) a[p][q] = rowa[tx + GJR_TX * q];
+            if (tid == 0) {
+                const T t = colk[k];
+                colk[k] = colk[pr];
+                colk[pr] = t;
+            }
+        }
+        __syncthreads();
+        // 4. scaled pivot row to shared memory
+        const T d = T(1) / colk[k];
+        {
+            const int ky = k % GJR_TY, kp = k / GJR_TY;
+            if (ty == ky)
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == kp)
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) {
+                            const int j = tx + GJR_TX * q;
+                            rowk[j] = (j == k) ? d : a[p][q] * d;
+                        }
+        }
+        __syncthreads();
+        // 5. eliminate column k from every other row
+        T rk[MC];
+#pragma unroll
+        for (int q = 0; q < MC; ++q) rk[q] = rowk[tx + GJR_TX * q];
+#pragma unroll
+        for (int p = 0; p < MR; ++p) {
+            const int i = ty + GJR_TY * p;
+            if (i >= b) continue;
+            const T ci = colk[i];
+#pragma unroll
+            for (int q = 0; q < MC; ++q) {
+                const int j = tx + GJR_TX * q;
+                if (i == k)
+                    a[p][q] = rk[q];
+                else if (j == k)
+                    a[p][q] = -ci * d;
+                else
+                    a[p][q] = a[p][q] - ci * rk[q];
+            }
+        }
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, ST_SINGULAR);
+        return;
+    }
+    // A^-1 = (PA)^-1 P: column q of the work matrix is column orig[q] of A^-1
+#pragma unroll
+    for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int i = ty + GJR_TY * p, j = tx + GJR_TX * q;
+            if (i < b && j < b) g.out[i + (int64_t)orig[j] * g.ldo] = a[p][q];
+        }
+}
+
+template <typename T, int MR, int MC>
+hodlr_status launch_gj_reg(hodlr_ctx *c, const GJDesc<T> *dd, int count, cudaStream_t s) {
+    gj_inverse_reg_kernel<T, MR, MC><<<count, GJR_THREADS, 0, s>>>(dd, c->d_status);
+    HODLR_TRY_CUDA(cudaGetLastError());
+    return HODLR_OK;
+}
+
 template <typename T>
 size_t gjs_smem(int b) {
     return ((size_t)(b + 1) * b + 2 * (size_t)b) * sizeof(T) + (size_t)b * sizeof(int) + 16;
@@ -351,6 +528,14 @@ size_t gjs_smem(int b) {
 
 template <typename T>
 hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, cudaStream_t s) {
+    if (bmax <= 32) return launch_gj_reg<T, 2, 1>(c, dd, count, s);
+    if (bmax <= 64) return launch_gj_reg<T, 4, 2>(c, dd, count, s);
+    if (bmax <= 96) return launch_gj_reg<T, 6, 3>(c, dd, count, s);
+    if (bmax <= 128) return launch_gj_reg<T, 8, 4>(c, dd, count, s);
+    if constexpr (sizeof(T) == 4) {   // FP64 tiles beyond 128 would spill registers
+        if (bmax <= 160) return launch_gj_reg<T, 10, 5>(c, dd, count, s);
+        if (bmax <= 192) return launch_gj_reg<T, 12, 6>(c, dd, count, s);
+    }
     if (gjs_smem<T>(bmax) <= GJS_SMEM_MAX) {
         const size_t sm = gjs_smem<T>(bmax);
         HODLR_TRY_CUDA(cudaFuncSetAttribute(gj_inverse_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

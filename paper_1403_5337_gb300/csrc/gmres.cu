@@ -200,13 +200,18 @@ __global__ void __launch_bounds__(MV_THREADS)
 // ------------------------------------------------------------------ Krylov kernels
 constexpr int KT = 256;
 
+// The Arnoldi step index of every kernel below is the per-rhs device counter
+// jcur[r] (all active right-hand sides advance together), so one recorded
+// iteration can be replayed by a device-side loop.
+
 // h[r][i] += sum_rows V_r(:, i) . w_r  for i <= j; rows split into chunks.
 __global__ void __launch_bounds__(KT)
-    gram_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, int j, const double *__restrict__ w,
-                int64_t ldw, const int *__restrict__ active, double *__restrict__ h, int hstride,
-                int64_t chunk) {
+    gram_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, const int *__restrict__ jcur,
+                const double *__restrict__ w, int64_t ldw, const int *__restrict__ active, double *__restrict__ h,
+                int hstride, int64_t chunk) {
     const int r = blockIdx.y;
     if (!active[r]) return;
+    const int j = jcur[r];
     const int64_t a = blockIdx.x * chunk, e = (a + chunk < n) ? a + chunk : n;
     const double *V = Vk + r * vstride;
     const double *wr = w + r * ldw;
@@ -223,11 +228,12 @@ __global__ void __launch_bounds__(KT)
 
 // w_r -= V_r(:, 0:j+1) h_r ; optionally accumulate ||w_r||^2.
 __global__ void __launch_bounds__(KT)
-    orth_update_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, int j, double *__restrict__ w,
-                       int64_t ldw, const int *__restrict__ active, const double *__restrict__ h, int hstride,
-                       double *__restrict__ nrm2) {
+    orth_update_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, const int *__restrict__ jcur,
+                       double *__restrict__ w, int64_t ldw, const int *__restrict__ active,
+                       const double *__restrict__ h, int hstride, double *__restrict__ nrm2) {
     const int r = blockIdx.y;
     if (!active[r]) return;
+    const int j = jcur[r];
     const double *V = Vk + r * vstride;
     const double *hr = h + (int64_t)r * hstride;
     double local = 0.0;
@@ -246,9 +252,11 @@ __global__ void __launch_bounds__(KT)
 
 // v_{j+1} = w / ||w||  (skipped for a zero norm: breakdown).
 __global__ void normalize_kernel(const double *__restrict__ w, int64_t ldw, int64_t n, const int *__restrict__ active,
-                                 const double *__restrict__ nrm2, double *__restrict__ Vk, int64_t vstride, int jn) {
+                                 const double *__restrict__ nrm2, double *__restrict__ Vk, int64_t vstride,
+                                 const int *__restrict__ jcur) {
     const int r = blockIdx.y;
     if (!active[r]) return;
+    const int jn = jcur[r] + 1;
     const double nr = sqrt(nrm2[r]);
     if (!(nr > 0.0)) return;
     double *dst = Vk + r * vstride + (int64_t)jn * n;
@@ -369,6 +377,34 @@ __global__ void count_active_kernel(const int *active, int s, int *nactive) {
     int c = 0;
     for (int r = 0; r < s; ++r) c += active[r];
     *nactive = c;
+}
+
+// Zcur(:, r) = V_r(:, jcur[r]) for active r (the vector to precondition).
+__global__ void gather_v_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, const int *__restrict__ jcur,
+                                const int *__restrict__ active, double *__restrict__ Zc) {
+    const int r = blockIdx.y;
+    if (!active[r]) return;
+    const double *src = Vk + r * vstride + (int64_t)jcur[r] * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        Zc[q + r * n] = src[q];
+}
+
+// Z_r(:, jcur[r]) = Zcur(:, r) for active r (the flexible basis).
+__global__ void scatter_z_kernel(const double *__restrict__ Zc, int64_t n, const int *__restrict__ jcur,
+                                 const int *__restrict__ active, double *__restrict__ Zk, int64_t zstride) {
+    const int r = blockIdx.y;
+    if (!active[r]) return;
+    double *dst = Zk + r * zstride + (int64_t)jcur[r] * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = Zc[q + r * n];
+}
+
+// End of one recorded iteration: continue the device loop while some rhs is
+// active, and never beyond `limit` iterations of one cycle.
+__global__ void loop_condition_kernel(cudaGraphConditionalHandle handle, const int *__restrict__ nactive,
+                                      int *__restrict__ loops, int limit) {
+    const int it = ++(*loops);
+    cudaGraphSetConditional(handle, (*nactive > 0 && it < limit) ? 1u : 0u);
 }
 
 __global__ void copy_active_kernel(const double *__restrict__ src, int64_t lds, double *__restrict__ dst, int64_t ldd,
@@ -503,6 +539,15 @@ extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const
 
 namespace {
 
+struct IterGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~IterGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
 struct GmresBufs {
     hodlr_ctx *c = nullptr;
     cudaStream_t st = nullptr;
@@ -559,8 +604,10 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     gs.est = (double *)bufs.get((size_t)s * 8);
     int *ibuf = (int *)bufs.get((size_t)(4 * s + 4) * sizeof(int));
     void *zsw = bufs.get((size_t)n * s * sizeof(float2));
+    double *Zc = (double *)bufs.get((size_t)n * s * 8);
+    int *loops = (int *)bufs.get(256);
     if (!Vk || !Zk || !Wv || !h1 || !h2 || !nrm || !gs.H || !gs.cs || !gs.sn || !gs.g || !gs.bnorm || !gs.est ||
-        !ibuf || !zsw) {
+        !ibuf || !zsw || !Zc || !loops) {
         set_error("gmres_solve: out of device memory");
         return HODLR_OUT_OF_MEMORY;
     }
@@ -600,6 +647,53 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         HODLR_TRY_CUDA(cudaMemset2DAsync(Wv, n * 8, 0, n * 8, s, st));
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
     }
+    // ---- one Arnoldi iteration, recorded once and replayed by a device-side
+    // while loop (a conditional graph node) until no right-hand side is active
+    if (P) HODLR_TRY(solve_prepare(P, s, st));
+    IterGraph iter;
+    {
+        cudaStream_t cs = c->side[HODLR_SIDE_STREAMS - 1];
+        HODLR_TRY_CUDA(cudaGraphCreate(&iter.graph, 0));
+        cudaGraphConditionalHandle handle;
+        HODLR_TRY_CUDA(cudaGraphConditionalHandleCreate(&handle, iter.graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        HODLR_TRY_CUDA(cudaGraphAddNode(&cnode, iter.graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        HODLR_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        auto record = [&]() -> hodlr_status {
+            gather_v_kernel<<<vgrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, gs.active, Zc);
+            if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs));
+            scatter_z_kernel<<<vgrid, KT, 0, cs>>>(Zc, n, gs.jcur, gs.active, Zk, zstride);
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw));
+            HODLR_TRY_CUDA(cudaMemsetAsync(h1, 0, (size_t)s * hstride * 8, cs));
+            HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, cs));
+            HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, cs));
+            gram_kernel<<<ggrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h1, hstride, gchunk);
+            orth_update_kernel<<<vgrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h1, hstride, nullptr);
+            gram_kernel<<<ggrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h2, hstride, gchunk);
+            orth_update_kernel<<<vgrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h2, hstride, nrm);
+            normalize_kernel<<<vgrid, KT, 0, cs>>>(Wv, n, n, gs.active, nrm, Vk, vstride, gs.jcur);
+            HODLR_TRY_CUDA(cudaMemsetAsync(gs.nactive, 0, sizeof(int), cs));
+            givens_kernel<<<(s + 127) / 128, 128, 0, cs>>>(gs, m, s, h1, h2, hstride, nrm, tol, max_iter);
+            loop_condition_kernel<<<1, 1, 0, cs>>>(handle, gs.nactive, loops, m + 1);
+            HODLR_TRY_CUDA(cudaGetLastError());
+            return HODLR_OK;
+        };
+        const hodlr_status rs = record();
+        cudaGraph_t captured = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+        if (rs != HODLR_OK) return rs;
+        if (ce != cudaSuccess) {
+            set_error("gmres_solve: graph capture failed: %s", cudaGetErrorString(ce));
+            return HODLR_CUDA_ERROR;
+        }
+        HODLR_TRY_CUDA(cudaGraphInstantiate(&iter.exec, iter.graph, 0));
+    }
     int restarts = 0;
     hodlr_status result = HODLR_OK;
     for (int cycle = 0;; ++cycle) {
@@ -610,30 +704,8 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         HODLR_TRY(take_status(c, st));
         if (h_pin[0] == 0) break;
         if (cycle > 0) ++restarts;
-        for (int j = 0; j < m; ++j) {
-            // z_j = P^-1 v_j
-            double *vj = Vk + (int64_t)j * n;
-            double *zj = Zk + (int64_t)j * n;
-            copy_active_kernel<<<vgrid, KT, 0, st>>>(vj, vstride, zj, zstride, n, gs.active);
-            if (P) HODLR_TRY(solve_impl(P, s, zj, zstride, st));
-            // w = A z_j
-            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, zj, zstride, Wv, n, st, zsw));
-            // CGS2
-            HODLR_TRY_CUDA(cudaMemsetAsync(h1, 0, (size_t)s * hstride * 8, st));
-            HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, st));
-            HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, st));
-            gram_kernel<<<ggrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h1, hstride, gchunk);
-            orth_update_kernel<<<vgrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h1, hstride, nullptr);
-            gram_kernel<<<ggrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h2, hstride, gchunk);
-            orth_update_kernel<<<vgrid, KT, 0, st>>>(Vk, vstride, n, j, Wv, n, gs.active, h2, hstride, nrm);
-            normalize_kernel<<<vgrid, KT, 0, st>>>(Wv, n, n, gs.active, nrm, Vk, vstride, j + 1);
-            HODLR_TRY_CUDA(cudaMemsetAsync(gs.nactive, 0, sizeof(int), st));
-            givens_kernel<<<(s + 127) / 128, 128, 0, st>>>(gs, m, s, h1, h2, hstride, nrm, tol, max_iter);
-            HODLR_TRY_CUDA(cudaGetLastError());
-            HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin, gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
-            HODLR_TRY_CUDA(cudaStreamSynchronize(st));
-            if (h_pin[0] == 0) break;
-        }
+        HODLR_TRY_CUDA(cudaMemsetAsync(loops, 0, sizeof(int), st));
+        HODLR_TRY_CUDA(cudaGraphLaunch(iter.exec, st));
         // x += Z y
         backsolve_kernel<<<s, KT, (size_t)m * 8, st>>>(gs, m, Zk, zstride, n, X, ldx);
         HODLR_TRY_CUDA(cudaGetLastError());

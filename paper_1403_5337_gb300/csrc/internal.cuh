@@ -145,10 +145,7 @@ struct AcaBlockDesc {
     int32_t *pcol;      // out: pivot cols (block-local)
     int32_t *cap_hit;   // out
 };
-hodlr_status launch_aca(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
-                        const AcaBlockDesc *d_blocks, int nblocks, int64_t max_m, double tol,
-                        cudaStream_t s);
-// One thread-block cluster per block, one launch per level on the context's side
+// Partial-pivoting ACA, one thread-block cluster per block, one launch per level on the context's side
 // streams (forked from and joined back into s).  level_first: first block of each
 // level in d_blocks (size nlev + 1); level_maxdim: largest block side per level.
 hodlr_status launch_aca_levels(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
@@ -178,6 +175,7 @@ hodlr_status factor_impl(hodlr_t *h, cudaStream_t s);
 hodlr_status plan_factor(hodlr_t *h, cudaStream_t s);
 void free_plan(hodlr_t *h, cudaStream_t s);
 hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s);
+hodlr_status solve_prepare(const hodlr_t *h, int s_rhs, cudaStream_t s);
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s_rhs,
                          const double *Z, int64_t ldz, double *W, int64_t ldw, cudaStream_t s,
                          void *work = nullptr);
