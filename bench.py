@@ -361,6 +361,9 @@ def main():
             "config": _config(args, F),
             "converged": converged, "iters": info.iters.tolist(), "true_relres": info.true_relres.tolist(),
             "ranks_max": st["rank_max"], "ms_compress": comp_ms,
+            "phases_ms": {"compress": comp_ms,
+                          "factor": statistics.median(s["ms_factor"] for _, s in infos),
+                          "gmres": statistics.median(i.ms_total for i, _ in infos)},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": 8 * n * n + 8 * B.numel(),
                     "d2h_bytes_per_step": 8 * B.numel()},

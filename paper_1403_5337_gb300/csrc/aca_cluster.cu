@@ -72,6 +72,33 @@ __device__ Cand cta_argmax(double a, int idx, double v, Cand *red) {
     return best;
 }
 
+// Best of the CL cluster candidates slot[which]: lane q of every warp loads rank
+// q's candidate over DSMEM, then an xor-shuffle argmax (ties -> lowest index)
+// leaves the same result in every thread.
+__device__ __forceinline__ Cand cluster_best(cg::cluster_group &cl, Cand *slot, int which, int CL) {
+    const int lane = threadIdx.x & 31;
+    double a = -1.0, v = 0.0;
+    int idx = INT_MAX;
+    if (lane < CL) {
+        const Cand o = cl.map_shared_rank(slot, lane)[which];
+        a = o.a;
+        v = o.v;
+        idx = o.idx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (better(oa, oi, a, idx)) {
+            a = oa;
+            v = ov;
+            idx = oi;
+        }
+    }
+    return Cand{a, v, idx, 0};
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -90,6 +117,7 @@ __global__ void __launch_bounds__(CT, 1)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t m = B.m, nc = B.nc, ld = B.ld;
     const int64_t mr = (m + CL - 1) / CL, nr = (nc + CL - 1) / CL;
+    const int64_t smr = mr + 1, snr = nr + 1;   // padded shared-memory strides (no bank conflicts)
     const int64_t i0 = std::min<int64_t>(m, c * mr), i1 = std::min<int64_t>(m, i0 + mr);
     const int64_t j0 = std::min<int64_t>(nc, c * nr), j1 = std::min<int64_t>(nc, j0 + nr);
     const int64_t mn = m < nc ? m : nc;
@@ -104,9 +132,9 @@ __global__ void __launch_bounds__(CT, 1)
     T *dots = reinterpret_cast<T *>(slot + 6);                       // [2][2 (ACA_CAP + 1)] partial dots
     T *pu = dots + 4 * (ACA_CAP + 1);                                // U(i_k, 0..k-1)
     T *pv = pu + ACA_CAP;                                            // V(j_k, 0..k-1)
-    T *Us = pv + ACA_CAP;                                            // [kcs][mr]
-    T *Vs = Us + (size_t)kcs * mr;                                   // [kcs][nr]
-    unsigned char *used = reinterpret_cast<unsigned char *>(Vs + (size_t)kcs * nr);   // [mr]
+    T *Us = pv + ACA_CAP;                                            // [kcs][smr]
+    T *Vs = Us + (size_t)kcs * smr;                                  // [kcs][snr]
+    unsigned char *used = reinterpret_cast<unsigned char *>(Vs + (size_t)kcs * snr);  // [mr]
     __shared__ Cand red[CW];
     __shared__ double s_norm2;
     __shared__ int s_i, s_stop;
@@ -124,7 +152,13 @@ __global__ void __launch_bounds__(CT, 1)
     while (k < kmax) {
         const int par = k & 1;
         const int i = s_i;
-        for (int l = tid; l < k; l += CT) pu[l] = Ug[(int64_t)l * ld + i];
+        {
+            // U(i_k, l): from the shared-memory slice of the CTA that owns row i_k
+            const int co = (int)(i / mr);
+            const int64_t li = i - (int64_t)co * mr;
+            const T *Uo = cl.map_shared_rank(Us, co);
+            for (int l = tid; l < k; l += CT) pu[l] = (l < kcs) ? Uo[(size_t)l * smr + li] : Ug[(int64_t)l * ld + i];
+        }
         __syncthreads();
         // ---- row pass on own columns -> v_k (unscaled)
         const int kin = k < kcs ? k : kcs;
@@ -135,9 +169,10 @@ __global__ void __launch_bounds__(CT, 1)
             const int64_t jl = j - j0;
             T r = dev::from_double<T>(arow[j]);
             int l = 0;
-            for (; l < kin; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vs[(size_t)l * nr + jl]));
+#pragma unroll 8
+            for (; l < kin; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vs[(size_t)l * snr + jl]));
             for (; l < k; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vg[(int64_t)l * ld + j]));
-            if (k < kcs) Vs[(size_t)k * nr + jl] = r;
+            if (k < kcs) Vs[(size_t)k * snr + jl] = r;
             Vg[(int64_t)k * ld + j] = r;
             const double a = fabs((double)r);
             if (a != a) atomicOr(status, ST_NONFINITE);
@@ -150,11 +185,7 @@ __global__ void __launch_bounds__(CT, 1)
         Cand cr = cta_argmax(ba, bi, bv, red);
         if (tid == 0) slot[par * 3 + 0] = cr;
         cl.sync();
-        Cand best = Cand{-1.0, 0.0, INT_MAX, 0};
-        for (int q = 0; q < CL; ++q) {
-            const Cand o = cl.map_shared_rank(slot, q)[par * 3 + 0];
-            if (better(o.a, o.idx, best.a, best.idx)) best = o;
-        }
+        const Cand best = cluster_best(cl, slot, par * 3 + 0, CL);
         const int jk = best.idx;
         const T piv = (T)best.v;
         // the owner of row i marks it used
@@ -172,11 +203,7 @@ __global__ void __launch_bounds__(CT, 1)
             Cand cf = cta_argmax(fa, fi, 0.0, red);
             if (tid == 0) slot[par * 3 + 2] = cf;
             cl.sync();
-            Cand bf = Cand{-1.0, 0.0, INT_MAX, 0};
-            for (int q = 0; q < CL; ++q) {
-                const Cand o = cl.map_shared_rank(slot, q)[par * 3 + 2];
-                if (better(o.a, o.idx, bf.a, bf.idx)) bf = o;
-            }
+            const Cand bf = cluster_best(cl, slot, par * 3 + 2, CL);
             if (bf.a < 0.0) break;
             if (tid == 0) s_i = bf.idx;
             __syncthreads();
@@ -186,11 +213,16 @@ __global__ void __launch_bounds__(CT, 1)
         for (int64_t j = j0 + tid; j < j1; j += CT) {
             const int64_t jl = j - j0;
             const T v = dev::div_rn(Vg[(int64_t)k * ld + j], piv);
-            if (k < kcs) Vs[(size_t)k * nr + jl] = v;
+            if (k < kcs) Vs[(size_t)k * snr + jl] = v;
             Vg[(int64_t)k * ld + j] = v;
         }
         // V(j_k, l) for l < k: written in earlier steps by the owner of column j_k
-        for (int l = tid; l < k; l += CT) pv[l] = Vg[(int64_t)l * ld + jk];
+        {
+            const int cv = (int)(jk / nr);
+            const int64_t lj = jk - (int64_t)cv * nr;
+            const T *Vo = cl.map_shared_rank(Vs, cv);
+            for (int l = tid; l < k; l += CT) pv[l] = (l < kcs) ? Vo[(size_t)l * snr + lj] : Vg[(int64_t)l * ld + jk];
+        }
         __syncthreads();
         // ---- column pass on own rows -> u_k
         const double *acol;
@@ -208,9 +240,10 @@ __global__ void __launch_bounds__(CT, 1)
             const int64_t ql = q - i0;
             T u = dev::from_double<T>(acol[q * astr]);
             int l = 0;
-            for (; l < kin; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Us[(size_t)l * mr + ql]));
+#pragma unroll 8
+            for (; l < kin; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Us[(size_t)l * smr + ql]));
             for (; l < k; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Ug[(int64_t)l * ld + q]));
-            if (k < kcs) Us[(size_t)k * mr + ql] = u;
+            if (k < kcs) Us[(size_t)k * smr + ql] = u;
             Ug[(int64_t)k * ld + q] = u;
             if (u != u) atomicOr(status, ST_NONFINITE);
             if (!used[ql]) {
@@ -223,35 +256,55 @@ __global__ void __launch_bounds__(CT, 1)
             }
         }
         Cand cc = cta_argmax(ca, ci, cv, red);
-        // ---- partial dots over own slices, l = 0..k (one warp per l)
+        // ---- partial dots over own slices, l = 0..k: one thread per l runs down the
+        // slice (padded strides keep the lanes on distinct banks); columns beyond
+        // the shared-memory capacity use one warp per l over global memory
         T *dp = dots + (size_t)par * 2 * (ACA_CAP + 1);
-        for (int l = warp; l <= k; l += CW) {
-            T su = T(0), sv = T(0);
-            if (l < kcs && k < kcs) {
-                for (int64_t q = lane; q < i1 - i0; q += 32) su = fma(Us[(size_t)l * mr + q], Us[(size_t)k * mr + q], su);
-                for (int64_t j = lane; j < j1 - j0; j += 32) sv = fma(Vs[(size_t)l * nr + j], Vs[(size_t)k * nr + j], sv);
-            } else {
+        if (k < kcs) {
+            const int64_t nrow = i1 - i0, ncol = j1 - j0;
+            const T *uk = Us + (size_t)k * smr;
+            const T *vk = Vs + (size_t)k * snr;
+            for (int l = tid; l <= k; l += CT) {
+                const T *ul = Us + (size_t)l * smr;
+                const T *vl = Vs + (size_t)l * snr;
+                // four interleaved partial sums (fixed combination order)
+                T su[4] = {T(0), T(0), T(0), T(0)}, sv[4] = {T(0), T(0), T(0), T(0)};
+                int64_t q = 0;
+                for (; q + 4 <= nrow; q += 4) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) su[t] = fma(ul[q + t], uk[q + t], su[t]);
+                }
+                for (; q < nrow; ++q) su[0] = fma(ul[q], uk[q], su[0]);
+                q = 0;
+                for (; q + 4 <= ncol; q += 4) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) sv[t] = fma(vl[q + t], vk[q + t], sv[t]);
+                }
+                for (; q < ncol; ++q) sv[0] = fma(vl[q], vk[q], sv[0]);
+                dp[l] = (su[0] + su[1]) + (su[2] + su[3]);
+                dp[ACA_CAP + 1 + l] = (sv[0] + sv[1]) + (sv[2] + sv[3]);
+            }
+        } else {
+            for (int l = warp; l <= k; l += CW) {
+                T su = T(0), sv = T(0);
                 for (int64_t q = i0 + lane; q < i1; q += 32) su = fma(Ug[(int64_t)l * ld + q], Ug[(int64_t)k * ld + q], su);
                 for (int64_t j = j0 + lane; j < j1; j += 32) sv = fma(Vg[(int64_t)l * ld + j], Vg[(int64_t)k * ld + j], sv);
-            }
-            su = warp_sum(su);
-            sv = warp_sum(sv);
-            if (lane == 0) {
-                dp[l] = su;
-                dp[ACA_CAP + 1 + l] = sv;
+                su = warp_sum(su);
+                sv = warp_sum(sv);
+                if (lane == 0) {
+                    dp[l] = su;
+                    dp[ACA_CAP + 1 + l] = sv;
+                }
             }
         }
         if (tid == 0) slot[par * 3 + 1] = cc;
         __syncthreads();
         cl.sync();
         // ---- cluster-wide: next row, dot products (rank order), stop decision
-        Cand bc = Cand{-1.0, 0.0, INT_MAX, 0};
-        for (int q = 0; q < CL; ++q) {
-            const Cand o = cl.map_shared_rank(slot, q)[par * 3 + 1];
-            if (better(o.a, o.idx, bc.a, bc.idx)) bc = o;
-        }
+        const Cand bc = cluster_best(cl, slot, par * 3 + 1, CL);
         for (int l = tid; l <= k; l += CT) {
             T su = T(0), sv = T(0);
+#pragma unroll 4
             for (int q = 0; q < CL; ++q) {
                 const T *rp = cl.map_shared_rank(dots, q) + (size_t)par * 2 * (ACA_CAP + 1);
                 su += rp[l];
@@ -261,9 +314,15 @@ __global__ void __launch_bounds__(CT, 1)
             tot[ACA_CAP + 1 + l] = (double)sv;
         }
         __syncthreads();
+        // cross term sum_{l<k} (u_k.u_l)(v_k.v_l): lane-strided partial sums, then a
+        // fixed xor-shuffle tree (the same order in every CTA of the cluster)
+        double cross = 0.0;
+        if (warp == 0) {
+            for (int l = lane; l < k; l += 32) cross += tot[l] * tot[ACA_CAP + 1 + l];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cross += __shfl_xor_sync(0xffffffffu, cross, o);
+        }
         if (tid == 0) {
-            double cross = 0.0;
-            for (int l = 0; l < k; ++l) cross += tot[l] * tot[ACA_CAP + 1 + l];
             const double uu = tot[k], vv = tot[ACA_CAP + 1 + k];
             s_norm2 = s_norm2 + 2.0 * cross + uu * vv;
             if (c == 0) {
@@ -301,8 +360,9 @@ hodlr_status launch_level(hodlr_ctx *c, const double *A, int64_t lda, int sym, c
                           int nblocks, int CL, int64_t mr, int64_t nr, double tol, cudaStream_t s) {
     const size_t fixed = fixed_smem<T>() + (size_t)mr + 16;
     int kcs = 0;
-    if (fixed < SMEM_BUDGET) kcs = (int)std::min<size_t>(ACA_CAP, (SMEM_BUDGET - fixed) / ((mr + nr) * sizeof(T)));
-    const size_t sm = fixed + (size_t)kcs * (mr + nr) * sizeof(T);
+    if (fixed < SMEM_BUDGET)
+        kcs = (int)std::min<size_t>(ACA_CAP, (SMEM_BUDGET - fixed) / ((mr + nr + 2) * sizeof(T)));
+    const size_t sm = fixed + (size_t)kcs * (mr + nr + 2) * sizeof(T);
     HODLR_TRY_CUDA(cudaFuncSetAttribute(aca_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (CL > 8)
         HODLR_TRY_CUDA(cudaFuncSetAttribute(aca_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));

@@ -234,6 +234,8 @@ hodlr_status hodlr_destroy(hodlr_t *h) {
     cudaStreamSynchronize(nullptr);
     cudaDeviceSynchronize();
     free_plan(h, nullptr);
+    for (auto &e : h->fev)
+        if (e) cudaEventDestroy(e);
     for (auto &b : h->owned) dfree(h->ctx, b.p, b.bytes, nullptr);
     if (h->work) dfree(h->ctx, h->work, h->work_bytes, nullptr);
     cudaDeviceSynchronize();
@@ -264,8 +266,8 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         set_error("hodlr_build: BDLR needs the graph of the matrix");
         return HODLR_INVALID_ARG;
     }
-    if (o.precision != HODLR_FP64 && o.precision != HODLR_FP32) {
-        set_error("hodlr_build: precision %d is not available in this build", o.precision);
+    if (o.precision < HODLR_FP64 || o.precision > HODLR_FP16) {
+        set_error("hodlr_build: unknown precision %d", o.precision);
         return HODLR_INVALID_ARG;
     }
     int cprec = o.compress_precision;
@@ -340,7 +342,8 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     h->sym = A->symmetric ? 1 : 0;
     h->L = L;
     h->bounds = bounds;
-    h->prec = o.precision;
+    h->prec = (o.precision == HODLR_FP64) ? HODLR_FP64 : HODLR_FP32;
+    h->store = o.precision;
     h->cprec = cprec;
     h->method = method;
     h->tol = tol;
@@ -423,6 +426,21 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         for (auto &q : temp) dfree(c, q.first, q.second, st);
         temp.clear();
     };
+    // The leaf inverses depend on A only: they run on a side stream while the
+    // off-diagonal blocks are compressed, and join the caller's stream after.
+    h->leafinv = own(h, (size_t)nleaf * bmax * bmax * elem_size(h->prec), st);
+    if (!h->leafinv) {
+        free_temp();
+        return fail(HODLR_OUT_OF_MEMORY);
+    }
+    cudaStream_t lstream = c->side[HODLR_SIDE_STREAMS - 1];
+    cudaEvent_t lfork = nullptr, ljoin = nullptr;
+    cudaEventCreateWithFlags(&lfork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ljoin, cudaEventDisableTiming);
+    cudaEventRecord(lfork, st);
+    cudaStreamWaitEvent(lstream, lfork, 0);
+    const hodlr_status rleaf = leaf_inverses(h, lstream);
+    cudaEventRecord(ljoin, lstream);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -454,6 +472,10 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         rs = run_bdlr(h, g, depth, st, Ust, Vst);
     }
     cudaEventRecord(e1, st);
+    cudaStreamWaitEvent(st, ljoin, 0);
+    cudaEventDestroy(lfork);
+    cudaEventDestroy(ljoin);
+    if (rs == HODLR_OK) rs = rleaf;
     if (rs != HODLR_OK) {
         cudaStreamSynchronize(st);
         free_temp();
@@ -505,7 +527,6 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     const size_t dvb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * pe;
     h->D = own(h, dvb, st);
     h->V = own(h, dvb, st);
-    h->leafinv = own(h, (size_t)nleaf * bmax * bmax * pe, st);
     h->Sinv.assign(L, nullptr);
     for (int l = 0; l < L; ++l) {
         const int64_t s2 = 2 * (int64_t)h->lv[l + 1].rp;
@@ -514,6 +535,27 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             free_temp();
             return fail(HODLR_OUT_OF_MEMORY);
         }
+    }
+    if (h->store == HODLR_BF16 || h->store == HODLR_FP16) {
+        const size_t qb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * 2;
+        h->Vq = own(h, qb, st);
+        h->Dq = own(h, qb, st);
+        if (!h->Vq || !h->Dq) {
+            free_temp();
+            return fail(HODLR_OUT_OF_MEMORY);
+        }
+        h->vscale.assign(L + 1, nullptr);
+        h->dscale.assign(L + 1, nullptr);
+        if (h->store == HODLR_FP16)
+            for (int l = 1; l <= L; ++l) {
+                const size_t sb = (size_t)h->lv[l].nnodes * std::max(h->lv[l].rp, 1) * sizeof(float);
+                h->vscale[l] = (float *)own(h, sb, st);
+                h->dscale[l] = (float *)own(h, sb, st);
+                if (!h->vscale[l] || !h->dscale[l]) {
+                    free_temp();
+                    return fail(HODLR_OUT_OF_MEMORY);
+                }
+            }
     }
     if (!h->D || !h->V || !h->leafinv) {
         free_temp();
@@ -585,7 +627,13 @@ hodlr_status hodlr_factor(hodlr_t *h, hodlr_stream stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
     h->factored = false;
+    if (!h->fev[0]) {
+        HODLR_TRY_CUDA(cudaEventCreate(&h->fev[0]));
+        HODLR_TRY_CUDA(cudaEventCreate(&h->fev[1]));
+    }
+    HODLR_TRY_CUDA(cudaEventRecord(h->fev[0], st));
     HODLR_TRY(factor_impl(h, st));
+    HODLR_TRY_CUDA(cudaEventRecord(h->fev[1], st));
     h->factored = true;
     return HODLR_OK;
 }
@@ -640,7 +688,12 @@ hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {
     o->bytes_factors = b;
     o->factored = h->factored ? 1 : 0;
     o->ms_compress = h->ms_compress;
-    o->ms_factor = h->ms_factor;
+    o->ms_factor = 0.0;
+    if (h->factored && h->fev[1] && cudaEventSynchronize(h->fev[1]) == cudaSuccess) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->fev[0], h->fev[1]) == cudaSuccess) o->ms_factor = ms;
+    }
+    cudaGetLastError();
     return HODLR_OK;
 }
 

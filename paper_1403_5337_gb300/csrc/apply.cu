@@ -6,6 +6,9 @@
 //       x_alpha -= d_alpha y2,  x_beta -= d_beta y1  (rank-rp updates)
 // X is FP64 in and out; the arithmetic runs in the factor's precision T on a
 // private copy of X.  Memory-bound: each level streams V and d once.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "internal.cuh"
@@ -15,6 +18,17 @@ namespace {
 
 constexpr int AP_THREADS = 256;
 constexpr int MAX_RHS_CHUNK = 8;
+
+// Storage -> arithmetic type of the streamed factors (V, d): FP64, FP32, or a
+// 16-bit copy (BF16, or FP16 scaled per node and column by a power of two).
+template <typename T>
+__device__ __forceinline__ T to_t(double x) { return (T)x; }
+template <typename T>
+__device__ __forceinline__ T to_t(float x) { return (T)x; }
+template <typename T>
+__device__ __forceinline__ T to_t(__nv_bfloat16 x) { return (T)__bfloat162float(x); }
+template <typename T>
+__device__ __forceinline__ T to_t(__half x) { return (T)__half2float(x); }
 
 // x_T(leaf rows, r) = Kinv_leaf * X(leaf rows, r).  One CTA per (leaf, rhs).
 template <typename T>
@@ -36,12 +50,13 @@ __global__ void __launch_bounds__(AP_THREADS)
 }
 
 // w(child, col, r) += sum_{rows of child} V(row, coff+col) x(row, r).
-// Grid: (child * row-chunks, column groups); one warp per column.
-template <typename T>
+// Grid: (child * row-chunks, column groups); one warp per column.  vscale (or
+// NULL) holds the dequantisation factor of each (child, column).
+template <typename T, typename S>
 __global__ void __launch_bounds__(AP_THREADS)
-    vtx_kernel(const T *__restrict__ V, int64_t ldn, int64_t coff, int rp, const int64_t *__restrict__ bounds,
+    vtx_kernel(const S *__restrict__ V, int64_t ldn, int64_t coff, int rp, const int64_t *__restrict__ bounds,
                int L, int c, int chunks, int64_t chunk_rows, const T *__restrict__ xt, int64_t ldt,
-               int s, T *__restrict__ w) {
+               int s, T *__restrict__ w, const float *__restrict__ vscale) {
     const int child = blockIdx.x / chunks, ch = blockIdx.x % chunks;
     const int64_t n0 = bounds[(size_t)child << (L - c)];
     const int64_t n1 = bounds[(size_t)(child + 1) << (L - c)];
@@ -51,14 +66,15 @@ __global__ void __launch_bounds__(AP_THREADS)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int col = blockIdx.y * (AP_THREADS / 32) + warp;
     if (col >= rp) return;
-    const T *vc = V + (coff + col) * ldn;
+    const S *vc = V + (coff + col) * ldn;
+    const T sc = vscale ? (T)vscale[(size_t)child * rp + col] : T(1);
     T acc[MAX_RHS_CHUNK];
     for (int r0 = 0; r0 < s; r0 += MAX_RHS_CHUNK) {
         const int rr = (s - r0) < MAX_RHS_CHUNK ? (s - r0) : MAX_RHS_CHUNK;
 #pragma unroll
         for (int q = 0; q < MAX_RHS_CHUNK; ++q) acc[q] = T(0);
         for (int64_t i = a + lane; i < e; i += 32) {
-            const T v = vc[i];
+            const T v = to_t<T>(vc[i]);
 #pragma unroll
             for (int q = 0; q < MAX_RHS_CHUNK; ++q)
                 if (q < rr) acc[q] = fma(v, xt[i + (r0 + q) * ldt], acc[q]);
@@ -69,7 +85,7 @@ __global__ void __launch_bounds__(AP_THREADS)
             T v = acc[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) atomicAdd(&w[((size_t)child * rp + col) * s + r0 + q], v);
+            if (lane == 0) atomicAdd(&w[((size_t)child * rp + col) * s + r0 + q], v * sc);
         }
     }
 }
@@ -126,11 +142,11 @@ __global__ void __launch_bounds__(AP_THREADS)
 // first child (alpha) and y1 for the second (beta).
 // Rows are tiled by TR = 32 per CTA (lane = row); the 8 warps split the rp
 // columns of d and the partial sums are reduced in shared memory.
-template <typename T>
+template <typename T, typename S>
 __global__ void __launch_bounds__(AP_THREADS)
-    update_kernel(const T *__restrict__ Dm, int64_t ldn, int64_t coff, int rp,
+    update_kernel(const S *__restrict__ Dm, int64_t ldn, int64_t coff, int rp,
                   const int64_t *__restrict__ bounds, int L, int c, int chunks, int64_t chunk_rows,
-                  const T *__restrict__ y, int s, T *__restrict__ xt, int64_t ldt) {
+                  const T *__restrict__ y, int s, T *__restrict__ xt, int64_t ldt, const float *__restrict__ dscale) {
     const int child = blockIdx.x / chunks, ch = blockIdx.x % chunks;
     const int64_t n0 = bounds[(size_t)child << (L - c)];
     const int64_t n1 = bounds[(size_t)(child + 1) << (L - c)];
@@ -144,7 +160,8 @@ __global__ void __launch_bounds__(AP_THREADS)
     const int node = child >> 1;
     const int half = (child & 1) ? 0 : rp;   // alpha uses y2 (second half)
     const T *yn = y + ((size_t)node * 2 * rp + half) * s;
-    for (int q = threadIdx.x; q < rp * s; q += AP_THREADS) ys[q] = yn[q];
+    for (int q = threadIdx.x; q < rp * s; q += AP_THREADS)
+        ys[q] = dscale ? yn[q] * (T)dscale[(size_t)child * rp + q / s] : yn[q];
     __syncthreads();
     const int kper = (rp + 7) / 8, kb = warp * kper, ke = min(rp, kb + kper);
     const int64_t i = a + lane;
@@ -156,7 +173,7 @@ __global__ void __launch_bounds__(AP_THREADS)
         if (i < e) {
 #pragma unroll 4
             for (int k = kb; k < ke; ++k) {
-                const T dv = Dm[i + (coff + k) * ldn];
+                const T dv = to_t<T>(Dm[i + (coff + k) * ldn]);
 #pragma unroll
                 for (int q = 0; q < MAX_RHS_CHUNK; ++q)
                     if (q < rr) acc[q] = fma(dv, ys[k * s + r0 + q], acc[q]);
@@ -194,8 +211,9 @@ __global__ void zero_kernel2(T *p, int64_t count) {
         p[e] = T(0);
 }
 
-template <typename T>
-hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st) {
+template <typename T, typename S>
+hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st, const S *V,
+                         const S *Dm, const float *const *vsc, const float *const *dsc) {
     const int L = h->L;
     const int64_t n = h->n, ldn = h->ldn;
     hodlr_t *hm = const_cast<hodlr_t *>(h);
@@ -213,8 +231,6 @@ hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
     T *w = reinterpret_cast<T *>(wp + ((xt_bytes + 255) & ~size_t(255)));
     T *y = w + w_elems;
     const T *Kinv = reinterpret_cast<const T *>(h->leafinv);
-    const T *V = reinterpret_cast<const T *>(h->V);
-    const T *Dm = reinterpret_cast<const T *>(h->D);
     {
         dim3 grid(1 << L, s);
         size_t sm = (size_t)h->bmax * sizeof(T);
@@ -236,8 +252,8 @@ hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
             int blocks = (int)std::min<int64_t>((cnt + 255) / 256, 1024);
             zero_kernel2<T><<<blocks, 256, 0, st>>>(w, cnt);
             dim3 grid(nch * chunks, (rp + AP_THREADS / 32 - 1) / (AP_THREADS / 32));
-            vtx_kernel<T><<<grid, AP_THREADS, 0, st>>>(V, ldn, coff, rp, h->d_bounds, L, c, chunks, chunk_rows,
-                                                        xt, ldn, s, w);
+            vtx_kernel<T, S><<<grid, AP_THREADS, 0, st>>>(V, ldn, coff, rp, h->d_bounds, L, c, chunks, chunk_rows,
+                                                           xt, ldn, s, w, vsc ? vsc[c] : nullptr);
             HODLR_TRY_CUDA(cudaGetLastError());
         }
         const size_t part_bytes = (size_t)(AP_THREADS / 32) * TR * MAX_RHS_CHUNK * sizeof(T);
@@ -256,10 +272,10 @@ hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
             const int uchunks = (int)((node_rows + urows - 1) / urows);
             const size_t sm = (size_t)rp * s * sizeof(T) + part_bytes;
             if (sm > 48 * 1024)
-                HODLR_TRY_CUDA(cudaFuncSetAttribute(update_kernel<T>,
+                HODLR_TRY_CUDA(cudaFuncSetAttribute(update_kernel<T, S>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            update_kernel<T><<<nch * uchunks, AP_THREADS, sm, st>>>(Dm, ldn, coff, rp, h->d_bounds, L, c, uchunks,
-                                                                     urows, y, s, xt, ldn);
+            update_kernel<T, S><<<nch * uchunks, AP_THREADS, sm, st>>>(Dm, ldn, coff, rp, h->d_bounds, L, c, uchunks,
+                                                                        urows, y, s, xt, ldn, dsc ? dsc[c] : nullptr);
             HODLR_TRY_CUDA(cudaGetLastError());
         }
     }
@@ -274,8 +290,18 @@ hodlr_status solve_typed(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
 }  // namespace
 
 hodlr_status solve_impl(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st) {
-    if (h->prec == HODLR_FP64) return solve_typed<double>(h, s, X, ldx, st);
-    return solve_typed<float>(h, s, X, ldx, st);
+    if (h->prec == HODLR_FP64)
+        return solve_typed<double, double>(h, s, X, ldx, st, reinterpret_cast<const double *>(h->V),
+                                           reinterpret_cast<const double *>(h->D), nullptr, nullptr);
+    if (h->store == HODLR_BF16)
+        return solve_typed<float, __nv_bfloat16>(h, s, X, ldx, st, reinterpret_cast<const __nv_bfloat16 *>(h->Vq),
+                                                 reinterpret_cast<const __nv_bfloat16 *>(h->Dq), nullptr, nullptr);
+    if (h->store == HODLR_FP16)
+        return solve_typed<float, __half>(h, s, X, ldx, st, reinterpret_cast<const __half *>(h->Vq),
+                                          reinterpret_cast<const __half *>(h->Dq), h->vscale.data(),
+                                          h->dscale.data());
+    return solve_typed<float, float>(h, s, X, ldx, st, reinterpret_cast<const float *>(h->V),
+                                     reinterpret_cast<const float *>(h->D), nullptr, nullptr);
 }
 
 }  // namespace hodlr

@@ -16,6 +16,9 @@
 //                D(beta,  0:coff(c)) -= d_beta  * (S^-1 [Y_alpha; Y_beta])(0:rp, :)
 // The 2x2 block inverse through M = I - P Q is the same algebra as solving with
 // S; it halves the size of the dense inversion.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -128,6 +131,10 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_inverse_kernel(const GJDesc<T> 
     const GJDesc<T> g = descs[blockIdx.x];
     const int b = g.b, tid = threadIdx.x;
     if (b <= 0) return;
+    if (g.work == nullptr) {   // host-side sizing error: report, never touch memory
+        if (tid == 0) atomicOr(status, ST_RANGE);
+        return;
+    }
     T *W = g.work;
     extern __shared__ __align__(16) unsigned char smem[];
     T *s_col = reinterpret_cast<T *>(smem);   // b
@@ -478,25 +485,31 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJ
                         }
         }
         __syncthreads();
-        // 5. eliminate column k from every other row
+        // 5. eliminate column k from every other row: a -= colk * rowk everywhere
+        // (rows beyond b hold zeros and stay zero), then overwrite the pivot row
+        // with rowk and the pivot column with -colk d.
         T rk[MC];
 #pragma unroll
         for (int q = 0; q < MC; ++q) rk[q] = rowk[tx + GJR_TX * q];
 #pragma unroll
         for (int p = 0; p < MR; ++p) {
             const int i = ty + GJR_TY * p;
-            if (i >= b) continue;
-            const T ci = colk[i];
+            const T ci = (i < b) ? colk[i] : T(0);
 #pragma unroll
-            for (int q = 0; q < MC; ++q) {
-                const int j = tx + GJR_TX * q;
-                if (i == k)
-                    a[p][q] = rk[q];
-                else if (j == k)
-                    a[p][q] = -ci * d;
-                else
-                    a[p][q] = a[p][q] - ci * rk[q];
+            for (int q = 0; q < MC; ++q) a[p][q] = fma(-ci, rk[q], a[p][q]);
+            if (tx == kx) {
+#pragma unroll
+                for (int q = 0; q < MC; ++q)
+                    if (q == kq) a[p][q] = -ci * d;
             }
+        }
+        if (ty == k % GJR_TY) {
+#pragma unroll
+            for (int p = 0; p < MR; ++p)
+                if (p == k / GJR_TY) {
+#pragma unroll
+                    for (int q = 0; q < MC; ++q) a[p][q] = rk[q];
+                }
         }
         __syncthreads();
     }
@@ -524,6 +537,59 @@ hodlr_status launch_gj_reg(hodlr_ctx *c, const GJDesc<T> *dd, int count, cudaStr
 template <typename T>
 size_t gjs_smem(int b) {
     return ((size_t)(b + 1) * b + 2 * (size_t)b) * sizeof(T) + (size_t)b * sizeof(int) + 16;
+}
+
+// 16-bit copy of the columns coff .. coff+rp of a level (node rows): BF16
+// directly; FP16 scaled per (node, column) by 2^e so that the column's largest
+// magnitude lands just below 2^14, with 2^-e stored as the dequantisation factor.
+template <typename S>
+__device__ __forceinline__ S to_store(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half to_store<__half>(float x) { return __float2half_rn(x); }
+
+template <typename S>
+__global__ void quantize_kernel(const float *__restrict__ src, S *__restrict__ dst, int64_t ldn, int64_t coff, int rp,
+                                const int64_t *__restrict__ bounds, int L, int l, float *__restrict__ scale) {
+    const int node = blockIdx.x, col = blockIdx.y;
+    const int64_t r0 = bounds[(size_t)node << (L - l)], r1 = bounds[(size_t)(node + 1) << (L - l)];
+    const float *x = src + (coff + col) * ldn;
+    S *y = dst + (coff + col) * ldn;
+    float f = 1.f;
+    if (scale) {
+        __shared__ float red[32];
+        float mx = 0.f;
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) mx = fmaxf(mx, fabsf(x[i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+            int e = 0;
+            if (m > 0.f) {
+                int E;
+                frexpf(m, &E);          // m = f 2^E, f in [0.5, 1)
+                e = 14 - E;
+            }
+            red[0] = ldexpf(1.f, e);
+            scale[(size_t)node * rp + col] = ldexpf(1.f, -e);
+        }
+        __syncthreads();
+        f = red[0];
+    }
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) y[i] = to_store<S>(x[i] * f);
+}
+
+// Which Gauss-Jordan variant launch_gj picks for matrices up to bmax: registers,
+// shared memory, or the global-memory kernel (the only one that needs GJDesc::work).
+template <typename T>
+bool gj_needs_work(int bmax) {
+    if (bmax <= 128) return false;
+    if (sizeof(T) == 4 && bmax <= 192) return false;
+    return gjs_smem<T>(bmax) > GJS_SMEM_MAX;
 }
 
 template <typename T>
@@ -683,19 +749,10 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
     char *lvl = carve(lvl_max);
     Rec<T> rec{c, Pl};
 
-    // ---- 1. leaf inverses
+    // ---- 1. leaf inverses: computed by hodlr_build (they depend on A only), while
+    // the off-diagonal blocks are being compressed
     T *Kinv = reinterpret_cast<T *>(h->leafinv);
-    {
-        std::vector<GJDesc<T>> gd(nleaf);
-        for (int i = 0; i < nleaf; ++i) {
-            int64_t r0, m;
-            node_range(L, i, r0, m);
-            gd[i] = GJDesc<T>{h->A + r0 * h->lda + r0, h->lda, nullptr, 0,
-                              gjw + (size_t)i * 2 * bmax * bmax, Kinv + (size_t)i * bmax * bmax,
-                              bmax, (int)m};
-        }
-        rec.gj(gd);
-    }
+    (void)gjw;
     // ---- 2. leaf stack: D2 = Kinv_leaf * D (all columns), then copy back
     if (W > 0) {
         rec.zero_(D2, ldn * W);
@@ -818,6 +875,42 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
             rec.gemm(gu, 0, T(-1));
         }
     }
+    // 16-bit copies of V and d for the apply (BF16 / FP16 storage)
+    if constexpr (sizeof(T) == 4) {
+        if (h->store == HODLR_BF16 || h->store == HODLR_FP16) {
+            for (int l = 1; l <= L; ++l) {
+                const int rp = h->lv[l].rp;
+                if (rp == 0) continue;
+                const int64_t coff = h->lv[l].coff;
+                const int nn = 1 << l;
+                const float *Vf = reinterpret_cast<const float *>(h->V);
+                const float *Df = reinterpret_cast<const float *>(h->D);
+                const int64_t *bd = h->d_bounds;
+                if (h->store == HODLR_BF16) {
+                    __nv_bfloat16 *Vq = reinterpret_cast<__nv_bfloat16 *>(h->Vq);
+                    __nv_bfloat16 *Dq = reinterpret_cast<__nv_bfloat16 *>(h->Dq);
+                    Pl->ops.push_back([=](cudaStream_t s) {
+                        quantize_kernel<__nv_bfloat16><<<dim3(nn, rp), 256, 0, s>>>(Vf, Vq, ldn, coff, rp, bd, L, l,
+                                                                                     nullptr);
+                        quantize_kernel<__nv_bfloat16><<<dim3(nn, rp), 256, 0, s>>>(Df, Dq, ldn, coff, rp, bd, L, l,
+                                                                                     nullptr);
+                        HODLR_TRY_CUDA(cudaGetLastError());
+                        return HODLR_OK;
+                    });
+                } else {
+                    __half *Vq = reinterpret_cast<__half *>(h->Vq);
+                    __half *Dq = reinterpret_cast<__half *>(h->Dq);
+                    float *vs = h->vscale[l], *ds = h->dscale[l];
+                    Pl->ops.push_back([=](cudaStream_t s) {
+                        quantize_kernel<__half><<<dim3(nn, rp), 256, 0, s>>>(Vf, Vq, ldn, coff, rp, bd, L, l, vs);
+                        quantize_kernel<__half><<<dim3(nn, rp), 256, 0, s>>>(Df, Dq, ldn, coff, rp, bd, L, l, ds);
+                        HODLR_TRY_CUDA(cudaGetLastError());
+                        return HODLR_OK;
+                    });
+                }
+            }
+        }
+    }
     // one upload of every descriptor (the caller synchronises before factor runs)
     Pl->dbytes = std::max<size_t>(Pl->blob.size(), 256);
     Pl->dblob = reinterpret_cast<char *>(dalloc(c, Pl->dbytes, s));
@@ -856,6 +949,39 @@ template hodlr_status gemm_batched<float>(hodlr_ctx *, const GemmDesc<float> *, 
                                           float, cudaStream_t);
 template hodlr_status gemm_batched<double>(hodlr_ctx *, const GemmDesc<double> *, int, int, int, int, int,
                                            double, cudaStream_t);
+
+namespace {
+
+template <typename T>
+hodlr_status leaf_inverses_typed(hodlr_t *h, cudaStream_t s) {
+    const int L = h->L, nleaf = 1 << L;
+    const int64_t bmax = h->bmax;
+    T *Kinv = reinterpret_cast<T *>(h->leafinv);
+    // work matrices are needed only by the global-memory variant (large leaves)
+    T *work = nullptr;
+    if (gj_needs_work<T>((int)bmax)) {
+        work = reinterpret_cast<T *>(own(h, (size_t)nleaf * 2 * bmax * bmax * sizeof(T), s));
+        if (!work) return HODLR_OUT_OF_MEMORY;
+    }
+    std::vector<GJDesc<T>> gd(nleaf);
+    for (int i = 0; i < nleaf; ++i) {
+        const int64_t r0 = h->bounds[i], m = h->bounds[i + 1] - r0;
+        gd[i] = GJDesc<T>{h->A + r0 * h->lda + r0, h->lda, nullptr, 0,
+                          work ? work + (size_t)i * 2 * bmax * bmax : nullptr, Kinv + (size_t)i * bmax * bmax,
+                          bmax, (int)m};
+    }
+    GJDesc<T> *dd = reinterpret_cast<GJDesc<T> *>(own(h, gd.size() * sizeof(GJDesc<T>), s));
+    if (!dd) return HODLR_OUT_OF_MEMORY;
+    HODLR_TRY_CUDA(cudaMemcpyAsync(dd, gd.data(), gd.size() * sizeof(GJDesc<T>), cudaMemcpyHostToDevice, s));
+    return launch_gj<T>(h->ctx, dd, nleaf, (int)bmax, s);
+}
+
+}  // namespace
+
+hodlr_status leaf_inverses(hodlr_t *h, cudaStream_t s) {
+    if (h->prec == HODLR_FP64) return leaf_inverses_typed<double>(h, s);
+    return leaf_inverses_typed<float>(h, s);
+}
 
 hodlr_status plan_factor(hodlr_t *h, cudaStream_t s) {
     if (h->plan) return HODLR_OK;

@@ -98,7 +98,10 @@ struct hodlr_s {
     int bmax = 0;                     // largest leaf
     std::vector<int64_t> bounds;      // 2^L + 1 leaf boundaries
     int64_t *d_bounds = nullptr;
-    int prec = HODLR_FP32;            // factor / apply precision
+    int prec = HODLR_FP32;            // factorisation arithmetic (FP64 or FP32)
+    int store = HODLR_FP32;           // storage of the streamed factors V, d in the apply
+    void *Vq = nullptr, *Dq = nullptr;   // 16-bit copies of V and d (BF16 / FP16 storage)
+    std::vector<float *> vscale, dscale; // FP16: per level 0..L, [nnodes * rp] dequantisation factors
     int cprec = HODLR_FP32;           // compression precision
     int method = HODLR_ACA;
     double tol = 0.0;
@@ -122,6 +125,8 @@ struct hodlr_s {
     size_t work_bytes = 0;
     // the recorded factorisation (workspace, descriptors, launches)
     hodlr::FactorPlan *plan = nullptr;
+    // events around the last factorisation, read lazily by hodlr_stats_get
+    cudaEvent_t fev[2] = {nullptr, nullptr};
 };
 
 namespace hodlr {
@@ -173,6 +178,8 @@ hodlr_status factor_impl(hodlr_t *h, cudaStream_t s);
 // Record the factorisation's launches and upload its descriptors (stream-ordered
 // on s; the caller synchronises before the first factor_impl).
 hodlr_status plan_factor(hodlr_t *h, cudaStream_t s);
+// Explicit inverses of the leaf blocks of A (stream-ordered; h->leafinv allocated).
+hodlr_status leaf_inverses(hodlr_t *h, cudaStream_t s);
 void free_plan(hodlr_t *h, cudaStream_t s);
 hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s);
 hodlr_status solve_prepare(const hodlr_t *h, int s_rhs, cudaStream_t s);
