@@ -173,6 +173,54 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_kernels(args):
+    """Component timings of one front: each call timed alone (median of reps)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_1403_5337_gb300 as H
+    F, Bh = make_inputs(args.workload, "cuda")
+    A = F.A
+    leaf = WORKLOADS[args.workload]["leaf"]
+    graph = (F.rowptr, F.colind)
+    B = torch.as_tensor(np.ascontiguousarray(Bh.T), device="cuda")
+    ctx = H.Context(0)
+
+    def timed(fn, reps=10):
+        ts = []
+        for i in range(reps + 3):
+            torch.cuda.synchronize()
+            last = i == reps + 2
+            if last:
+                torch.cuda.nvtx.range_push("kernels")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            if last:
+                torch.cuda.nvtx.range_pop()
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1) * 1e3)
+        return statistics.median(ts)
+
+    out = {"workload": args.workload, "precision": args.precision, "method": args.method, "tol": args.tol}
+    out["build_us"] = timed(lambda: H.hodlr_build(ctx, A, leaf, args.tol, args.method, graph=graph,
+                                                  precision=args.precision).close(), 5)
+    h = H.hodlr_build(ctx, A, leaf, args.tol, args.method, graph=graph, precision=args.precision)
+    out["factor_us"] = timed(lambda: H.hodlr_factor(h), 5)
+    X = B.clone()
+    out["apply_us"] = timed(lambda: H.hodlr_solve(h, X))
+    out["matvec_us"] = timed(lambda: H.hodlr_matvec(ctx, A, B))
+    out["gmres_us"] = timed(lambda: H.gmres_solve(ctx, A, B, h, tol=1e-12), 3)
+    _, info = H.gmres_solve(ctx, A, B, h, tol=1e-12)
+    out["iters"] = info.iters.tolist()
+    out["true_relres"] = info.true_relres.tolist()
+    out["ranks_max"] = h.stats()["rank_max"]
+    print(json.dumps(out))
+
+
 def _config(args, F):
     return {"workload": f"{args.workload}: n={F.n} plane front of a {F.nx}x{F.ny}x{F.meta['nz']} lognormal "
                         f"7-point operator, {WORKLOADS[args.workload]['nrhs']} rhs",
@@ -194,9 +242,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--nvtx", action="store_true", help="wrap every timed step in an NVTX range 'bench_step'")
+    ap.add_argument("--kernels", action="store_true",
+                    help="time each component alone (build, factor, apply, matvec, GMRES) with CUDA events; "
+                         "the last repetition of each runs inside an NVTX range 'kernels' for ncu")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernels:
+        return run_kernels(args)
 
     import torch
     import torch.distributed as dist

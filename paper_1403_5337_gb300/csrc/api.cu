@@ -426,6 +426,24 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         for (auto &q : temp) dfree(c, q.first, q.second, st);
         temp.clear();
     };
+    // Row tiles of the fused apply (32 rows, never straddling a leaf) and its
+    // grid-barrier state.
+    {
+        std::vector<int4> tiles;
+        for (int i = 0; i < nleaf; ++i)
+            for (int64_t r = bounds[i]; r < bounds[i + 1]; r += 32)
+                tiles.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(32, bounds[i + 1] - r), 0));
+        int4 *dt = (int4 *)own(h, tiles.size() * sizeof(int4), st);
+        h->d_bar = (unsigned *)own(h, 2 * sizeof(unsigned), st);
+        if (!dt || !h->d_bar) {
+            free_temp();
+            return fail(HODLR_OUT_OF_MEMORY);
+        }
+        cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), st);
+        h->d_tiles = dt;
+        h->ntiles = (int)tiles.size();
+    }
     // The leaf inverses depend on A only: they run on a side stream while the
     // off-diagonal blocks are compressed, and join the caller's stream after.
     h->leafinv = own(h, (size_t)nleaf * bmax * bmax * elem_size(h->prec), st);
@@ -525,6 +543,7 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     h->Wtot = coff;
     const size_t pe = elem_size(h->prec);
     const size_t dvb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * pe;
+    h->U = own(h, dvb, st);
     h->D = own(h, dvb, st);
     h->V = own(h, dvb, st);
     h->Sinv.assign(L, nullptr);
@@ -557,11 +576,12 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
                 }
             }
     }
-    if (!h->D || !h->V || !h->leafinv) {
+    if (!h->U || !h->D || !h->V || !h->leafinv) {
         free_temp();
         return fail(HODLR_OUT_OF_MEMORY);
     }
     if (h->Wtot > 0) {
+        cudaMemsetAsync(h->U, 0, dvb, st);
         cudaMemsetAsync(h->D, 0, dvb, st);
         cudaMemsetAsync(h->V, 0, dvb, st);
     }
@@ -574,7 +594,7 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             node_max = std::max(node_max, m);
         }
         const size_t off = (size_t)lv.coff * h->ldn * pe;
-        char *Dl = (char *)h->D + off, *Vl = (char *)h->V + off;
+        char *Dl = (char *)h->U + off, *Vl = (char *)h->V + off;
         hodlr_status s3 = HODLR_OK;
         if (cprec == HODLR_FP64 && h->prec == HODLR_FP64) {
             s3 = launch_compact<double, double>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
@@ -713,7 +733,7 @@ hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U_or_d, dou
         for (int which = 0; which < 2; ++which) {
             double *dst = which == 0 ? U_or_d : V;
             if (!dst) continue;
-            const void *src = which == 0 ? h->D : h->V;
+            const void *src = which == 0 ? (h->factored ? h->D : h->U) : h->V;
             int blocks = (int)std::min<int64_t>((n * rp + 255) / 256, 4096);
             if (h->prec == HODLR_FP64)
                 to_double_kernel<double><<<blocks, 256, 0, st>>>((const double *)src + lv.coff * h->ldn, h->ldn, tmp, n,

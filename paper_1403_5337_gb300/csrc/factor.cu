@@ -717,8 +717,6 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
     // ---- workspace sizing
     const int64_t bmax = h->bmax;
     size_t need = 0;
-    need += (size_t)nleaf * 2 * bmax * bmax * sizeof(T);      // GJ work (leaves)
-    need += (size_t)ldn * W * sizeof(T);                         // leaf stack output
     size_t lvl_max = 0;
     for (int l = 0; l < L; ++l) {
         const int cch = l + 1;
@@ -744,27 +742,25 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
         wp += (bytes + 255) & ~size_t(255);
         return p;
     };
-    T *gjw = reinterpret_cast<T *>(carve((size_t)nleaf * 2 * bmax * bmax * sizeof(T)));
-    T *D2 = reinterpret_cast<T *>(carve((size_t)ldn * W * sizeof(T)));
     char *lvl = carve(lvl_max);
     Rec<T> rec{c, Pl};
+    const T *U = reinterpret_cast<const T *>(h->U);
 
     // ---- 1. leaf inverses: computed by hodlr_build (they depend on A only), while
     // the off-diagonal blocks are being compressed
     T *Kinv = reinterpret_cast<T *>(h->leafinv);
-    (void)gjw;
-    // ---- 2. leaf stack: D2 = Kinv_leaf * D (all columns), then copy back
+    // ---- 2. leaf stack: D = Kinv_leaf * U (all columns).  U is left intact, so
+    // the factorisation can be repeated.
     if (W > 0) {
-        rec.zero_(D2, ldn * W);
+        rec.zero_(D, ldn * W);
         std::vector<GemmDesc<T>> gd(nleaf);
         for (int i = 0; i < nleaf; ++i) {
             int64_t r0, m;
             node_range(L, i, r0, m);
-            gd[i] = GemmDesc<T>{Kinv + (size_t)i * bmax * bmax, D + r0, D2 + r0, bmax, ldn, ldn,
+            gd[i] = GemmDesc<T>{Kinv + (size_t)i * bmax * bmax, U + r0, D + r0, bmax, ldn, ldn,
                                 (int)m, (int)W, (int)m};
         }
         rec.gemm(gd, 0, T(1));
-        rec.copy(D, D2, ldn * W);
     }
     // ---- 3. levels, bottom-up
     for (int l = L - 1; l >= 0; --l) {

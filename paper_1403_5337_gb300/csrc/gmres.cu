@@ -407,14 +407,6 @@ __global__ void loop_condition_kernel(cudaGraphConditionalHandle handle, const i
     cudaGraphSetConditional(handle, (*nactive > 0 && it < limit) ? 1u : 0u);
 }
 
-__global__ void copy_active_kernel(const double *__restrict__ src, int64_t lds, double *__restrict__ dst, int64_t ldd,
-                                   int64_t n, const int *__restrict__ active) {
-    const int r = blockIdx.y;
-    if (!active[r]) return;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        dst[q + r * ldd] = src[q + r * lds];
-}
-
 }  // namespace
 
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s, const double *Z, int64_t ldz,

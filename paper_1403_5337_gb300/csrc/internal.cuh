@@ -110,7 +110,8 @@ struct hodlr_s {
     std::vector<hodlr::Level> lv;     // index 1..L used
     int64_t ldn = 0;                  // leading dimension of D, V (n rounded up to 32)
     int64_t Wtot = 0;                 // total columns of D, V
-    void *D = nullptr;                // elem[ldn * Wtot]: U, then d after factor
+    void *U = nullptr;                // elem[ldn * Wtot]: the compressed U columns (kept: re-factorable)
+    void *D = nullptr;                // elem[ldn * Wtot]: d = K_node^-1 U_node after factorisation
     void *V = nullptr;                // elem[ldn * Wtot]
     void *leafinv = nullptr;          // elem[2^L * bmax * bmax], column-major per leaf
     std::vector<void *> Sinv;         // level l = 0..L-1: elem[2^l * (2 rp(l+1))^2]
@@ -123,6 +124,11 @@ struct hodlr_s {
     // scratch of the apply
     void *work = nullptr;
     size_t work_bytes = 0;
+    // fused apply: 32-row tiles of the leaves (leaf, first row, rows, 0) and the
+    // grid-barrier counter/generation pair
+    const int4 *d_tiles = nullptr;
+    int ntiles = 0;
+    unsigned *d_bar = nullptr;
     // the recorded factorisation (workspace, descriptors, launches)
     hodlr::FactorPlan *plan = nullptr;
     // events around the last factorisation, read lazily by hodlr_stats_get

@@ -154,6 +154,27 @@ def test_factor_and_solve_fp64(H, ctx, front576):
     h.close()
 
 
+def test_refactor_is_idempotent(H, ctx, front576):
+    """hodlr_factor may be called again on the same compressed matrix (it starts
+    from the stored U every time) and gives the same solve."""
+    F = front576
+    A = _dev(F.A)
+    h = H.hodlr_build(ctx, A, 64, 1e-6, "aca", precision="fp32")
+    b = fg.rhs(F.n, 2, seed=4)
+    outs = []
+    for _ in range(3):
+        H.hodlr_factor(h)
+        X = _dev(b.T)
+        H.hodlr_solve(h, X)
+        outs.append(X.cpu().numpy())
+    ref = outs[0]
+    for o in outs[1:]:
+        assert np.linalg.norm(o - ref) / np.linalg.norm(ref) < 1e-5
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    assert info.converged and np.all(info.iters <= 6)
+    h.close()
+
+
 def test_solve_fp32(H, ctx, front576):
     F = front576
     tree = O.make_tree(F.n, 64, F.bounds)
