@@ -31,6 +31,8 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "time to 1e-12 relative residual per frontal solve"
+# arithmetic of the path per --precision: preconditioner storage + factor, then the FP64 Krylov loop
+DTYPE = {"fp32": "f32+f64", "bf16": "bf16+f32+f64", "fp16": "f16+f32+f64", "fp64": "f64"}
 WORKLOADS = {
     "plane4096": dict(nx=64, ny=64, below=32, above=32, field="lognormal", sigma=0.5, leaf=128, seed=0, nrhs=4),
     "plane576": dict(nx=24, ny=24, below=8, above=8, field="lognormal", sigma=0.5, leaf=64, seed=0, nrhs=1),
@@ -238,7 +240,7 @@ def main():
     ap.add_argument("--workload", default="plane4096", choices=sorted(WORKLOADS))
     ap.add_argument("--method", default="aca", choices=["aca", "bdlr"])
     ap.add_argument("--tol", type=float, default=1e-4)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--nvtx", action="store_true", help="wrap every timed step in an NVTX range 'bench_step'")
@@ -281,6 +283,8 @@ def main():
         h.close()
         return X, info, st
 
+    launches = [0, 0]
+
     def timed(prec, k, w):
         for _ in range(w):
             step(prec)
@@ -290,6 +294,7 @@ def main():
         torch.cuda.synchronize()
         tot = 0.0
         infos = []
+        launches[0] = H.hodlr_launch_count()
         for _ in range(k):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -304,6 +309,7 @@ def main():
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
             infos.append((info, st))
+        launches[1] = H.hodlr_launch_count()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -313,6 +319,7 @@ def main():
     clocks.start()
     total_ms, infos, X = timed(args.precision, args.steps, args.warmup)
     clk = clocks.stop()
+    n_launches = launches[1] - launches[0]
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -325,7 +332,7 @@ def main():
     # ---- the dominant kernels, timed alone with CUDA events on the launching stream
     hbm, _, peak_kind = _peaks()
     comp_ms = statistics.median(s["ms_compress"] for _, s in infos)
-    w = 4 if args.precision == "fp32" else 8
+    w = 8 if args.precision == "fp64" else 4   # compression precision (FP32 below FP64)
     ranks = st["rank_mean"]
     # ACA reads each pivot row/column of A once (FP64) and writes u_k, v_k once:
     # sum over levels of (2^l nodes) * rank * (m + n) * (8 + w), m = n = n/2^l per block.
@@ -410,7 +417,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": _config(args, F),
             "converged": converged, "iters": info.iters.tolist(), "true_relres": info.true_relres.tolist(),
             "ranks_max": st["rank_max"], "ms_compress": comp_ms,
@@ -421,7 +428,7 @@ def main():
             "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": 8 * n * n + 8 * B.numel(),
                     "d2h_bytes_per_step": 8 * B.numel()},
             "fp64_path": compare,
-            "gpu_launches": None,
+            "gpu_launches": n_launches, "gpu_launches_per_step": n_launches / args.steps,
         }
         print(json.dumps(line))
     if world > 1:

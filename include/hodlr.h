@@ -245,6 +245,12 @@ hodlr_status hodlr_destroy(hodlr_t *h);
 const char *hodlr_status_string(hodlr_status s);
 const char *hodlr_last_error(void);
 
+/* Diagnostics (no counterpart in the paper): the number of GPU kernels this
+ * library has launched in the calling process so far, kernels replayed by a
+ * device-side loop of a recorded GMRES iteration included (counted once the
+ * solve returns).  `out` is host memory; never fails unless `out` is NULL. */
+hodlr_status hodlr_launch_count(long long *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -148,7 +148,8 @@ def aca(row, col, m: int, n: int, tol: float, rank_cap: int, dtype=np.float64) -
     scaled vectors are formed and decided in (float64, or float32 for the
     single-precision compression: block entries are rounded to float32 first).
     The dot products are formed in that precision too; the norm recurrence and
-    the stopping test are evaluated in float64."""
+    the stopping test are evaluated in float64, the test in its squared form
+    ||u_k||^2 ||v_k||^2 <= tol^2 ||S_k||_F^2."""
     dt = np.dtype(dtype)
     kmax = min(m, n, rank_cap)
     us, vs = [], []
@@ -182,7 +183,8 @@ def aca(row, col, m: int, n: int, tol: float, rank_cap: int, dtype=np.float64) -
         vs.append(v)
         rows.append(i)
         cols.append(j)
-        if math.sqrt(uu) * math.sqrt(vv) <= tol * math.sqrt(max(norm2, 0.0)):
+        # ||u_k|| ||v_k|| <= tol ||S_k||_F, tested squared (no square roots)
+        if uu * vv <= tol * tol * max(norm2, 0.0):
             break
         if len(us) >= min(m, n):
             break

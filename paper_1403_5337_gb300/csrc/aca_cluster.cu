@@ -6,19 +6,22 @@
 // shared memory (as many columns as fit; later ones stay in global memory), so
 // the k-term residual of a row or column entry is read at shared-memory latency
 // instead of being streamed from L2 by one SM.  Per step:
-//   row pass     r_j = A(i_k, j) - sum_l U(i_k, l) V(j, l) on the CTA's columns,
-//                local argmax -> candidate in shared memory
+//   row pass     r_j = A(i_k, j) - sum_l U(i_k, l) V(j, l) on the CTA's columns
+//                (kept in registers), local argmax -> candidate slot
 //   cluster barrier; every CTA reduces the CL candidates over DSMEM (same order,
-//                so the same pivot everywhere)
+//                so the same pivot everywhere) and starts loading column j_k of A
 //   v_k = r / r(j_k) on the CTA's columns
 //   column pass  u_i = A(i, j_k) - sum_l V(j_k, l) U(i, l) on the CTA's rows,
 //                local argmax over unused rows, partial dot products u_k.u_l and
-//                v_k.v_l over the CTA's slices
-//   cluster barrier; every CTA sums the partials over DSMEM in rank order and
-//                takes the same stop decision
+//                v_k.v_l over the CTA's slices (16-byte shared-memory loads)
+//   cluster barrier; every CTA picks the next row i_{k+1}, starts loading row
+//                i_{k+1} of A and gathering U(i_{k+1}, :), sums the partials over
+//                DSMEM in rank order and takes the same stop decision
 // Candidate and partial-sum slots are double-buffered by step parity, so two
-// cluster barriers per step suffice.  The arithmetic of each residual entry
-// (terms l = 0..k-1, separate round-to-nearest multiply and subtract), the
+// cluster barriers per step suffice.  Pivot candidates are compared in the
+// compression precision (the same argmax as after widening); the norm
+// recurrence and the stopping test are FP64.  The arithmetic of each residual
+// entry (terms l = 0..k-1, separate round-to-nearest multiply and subtract), the
 // tie-breaking (lowest index) and the zero-row rule are those of the
 // single-block formulation.
 #include <cooperative_groups.h>
@@ -37,58 +40,32 @@ namespace {
 constexpr int CT = 256;            // threads per CTA
 constexpr int CW = CT / 32;
 constexpr int ACA_CAP = 1024;      // maximum rank (staging width)
+constexpr int MAX_CL = 16;         // largest cluster
 
+// A pivot candidate in the compression precision T: comparing |r| in T picks the
+// same entry as comparing it after a widening conversion, and keeps the
+// reductions off GB300's narrow FP64 pipe.
+template <typename T>
 struct Cand {
-    double a;     // |value|, -1 = none
-    double v;     // signed value
-    int idx;      // block-local index, INT_MAX = none
+    T a;      // |value|, -1 = none
+    T v;      // signed value
+    int idx;  // block-local index, INT_MAX = none
     int pad;
 };
 
-__device__ __forceinline__ bool better(double a, int i, double ba, int bi) {
+template <typename T>
+__device__ __forceinline__ bool better(T a, int i, T ba, int bi) {
     return a > ba || (a == ba && i < bi);
 }
 
-// CTA-wide argmax of (a, idx, v); the result is returned in every thread.
-__device__ Cand cta_argmax(double a, int idx, double v, Cand *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// xor-shuffle argmax inside groups of W lanes: every lane of a group ends with
+// the group's best (largest |value|, lowest index on ties).
+template <typename T, int W>
+__device__ __forceinline__ void shfl_argmax(T &a, T &v, int &idx) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double oa = __shfl_down_sync(0xffffffffu, a, o);
-        const int oi = __shfl_down_sync(0xffffffffu, idx, o);
-        const double ov = __shfl_down_sync(0xffffffffu, v, o);
-        if (better(oa, oi, a, idx)) {
-            a = oa;
-            idx = oi;
-            v = ov;
-        }
-    }
-    if (lane == 0) red[warp] = Cand{a, v, idx, 0};
-    __syncthreads();
-    Cand best = red[0];
-    for (int w = 1; w < CW; ++w)
-        if (better(red[w].a, red[w].idx, best.a, best.idx)) best = red[w];
-    __syncthreads();
-    return best;
-}
-
-// Best of the CL cluster candidates slot[which]: lane q of every warp loads rank
-// q's candidate over DSMEM, then an xor-shuffle argmax (ties -> lowest index)
-// leaves the same result in every thread.
-__device__ __forceinline__ Cand cluster_best(cg::cluster_group &cl, Cand *slot, int which, int CL) {
-    const int lane = threadIdx.x & 31;
-    double a = -1.0, v = 0.0;
-    int idx = INT_MAX;
-    if (lane < CL) {
-        const Cand o = cl.map_shared_rank(slot, lane)[which];
-        a = o.a;
-        v = o.v;
-        idx = o.idx;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double oa = __shfl_xor_sync(0xffffffffu, a, o);
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = W / 2; o > 0; o >>= 1) {
+        const T oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         if (better(oa, oi, a, idx)) {
             a = oa;
@@ -96,7 +73,56 @@ __device__ __forceinline__ Cand cluster_best(cg::cluster_group &cl, Cand *slot, 
             idx = oi;
         }
     }
-    return Cand{a, v, idx, 0};
+}
+
+template <typename T>
+__device__ __forceinline__ Cand<T> lane0(T a, T v, int idx) {
+    return Cand<T>{__shfl_sync(0xffffffffu, a, 0), __shfl_sync(0xffffffffu, v, 0),
+                   __shfl_sync(0xffffffffu, idx, 0), 0};
+}
+
+// CTA-wide argmax; the result is returned in every thread.  One barrier: the
+// caller keeps consecutive uses of the same `red` apart by another barrier.
+template <typename T>
+__device__ Cand<T> cta_argmax(T a, int idx, T v, Cand<T> *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    shfl_argmax<T, 32>(a, v, idx);
+    if (lane == 0) red[warp] = Cand<T>{a, v, idx, 0};
+    __syncthreads();
+    T ra = T(-1), rv = T(0);
+    int ri = INT_MAX;
+    if (lane < CW) {
+        const Cand<T> o = red[lane];
+        ra = o.a;
+        rv = o.v;
+        ri = o.idx;
+    }
+    shfl_argmax<T, CW>(ra, rv, ri);
+    return lane0(ra, rv, ri);
+}
+
+// Candidate exchange: every CTA posts its candidate into slot c of every CTA
+// of the cluster (remote shared-memory stores, ordered by the cluster barrier
+// that follows), so that after the barrier each CTA reduces the CL candidates
+// from its own shared memory, in the same order everywhere.
+template <typename T>
+__device__ __forceinline__ void post_cand(cg::cluster_group &cl, Cand<T> *slots, int c, int CL, const Cand<T> &v) {
+    const int t = threadIdx.x;
+    if (t < CL) cl.map_shared_rank(slots, t)[c] = v;
+}
+template <typename T>
+__device__ __forceinline__ Cand<T> best_of_slots(const Cand<T> *slots, int CL) {
+    const int lane = threadIdx.x & 31;
+    T a = T(-1), v = T(0);
+    int idx = INT_MAX;
+    if (lane < CL) {
+        const Cand<T> o = slots[lane];
+        a = o.a;
+        v = o.v;
+        idx = o.idx;
+    }
+    shfl_argmax<T, MAX_CL>(a, v, idx);
+    return lane0(a, v, idx);
 }
 
 template <typename T>
@@ -106,18 +132,98 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Dot product of two shared-memory columns of nv 16-byte groups (zero-padded).
+__device__ __forceinline__ float vdot(const float *x, const float *y, int nv) {
+    const float4 *x4 = reinterpret_cast<const float4 *>(x), *y4 = reinterpret_cast<const float4 *>(y);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int q = 0; q < nv; ++q) {
+        const float4 a = x4[q], b = y4[q];
+        s0 = fmaf(a.x, b.x, s0);
+        s1 = fmaf(a.y, b.y, s1);
+        s2 = fmaf(a.z, b.z, s2);
+        s3 = fmaf(a.w, b.w, s3);
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+__device__ __forceinline__ double vdot(const double *x, const double *y, int nv) {
+    const double2 *x2 = reinterpret_cast<const double2 *>(x), *y2 = reinterpret_cast<const double2 *>(y);
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q < nv; ++q) {
+        const double2 a = x2[q], b = y2[q];
+        s0 = fma(a.x, b.x, s0);
+        s1 = fma(a.y, b.y, s1);
+    }
+    return s0 + s1;
+}
+
+// Sum of the exact products su sv over the cross terms.  FP32 dots: the products
+// are formed exactly (TwoProduct) and summed as unevaluated float pairs
+// (TwoSum), so the sum carries ~2^-48 relative error without FP64 arithmetic;
+// FP64 dots: plain FP64.
 template <typename T>
+struct CrossAcc;
+template <>
+struct CrossAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_pair(float p, float e) {
+        const float s = hi + p;
+        const float bp = s - hi;
+        const float err = (hi - (s - bp)) + (p - bp);
+        hi = s;
+        lo += err + e;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = a * b;
+        add_pair(p, fmaf(a, b, -p));
+    }
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            add_pair(oh, ol);
+        }
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct CrossAcc<double> {
+    double hi = 0.0;
+    __device__ __forceinline__ void add_pair(double p, double e) { hi += p + e; }
+    __device__ __forceinline__ void add_prod(double a, double b) { hi += a * b; }
+    __device__ __forceinline__ void warp_reduce() { hi = warp_sum(hi); }
+    __device__ __forceinline__ double value() const { return hi; }
+};
+
+// Padded stride of a shared-memory column slice of m entries: a whole number of
+// 16-byte groups, and an odd number of them, so that eight threads reading
+// eight consecutive columns with 16-byte loads hit distinct banks.
+template <typename T>
+__host__ __device__ __forceinline__ int64_t slice_stride(int64_t m) {
+    constexpr int64_t VW = 16 / sizeof(T);
+    int64_t q = (m + VW - 1) / VW;
+    if ((q & 1) == 0) ++q;
+    return q * VW;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ size_t fixed_smem_bytes() {
+    return sizeof(T) * (4 * (ACA_CAP + 1) + 2 * ACA_CAP) + 16;
+}
+
+template <typename T, int NPT>
 __global__ void __launch_bounds__(CT, 1)
     aca_cluster_kernel(const double *__restrict__ A, int64_t lda, int sym, const AcaBlockDesc *__restrict__ blocks,
-                       double tol, int kcs, int *status) {
+                       double tol2, int kcs, int *status) {
     cg::cluster_group cl = cg::this_cluster();
     const int CL = (int)cl.num_blocks();
     const int c = (int)cl.block_rank();
     const AcaBlockDesc B = blocks[blockIdx.x / CL];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int VW = 16 / sizeof(T);
     const int64_t m = B.m, nc = B.nc, ld = B.ld;
     const int64_t mr = (m + CL - 1) / CL, nr = (nc + CL - 1) / CL;
-    const int64_t smr = mr + 1, snr = nr + 1;   // padded shared-memory strides (no bank conflicts)
+    const int64_t smr = slice_stride<T>(mr), snr = slice_stride<T>(nr);
     const int64_t i0 = std::min<int64_t>(m, c * mr), i1 = std::min<int64_t>(m, i0 + mr);
     const int64_t j0 = std::min<int64_t>(nc, c * nr), j1 = std::min<int64_t>(nc, j0 + nr);
     const int64_t mn = m < nc ? m : nc;
@@ -125,26 +231,66 @@ __global__ void __launch_bounds__(CT, 1)
     T *Ug = reinterpret_cast<T *>(B.U) + B.r0;   // Ug[l * ld + i], i block-local row
     T *Vg = reinterpret_cast<T *>(B.V) + B.c0;   // Vg[l * ld + j]
 
-    // shared memory: 8-byte-aligned parts first, then the T arrays, then flags
+    // shared memory: candidate slots, partial dots, the pivot row/column of U/V,
+    // the U and V slices, the used-row flags
     extern __shared__ __align__(16) unsigned char smem[];
-    double *tot = reinterpret_cast<double *>(smem);                  // [2 (ACA_CAP + 1)] summed dots
-    Cand *slot = reinterpret_cast<Cand *>(tot + 2 * (ACA_CAP + 1));  // [2 parities][row, col, free]
-    T *dots = reinterpret_cast<T *>(slot + 6);                       // [2][2 (ACA_CAP + 1)] partial dots
-    T *pu = dots + 4 * (ACA_CAP + 1);                                // U(i_k, 0..k-1)
-    T *pv = pu + ACA_CAP;                                            // V(j_k, 0..k-1)
-    T *Us = pv + ACA_CAP;                                            // [kcs][smr]
-    T *Vs = Us + (size_t)kcs * smr;                                  // [kcs][snr]
-    unsigned char *used = reinterpret_cast<unsigned char *>(Vs + (size_t)kcs * snr);  // [mr]
-    __shared__ Cand red[CW];
-    __shared__ double s_norm2;
+    T *dots = reinterpret_cast<T *>(smem);                                         // [2][2 (ACA_CAP + 1)]
+    T *pu = dots + 4 * (ACA_CAP + 1);                                              // U(i_k, 0..k-1)
+    T *pv = pu + ACA_CAP;                                                          // V(j_k, 0..k-1)
+    T *Us = pv + ACA_CAP;                                                          // [kcs][smr]
+    T *Vs = Us + (size_t)kcs * smr;                                                // [kcs][snr]
+    unsigned char *used = reinterpret_cast<unsigned char *>(Vs + (size_t)kcs * snr);   // [mr]
+    __shared__ Cand<T> slots[2][3][MAX_CL];   // [parity][row, col, free row][posting CTA]
+    __shared__ Cand<T> red[2][CW];
+    __shared__ float xr_hi[CW], xr_lo[CW];
+    __shared__ double xr_d[CW];
+    __shared__ double s_norm2, s_uu, s_vv;
     __shared__ int s_i, s_stop;
 
-    for (int64_t i = tid; i < mr; i += CT) used[i] = 0;
+    for (int64_t e = tid; e < (int64_t)kcs * (smr + snr); e += CT) Us[e] = T(0);
+    for (int64_t q = tid; q < mr; q += CT) used[q] = 0;
     if (tid == 0) {
         s_norm2 = 0.0;
         s_i = 0;
         s_stop = 0;
     }
+
+    // A entries of the next row pass and of the current column pass, loaded into
+    // registers as soon as the pivot index is known (thread tid owns the slice
+    // entries tid + t CT, t < NPT)
+    double arow_pf[NPT], acol_pf[NPT];
+    auto load_row = [&](int ir) {
+        const double *arow = A + (B.r0 + ir) * lda + B.c0;
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            const int64_t j = j0 + tid + (int64_t)t * CT;
+            arow_pf[t] = (j < j1) ? __ldg(arow + j) : 0.0;
+        }
+    };
+    auto load_col = [&](int jc) {
+        const double *acol;
+        int64_t astr;
+        if (sym) {
+            acol = A + (B.c0 + jc) * lda + B.r0;
+            astr = 1;
+        } else {
+            acol = A + B.r0 * lda + B.c0 + jc;
+            astr = lda;
+        }
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            const int64_t q = i0 + tid + (int64_t)t * CT;
+            acol_pf[t] = (q < i1) ? __ldg(acol + q * astr) : 0.0;
+        }
+    };
+    // U(ir, l), l < kk: from the shared-memory slice of the CTA that owns row ir
+    auto gather_pu = [&](int ir, int kk) {
+        const int co = (int)(ir / mr);
+        const int64_t li = ir - (int64_t)co * mr;
+        const T *Uo = cl.map_shared_rank(Us, co);
+        for (int l = tid; l < kk; l += CT) pu[l] = (l < kcs) ? Uo[(size_t)l * smr + li] : Ug[(int64_t)l * ld + ir];
+    };
+    load_row(0);
     __syncthreads();
     cl.sync();
 
@@ -152,69 +298,73 @@ __global__ void __launch_bounds__(CT, 1)
     while (k < kmax) {
         const int par = k & 1;
         const int i = s_i;
-        {
-            // U(i_k, l): from the shared-memory slice of the CTA that owns row i_k
-            const int co = (int)(i / mr);
-            const int64_t li = i - (int64_t)co * mr;
-            const T *Uo = cl.map_shared_rank(Us, co);
-            for (int l = tid; l < k; l += CT) pu[l] = (l < kcs) ? Uo[(size_t)l * smr + li] : Ug[(int64_t)l * ld + i];
-        }
-        __syncthreads();
-        // ---- row pass on own columns -> v_k (unscaled)
+        // ---- row pass on own columns -> v_k (unscaled, kept in registers); U(i_k, :)
+        // was gathered into pu at the end of the previous step
         const int kin = k < kcs ? k : kcs;
-        double ba = -1.0, bv = 0.0;
+        T ba = T(-1), bv = T(0);
         int bi = INT_MAX;
-        const double *arow = A + (B.r0 + i) * lda + B.c0;
-        for (int64_t j = j0 + tid; j < j1; j += CT) {
-            const int64_t jl = j - j0;
-            T r = dev::from_double<T>(arow[j]);
-            int l = 0;
+        T rreg[NPT];
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            const int64_t j = j0 + tid + (int64_t)t * CT;
+            T r = T(0);
+            if (j < j1) {
+                const int64_t jl = j - j0;
+                r = dev::from_double<T>(arow_pf[t]);
+                int l = 0;
 #pragma unroll 8
-            for (; l < kin; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vs[(size_t)l * snr + jl]));
-            for (; l < k; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vg[(int64_t)l * ld + j]));
-            if (k < kcs) Vs[(size_t)k * snr + jl] = r;
-            Vg[(int64_t)k * ld + j] = r;
-            const double a = fabs((double)r);
-            if (a != a) atomicOr(status, ST_NONFINITE);
-            if (a > ba) {
-                ba = a;
-                bi = (int)j;
-                bv = (double)r;
+                for (; l < kin; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vs[(size_t)l * snr + jl]));
+                for (; l < k; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vg[(int64_t)l * ld + j]));
+                const T a = fabs(r);
+                if (a != a) atomicOr(status, ST_NONFINITE);
+                if (a > ba) {
+                    ba = a;
+                    bi = (int)j;
+                    bv = r;
+                }
             }
+            rreg[t] = r;
         }
-        Cand cr = cta_argmax(ba, bi, bv, red);
-        if (tid == 0) slot[par * 3 + 0] = cr;
+        const Cand<T> cr = cta_argmax(ba, bi, bv, red[0]);
+        post_cand(cl, &slots[par][0][0], c, CL, cr);
         cl.sync();
-        const Cand best = cluster_best(cl, slot, par * 3 + 0, CL);
+        const Cand<T> best = best_of_slots(&slots[par][0][0], CL);
         const int jk = best.idx;
-        const T piv = (T)best.v;
+        const T piv = best.v;
+        const bool have = !(jk == INT_MAX || piv == T(0));
+        if (have) load_col(jk);
         // the owner of row i marks it used
         if (i >= i0 && i < i1 && tid == 0) used[i - i0] = 1;
-        __syncthreads();
-        if (jk == INT_MAX || piv == T(0)) {
+        if (!have) {
             // exhausted row: the lowest unused row of the whole block, if any
-            double fa = -1.0;
+            __syncthreads();
+            T fa = T(-1);
             int fi = INT_MAX;
             for (int64_t q = i0 + tid; q < i1; q += CT)
-                if (!used[q - i0] && fa < 0.0) {
-                    fa = 0.0;
+                if (!used[q - i0] && fa < T(0)) {
+                    fa = T(0);
                     fi = (int)q;
                 }
-            Cand cf = cta_argmax(fa, fi, 0.0, red);
-            if (tid == 0) slot[par * 3 + 2] = cf;
+            const Cand<T> cf = cta_argmax(fa, fi, T(0), red[1]);
+            post_cand(cl, &slots[par][2][0], c, CL, cf);
             cl.sync();
-            const Cand bf = cluster_best(cl, slot, par * 3 + 2, CL);
-            if (bf.a < 0.0) break;
+            const Cand<T> bf = best_of_slots(&slots[par][2][0], CL);
+            if (bf.a < T(0)) break;
+            load_row(bf.idx);
+            gather_pu(bf.idx, k);
             if (tid == 0) s_i = bf.idx;
             __syncthreads();
             continue;
         }
-        // ---- scale own columns of v_k
-        for (int64_t j = j0 + tid; j < j1; j += CT) {
-            const int64_t jl = j - j0;
-            const T v = dev::div_rn(Vg[(int64_t)k * ld + j], piv);
-            if (k < kcs) Vs[(size_t)k * snr + jl] = v;
-            Vg[(int64_t)k * ld + j] = v;
+        // ---- v_k = r / r(j_k) on own columns
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            const int64_t j = j0 + tid + (int64_t)t * CT;
+            if (j < j1) {
+                const T v = dev::div_rn(rreg[t], piv);
+                if (k < kcs) Vs[(size_t)k * snr + (j - j0)] = v;
+                Vg[(int64_t)k * ld + j] = v;
+            }
         }
         // V(j_k, l) for l < k: written in earlier steps by the owner of column j_k
         {
@@ -225,64 +375,43 @@ __global__ void __launch_bounds__(CT, 1)
         }
         __syncthreads();
         // ---- column pass on own rows -> u_k
-        const double *acol;
-        int64_t astr;
-        if (sym) {
-            acol = A + (B.c0 + jk) * lda + B.r0;
-            astr = 1;
-        } else {
-            acol = A + B.r0 * lda + B.c0 + jk;
-            astr = lda;
-        }
-        double ca = -1.0, cv = 0.0;
+        T ca = T(-1), cvv = T(0);
         int ci = INT_MAX;
-        for (int64_t q = i0 + tid; q < i1; q += CT) {
-            const int64_t ql = q - i0;
-            T u = dev::from_double<T>(acol[q * astr]);
-            int l = 0;
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            const int64_t q = i0 + tid + (int64_t)t * CT;
+            if (q < i1) {
+                const int64_t ql = q - i0;
+                T u = dev::from_double<T>(acol_pf[t]);
+                int l = 0;
 #pragma unroll 8
-            for (; l < kin; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Us[(size_t)l * smr + ql]));
-            for (; l < k; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Ug[(int64_t)l * ld + q]));
-            if (k < kcs) Us[(size_t)k * smr + ql] = u;
-            Ug[(int64_t)k * ld + q] = u;
-            if (u != u) atomicOr(status, ST_NONFINITE);
-            if (!used[ql]) {
-                const double a = fabs((double)u);
-                if (a > ca) {
-                    ca = a;
-                    ci = (int)q;
-                    cv = (double)u;
+                for (; l < kin; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Us[(size_t)l * smr + ql]));
+                for (; l < k; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Ug[(int64_t)l * ld + q]));
+                if (k < kcs) Us[(size_t)k * smr + ql] = u;
+                Ug[(int64_t)k * ld + q] = u;
+                if (u != u) atomicOr(status, ST_NONFINITE);
+                if (!used[ql]) {
+                    const T a = fabs(u);
+                    if (a > ca) {
+                        ca = a;
+                        ci = (int)q;
+                        cvv = u;
+                    }
                 }
             }
         }
-        Cand cc = cta_argmax(ca, ci, cv, red);
-        // ---- partial dots over own slices, l = 0..k: one thread per l runs down the
-        // slice (padded strides keep the lanes on distinct banks); columns beyond
-        // the shared-memory capacity use one warp per l over global memory
+        // (its barrier also publishes column k of the U slice to the dots below)
+        const Cand<T> cc = cta_argmax(ca, ci, cvv, red[1]);
+        // ---- partial dots u_k.u_l and v_k.v_l (l = 0..k) over own slices
         T *dp = dots + (size_t)par * 2 * (ACA_CAP + 1);
         if (k < kcs) {
-            const int64_t nrow = i1 - i0, ncol = j1 - j0;
-            const T *uk = Us + (size_t)k * smr;
-            const T *vk = Vs + (size_t)k * snr;
-            for (int l = tid; l <= k; l += CT) {
-                const T *ul = Us + (size_t)l * smr;
-                const T *vl = Vs + (size_t)l * snr;
-                // four interleaved partial sums (fixed combination order)
-                T su[4] = {T(0), T(0), T(0), T(0)}, sv[4] = {T(0), T(0), T(0), T(0)};
-                int64_t q = 0;
-                for (; q + 4 <= nrow; q += 4) {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) su[t] = fma(ul[q + t], uk[q + t], su[t]);
-                }
-                for (; q < nrow; ++q) su[0] = fma(ul[q], uk[q], su[0]);
-                q = 0;
-                for (; q + 4 <= ncol; q += 4) {
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) sv[t] = fma(vl[q + t], vk[q + t], sv[t]);
-                }
-                for (; q < ncol; ++q) sv[0] = fma(vl[q], vk[q], sv[0]);
-                dp[l] = (su[0] + su[1]) + (su[2] + su[3]);
-                dp[ACA_CAP + 1 + l] = (sv[0] + sv[1]) + (sv[2] + sv[3]);
+            const int nvr = (int)((i1 - i0 + VW - 1) / VW), nvc = (int)((j1 - j0 + VW - 1) / VW);
+            for (int it = tid; it < 2 * (k + 1); it += CT) {
+                const bool isu = it <= k;
+                const int l = isu ? it : it - (k + 1);
+                const T d = isu ? vdot(Us + (size_t)l * smr, Us + (size_t)k * smr, nvr)
+                                : vdot(Vs + (size_t)l * snr, Vs + (size_t)k * snr, nvc);
+                dp[(isu ? 0 : ACA_CAP + 1) + l] = d;
             }
         } else {
             for (int l = warp; l <= k; l += CW) {
@@ -297,42 +426,68 @@ __global__ void __launch_bounds__(CT, 1)
                 }
             }
         }
-        if (tid == 0) slot[par * 3 + 1] = cc;
-        __syncthreads();
+        post_cand(cl, &slots[par][1][0], c, CL, cc);
         cl.sync();
         // ---- cluster-wide: next row, dot products (rank order), stop decision
-        const Cand bc = cluster_best(cl, slot, par * 3 + 1, CL);
+        const Cand<T> bc = best_of_slots(&slots[par][1][0], CL);
+        if (bc.a >= T(0)) {
+            load_row(bc.idx);          // the next pivot row and its U entries, while the stop test is made
+            gather_pu(bc.idx, k + 1);
+        }
+        CrossAcc<T> xacc;
         for (int l = tid; l <= k; l += CT) {
+            T pu_[MAX_CL], pv_[MAX_CL];
+#pragma unroll
+            for (int q = 0; q < MAX_CL; ++q)
+                if (q < CL) {
+                    const T *rp = cl.map_shared_rank(dots, q) + (size_t)par * 2 * (ACA_CAP + 1);
+                    pu_[q] = rp[l];
+                    pv_[q] = rp[ACA_CAP + 1 + l];
+                }
             T su = T(0), sv = T(0);
-#pragma unroll 4
-            for (int q = 0; q < CL; ++q) {
-                const T *rp = cl.map_shared_rank(dots, q) + (size_t)par * 2 * (ACA_CAP + 1);
-                su += rp[l];
-                sv += rp[ACA_CAP + 1 + l];
+#pragma unroll
+            for (int q = 0; q < MAX_CL; ++q)
+                if (q < CL) {
+                    su += pu_[q];
+                    sv += pv_[q];
+                }
+            if (l < k) {
+                xacc.add_prod(su, sv);
+            } else {
+                s_uu = (double)su;
+                s_vv = (double)sv;
             }
-            tot[l] = (double)su;
-            tot[ACA_CAP + 1 + l] = (double)sv;
+        }
+        xacc.warp_reduce();
+        if (lane == 0) {
+            if constexpr (sizeof(T) == 4) {
+                xr_hi[warp] = (float)xacc.hi;
+                xr_lo[warp] = (float)xacc.lo;
+            } else {
+                xr_d[warp] = (double)xacc.hi;
+            }
         }
         __syncthreads();
-        // cross term sum_{l<k} (u_k.u_l)(v_k.v_l): lane-strided partial sums, then a
-        // fixed xor-shuffle tree (the same order in every CTA of the cluster)
-        double cross = 0.0;
-        if (warp == 0) {
-            for (int l = lane; l < k; l += 32) cross += tot[l] * tot[ACA_CAP + 1 + l];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cross += __shfl_xor_sync(0xffffffffu, cross, o);
-        }
         if (tid == 0) {
-            const double uu = tot[k], vv = tot[ACA_CAP + 1 + k];
-            s_norm2 = s_norm2 + 2.0 * cross + uu * vv;
+            CrossAcc<T> tot;
+#pragma unroll
+            for (int w = 0; w < CW; ++w) {
+                if constexpr (sizeof(T) == 4)
+                    tot.add_pair(xr_hi[w], xr_lo[w]);
+                else
+                    tot.add_pair(xr_d[w], 0.0);
+            }
+            const double cross = tot.value(), uu = s_uu, vv = s_vv;
+            // ||S_k||^2 = ||S_{k-1}||^2 + 2 cross + ||u_k||^2 ||v_k||^2, evaluated left to right
+            s_norm2 = __dadd_rn(__dadd_rn(s_norm2, __dmul_rn(2.0, cross)), __dmul_rn(uu, vv));
             if (c == 0) {
                 B.prow[k] = i;
                 B.pcol[k] = jk;
             }
             const double nrm = s_norm2 > 0.0 ? s_norm2 : 0.0;
-            int stop = (sqrt(uu) * sqrt(vv) <= tol * sqrt(nrm));
+            int stop = (__dmul_rn(uu, vv) <= __dmul_rn(tol2, nrm));   // ||u|| ||v|| <= tol ||S||, squared
             if ((int64_t)(k + 1) >= mn) stop = 1;
-            if (bc.a < 0.0) stop = 1;   // every row used
+            if (bc.a < T(0)) stop = 1;   // every row used
             s_stop = stop;
             s_i = bc.idx;
         }
@@ -350,22 +505,18 @@ __global__ void __launch_bounds__(CT, 1)
 
 constexpr size_t SMEM_BUDGET = 220 * 1024;
 
-template <typename T>
-size_t fixed_smem() {
-    return sizeof(T) * (2 * ACA_CAP + 4 * (ACA_CAP + 1)) + sizeof(double) * 2 * (ACA_CAP + 1) + sizeof(Cand) * 6 + 16;
-}
-
-template <typename T>
-hodlr_status launch_level(hodlr_ctx *c, const double *A, int64_t lda, int sym, const AcaBlockDesc *d_blocks,
-                          int nblocks, int CL, int64_t mr, int64_t nr, double tol, cudaStream_t s) {
-    const size_t fixed = fixed_smem<T>() + (size_t)mr + 16;
+template <typename T, int NPT>
+hodlr_status launch_level_npt(hodlr_ctx *c, const double *A, int64_t lda, int sym, const AcaBlockDesc *d_blocks,
+                              int nblocks, int CL, int64_t mr, int64_t nr, double tol, cudaStream_t s) {
+    const int64_t smr = slice_stride<T>(mr), snr = slice_stride<T>(nr);
+    const size_t fixed = fixed_smem_bytes<T>() + (size_t)mr + 16;
     int kcs = 0;
     if (fixed < SMEM_BUDGET)
-        kcs = (int)std::min<size_t>(ACA_CAP, (SMEM_BUDGET - fixed) / ((mr + nr + 2) * sizeof(T)));
-    const size_t sm = fixed + (size_t)kcs * (mr + nr + 2) * sizeof(T);
-    HODLR_TRY_CUDA(cudaFuncSetAttribute(aca_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        kcs = (int)std::min<size_t>(ACA_CAP, (SMEM_BUDGET - fixed) / ((smr + snr) * sizeof(T)));
+    const size_t sm = fixed + (size_t)kcs * (smr + snr) * sizeof(T);
+    HODLR_TRY_CUDA(cudaFuncSetAttribute(aca_cluster_kernel<T, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (CL > 8)
-        HODLR_TRY_CUDA(cudaFuncSetAttribute(aca_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        HODLR_TRY_CUDA(cudaFuncSetAttribute(aca_cluster_kernel<T, NPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nblocks * CL));
     cfg.blockDim = dim3(CT);
@@ -378,8 +529,24 @@ hodlr_status launch_level(hodlr_ctx *c, const double *A, int64_t lda, int sym, c
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, aca_cluster_kernel<T>, A, lda, sym, d_blocks, tol, kcs, c->d_status));
+    HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, aca_cluster_kernel<T, NPT>, A, lda, sym, d_blocks, tol * tol, kcs, c->d_status));
+    note_launch();
     return HODLR_OK;
+}
+
+// Slices of up to NPT * CT rows (columns) per CTA: every thread keeps NPT
+// entries of the row and column passes in registers.
+template <typename T>
+hodlr_status launch_level(hodlr_ctx *c, const double *A, int64_t lda, int sym, const AcaBlockDesc *d_blocks,
+                          int nblocks, int CL, int64_t mr, int64_t nr, double tol, cudaStream_t s) {
+    const int64_t w = std::max(mr, nr);
+    if (w <= CT) return launch_level_npt<T, 1>(c, A, lda, sym, d_blocks, nblocks, CL, mr, nr, tol, s);
+    if (w <= 2 * CT) return launch_level_npt<T, 2>(c, A, lda, sym, d_blocks, nblocks, CL, mr, nr, tol, s);
+    if (w <= 4 * CT) return launch_level_npt<T, 4>(c, A, lda, sym, d_blocks, nblocks, CL, mr, nr, tol, s);
+    if (w <= 8 * CT) return launch_level_npt<T, 8>(c, A, lda, sym, d_blocks, nblocks, CL, mr, nr, tol, s);
+    set_error("ACA: off-diagonal blocks of %lld rows exceed the %d-row limit of one cluster",
+              (long long)w * CL, 8 * CT * CL);
+    return HODLR_INVALID_ARG;
 }
 
 }  // namespace

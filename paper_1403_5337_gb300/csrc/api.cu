@@ -1,6 +1,7 @@
 // C ABI of libhodlr: contexts, HODLR construction (tree, compression staging,
 // rank compaction), factor / solve entry points, statistics and export.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -19,6 +20,19 @@ void set_error(const char *fmt, ...) {
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
 }
+
+static std::atomic<long long> g_launches{0};
+static thread_local LaunchCapture *t_capture = nullptr;
+
+void note_launch(long long k) {
+    if (t_capture)
+        t_capture->captured += k;
+    else
+        g_launches.fetch_add(k, std::memory_order_relaxed);
+}
+long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
+LaunchCapture::LaunchCapture() : prev(t_capture) { t_capture = this; }
+LaunchCapture::~LaunchCapture() { t_capture = prev; }
 
 hodlr_status status_from_word(int w) {
     if (w & ST_NONFINITE) return HODLR_NONFINITE_INPUT;
@@ -116,6 +130,7 @@ hodlr_status launch_compact(const void *src, int64_t lds, void *dst, int64_t ldd
     // src/dst given as the U pair: U(node rows) uses rank(node)
     compact_kernel<S, D><<<grid, 256, 0, s>>>(reinterpret_cast<const S *>(src), lds, reinterpret_cast<D *>(dst), ldd,
                                               bounds, L, l, ranks, rp, 0);
+    note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
 }
@@ -127,6 +142,7 @@ hodlr_status launch_compact_v(const void *src, int64_t lds, void *dst, int64_t l
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((node_max + 255) / 256, 64)), rp, 1u << l);
     compact_kernel<S, D><<<grid, 256, 0, s>>>(reinterpret_cast<const S *>(src), lds, reinterpret_cast<D *>(dst), ldd,
                                               bounds, L, l, ranks, rp, 1);
+    note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
 }
@@ -163,6 +179,12 @@ const char *hodlr_status_string(hodlr_status s) {
 }
 
 const char *hodlr_last_error(void) { return g_err; }
+
+hodlr_status hodlr_launch_count(long long *out) {
+    if (!out) return HODLR_INVALID_ARG;
+    *out = hodlr::launch_total();
+    return HODLR_OK;
+}
 
 void hodlr_opts_default(hodlr_opts *o) {
     if (!o) return;
@@ -426,21 +448,26 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         for (auto &q : temp) dfree(c, q.first, q.second, st);
         temp.clear();
     };
-    // Row tiles of the fused apply (32 rows, never straddling a leaf) and its
-    // grid-barrier state.
+    // Row tiles of the fused apply (32 rows, never straddling a leaf) and the
+    // first tile of every leaf.
     {
         std::vector<int4> tiles;
-        for (int i = 0; i < nleaf; ++i)
+        std::vector<int> first(nleaf + 1);
+        for (int i = 0; i < nleaf; ++i) {
+            first[i] = (int)tiles.size();
             for (int64_t r = bounds[i]; r < bounds[i + 1]; r += 32)
                 tiles.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(32, bounds[i + 1] - r), 0));
-        int4 *dt = (int4 *)own(h, tiles.size() * sizeof(int4), st);
-        h->d_bar = (unsigned *)own(h, 2 * sizeof(unsigned), st);
-        if (!dt || !h->d_bar) {
+        }
+        first[nleaf] = (int)tiles.size();
+        int4 *dt = (int4 *)own(h, std::max<size_t>(tiles.size(), 1) * sizeof(int4), st);
+        h->d_tile_first = (int *)own(h, first.size() * sizeof(int), st);
+        if (!dt || !h->d_tile_first) {
             free_temp();
             return fail(HODLR_OUT_OF_MEMORY);
         }
-        cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
-        cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), st);
+        if (!tiles.empty())
+            cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(h->d_tile_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, st);
         h->d_tiles = dt;
         h->ntiles = (int)tiles.size();
     }
@@ -741,6 +768,7 @@ hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U_or_d, dou
             else
                 to_double_kernel<float><<<blocks, 256, 0, st>>>((const float *)src + lv.coff * h->ldn, h->ldn, tmp, n, n,
                                                                 rp);
+            note_launch();
             HODLR_TRY_CUDA(cudaMemcpyAsync(dst, tmp, (size_t)n * rp * 8, cudaMemcpyDeviceToHost, st));
         }
         HODLR_TRY_CUDA(cudaStreamSynchronize(st));
@@ -778,6 +806,7 @@ hodlr_status hodlr_export_core(const hodlr_t *h, int level, double *Sinv, hodlr_
         to_double_kernel<double><<<blocks, 256, 0, st>>>((const double *)h->Sinv[level], cnt, tmp, cnt, cnt, 1);
     else
         to_double_kernel<float><<<blocks, 256, 0, st>>>((const float *)h->Sinv[level], cnt, tmp, cnt, cnt, 1);
+    note_launch();
     HODLR_TRY_CUDA(cudaMemcpyAsync(Sinv, tmp, (size_t)cnt * 8, cudaMemcpyDeviceToHost, st));
     HODLR_TRY_CUDA(cudaStreamSynchronize(st));
     dfree(h->ctx, tmp, (size_t)cnt * 8, st);

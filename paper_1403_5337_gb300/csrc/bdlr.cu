@@ -319,12 +319,18 @@ hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t 
         const dim3 tgrid((unsigned)((max_rows + 127) / 128), nb);
         if (h->cprec == HODLR_FP64) {
             bdlr_lu_kernel<double><<<nb, LU_THREADS, 0, s>>>(h->A, h->lda, d_desc, h->tol, c->d_status);
+            note_launch();
             bdlr_u_kernel<double><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
+            note_launch();
             bdlr_v_kernel<double><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
+            note_launch();
         } else {
             bdlr_lu_kernel<float><<<nb, LU_THREADS, 0, s>>>(h->A, h->lda, d_desc, h->tol, c->d_status);
+            note_launch();
             bdlr_u_kernel<float><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
+            note_launch();
             bdlr_v_kernel<float><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
+            note_launch();
         }
         if (cudaGetLastError() != cudaSuccess) rs = HODLR_CUDA_ERROR;
     }

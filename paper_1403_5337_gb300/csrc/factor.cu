@@ -30,71 +30,96 @@ namespace hodlr {
 namespace {
 
 // ------------------------------------------------------------------ batched GEMM
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16, GB_THREADS = 256;
+// C_b += alpha op(A_b) B_b on BM x BM output tiles (BM = 64 or 32) with 16-deep
+// K slices; 256 threads as 16 x 16, each owning (BM/16)^2 outputs.  The next K
+// slice is loaded into registers while the current one is multiplied from
+// shared memory.  splitK > 1 splits K into that many chunks (multiples of 16)
+// whose partial products are combined with atomics.
+constexpr int GB_K = 16, GB_THREADS = 256;
 
-template <typename T>
+template <typename T, int BM>
 __global__ void __launch_bounds__(GB_THREADS)
     gemm_batched_kernel(const GemmDesc<T> *__restrict__ descs, int transA, T alpha, int splitK) {
+    constexpr int TPT = BM / 16;                 // outputs per thread per dimension
+    constexpr int LPT = BM * GB_K / GB_THREADS;  // tile elements loaded per thread
     const GemmDesc<T> d = descs[blockIdx.z / splitK];
     const int kz = blockIdx.z % splitK;
-    const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BM;
     if (m0 >= d.M || n0 >= d.N || d.K <= 0) return;
     const int kper = ((d.K + splitK - 1) / splitK + GB_K - 1) / GB_K * GB_K;
     const int kbeg = kz * kper;
     const int kend = min(d.K, kbeg + kper);
     if (kbeg >= kend) return;
-    __shared__ T As[GB_K][GB_M + 1];
-    __shared__ T Bs[GB_K][GB_N + 1];
+    __shared__ T As[GB_K][BM + 1];
+    __shared__ T Bs[GB_K][BM + 1];
     const int tid = threadIdx.x;
     const int ty = tid & 15, tx = tid >> 4;
-    T acc[4][4];
+    T ra[LPT], rb[LPT];
+    auto load = [&](int k0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
-        for (int e = tid; e < GB_M * GB_K; e += GB_THREADS) {
+        for (int u = 0; u < LPT; ++u) {
+            const int e = tid + u * GB_THREADS;
             int i, kk;
-            T v = T(0);
             if (!transA) {
-                i = e % GB_M;
-                kk = e / GB_M;
-                if (m0 + i < d.M && k0 + kk < kend) v = d.A[(int64_t)(m0 + i) + (int64_t)(k0 + kk) * d.lda];
+                i = e % BM;
+                kk = e / BM;
             } else {
                 kk = e % GB_K;
                 i = e / GB_K;
-                if (m0 + i < d.M && k0 + kk < kend) v = d.A[(int64_t)(k0 + kk) + (int64_t)(m0 + i) * d.lda];
             }
-            As[kk][i] = v;
-        }
-        for (int e = tid; e < GB_N * GB_K; e += GB_THREADS) {
-            int kk = e % GB_K, j = e / GB_K;
             T v = T(0);
-            if (n0 + j < d.N && k0 + kk < kend) v = d.B[(int64_t)(k0 + kk) + (int64_t)(n0 + j) * d.ldb];
-            Bs[kk][j] = v;
+            if (m0 + i < d.M && k0 + kk < kend)
+                v = transA ? d.A[(int64_t)(k0 + kk) + (int64_t)(m0 + i) * d.lda]
+                           : d.A[(int64_t)(m0 + i) + (int64_t)(k0 + kk) * d.lda];
+            ra[u] = v;
+            const int kb = e % GB_K, j = e / GB_K;
+            T w = T(0);
+            if (n0 + j < d.N && k0 + kb < kend) w = d.B[(int64_t)(k0 + kb) + (int64_t)(n0 + j) * d.ldb];
+            rb[u] = w;
         }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int u = 0; u < LPT; ++u) {
+            const int e = tid + u * GB_THREADS;
+            if (!transA)
+                As[e / BM][e % BM] = ra[u];
+            else
+                As[e % GB_K][e / GB_K] = ra[u];
+            Bs[e % GB_K][e / GB_K] = rb[u];
+        }
+    };
+    T acc[TPT][TPT];
+#pragma unroll
+    for (int a = 0; a < TPT; ++a)
+#pragma unroll
+        for (int b = 0; b < TPT; ++b) acc[a][b] = T(0);
+    load(kbeg);
+    for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
+        store();
         __syncthreads();
+        if (k0 + GB_K < kend) load(k0 + GB_K);
 #pragma unroll
         for (int kk = 0; kk < GB_K; ++kk) {
-            T a[4], b[4];
+            T a[TPT], b[TPT];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < TPT; ++q) {
                 a[q] = As[kk][ty + 16 * q];
                 b[q] = Bs[kk][tx + 16 * q];
             }
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
+            for (int p = 0; p < TPT; ++p)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+                for (int q = 0; q < TPT; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < TPT; ++q) {
         const int j = n0 + tx + 16 * q;
         if (j >= d.N) continue;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < TPT; ++p) {
             const int i = m0 + ty + 16 * p;
             if (i >= d.M) continue;
             T *cp = d.C + (int64_t)i + (int64_t)j * d.ldc;
@@ -221,32 +246,30 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_inverse_kernel(const GJDesc<T> 
     }
 }
 
+// Fill of the factorisation's workspace before a sweep: block m of a task is the
+// rows x cols column-major array at p + m stride (ld), set to 1 on the diagonal
+// from row d0 on and to 0 elsewhere.  One launch serves every task (blockIdx.y).
 template <typename T>
-__global__ void set_identity_kernel(T *M, int64_t ld, int n, int count, int64_t stride) {
-    const int m = blockIdx.y;
-    if (m >= count) return;
-    T *P = M + m * stride;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+struct FillDesc {
+    T *p;
+    int64_t ld;
+    int64_t rows, cols;
+    int d0;
+    int count;
+    int64_t stride;
+};
+
+template <typename T>
+__global__ void fill_kernel(const FillDesc<T> *__restrict__ tasks) {
+    const FillDesc<T> f = tasks[blockIdx.y];
+    const int64_t per = f.rows * f.cols, total = per * f.count;
+    const int64_t ld = f.ld > 0 ? f.ld : f.rows;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = e / n, i = e % n;
-        P[i + j * ld] = (i == j) ? T(1) : T(0);
+        const int64_t m = e / per, r = e % per;
+        const int64_t j = r / f.rows, i = r % f.rows;
+        f.p[m * f.stride + i + j * ld] = (i == j && i >= f.d0) ? T(1) : T(0);
     }
-}
-
-template <typename T>
-__global__ void zero_kernel(T *p, int64_t count) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
-         e += (int64_t)gridDim.x * blockDim.x)
-        p[e] = T(0);
-}
-
-template <typename T>
-hodlr_status zero(T *p, int64_t count, cudaStream_t s) {
-    if (count <= 0) return HODLR_OK;
-    int blocks = (int)std::min<int64_t>((count + 255) / 256, 4096);
-    zero_kernel<T><<<blocks, 256, 0, s>>>(p, count);
-    HODLR_TRY_CUDA(cudaGetLastError());
-    return HODLR_OK;
 }
 
 // Gauss-Jordan inversion in place in shared memory (ld = b + 1, conflict-free
@@ -353,11 +376,17 @@ constexpr size_t GJS_SMEM_MAX = 200 * 1024;
 
 // Gauss-Jordan inversion with the matrix held in registers: 512 threads as a
 // 16 x 32 grid, thread (ty, tx) owns rows ty + 16 p (p < MR) and columns
-// tx + 32 q (q < MC).  Per step only pivot column k and pivot row k pass
-// through shared memory (the row swap too), so each step costs MR + MC shared
-// loads and MR * MC FMAs per thread.  Same pivot rule and the same in-place
-// update as gj_inverse_smem_kernel.  Register slots are selected with unrolled
-// predicated loops, never by a run-time index.
+// tx + 32 q (q < MC).  Pivoting is implicit (no row exchanges): step k sweeps
+// the pivot (p_k, k), p_k = argmax |a(i, k)| over the rows not yet used as
+// pivots (lowest row on ties):
+//   a(i, j) -= a(i, k) a(p_k, j) / a(p_k, k)   (i != p_k, j != k)
+//   a(i, k)  = -a(i, k) / a(p_k, k),  a(p_k, j) = a(p_k, j) / a(p_k, k),
+//   a(p_k, k) = 1 / a(p_k, k).
+// After the b sweeps the table maps outputs to inputs, M^-1(k, p_j) =
+// a(p_k, j).  A step costs two CTA barriers: one after the column owners post
+// their candidate pivots, one after the pivot row's owner posts that row; the
+// pivot column and row buffers are double-buffered by step parity.  Register
+// slots are selected with unrolled predicated loops, never by a run-time index.
 constexpr int GJR_TY = 16, GJR_TX = 32, GJR_THREADS = GJR_TY * GJR_TX;
 
 template <typename T, int MR, int MC>
@@ -367,169 +396,122 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJ
     const int b = g.b;
     if (b <= 0) return;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    __shared__ T colk[MR * GJR_TY];
-    __shared__ T rowk[MC * GJR_TX];
-    __shared__ T rowa[MC * GJR_TX];
-    __shared__ T rowb[MC * GJR_TX];
-    __shared__ int orig[MR * GJR_TY];
-    __shared__ int s_p, s_fail;
+    __shared__ T colk[2][MR * GJR_TY];
+    __shared__ T rowk[2][MC * GJR_TX];
+    __shared__ T cand_v[2][GJR_TY];
+    __shared__ int cand_i[2][GJR_TY];
+    __shared__ int prow[MR * GJR_TY];   // pivot row of step k
+    __shared__ int krow[MR * GJR_TY];   // step at which row i was the pivot
     T a[MR][MC];
+    unsigned used = 0;                  // bit p: row ty + 16 p is a pivot already (or beyond b)
 #pragma unroll
-    for (int p = 0; p < MR; ++p)
+    for (int p = 0; p < MR; ++p) {
+        const int i = ty + GJR_TY * p;
+        if (i >= b) used |= 1u << p;
 #pragma unroll
         for (int q = 0; q < MC; ++q) {
-            const int i = ty + GJR_TY * p, j = tx + GJR_TX * q;
+            const int j = tx + GJR_TX * q;
             T v = T(0);
             if (i < b && j < b)
                 v = g.srcA ? dev::from_double<T>(g.srcA[(int64_t)i * g.lda + j]) : g.srcM[i + (int64_t)j * g.ldm];
             a[p][q] = v;
         }
-    for (int i = tid; i < b; i += GJR_THREADS) orig[i] = i;
-    if (tid == 0) s_fail = 0;
-    __syncthreads();
+    }
+    bool fail = false;
     for (int k = 0; k < b; ++k) {
-        const int kq = k / GJR_TX, kx = k % GJR_TX;
-        // 1. column k to shared memory
+        const int par = k & 1, kq = k / GJR_TX, kx = k % GJR_TX;
+        // A. the owners of column k post it and their best unused row
         if (tx == kx) {
-#pragma unroll
-            for (int q = 0; q < MC; ++q)
-                if (q == kq) {
-#pragma unroll
-                    for (int p = 0; p < MR; ++p) {
-                        const int i = ty + GJR_TY * p;
-                        if (i < b) colk[i] = a[p][q];
-                    }
-                }
-        }
-        __syncthreads();
-        // 2. pivot row: argmax_{i >= k} |colk[i]|, lowest row on ties
-        if (ty == 0) {
-            T bv = T(-1);
+            T bv = T(-1), sv = T(0);
             int bi = INT_MAX;
-            for (int i = k + tx; i < b; i += 32) {
-                const T v = fabs(colk[i]);
-                if (v > bv) {
-                    bv = v;
-                    bi = i;
-                }
-            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const T ov = __shfl_down_sync(0xffffffffu, bv, o);
-                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && oi < bi)) {
-                    bv = ov;
-                    bi = oi;
-                }
-            }
-            if (tx == 0) {
-                s_p = bi;
-                if (!(bv > T(0))) s_fail = 1;
-                else if (bi != k) {
-                    const int t = orig[k];
-                    orig[k] = orig[bi];
-                    orig[bi] = t;
-                }
-            }
-        }
-        __syncthreads();
-        if (s_fail) break;
-        const int pr = s_p;
-        // 3. swap rows k and pr through shared memory
-        if (pr != k) {
-            const int ky = k % GJR_TY, kp = k / GJR_TY, py = pr % GJR_TY, pp = pr / GJR_TY;
-            if (ty == ky)
-#pragma unroll
-                for (int p = 0; p < MR; ++p)
-                    if (p == kp)
-#pragma unroll
-                        for (int q = 0; q < MC; ++q) rowa[tx + GJR_TX * q] = a[p][q];
-            if (ty == py)
-#pragma unroll
-                for (int p = 0; p < MR; ++p)
-                    if (p == pp)
-#pragma unroll
-                        for (int q = 0; q < MC; ++q) rowb[tx + GJR_TX * q] = a[p][q];
-            __syncthreads();
-            if (ty == ky)
-#pragma unroll
-                for (int p = 0; p < MR; ++p)
-                    if (p == kp)
-#pragma unroll
-                        for (int q = 0; q < MC; ++q) a[p][q] = rowb[tx + GJR_TX * q];
-            if (ty == py)
-#pragma unroll
-                for (int p = 0; p < MR; ++p)
-                    if (p == pp)
-#pragma unroll
-                        for (int q = 0; q < MC; ++q) a[p][q] = rowa[tx + GJR_TX * q];
-            if (tid == 0) {
-                const T t = colk[k];
-                colk[k] = colk[pr];
-                colk[pr] = t;
-            }
-        }
-        __syncthreads();
-        // 4. scaled pivot row to shared memory
-        const T d = T(1) / colk[k];
-        {
-            const int ky = k % GJR_TY, kp = k / GJR_TY;
-            if (ty == ky)
-#pragma unroll
-                for (int p = 0; p < MR; ++p)
-                    if (p == kp)
-#pragma unroll
-                        for (int q = 0; q < MC; ++q) {
-                            const int j = tx + GJR_TX * q;
-                            rowk[j] = (j == k) ? d : a[p][q] * d;
-                        }
-        }
-        __syncthreads();
-        // 5. eliminate column k from every other row: a -= colk * rowk everywhere
-        // (rows beyond b hold zeros and stay zero), then overwrite the pivot row
-        // with rowk and the pivot column with -colk d.
-        T rk[MC];
-#pragma unroll
-        for (int q = 0; q < MC; ++q) rk[q] = rowk[tx + GJR_TX * q];
-#pragma unroll
-        for (int p = 0; p < MR; ++p) {
-            const int i = ty + GJR_TY * p;
-            const T ci = (i < b) ? colk[i] : T(0);
-#pragma unroll
-            for (int q = 0; q < MC; ++q) a[p][q] = fma(-ci, rk[q], a[p][q]);
-            if (tx == kx) {
+            for (int p = 0; p < MR; ++p) {
+                T v = T(0);
 #pragma unroll
                 for (int q = 0; q < MC; ++q)
-                    if (q == kq) a[p][q] = -ci * d;
-            }
-        }
-        if (ty == k % GJR_TY) {
-#pragma unroll
-            for (int p = 0; p < MR; ++p)
-                if (p == k / GJR_TY) {
-#pragma unroll
-                    for (int q = 0; q < MC; ++q) a[p][q] = rk[q];
+                    if (q == kq) v = a[p][q];
+                colk[par][ty + GJR_TY * p] = v;
+                const T av = fabs(v);
+                if (!((used >> p) & 1u) && av > bv) {
+                    bv = av;
+                    sv = v;
+                    bi = ty + GJR_TY * p;
                 }
+            }
+            cand_v[par][ty] = sv;
+            cand_i[par][ty] = bi;
         }
         __syncthreads();
+        // B. every thread merges the 16 candidates (same order, same result)
+        T piv = T(0), pa = T(-1);
+        int pr = INT_MAX;
+#pragma unroll
+        for (int w = 0; w < GJR_TY; ++w) {
+            const int wi = cand_i[par][w];
+            const T wv = cand_v[par][w], wa = fabs(wv);
+            if (wi != INT_MAX && (wa > pa || (wa == pa && wi < pr))) {
+                pa = wa;
+                piv = wv;
+                pr = wi;
+            }
+        }
+        if (!(pa > T(0))) {   // uniform: no usable pivot in column k
+            fail = true;
+            break;
+        }
+        const int py = pr % GJR_TY, pp = pr / GJR_TY;
+        if (ty == py) {
+#pragma unroll
+            for (int p = 0; p < MR; ++p)
+                if (p == pp) {
+                    used |= 1u << p;
+#pragma unroll
+                    for (int q = 0; q < MC; ++q) rowk[par][tx + GJR_TX * q] = a[p][q];
+                }
+        }
+        if (tid == 0) {
+            prow[k] = pr;
+            krow[pr] = k;
+        }
+        __syncthreads();
+        // C. sweep the pivot (pr, k)
+        const T d = T(1) / piv;
+        T rk[MC];
+#pragma unroll
+        for (int q = 0; q < MC; ++q) rk[q] = rowk[par][tx + GJR_TX * q];
+#pragma unroll
+        for (int p = 0; p < MR; ++p) {
+            const T f = colk[par][ty + GJR_TY * p] * d;
+            const bool prow_here = (ty == py) && (p == pp);
+#pragma unroll
+            for (int q = 0; q < MC; ++q) {
+                const bool kcol = (tx == kx) && (q == kq);
+                T v = fma(-f, rk[q], a[p][q]);
+                if (kcol) v = -f;
+                if (prow_here) v = kcol ? d : rk[q] * d;
+                a[p][q] = v;
+            }
+        }
     }
-    if (s_fail) {
+    if (fail) {
         if (tid == 0) atomicOr(status, ST_SINGULAR);
         return;
     }
-    // A^-1 = (PA)^-1 P: column q of the work matrix is column orig[q] of A^-1
+    __syncthreads();
+    // M^-1(krow[i], prow[j]) = a(i, j)
 #pragma unroll
     for (int p = 0; p < MR; ++p)
 #pragma unroll
         for (int q = 0; q < MC; ++q) {
             const int i = ty + GJR_TY * p, j = tx + GJR_TX * q;
-            if (i < b && j < b) g.out[i + (int64_t)orig[j] * g.ldo] = a[p][q];
+            if (i < b && j < b) g.out[krow[i] + (int64_t)prow[j] * g.ldo] = a[p][q];
         }
 }
 
 template <typename T, int MR, int MC>
 hodlr_status launch_gj_reg(hodlr_ctx *c, const GJDesc<T> *dd, int count, cudaStream_t s) {
     gj_inverse_reg_kernel<T, MR, MC><<<count, GJR_THREADS, 0, s>>>(dd, c->d_status);
+    note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
 }
@@ -607,6 +589,7 @@ hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, c
         HODLR_TRY_CUDA(cudaFuncSetAttribute(gj_inverse_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)sm));
         gj_inverse_smem_kernel<T><<<count, GJS_THREADS, sm, s>>>(dd, c->d_status);
+        note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
         return HODLR_OK;
     }
@@ -614,6 +597,7 @@ hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, c
     HODLR_TRY_CUDA(cudaFuncSetAttribute(gj_inverse_kernel<T>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     gj_inverse_kernel<T><<<count, GJ_THREADS, sm, s>>>(dd, c->d_status);
+    note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
 }
@@ -677,26 +661,18 @@ struct Rec {
                                    maxK, transA, alpha, s);
         });
     }
-    void zero_(T *p, int64_t count) {
-        P->ops.push_back([=](cudaStream_t s) { return zero<T>(p, count, s); });
-    }
-    void identity(T *M, int64_t ld, int n, int count, int64_t stride) {
+    void fill(const std::vector<FillDesc<T>> &hd) {
+        if (hd.empty()) return;
+        int64_t most = 0;
+        for (auto &f : hd) most = std::max(most, f.rows * f.cols * f.count);
+        const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(512, (most + 2047) / 2048));
+        const size_t off = P->put(hd.data(), hd.size() * sizeof(FillDesc<T>));
+        const int cnt = (int)hd.size();
+        FactorPlan *PP = P;
         P->ops.push_back([=](cudaStream_t s) {
-            dim3 grid(std::max(1, std::min(64, (n * n + 255) / 256)), count);
-            set_identity_kernel<T><<<grid, 256, 0, s>>>(M, ld, n, count, stride);
+            fill_kernel<T><<<dim3(gx, cnt), 256, 0, s>>>(reinterpret_cast<const FillDesc<T> *>(PP->dblob + off));
+            note_launch();
             HODLR_TRY_CUDA(cudaGetLastError());
-            return HODLR_OK;
-        });
-    }
-    void memset2d(T *p, int64_t pitch_elems, int64_t width_elems, int64_t height) {
-        P->ops.push_back([=](cudaStream_t s) {
-            HODLR_TRY_CUDA(cudaMemset2DAsync(p, pitch_elems * sizeof(T), 0, width_elems * sizeof(T), height, s));
-            return HODLR_OK;
-        });
-    }
-    void copy(T *dst, const T *src, int64_t count) {
-        P->ops.push_back([=](cudaStream_t s) {
-            HODLR_TRY_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToDevice, s));
             return HODLR_OK;
         });
     }
@@ -714,22 +690,27 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
         r0 = h->bounds[(size_t)i << (L - l)];
         m = h->bounds[(size_t)(i + 1) << (L - l)] - r0;
     };
-    // ---- workspace sizing
+    // ---- workspace: every level has its own Y, S^-1 W and M areas, so one
+    // fill launch at the start prepares all of them (zeros, identities)
     const int64_t bmax = h->bmax;
+    struct LvlWs {
+        size_t y = 0, yv = 0, m = 0, gw = 0;
+    };
+    std::vector<LvlWs> ws(L);
     size_t need = 0;
-    size_t lvl_max = 0;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     for (int l = 0; l < L; ++l) {
         const int cch = l + 1;
         const int rp = h->lv[cch].rp;
         const int64_t Wc = h->lv[cch].coff + rp;
         const int nn = 1 << l;
-        size_t y = (size_t)(2 * nn) * rp * Wc;                   // Y per child
-        size_t yv = (size_t)nn * 2 * rp * h->lv[cch].coff;       // S^-1 W per node
-        size_t mm = (size_t)nn * rp * rp;                        // M per node
-        size_t gw = (size_t)nn * 2 * rp * rp;                    // GJ work per node
-        lvl_max = std::max(lvl_max, (y + yv + mm + gw) * sizeof(T) + 4096);
+        ws[l].y = al((size_t)nn * 2 * rp * Wc * sizeof(T));                                   // [Y_a; Y_b] per node
+        ws[l].yv = al((size_t)nn * 2 * rp * std::max<int64_t>(h->lv[cch].coff, 1) * sizeof(T)); // S^-1 [Y_a; Y_b]
+        ws[l].m = al((size_t)nn * rp * rp * sizeof(T));                                       // M per node
+        ws[l].gw = gj_needs_work<T>(rp) ? al((size_t)nn * 2 * rp * rp * sizeof(T)) : 0;      // GJ work
+        need += ws[l].y + ws[l].yv + ws[l].m + ws[l].gw;
     }
-    need += lvl_max + 4096;
+    need += 4096;
     Pl->work = dalloc(c, need, s);
     if (!Pl->work) {
         set_error("factor plan: out of device memory (%zu bytes)", need);
@@ -739,20 +720,39 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
     char *wp = reinterpret_cast<char *>(Pl->work);
     auto carve = [&](size_t bytes) {
         char *p = wp;
-        wp += (bytes + 255) & ~size_t(255);
+        wp += al(bytes);
         return p;
     };
-    char *lvl = carve(lvl_max);
     Rec<T> rec{c, Pl};
     const T *U = reinterpret_cast<const T *>(h->U);
-
+    std::vector<FillDesc<T>> fills;
+    struct LvlPtr {
+        T *Y, *Yv, *M, *gw;
+    };
+    std::vector<LvlPtr> lp(L);
+    for (int l = 0; l < L; ++l) {
+        const int cch = l + 1;
+        const int rp = h->lv[cch].rp;
+        const int nn = 1 << l;
+        lp[l].Y = reinterpret_cast<T *>(carve(ws[l].y));
+        lp[l].Yv = reinterpret_cast<T *>(carve(ws[l].yv));
+        lp[l].M = reinterpret_cast<T *>(carve(ws[l].m));
+        lp[l].gw = ws[l].gw ? reinterpret_cast<T *>(carve(ws[l].gw)) : nullptr;
+        if (rp == 0) continue;
+        const int64_t s2 = 2 * (int64_t)rp;
+        fills.push_back(FillDesc<T>{lp[l].Y, 0, (int64_t)(ws[l].y / sizeof(T)), 1, INT_MAX, 1, 0});
+        fills.push_back(FillDesc<T>{lp[l].Yv, 0, (int64_t)(ws[l].yv / sizeof(T)), 1, INT_MAX, 1, 0});
+        fills.push_back(FillDesc<T>{lp[l].M, rp, rp, rp, 0, nn, (int64_t)rp * rp});               // I
+        fills.push_back(FillDesc<T>{reinterpret_cast<T *>(h->Sinv[l]), s2, s2, s2, rp, nn, s2 * s2});  // [0 0; 0 I]
+    }
     // ---- 1. leaf inverses: computed by hodlr_build (they depend on A only), while
     // the off-diagonal blocks are being compressed
     T *Kinv = reinterpret_cast<T *>(h->leafinv);
+    if (W > 0) fills.push_back(FillDesc<T>{D, 0, ldn * W, 1, INT_MAX, 1, 0});
+    rec.fill(fills);
     // ---- 2. leaf stack: D = Kinv_leaf * U (all columns).  U is left intact, so
     // the factorisation can be repeated.
     if (W > 0) {
-        rec.zero_(D, ldn * W);
         std::vector<GemmDesc<T>> gd(nleaf);
         for (int i = 0; i < nleaf; ++i) {
             int64_t r0, m;
@@ -762,7 +762,11 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
         }
         rec.gemm(gd, 0, T(1));
     }
-    // ---- 3. levels, bottom-up
+    // ---- 3. levels, bottom-up.  Node i of level l has children a = 2i, b = 2i+1
+    // at level l+1, whose blocks V(a, blk)^T D(a, :) and V(b, blk)^T D(b, :) are
+    // stacked as Y_i = [Y_a; Y_b] (2 rp x Wc, ld 2 rp).  P = Y_a(:, own block),
+    // Q = Y_b(:, own block); S = [[I, P], [Q, I]], M = I - P Q,
+    // S^-1 = [[M^-1, -M^-1 P], [-Q M^-1, I + Q M^-1 P]].
     for (int l = L - 1; l >= 0; --l) {
         const int cch = l + 1;
         const int rp = h->lv[cch].rp;
@@ -773,36 +777,26 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
         T *Sinv = reinterpret_cast<T *>(h->Sinv[l]);
         const int64_t s2 = 2 * (int64_t)rp;
         if (rp == 0) continue;
-        char *lp = lvl;
-        auto lcarve = [&](size_t bytes) {
-            char *p = lp;
-            lp += (bytes + 255) & ~size_t(255);
-            return p;
-        };
-        T *Y = reinterpret_cast<T *>(lcarve((size_t)nch * rp * Wc * sizeof(T)));
-        T *Yv = reinterpret_cast<T *>(lcarve((size_t)nn * s2 * std::max<int64_t>(coffc, 1) * sizeof(T)));
-        T *M = reinterpret_cast<T *>(lcarve((size_t)nn * rp * rp * sizeof(T)));
-        T *gw = reinterpret_cast<T *>(lcarve((size_t)nn * 2 * rp * rp * sizeof(T)));
-        // (a) Y_child = V(child, blk c)^T D(child, 0:Wc)
-        rec.zero_(Y, (int64_t)nch * rp * Wc);
+        T *Y = lp[l].Y, *Yv = lp[l].Yv, *M = lp[l].M, *gw = lp[l].gw;
+        auto Yi = [&](int i) { return Y + (size_t)i * s2 * Wc; };
+        // (a) Y_child = V(child, blk)^T D(child, 0:Wc)
         {
             std::vector<GemmDesc<T>> gd(nch);
             for (int i = 0; i < nch; ++i) {
                 int64_t r0, m;
                 node_range(cch, i, r0, m);
-                gd[i] = GemmDesc<T>{V + coffc * ldn + r0, D + r0, Y + (size_t)i * rp * Wc, ldn, ldn,
-                                    rp, rp, (int)Wc, (int)m};
+                gd[i] = GemmDesc<T>{V + coffc * ldn + r0, D + r0, Yi(i / 2) + (i & 1) * rp, ldn, ldn,
+                                    s2, rp, (int)Wc, (int)m};
             }
             rec.gemm(gd, 1, T(1));
         }
         // (b) M = I - P Q per node
         {
-            rec.identity(M, rp, rp, nn, (int64_t)rp * rp);
             std::vector<GemmDesc<T>> gd(nn);
             for (int i = 0; i < nn; ++i) {
-                const T *P = Y + (size_t)(2 * i) * rp * Wc + coffc * rp;
-                const T *Q = Y + (size_t)(2 * i + 1) * rp * Wc + coffc * rp;
-                gd[i] = GemmDesc<T>{P, Q, M + (size_t)i * rp * rp, rp, rp, rp, rp, rp, rp};
+                const T *P = Yi(i) + coffc * s2;
+                const T *Q = Yi(i) + rp + coffc * s2;
+                gd[i] = GemmDesc<T>{P, Q, M + (size_t)i * rp * rp, s2, s2, rp, rp, rp, rp};
             }
             rec.gemm(gd, 0, T(-1));
         }
@@ -810,59 +804,38 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
         {
             std::vector<GJDesc<T>> gd(nn);
             for (int i = 0; i < nn; ++i)
-                gd[i] = GJDesc<T>{nullptr, 0, M + (size_t)i * rp * rp, rp, gw + (size_t)i * 2 * rp * rp,
+                gd[i] = GJDesc<T>{nullptr, 0, M + (size_t)i * rp * rp, rp, gw ? gw + (size_t)i * 2 * rp * rp : nullptr,
                                   Sinv + (size_t)i * s2 * s2, s2, rp};
             rec.gj(gd);
         }
-        // (d) the other three blocks of S^-1
+        // (d) TR = -M^-1 P and BL = -Q M^-1 (one launch), then BR = I - Q TR
         {
-            // TR = -M^-1 P ; BL = -Q M^-1 (zeroed first), BR = I - Q TR
+            std::vector<GemmDesc<T>> g12(2 * nn), g3(nn);
             for (int i = 0; i < nn; ++i) {
                 T *S = Sinv + (size_t)i * s2 * s2;
-                rec.memset2d(S + rp * s2, s2, rp, rp);
-                rec.memset2d(S + rp, s2, rp, rp);
+                const T *P = Yi(i) + coffc * s2;
+                const T *Q = Yi(i) + rp + coffc * s2;
+                g12[2 * i] = GemmDesc<T>{S, P, S + rp * s2, s2, s2, s2, rp, rp, rp};
+                g12[2 * i + 1] = GemmDesc<T>{Q, S, S + rp, s2, s2, s2, rp, rp, rp};
+                g3[i] = GemmDesc<T>{Q, S + rp * s2, S + rp + rp * s2, s2, s2, s2, rp, rp, rp};
             }
-            rec.identity(Sinv + rp + rp * s2, s2, rp, nn, s2 * s2);
-            std::vector<GemmDesc<T>> g1(nn), g2(nn), g3(nn);
-            for (int i = 0; i < nn; ++i) {
-                T *S = Sinv + (size_t)i * s2 * s2;
-                const T *P = Y + (size_t)(2 * i) * rp * Wc + coffc * rp;
-                const T *Q = Y + (size_t)(2 * i + 1) * rp * Wc + coffc * rp;
-                g1[i] = GemmDesc<T>{S, P, S + rp * s2, s2, rp, s2, rp, rp, rp};        // TR -= Minv P
-                g2[i] = GemmDesc<T>{Q, S, S + rp, rp, s2, s2, rp, rp, rp};              // BL -= Q Minv
-                g3[i] = GemmDesc<T>{Q, S + rp * s2, S + rp + rp * s2, rp, s2, s2, rp, rp, rp};  // BR -= Q TR
-            }
-            rec.gemm(g1, 0, T(-1));
-            rec.gemm(g2, 0, T(-1));
+            rec.gemm(g12, 0, T(-1));
             rec.gemm(g3, 0, T(-1));
         }
-        // (e) update the ancestor columns (levels 1..l) for l >= 1
+        // (e) update the ancestor columns (levels 1..l) for l >= 1:
+        // [y1; y2] = S^-1 [Y_a; Y_b](:, 0:coffc), D(a) -= d_a y2, D(b) -= d_b y1
         if (l >= 1 && coffc > 0) {
-            rec.zero_(Yv, (int64_t)nn * s2 * coffc);
-            std::vector<GemmDesc<T>> ga(2 * nn);
-            for (int i = 0; i < nn; ++i) {
-                T *S = Sinv + (size_t)i * s2 * s2;
-                const T *Ya = Y + (size_t)(2 * i) * rp * Wc;
-                const T *Yb = Y + (size_t)(2 * i + 1) * rp * Wc;
-                T *out = Yv + (size_t)i * s2 * coffc;
-                ga[2 * i] = GemmDesc<T>{S, Ya, out, s2, rp, s2, (int)s2, (int)coffc, rp};
-                ga[2 * i + 1] = GemmDesc<T>{S + rp * s2, Yb, out, s2, rp, s2, (int)s2, (int)coffc, rp};
-            }
-            // the two halves accumulate into the same output: run them as two launches
-            std::vector<GemmDesc<T>> gA(nn), gB(nn);
-            for (int i = 0; i < nn; ++i) {
-                gA[i] = ga[2 * i];
-                gB[i] = ga[2 * i + 1];
-            }
-            rec.gemm(gA, 0, T(1));
-            rec.gemm(gB, 0, T(1));
+            std::vector<GemmDesc<T>> gs(nn);
+            for (int i = 0; i < nn; ++i)
+                gs[i] = GemmDesc<T>{Sinv + (size_t)i * s2 * s2, Yi(i), Yv + (size_t)i * s2 * coffc, s2, s2, s2,
+                                    (int)s2, (int)coffc, (int)s2};
+            rec.gemm(gs, 0, T(1));
             std::vector<GemmDesc<T>> gu(nch);
             for (int i = 0; i < nn; ++i) {
                 int64_t ra, ma, rb, mb;
                 node_range(cch, 2 * i, ra, ma);
                 node_range(cch, 2 * i + 1, rb, mb);
                 const T *yv = Yv + (size_t)i * s2 * coffc;
-                // alpha rows: -= d_alpha * y2 ; beta rows: -= d_beta * y1
                 gu[2 * i] = GemmDesc<T>{D + coffc * ldn + ra, yv + rp, D + ra, ldn, s2, ldn,
                                         (int)ma, (int)coffc, rp};
                 gu[2 * i + 1] = GemmDesc<T>{D + coffc * ldn + rb, yv, D + rb, ldn, s2, ldn,
@@ -888,8 +861,10 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
                     Pl->ops.push_back([=](cudaStream_t s) {
                         quantize_kernel<__nv_bfloat16><<<dim3(nn, rp), 256, 0, s>>>(Vf, Vq, ldn, coff, rp, bd, L, l,
                                                                                      nullptr);
+                        note_launch();
                         quantize_kernel<__nv_bfloat16><<<dim3(nn, rp), 256, 0, s>>>(Df, Dq, ldn, coff, rp, bd, L, l,
                                                                                      nullptr);
+                        note_launch();
                         HODLR_TRY_CUDA(cudaGetLastError());
                         return HODLR_OK;
                     });
@@ -899,7 +874,9 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
                     float *vs = h->vscale[l], *ds = h->dscale[l];
                     Pl->ops.push_back([=](cudaStream_t s) {
                         quantize_kernel<__half><<<dim3(nn, rp), 256, 0, s>>>(Vf, Vq, ldn, coff, rp, bd, L, l, vs);
+                        note_launch();
                         quantize_kernel<__half><<<dim3(nn, rp), 256, 0, s>>>(Df, Dq, ldn, coff, rp, bd, L, l, ds);
+                        note_launch();
                         HODLR_TRY_CUDA(cudaGetLastError());
                         return HODLR_OK;
                     });
@@ -924,19 +901,26 @@ hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
 template <typename T>
 hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T> *d_desc, int nbatch, int maxM, int maxN,
                           int maxK, int transA, T alpha, cudaStream_t s) {
-    const int tm = (maxM + GB_M - 1) / GB_M, tn = (maxN + GB_N - 1) / GB_N;
-    const int64_t tiles = (int64_t)tm * tn * nbatch;
-    int splitK = 1;
-    const int64_t want = 2LL * std::max(1, c->num_sms);
-    if (tiles < want) splitK = (int)std::min<int64_t>((want + tiles - 1) / tiles, std::max(1, maxK / 128));
-    splitK = std::max(1, std::min(splitK, 64));
-    if ((int64_t)nbatch * splitK > 65535) splitK = std::max(1, 65535 / nbatch);
     if (nbatch > 65535) {
         hodlr::set_error("gemm_batched: too many batches (%d)", nbatch);
         return HODLR_RANGE;
     }
+    const int64_t want = 2LL * std::max(1, c->num_sms);
+    // 64-wide tiles unless that leaves most of the GPU idle
+    int bm = 64;
+    if ((int64_t)((maxM + 63) / 64) * ((maxN + 63) / 64) * nbatch < c->num_sms) bm = 32;
+    const int tm = (maxM + bm - 1) / bm, tn = (maxN + bm - 1) / bm;
+    const int64_t tiles = (int64_t)tm * tn * nbatch;
+    int splitK = 1;
+    if (tiles < want) splitK = (int)std::min<int64_t>((want + tiles - 1) / tiles, std::max(1, maxK / 64));
+    splitK = std::max(1, std::min(splitK, 64));
+    if ((int64_t)nbatch * splitK > 65535) splitK = std::max(1, 65535 / nbatch);
     dim3 grid(tn, tm, nbatch * splitK);
-    gemm_batched_kernel<T><<<grid, GB_THREADS, 0, s>>>(d_desc, transA, alpha, splitK);
+    if (bm == 64)
+        gemm_batched_kernel<T, 64><<<grid, GB_THREADS, 0, s>>>(d_desc, transA, alpha, splitK);
+    else
+        gemm_batched_kernel<T, 32><<<grid, GB_THREADS, 0, s>>>(d_desc, transA, alpha, splitK);
+    note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
 }

@@ -72,7 +72,7 @@ constexpr int MV_RPW = 2;            // rows per warp
 constexpr int MV_ROWS = MV_WARPS * MV_RPW;
 constexpr int MV_KC = 1024;          // columns per CTA (one column split)
 constexpr int MV_S = 4;              // right-hand sides per pass
-constexpr int MV_U = 4;              // 16-byte loads in flight per lane and row
+constexpr int MV_U = 2;              // 16-byte loads in flight per lane and row
 
 __global__ void split_vec_kernel(const double *__restrict__ Z, int64_t ldz, int64_t n, int s,
                                  float2 *__restrict__ zs) {
@@ -93,7 +93,7 @@ __global__ void split_vec_kernel(const double *__restrict__ Z, int64_t ldz, int6
 // the compensation term's own FP32 rounding never accumulates further.
 // VEC: A rows are 16-byte aligned (even lda, aligned base) -> double2 loads.
 template <bool VEC>
-__global__ void __launch_bounds__(MV_THREADS)
+__global__ void __launch_bounds__(MV_THREADS, 4)
     df_matvec_kernel(const double *__restrict__ A, int64_t n, int64_t lda, const float2 *__restrict__ zs,
                      int s, int r0, double *__restrict__ W, int64_t ldw, int *status) {
     __shared__ __align__(16) float2 zsm[MV_S][MV_KC];
@@ -184,16 +184,34 @@ __global__ void __launch_bounds__(MV_THREADS)
         }
     }
     if (bad) atomicOr(status, ST_NONFINITE);
+    // Warp sums of the float pairs (TwoSum on the leading parts; after the xor
+    // butterfly every lane holds every sum), then lane a MV_S + q converts sum
+    // (a, q) to FP64 and adds it to W: three FP64 instructions per warp.
+    float rs = 0.f, rc = 0.f;
 #pragma unroll
-    for (int a = 0; a < MV_RPW; ++a) {
-        const int64_t row = row0 + a;
+    for (int a = 0; a < MV_RPW; ++a)
 #pragma unroll
         for (int q = 0; q < MV_S; ++q) {
-            double v = (double)acc[a][q].s + (double)acc[a][q].c;
+            DF p = acc[a][q];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && row < n && q < sr) atomicAdd(&W[row + (int64_t)(r0 + q) * ldw], v);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, p.s, o);
+                const float ol = __shfl_xor_sync(0xffffffffu, p.c, o);
+                const float t = p.s + oh;
+                const float bp = t - p.s;
+                const float err = (p.s - (t - bp)) + (oh - bp);
+                p.s = t;
+                p.c = (p.c + ol) + err;
+            }
+            if (lane == a * MV_S + q) {
+                rs = p.s;
+                rc = p.c;
+            }
         }
+    if (lane < MV_RPW * MV_S) {
+        const int a = lane / MV_S, q = lane % MV_S;
+        const int64_t row = row0 + a;
+        if (row < n && q < sr) atomicAdd(&W[row + (int64_t)(r0 + q) * ldw], (double)rs + (double)rc);
     }
 }
 
@@ -204,108 +222,12 @@ constexpr int KT = 256;
 // jcur[r] (all active right-hand sides advance together), so one recorded
 // iteration can be replayed by a device-side loop.
 
-// h[r][i] += sum_rows V_r(:, i) . w_r  for i <= j; rows split into chunks.
-__global__ void __launch_bounds__(KT)
-    gram_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, const int *__restrict__ jcur,
-                const double *__restrict__ w, int64_t ldw, const int *__restrict__ active, double *__restrict__ h,
-                int hstride, int64_t chunk) {
-    const int r = blockIdx.y;
-    if (!active[r]) return;
-    const int j = jcur[r];
-    const int64_t a = blockIdx.x * chunk, e = (a + chunk < n) ? a + chunk : n;
-    const double *V = Vk + r * vstride;
-    const double *wr = w + r * ldw;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i <= j; i += KT / 32) {
-        const double *vi = V + (int64_t)i * n;
-        double acc = 0.0;
-        for (int64_t q = a + lane; q < e; q += 32) acc = fma(vi[q], wr[q], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) atomicAdd(&h[(int64_t)r * hstride + i], acc);
-    }
-}
-
-// w_r -= V_r(:, 0:j+1) h_r ; optionally accumulate ||w_r||^2.
-__global__ void __launch_bounds__(KT)
-    orth_update_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, const int *__restrict__ jcur,
-                       double *__restrict__ w, int64_t ldw, const int *__restrict__ active,
-                       const double *__restrict__ h, int hstride, double *__restrict__ nrm2) {
-    const int r = blockIdx.y;
-    if (!active[r]) return;
-    const int j = jcur[r];
-    const double *V = Vk + r * vstride;
-    const double *hr = h + (int64_t)r * hstride;
-    double local = 0.0;
-    for (int64_t q = blockIdx.x * (int64_t)KT + threadIdx.x; q < n; q += (int64_t)gridDim.x * KT) {
-        double v = w[q + r * ldw];
-        for (int i = 0; i <= j; ++i) v = fma(-hr[i], V[(int64_t)i * n + q], v);
-        w[q + r * ldw] = v;
-        local = fma(v, v, local);
-    }
-    if (nrm2) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&nrm2[r], local);
-    }
-}
-
-// v_{j+1} = w / ||w||  (skipped for a zero norm: breakdown).
-__global__ void normalize_kernel(const double *__restrict__ w, int64_t ldw, int64_t n, const int *__restrict__ active,
-                                 const double *__restrict__ nrm2, double *__restrict__ Vk, int64_t vstride,
-                                 const int *__restrict__ jcur) {
-    const int r = blockIdx.y;
-    if (!active[r]) return;
-    const int jn = jcur[r] + 1;
-    const double nr = sqrt(nrm2[r]);
-    if (!(nr > 0.0)) return;
-    double *dst = Vk + r * vstride + (int64_t)jn * n;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        dst[q] = w[q + r * ldw] / nr;
-}
-
 struct GState {
     double *H;       // (m+1) x m per rhs
     double *cs, *sn, *g;
     double *bnorm, *est;
     int *iters, *jcur, *active, *nactive;
 };
-
-// Givens update of column j for every active rhs; one thread per rhs.
-__global__ void givens_kernel(GState st, int m, int s, const double *__restrict__ h1, const double *__restrict__ h2,
-                              int hstride, const double *__restrict__ nrm2, double tol, int max_iter) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= s || !st.active[r]) return;
-    const int j = st.jcur[r];
-    double *Hc = st.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
-    double *cs = st.cs + (int64_t)r * m, *sn = st.sn + (int64_t)r * m, *g = st.g + (int64_t)r * (m + 1);
-    for (int i = 0; i <= j; ++i) Hc[i] = h1[(int64_t)r * hstride + i] + h2[(int64_t)r * hstride + i];
-    const double hn = sqrt(nrm2[r]);
-    Hc[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * Hc[i] + sn[i] * Hc[i + 1];
-        Hc[i + 1] = -sn[i] * Hc[i] + cs[i] * Hc[i + 1];
-        Hc[i] = t;
-    }
-    const double rho = hypot(Hc[j], Hc[j + 1]);
-    if (rho == 0.0) {
-        cs[j] = 1.0;
-        sn[j] = 0.0;
-    } else {
-        cs[j] = Hc[j] / rho;
-        sn[j] = Hc[j + 1] / rho;
-    }
-    Hc[j] = rho;
-    Hc[j + 1] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    st.iters[r] += 1;
-    st.jcur[r] = j + 1;
-    const double est = fabs(g[j + 1]) / st.bnorm[r];
-    st.est[r] = est;
-    if (est <= tol || rho == 0.0 || hn == 0.0 || j + 1 >= m || st.iters[r] >= max_iter) st.active[r] = 0;
-    else atomicAdd(st.nactive, 1);
-}
 
 // y = H(0:j,0:j)^-1 g(0:j) by back substitution, then X_r += Z_r y.  One CTA per rhs.
 __global__ void __launch_bounds__(KT)
@@ -349,9 +271,9 @@ __global__ void residual_kernel(const double *__restrict__ B, int64_t ldb, doubl
 }
 
 // Start a cycle: v_0 = r / ||r||, g = ||r|| e_1, jcur = 0, activity from the residual.
-__global__ void start_cycle_kernel(GState st, int m, int s, const double *__restrict__ R, int64_t ldr, int64_t n,
+__global__ void start_cycle_kernel(GState st, int m, int s, double *__restrict__ R, int64_t ldr, int64_t n,
                                    const double *__restrict__ nrm2, double *__restrict__ Vk, int64_t vstride, double tol,
-                                   int max_iter, int first) {
+                                   int max_iter, int first, double *__restrict__ Zc) {
     // Every block decides activity from values no block of this launch writes:
     // iters was zeroed before the first cycle, and bnorm is only written (by
     // block 0) on the first cycle, when every block uses beta instead.
@@ -369,8 +291,12 @@ __global__ void start_cycle_kernel(GState st, int m, int s, const double *__rest
     }
     if (!act) return;
     double *v0 = Vk + r * vstride;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        v0[q] = R[q + r * ldr] / beta;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const double v = R[q + r * ldr] / beta;
+        v0[q] = v;
+        Zc[q + r * n] = v;     // the first vector to precondition
+        R[q + r * ldr] = 0.0;  // the first product accumulates into R
+    }
 }
 
 __global__ void count_active_kernel(const int *active, int s, int *nactive) {
@@ -379,45 +305,279 @@ __global__ void count_active_kernel(const int *active, int s, int *nactive) {
     *nactive = c;
 }
 
-// Zcur(:, r) = V_r(:, jcur[r]) for active r (the vector to precondition).
-__global__ void gather_v_kernel(const double *__restrict__ Vk, int64_t vstride, int64_t n, const int *__restrict__ jcur,
-                                const int *__restrict__ active, double *__restrict__ Zc) {
-    const int r = blockIdx.y;
-    if (!active[r]) return;
-    const double *src = Vk + r * vstride + (int64_t)jcur[r] * n;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        Zc[q + r * n] = src[q];
+// ------------------------------------------------------------------ fused Arnoldi step
+// After w = A z_j: classical Gram-Schmidt twice against v_0..v_j, the new basis
+// vector, the Givens update of the Hessenberg column and the loop test, in one
+// cooperative kernel with three software grid barriers (bounded waits).
+// Work units are (256-row chunk, rhs); thread t of a unit owns one row.
+//   P1  Z(:, j) = z_j; h1 = V^T w                      (partial sums, atomics)
+//   P2  w -= V h1; h2 = V^T w
+//   P3  w -= V h2; ||w||^2;  CTA 0: H(:, j) = h1 + h2, h1 = 0
+//   P4  v_{j+1} = w / ||w|| (also the next apply's input), w = 0 (the next
+//       product accumulates into it); CTA 0: h2 = 0, Givens rotation of
+//       H(:, j), residual estimate, activity, loop condition
+// nrm is cleared by CTA 0 in P1 (it is only accumulated in P3).  The step j
+// and the activity of every rhs are fixed until CTA 0 advances them at the end.
+constexpr int TT = 256;
+constexpr int TW = TT / 32;
+constexpr unsigned long long TAIL_SPIN_LIMIT = 1ull << 26;
+
+struct TailArgs {
+    double *Vk;
+    int64_t vstride, n;
+    double *w;          // n x s (ld n)
+    double *Zc;         // n x s
+    double *Zk;
+    int64_t zstride;
+    double *h1, *h2, *nrm;
+    int hstride;
+    GState gs;
+    int m, s, max_iter;
+    double tol;
+    unsigned *bar;
+    int *status;
+    int *loops;
+    int limit;
+    cudaGraphConditionalHandle handle;
+};
+
+__device__ void tail_grid_sync(unsigned *bar, int *status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > TAIL_SPIN_LIMIT) {
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
 }
 
-// Z_r(:, jcur[r]) = Zcur(:, r) for active r (the flexible basis).
-__global__ void scatter_z_kernel(const double *__restrict__ Zc, int64_t n, const int *__restrict__ jcur,
-                                 const int *__restrict__ active, double *__restrict__ Zk, int64_t zstride) {
-    const int r = blockIdx.y;
-    if (!active[r]) return;
-    double *dst = Zk + r * zstride + (int64_t)jcur[r] * n;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        dst[q] = Zc[q + r * n];
+// Butterfly sum of 32 values per lane over the warp: after five exchange rounds
+// (each lane keeps the half of its values selected by one bit of its lane
+// index) lane L holds the warp total of value L.  31 additions per lane instead
+// of 32 separate five-round reductions.
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < o; ++k) {
+            const double send = up ? v[k] : v[k + o];
+            const double keep = up ? v[k + o] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
 }
 
-// End of one recorded iteration: continue the device loop while some rhs is
-// active, and never beyond `limit` iterations of one cycle.
-__global__ void loop_condition_kernel(cudaGraphConditionalHandle handle, const int *__restrict__ nactive,
-                                      int *__restrict__ loops, int limit) {
-    const int it = ++(*loops);
-    cudaGraphSetConditional(handle, (*nactive > 0 && it < limit) ? 1u : 0u);
+// h[i] += sum over the unit's rows of V(q, i) x(q), i <= j (one atomic per i).
+__device__ void unit_gram(const double *V, int64_t n, int64_t q, bool own, double x, int j, double *h,
+                          double *part, int lane, int warp) {
+    for (int g0 = 0; g0 <= j; g0 += 32) {
+        double v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = (own && g0 + k <= j) ? V[(int64_t)(g0 + k) * n + q] * x : 0.0;
+        part[warp * 32 + lane] = warp_transpose_sum(v, lane);
+        __syncthreads();
+        if (threadIdx.x < 32 && g0 + (int)threadIdx.x <= j) {
+            double t = 0.0;
+#pragma unroll
+            for (int wv = 0; wv < TW; ++wv) t += part[wv * 32 + threadIdx.x];
+            atomicAdd(h + g0 + threadIdx.x, t);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
+    extern __shared__ double hs[];                      // [m + 1]: the coefficients of the unit's rhs
+    int *sj = reinterpret_cast<int *>(hs + a.m + 1);    // [s]: j of every rhs at entry
+    int *sa = sj + a.s;                                 // [s]: its activity at entry
+    __shared__ double part[TW * 32];
+    __shared__ double s_inv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t chunks = (a.n + TT - 1) / TT;
+    const int64_t units = chunks * a.s;
+    for (int r = threadIdx.x; r < a.s; r += TT) {
+        sj[r] = a.gs.jcur[r];
+        sa[r] = a.gs.active[r];
+    }
+    __syncthreads();
+    // ---- P1: Z(:, j) = z_j; h1 = V^T w
+    if (blockIdx.x == 0)
+        for (int r = threadIdx.x; r < a.s; r += TT) a.nrm[r] = 0.0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int r = (int)(u / chunks);
+        if (!sa[r]) continue;
+        const int j = sj[r];
+        const int64_t q = (u % chunks) * TT + threadIdx.x;
+        const bool own = q < a.n;
+        double x = 0.0;
+        if (own) {
+            x = a.w[q + r * a.n];
+            a.Zk[r * a.zstride + (int64_t)j * a.n + q] = a.Zc[q + r * a.n];
+        }
+        unit_gram(a.Vk + r * a.vstride, a.n, q, own, x, j, a.h1 + (int64_t)r * a.hstride, part, lane, warp);
+    }
+    tail_grid_sync(a.bar, a.status);
+    // ---- P2: w -= V h1; h2 = V^T w
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int r = (int)(u / chunks);
+        if (!sa[r]) continue;
+        const int j = sj[r];
+        const int64_t q = (u % chunks) * TT + threadIdx.x;
+        const bool own = q < a.n;
+        const double *V = a.Vk + r * a.vstride;
+        for (int i = threadIdx.x; i <= j; i += TT) hs[i] = __ldcg(a.h1 + (int64_t)r * a.hstride + i);
+        __syncthreads();
+        double x = 0.0;
+        if (own) {
+            x = a.w[q + r * a.n];
+            for (int i = 0; i <= j; ++i) x = fma(-hs[i], V[(int64_t)i * a.n + q], x);
+            a.w[q + r * a.n] = x;
+        }
+        unit_gram(V, a.n, q, own, x, j, a.h2 + (int64_t)r * a.hstride, part, lane, warp);
+    }
+    tail_grid_sync(a.bar, a.status);
+    // ---- P3: w -= V h2; ||w||^2
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int r = (int)(u / chunks);
+        if (!sa[r]) continue;
+        const int j = sj[r];
+        const int64_t q = (u % chunks) * TT + threadIdx.x;
+        const double *V = a.Vk + r * a.vstride;
+        for (int i = threadIdx.x; i <= j; i += TT) hs[i] = __ldcg(a.h2 + (int64_t)r * a.hstride + i);
+        __syncthreads();
+        double x = 0.0;
+        if (q < a.n) {
+            x = a.w[q + r * a.n];
+            for (int i = 0; i <= j; ++i) x = fma(-hs[i], V[(int64_t)i * a.n + q], x);
+            a.w[q + r * a.n] = x;
+        }
+        double p = x * x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (lane == 0) part[warp] = p;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int wv = 0; wv < TW; ++wv) t += part[wv];
+            atomicAdd(a.nrm + r, t);
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0) {
+        // H(:, j) = h1 + h2 (h2 is complete: P2 ended at the barrier); h1 is no longer read
+        for (int r = 0; r < a.s; ++r) {
+            if (!sa[r]) continue;
+            const int j = sj[r];
+            double *Hc = a.gs.H + (int64_t)r * (a.m + 1) * a.m + (int64_t)j * (a.m + 1);
+            for (int i = threadIdx.x; i <= j; i += TT) {
+                Hc[i] = __ldcg(a.h1 + (int64_t)r * a.hstride + i) + __ldcg(a.h2 + (int64_t)r * a.hstride + i);
+                a.h1[(int64_t)r * a.hstride + i] = 0.0;
+            }
+        }
+    }
+    tail_grid_sync(a.bar, a.status);
+    // ---- P4: v_{j+1} = w / ||w||; w = 0
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int r = (int)(u / chunks);
+        if (!sa[r]) continue;
+        const int j = sj[r];
+        const int64_t q = (u % chunks) * TT + threadIdx.x;
+        if (threadIdx.x == 0) {
+            const double nr = sqrt(__ldcg(a.nrm + r));
+            s_inv = nr > 0.0 ? 1.0 / nr : 0.0;
+        }
+        __syncthreads();
+        const double inv = s_inv;
+        if (q < a.n) {
+            const double x = a.w[q + r * a.n];
+            if (inv > 0.0) {
+                const double v = x * inv;
+                a.Vk[r * a.vstride + (int64_t)(j + 1) * a.n + q] = v;
+                a.Zc[q + r * a.n] = v;
+            }
+            a.w[q + r * a.n] = 0.0;
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x != 0) return;
+    // ---- CTA 0: Givens rotation of H(:, j), residual estimate, activity, loop test
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < a.s; r += TT) {
+        if (!sa[r]) continue;
+        const int j = sj[r];
+        double *h2r = a.h2 + (int64_t)r * a.hstride;
+        for (int i = 0; i <= j; ++i) h2r[i] = 0.0;
+        double *Hc = a.gs.H + (int64_t)r * (a.m + 1) * a.m + (int64_t)j * (a.m + 1);
+        double *cs = a.gs.cs + (int64_t)r * a.m, *sn = a.gs.sn + (int64_t)r * a.m;
+        double *g = a.gs.g + (int64_t)r * (a.m + 1);
+        const double hn = sqrt(__ldcg(a.nrm + r));
+        Hc[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * Hc[i] + sn[i] * Hc[i + 1];
+            Hc[i + 1] = -sn[i] * Hc[i] + cs[i] * Hc[i + 1];
+            Hc[i] = t;
+        }
+        const double rho = hypot(Hc[j], Hc[j + 1]);
+        if (rho == 0.0) {
+            cs[j] = 1.0;
+            sn[j] = 0.0;
+        } else {
+            cs[j] = Hc[j] / rho;
+            sn[j] = Hc[j + 1] / rho;
+        }
+        Hc[j] = rho;
+        Hc[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        a.gs.iters[r] += 1;
+        a.gs.jcur[r] = j + 1;
+        const double est = fabs(g[j + 1]) / a.gs.bnorm[r];
+        a.gs.est[r] = est;
+        if (est <= a.tol || rho == 0.0 || hn == 0.0 || j + 1 >= a.m || a.gs.iters[r] >= a.max_iter)
+            a.gs.active[r] = 0;
+        else
+            atomicAdd(&s_cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *a.gs.nactive = s_cnt;
+        const int it = ++(*a.loops);
+        cudaGraphSetConditional(a.handle, (s_cnt > 0 && it < a.limit) ? 1u : 0u);
+    }
 }
 
 }  // namespace
 
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s, const double *Z, int64_t ldz,
-                         double *W, int64_t ldw, cudaStream_t st, void *work) {
+                         double *W, int64_t ldw, cudaStream_t st, void *work, bool w_zeroed) {
     if (n == 0 || s == 0) return HODLR_OK;
     float2 *zs = work ? reinterpret_cast<float2 *>(work)
                       : reinterpret_cast<float2 *>(dalloc(c, (size_t)n * s * sizeof(float2), st));
     if (!zs) return HODLR_OUT_OF_MEMORY;
     int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
     split_vec_kernel<<<blocks, 256, 0, st>>>(Z, ldz, n, s, zs);
-    cudaError_t e = cudaMemset2DAsync(W, ldw * sizeof(double), 0, n * sizeof(double), s, st);
+    note_launch();
+    cudaError_t e = w_zeroed ? cudaSuccess : cudaMemset2DAsync(W, ldw * sizeof(double), 0, n * sizeof(double), s, st);
     const dim3 grid((unsigned)((n + MV_ROWS - 1) / MV_ROWS), (unsigned)((n + MV_KC - 1) / MV_KC));
     const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     for (int r0 = 0; r0 < s && e == cudaSuccess; r0 += MV_S) {
@@ -425,6 +585,7 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
             df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
         else
             df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
+        note_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -509,6 +670,7 @@ extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const
     HODLR_TRY_CUDA(cudaMemset2DAsync(W, ldw * sizeof(double), 0, n * sizeof(double), s, st));
     const int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
     split_vec_kernel<<<blocks, 256, 0, st>>>(Z, ldz, n, s, slot.split);
+    note_launch();
     const dim3 grid((unsigned)((n + MV_ROWS - 1) / MV_ROWS), (unsigned)((n + MV_KC - 1) / MV_KC));
     const bool vec = (A->ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(A->data) & 15) == 0);
     for (int r0 = 0; r0 < s; r0 += MV_S) {
@@ -517,6 +679,7 @@ extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const
         else
             df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw,
                                                                  slot.status);
+        note_launch();
     }
     HODLR_TRY_CUDA(cudaGetLastError());
     int hstat = 0;
@@ -620,8 +783,6 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     HODLR_TRY_CUDA(cudaEventRecord(e0, st));
 
     const dim3 vgrid((unsigned)std::min<int64_t>((n + KT - 1) / KT, 1024), s);
-    const int64_t gchunk = 256;
-    const dim3 ggrid((unsigned)((n + gchunk - 1) / gchunk), s);
     // x0 = 0; iteration counters and per-rhs state start at zero
     HODLR_TRY_CUDA(cudaMemset2DAsync(X, ldx * 8, 0, n * 8, s, st));
     HODLR_TRY_CUDA(cudaMemsetAsync(ibuf, 0, (size_t)(4 * s + 4) * sizeof(int), st));
@@ -638,11 +799,50 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         // R := B - 0 computed as residual_kernel(B, Wv=0): zero Wv first
         HODLR_TRY_CUDA(cudaMemset2DAsync(Wv, n * 8, 0, n * 8, s, st));
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
+        note_launch();
     }
     // ---- one Arnoldi iteration, recorded once and replayed by a device-side
-    // while loop (a conditional graph node) until no right-hand side is active
+    // while loop (a conditional graph node) until no right-hand side is active:
+    // z = P^-1 v_j, w = A z, then the fused Gram-Schmidt / Givens step
     if (P) HODLR_TRY(solve_prepare(P, s, st));
+    HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, st));
+    TailArgs ta{};
+    ta.Vk = Vk;
+    ta.vstride = vstride;
+    ta.n = n;
+    ta.w = Wv;
+    ta.Zc = Zc;
+    ta.Zk = Zk;
+    ta.zstride = zstride;
+    ta.h1 = h1;
+    ta.h2 = h2;
+    ta.nrm = nrm;
+    ta.hstride = hstride;
+    ta.gs = gs;
+    ta.m = m;
+    ta.s = s;
+    ta.max_iter = max_iter;
+    ta.tol = tol;
+    ta.bar = reinterpret_cast<unsigned *>(ibuf + 3 * s + 2);
+    ta.status = c->d_status;
+    ta.loops = loops;
+    ta.limit = m + 1;
+    const size_t tail_smem = (size_t)(m + 1) * sizeof(double) + 2 * (size_t)s * sizeof(int);
+    HODLR_TRY_CUDA(cudaFuncSetAttribute(arnoldi_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tail_smem));
+    int tail_grid = 0;
+    {
+        int per_sm = 0;
+        HODLR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_tail_kernel, TT, tail_smem));
+        if (per_sm <= 0) {
+            set_error("gmres_solve: restart length %d needs too much shared memory", m);
+            return HODLR_INVALID_ARG;
+        }
+        const int64_t units = ((n + TT - 1) / TT) * s;
+        tail_grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->num_sms * per_sm));
+    }
     IterGraph iter;
+    long long body_kernels = 0;   // kernels of one recorded iteration
     {
         cudaStream_t cs = c->side[HODLR_SIDE_STREAMS - 1];
         HODLR_TRY_CUDA(cudaGraphCreate(&iter.graph, 0));
@@ -658,25 +858,29 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         HODLR_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         auto record = [&]() -> hodlr_status {
-            gather_v_kernel<<<vgrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, gs.active, Zc);
             if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs));
-            scatter_z_kernel<<<vgrid, KT, 0, cs>>>(Zc, n, gs.jcur, gs.active, Zk, zstride);
-            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw));
-            HODLR_TRY_CUDA(cudaMemsetAsync(h1, 0, (size_t)s * hstride * 8, cs));
-            HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, cs));
-            HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, cs));
-            gram_kernel<<<ggrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h1, hstride, gchunk);
-            orth_update_kernel<<<vgrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h1, hstride, nullptr);
-            gram_kernel<<<ggrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h2, hstride, gchunk);
-            orth_update_kernel<<<vgrid, KT, 0, cs>>>(Vk, vstride, n, gs.jcur, Wv, n, gs.active, h2, hstride, nrm);
-            normalize_kernel<<<vgrid, KT, 0, cs>>>(Wv, n, n, gs.active, nrm, Vk, vstride, gs.jcur);
-            HODLR_TRY_CUDA(cudaMemsetAsync(gs.nactive, 0, sizeof(int), cs));
-            givens_kernel<<<(s + 127) / 128, 128, 0, cs>>>(gs, m, s, h1, h2, hstride, nrm, tol, max_iter);
-            loop_condition_kernel<<<1, 1, 0, cs>>>(handle, gs.nactive, loops, m + 1);
-            HODLR_TRY_CUDA(cudaGetLastError());
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true));
+            ta.handle = handle;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)tail_grid);
+            cfg.blockDim = dim3(TT);
+            cfg.dynamicSmemBytes = tail_smem;
+            cfg.stream = cs;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, arnoldi_tail_kernel, ta));
+            note_launch();
             return HODLR_OK;
         };
-        const hodlr_status rs = record();
+        hodlr_status rs;
+        {
+            LaunchCapture cap;
+            rs = record();
+            body_kernels = cap.captured;
+        }
         cudaGraph_t captured = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
         if (rs != HODLR_OK) return rs;
@@ -689,22 +893,28 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     int restarts = 0;
     hodlr_status result = HODLR_OK;
     for (int cycle = 0;; ++cycle) {
-        start_cycle_kernel<<<vgrid, KT, 0, st>>>(gs, m, s, Wv, n, n, nrm, Vk, vstride, tol, max_iter, cycle == 0);
+        start_cycle_kernel<<<vgrid, KT, 0, st>>>(gs, m, s, Wv, n, n, nrm, Vk, vstride, tol, max_iter, cycle == 0, Zc);
+        note_launch();
         count_active_kernel<<<1, 1, 0, st>>>(gs.active, s, gs.nactive);
+        note_launch();
         HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin, gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
         HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+        if (cycle > 0) note_launch((long long)h_pin[1] * body_kernels);   // replays of the previous cycle
         HODLR_TRY(take_status(c, st));
         if (h_pin[0] == 0) break;
         if (cycle > 0) ++restarts;
         HODLR_TRY_CUDA(cudaMemsetAsync(loops, 0, sizeof(int), st));
         HODLR_TRY_CUDA(cudaGraphLaunch(iter.exec, st));
+        HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin + 1, loops, sizeof(int), cudaMemcpyDeviceToHost, st));
         // x += Z y
         backsolve_kernel<<<s, KT, (size_t)m * 8, st>>>(gs, m, Zk, zstride, n, X, ldx);
+        note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
         // true residual R = B - A X
         HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, X, ldx, Wv, n, st, zsw));
         HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, st));
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
+        note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
         if (cycle > 10000) break;
     }

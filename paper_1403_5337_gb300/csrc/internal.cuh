@@ -40,6 +40,21 @@ enum : int {
 
 hodlr_status status_from_word(int w);
 
+// Process-wide count of the kernels the library launches (hodlr_launch_count).
+// While a LaunchCapture lives on the calling thread, launches are being recorded
+// into a graph: they are tallied in it instead, and the caller adds them once
+// per replay.
+void note_launch(long long k = 1);
+long long launch_total();
+struct LaunchCapture {
+    long long captured = 0;
+    LaunchCapture *prev = nullptr;
+    LaunchCapture();
+    ~LaunchCapture();
+    LaunchCapture(const LaunchCapture &) = delete;
+    LaunchCapture &operator=(const LaunchCapture &) = delete;
+};
+
 // ------------------------------------------------------------------ context
 }  // namespace hodlr
 
@@ -125,10 +140,10 @@ struct hodlr_s {
     void *work = nullptr;
     size_t work_bytes = 0;
     // fused apply: 32-row tiles of the leaves (leaf, first row, rows, 0) and the
-    // grid-barrier counter/generation pair
+    // first tile of every leaf (2^L + 1 entries)
     const int4 *d_tiles = nullptr;
     int ntiles = 0;
-    unsigned *d_bar = nullptr;
+    int *d_tile_first = nullptr;
     // the recorded factorisation (workspace, descriptors, launches)
     hodlr::FactorPlan *plan = nullptr;
     // events around the last factorisation, read lazily by hodlr_stats_get
@@ -191,7 +206,7 @@ hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cud
 hodlr_status solve_prepare(const hodlr_t *h, int s_rhs, cudaStream_t s);
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s_rhs,
                          const double *Z, int64_t ldz, double *W, int64_t ldw, cudaStream_t s,
-                         void *work = nullptr);
+                         void *work = nullptr, bool w_zeroed = false);
 
 // Convert / pad kernels
 hodlr_status copy_columns(int prec_src, int prec_dst, const void *src, int64_t ld_src,

@@ -76,7 +76,7 @@ SYMBOLS = ["hodlr_ctx_create", "hodlr_ctx_destroy", "hodlr_opts_default", "hodlr
            "hodlr_solve", "gmres_solve", "hodlr_matvec", "hodlr_matvec_noalloc", "hodlr_precond_error",
            "hodlr_stats_get",
            "hodlr_export_level", "hodlr_export_core", "hodlr_destroy", "hodlr_status_string",
-           "hodlr_last_error"]
+           "hodlr_last_error", "hodlr_launch_count"]
 
 _lib = None
 # Library calls in progress on this process.  The torch allocator callbacks run
@@ -384,6 +384,14 @@ def gmres_solve(ctx: Context, A: torch.Tensor, B: torch.Tensor, P: Hodlr | None 
     if code not in (0, 6) or (code == 6 and raise_on_fail):
         _check(code)
     return X, GmresInfo(it, est, tr, info.restarts, info.ms_total, code == 0)
+
+
+def hodlr_launch_count() -> int:
+    """Kernels launched by libhodlr in this process so far (see include/hodlr.h)."""
+    lib = load_library()
+    out = C.c_longlong(0)
+    _check(lib.hodlr_launch_count(C.byref(out)))
+    return int(out.value)
 
 
 def hodlr_precond_error(h: Hodlr, Omega: torch.Tensor, stream=None) -> float:

@@ -175,6 +175,26 @@ def test_refactor_is_idempotent(H, ctx, front576):
     h.close()
 
 
+def test_launch_count_covers_replayed_iterations(H, ctx, front576):
+    """hodlr_launch_count includes the kernels a recorded Arnoldi iteration runs
+    on every device-side replay, not only the host-side launches."""
+    F = front576
+    A = _dev(F.A)
+    h = H.hodlr_build(ctx, A, 64, 1e-6, "aca", precision="fp32")
+    H.hodlr_factor(h)
+    b = fg.rhs(F.n, 1, seed=5)
+    c0 = H.hodlr_launch_count()
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    c1 = H.hodlr_launch_count()
+    it = int(info.iters.max())
+    assert info.converged and it >= 2
+    # per replayed iteration: the apply, the split of z, the product, the fused
+    # Arnoldi step; per cycle at least the start, the back substitution, the
+    # true-residual product and the residual
+    assert c1 - c0 >= 4 * it + 4
+    h.close()
+
+
 def test_solve_fp32(H, ctx, front576):
     F = front576
     tree = O.make_tree(F.n, 64, F.bounds)
