@@ -137,9 +137,47 @@ __device__ void fa_vtx(const FusedArgs<T, S> &a, int c, int child, int64_t row0,
     __syncthreads();
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Pull everything this CTA's tiles will read into L2 up front (the leaf inverse
+// rows, every level's d and V rows of the tiles, a 1/gridDim share of the S^-1
+// cores), so that the dependent phases later hit L2 instead of HBM.
+template <typename T, typename S>
+__device__ void prefetch_tiles(const FusedArgs<T, S> &a) {
+    constexpr int LINE = 128;
+    constexpr int per_line = LINE / sizeof(S);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int4 tl = a.tiles[t];
+        const int leaf = tl.x, nrows = tl.z;
+        const int64_t row0 = tl.y;
+        const int64_t l0 = a.bounds[leaf];
+        const int b = (int)(a.bounds[leaf + 1] - l0);
+        const T *K = a.Kinv + (size_t)leaf * a.bmax * a.bmax + (row0 - l0);
+        for (int k = threadIdx.x; k < b; k += AP_THREADS) prefetch_l2(K + (size_t)k * a.bmax);
+        const int lines = (nrows + per_line - 1) / per_line;   // every line starts inside the tile
+        for (int c = 1; c <= a.L; ++c) {
+            const int rp = a.rp[c];
+            for (int e = threadIdx.x; e < 2 * rp * lines; e += AP_THREADS) {
+                const int col = e / (2 * lines), r = e % (2 * lines);
+                const S *base = (r < lines ? a.D : a.V) + (a.coff[c] + col) * a.ldn + row0;
+                prefetch_l2(base + (int64_t)(r % lines) * per_line);
+            }
+        }
+    }
+    for (int c = 1; c <= a.L; ++c) {
+        const int64_t s2 = 2 * (int64_t)a.rp[c];
+        const int64_t bytes = (int64_t)(1 << (c - 1)) * s2 * s2 * sizeof(T);
+        const char *p = reinterpret_cast<const char *>(a.Sinv[c - 1]);
+        for (int64_t o = ((int64_t)blockIdx.x * AP_THREADS + threadIdx.x) * LINE; o < bytes;
+             o += (int64_t)gridDim.x * AP_THREADS * LINE)
+            prefetch_l2(p + o);
+    }
+}
+
 template <typename T, typename S>
 __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs<T, S> a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    prefetch_tiles(a);
     extern __shared__ __align__(16) unsigned char smem[];
     T *part = reinterpret_cast<T *>(smem);                          // 8 warps x 32 rows x FA_RC
     T *ys = part + (AP_THREADS / 32) * TR * FA_RC;                  // this tile's half of y: rp x FA_RC

@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(GJS_THREADS) gj_inverse_smem_kernel(const GJDe
 
 constexpr size_t GJS_SMEM_MAX = 200 * 1024;
 
-// Gauss-Jordan inversion with the matrix held in registers: 512 threads as a
-// 16 x 32 grid, thread (ty, tx) owns rows ty + 16 p (p < MR) and columns
+// Gauss-Jordan inversion with the matrix held in registers: 256 threads as an
+// 8 x 32 grid, thread (ty, tx) owns rows ty + 8 p (p < MR) and columns
 // tx + 32 q (q < MC).  Pivoting is implicit (no row exchanges): step k sweeps
 // the pivot (p_k, k), p_k = argmax |a(i, k)| over the rows not yet used as
 // pivots (lowest row on ties):
@@ -383,11 +383,14 @@ constexpr size_t GJS_SMEM_MAX = 200 * 1024;
 //   a(i, k)  = -a(i, k) / a(p_k, k),  a(p_k, j) = a(p_k, j) / a(p_k, k),
 //   a(p_k, k) = 1 / a(p_k, k).
 // After the b sweeps the table maps outputs to inputs, M^-1(k, p_j) =
-// a(p_k, j).  A step costs two CTA barriers: one after the column owners post
-// their candidate pivots, one after the pivot row's owner posts that row; the
-// pivot column and row buffers are double-buffered by step parity.  Register
-// slots are selected with unrolled predicated loops, never by a run-time index.
-constexpr int GJR_TY = 16, GJR_TX = 32, GJR_THREADS = GJR_TY * GJR_TX;
+// a(p_k, j).  The steps run as MC unrolled blocks of 32, so the register slot of
+// column k is a compile-time index.  A step costs two CTA barriers: one after
+// the column owners post their candidate pivots (merged by a shuffle argmax in
+// every warp), one after the pivot row's owner posts that row, with the pivot
+// entries of the posted row and column adjusted so that a single FMA per
+// element performs all four cases of the sweep.  The pivot column and row
+// buffers are double-buffered by step parity.
+constexpr int GJR_TY = 8, GJR_TX = 32, GJR_THREADS = GJR_TY * GJR_TX;
 
 template <typename T, int MR, int MC>
 __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJDesc<T> *__restrict__ descs,
@@ -403,11 +406,11 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJ
     __shared__ int prow[MR * GJR_TY];   // pivot row of step k
     __shared__ int krow[MR * GJR_TY];   // step at which row i was the pivot
     T a[MR][MC];
-    unsigned used = 0;                  // bit p: row ty + 16 p is a pivot already (or beyond b)
+    unsigned long long used = 0;        // bit p: row ty + 8 p is a pivot already (or beyond b)
 #pragma unroll
     for (int p = 0; p < MR; ++p) {
         const int i = ty + GJR_TY * p;
-        if (i >= b) used |= 1u << p;
+        if (i >= b) used |= 1ull << p;
 #pragma unroll
         for (int q = 0; q < MC; ++q) {
             const int j = tx + GJR_TX * q;
@@ -418,78 +421,94 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJ
         }
     }
     bool fail = false;
-    for (int k = 0; k < b; ++k) {
-        const int par = k & 1, kq = k / GJR_TX, kx = k % GJR_TX;
-        // A. the owners of column k post it and their best unused row
-        if (tx == kx) {
-            T bv = T(-1), sv = T(0);
-            int bi = INT_MAX;
+#pragma unroll
+    for (int kq = 0; kq < MC; ++kq) {
+        const int kxe = min(GJR_TX, b - kq * GJR_TX);
+        for (int kx = 0; kx < kxe && !fail; ++kx) {
+            const int k = kq * GJR_TX + kx;
+            const int par = k & 1;
+            // A. the owners of column k post it and their best unused row
+            if (tx == kx) {
+                T bv = T(-1), sv = T(0);
+                int bi = INT_MAX;
+#pragma unroll
+                for (int p = 0; p < MR; ++p) {
+                    const T v = a[p][kq];
+                    colk[par][ty + GJR_TY * p] = v;
+                    const T av = fabs(v);
+                    if (!((used >> p) & 1ull) && av > bv) {
+                        bv = av;
+                        sv = v;
+                        bi = ty + GJR_TY * p;
+                    }
+                }
+                cand_v[par][ty] = sv;
+                cand_i[par][ty] = bi;
+            }
+            __syncthreads();
+            // B. every warp merges the candidates with a shuffle argmax (same result everywhere)
+            T pa = T(-1), piv = T(0);
+            int pr = INT_MAX;
+            if (tx < GJR_TY) {
+                pr = cand_i[par][tx];
+                piv = cand_v[par][tx];
+                pa = pr == INT_MAX ? T(-1) : fabs(piv);
+            }
+#pragma unroll
+            for (int o = GJR_TY / 2; o > 0; o >>= 1) {
+                const T oa = __shfl_xor_sync(0xffffffffu, pa, o);
+                const T ov = __shfl_xor_sync(0xffffffffu, piv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, pr, o);
+                if (oa > pa || (oa == pa && oi < pr)) {
+                    pa = oa;
+                    piv = ov;
+                    pr = oi;
+                }
+            }
+            pa = __shfl_sync(0xffffffffu, pa, 0);
+            piv = __shfl_sync(0xffffffffu, piv, 0);
+            pr = __shfl_sync(0xffffffffu, pr, 0);
+            if (!(pa > T(0))) {   // uniform: no usable pivot in column k
+                fail = true;
+                break;
+            }
+            const int py = pr % GJR_TY, pp = pr / GJR_TY;
+            // The four cases of the sweep as one update a(i, j) -= (c_i / p) r_j, with
+            // the pivot row r = a(pr, :) except r_k = p + 1 and the pivot column
+            // c = a(:, k) except c_pr = p - 1 (p = a(pr, k)):
+            //   i != pr, j != k:  a - a(i,k) a(pr,j) / p
+            //   i != pr, j == k:  a(i,k) - a(i,k)(p + 1)/p      = -a(i,k) / p
+            //   i == pr, j != k:  a(pr,j) - (p - 1) a(pr,j) / p =  a(pr,j) / p
+            //   i == pr, j == k:  p - (p - 1)(p + 1) / p        =  1 / p
+            // (each exact up to the rounding of 1/p, p +- 1 and the update).
+            if (ty == py) {
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == pp) {
+                        used |= 1ull << p;
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) {
+                            const int j = tx + GJR_TX * q;
+                            rowk[par][j] = (j == k) ? piv + T(1) : a[p][q];
+                        }
+                    }
+            }
+            if (tid == 0) {
+                prow[k] = pr;
+                krow[pr] = k;
+                colk[par][pr] = piv - T(1);
+            }
+            __syncthreads();
+            // C. sweep the pivot (pr, k)
+            const T d = T(1) / piv;
+            T rk[MC];
+#pragma unroll
+            for (int q = 0; q < MC; ++q) rk[q] = rowk[par][tx + GJR_TX * q];
 #pragma unroll
             for (int p = 0; p < MR; ++p) {
-                T v = T(0);
+                const T f = colk[par][ty + GJR_TY * p] * d;
 #pragma unroll
-                for (int q = 0; q < MC; ++q)
-                    if (q == kq) v = a[p][q];
-                colk[par][ty + GJR_TY * p] = v;
-                const T av = fabs(v);
-                if (!((used >> p) & 1u) && av > bv) {
-                    bv = av;
-                    sv = v;
-                    bi = ty + GJR_TY * p;
-                }
-            }
-            cand_v[par][ty] = sv;
-            cand_i[par][ty] = bi;
-        }
-        __syncthreads();
-        // B. every thread merges the 16 candidates (same order, same result)
-        T piv = T(0), pa = T(-1);
-        int pr = INT_MAX;
-#pragma unroll
-        for (int w = 0; w < GJR_TY; ++w) {
-            const int wi = cand_i[par][w];
-            const T wv = cand_v[par][w], wa = fabs(wv);
-            if (wi != INT_MAX && (wa > pa || (wa == pa && wi < pr))) {
-                pa = wa;
-                piv = wv;
-                pr = wi;
-            }
-        }
-        if (!(pa > T(0))) {   // uniform: no usable pivot in column k
-            fail = true;
-            break;
-        }
-        const int py = pr % GJR_TY, pp = pr / GJR_TY;
-        if (ty == py) {
-#pragma unroll
-            for (int p = 0; p < MR; ++p)
-                if (p == pp) {
-                    used |= 1u << p;
-#pragma unroll
-                    for (int q = 0; q < MC; ++q) rowk[par][tx + GJR_TX * q] = a[p][q];
-                }
-        }
-        if (tid == 0) {
-            prow[k] = pr;
-            krow[pr] = k;
-        }
-        __syncthreads();
-        // C. sweep the pivot (pr, k)
-        const T d = T(1) / piv;
-        T rk[MC];
-#pragma unroll
-        for (int q = 0; q < MC; ++q) rk[q] = rowk[par][tx + GJR_TX * q];
-#pragma unroll
-        for (int p = 0; p < MR; ++p) {
-            const T f = colk[par][ty + GJR_TY * p] * d;
-            const bool prow_here = (ty == py) && (p == pp);
-#pragma unroll
-            for (int q = 0; q < MC; ++q) {
-                const bool kcol = (tx == kx) && (q == kq);
-                T v = fma(-f, rk[q], a[p][q]);
-                if (kcol) v = -f;
-                if (prow_here) v = kcol ? d : rk[q] * d;
-                a[p][q] = v;
+                for (int q = 0; q < MC; ++q) a[p][q] = fma(-f, rk[q], a[p][q]);
             }
         }
     }
@@ -576,13 +595,14 @@ bool gj_needs_work(int bmax) {
 
 template <typename T>
 hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, cudaStream_t s) {
-    if (bmax <= 32) return launch_gj_reg<T, 2, 1>(c, dd, count, s);
-    if (bmax <= 64) return launch_gj_reg<T, 4, 2>(c, dd, count, s);
-    if (bmax <= 96) return launch_gj_reg<T, 6, 3>(c, dd, count, s);
-    if (bmax <= 128) return launch_gj_reg<T, 8, 4>(c, dd, count, s);
+    if (bmax <= 32) return launch_gj_reg<T, 4, 1>(c, dd, count, s);
+    if (bmax <= 64) return launch_gj_reg<T, 8, 2>(c, dd, count, s);
+    if (bmax <= 96) return launch_gj_reg<T, 12, 3>(c, dd, count, s);
+    if (bmax <= 128) return launch_gj_reg<T, 16, 4>(c, dd, count, s);
     if constexpr (sizeof(T) == 4) {   // FP64 tiles beyond 128 would spill registers
-        if (bmax <= 160) return launch_gj_reg<T, 10, 5>(c, dd, count, s);
-        if (bmax <= 192) return launch_gj_reg<T, 12, 6>(c, dd, count, s);
+        if (bmax <= 144) return launch_gj_reg<T, 18, 5>(c, dd, count, s);
+        if (bmax <= 160) return launch_gj_reg<T, 20, 5>(c, dd, count, s);
+        if (bmax <= 192) return launch_gj_reg<T, 24, 6>(c, dd, count, s);
     }
     if (gjs_smem<T>(bmax) <= GJS_SMEM_MAX) {
         const size_t sm = gjs_smem<T>(bmax);
