@@ -290,6 +290,38 @@ __global__ void __launch_bounds__(CT, 1)
         const T *Uo = cl.map_shared_rank(Us, co);
         for (int l = tid; l < kk; l += CT) pu[l] = (l < kcs) ? Uo[(size_t)l * smr + li] : Ug[(int64_t)l * ld + ir];
     };
+    // The same gathers split into a register-staged load, issued as soon as the
+    // index is known, and the store to shared memory where the values are due,
+    // so that the remote (DSMEM) latency overlaps other work.
+    constexpr int GR = ACA_CAP / CT;
+    T greg[GR];
+    auto pu_load = [&](int ir, int kk) {
+        const int co = (int)(ir / mr);
+        const int64_t li = ir - (int64_t)co * mr;
+        const T *Uo = cl.map_shared_rank(Us, co);
+#pragma unroll
+        for (int t = 0; t < GR; ++t) {
+            const int l = tid + t * CT;
+            greg[t] = (l < kk) ? ((l < kcs) ? Uo[(size_t)l * smr + li] : Ug[(int64_t)l * ld + ir]) : T(0);
+        }
+    };
+    auto pv_load = [&](int jc, int kk) {
+        const int cv = (int)(jc / nr);
+        const int64_t lj = jc - (int64_t)cv * nr;
+        const T *Vo = cl.map_shared_rank(Vs, cv);
+#pragma unroll
+        for (int t = 0; t < GR; ++t) {
+            const int l = tid + t * CT;
+            greg[t] = (l < kk) ? ((l < kcs) ? Vo[(size_t)l * snr + lj] : Vg[(int64_t)l * ld + jc]) : T(0);
+        }
+    };
+    auto greg_store = [&](T *dst, int kk) {
+#pragma unroll
+        for (int t = 0; t < GR; ++t) {
+            const int l = tid + t * CT;
+            if (l < kk) dst[l] = greg[t];
+        }
+    };
     load_row(0);
     __syncthreads();
     cl.sync();
@@ -332,7 +364,10 @@ __global__ void __launch_bounds__(CT, 1)
         const int jk = best.idx;
         const T piv = best.v;
         const bool have = !(jk == INT_MAX || piv == T(0));
-        if (have) load_col(jk);
+        if (have) {
+            load_col(jk);
+            pv_load(jk, k);   // V(j_k, l), l < k: written in earlier steps by the owner of column j_k
+        }
         // the owner of row i marks it used
         if (i >= i0 && i < i1 && tid == 0) used[i - i0] = 1;
         if (!have) {
@@ -366,13 +401,7 @@ __global__ void __launch_bounds__(CT, 1)
                 Vg[(int64_t)k * ld + j] = v;
             }
         }
-        // V(j_k, l) for l < k: written in earlier steps by the owner of column j_k
-        {
-            const int cv = (int)(jk / nr);
-            const int64_t lj = jk - (int64_t)cv * nr;
-            const T *Vo = cl.map_shared_rank(Vs, cv);
-            for (int l = tid; l < k; l += CT) pv[l] = (l < kcs) ? Vo[(size_t)l * snr + lj] : Vg[(int64_t)l * ld + jk];
-        }
+        greg_store(pv, k);
         __syncthreads();
         // ---- column pass on own rows -> u_k
         T ca = T(-1), cvv = T(0);
@@ -432,7 +461,7 @@ __global__ void __launch_bounds__(CT, 1)
         const Cand<T> bc = best_of_slots(&slots[par][1][0], CL);
         if (bc.a >= T(0)) {
             load_row(bc.idx);          // the next pivot row and its U entries, while the stop test is made
-            gather_pu(bc.idx, k + 1);
+            pu_load(bc.idx, k + 1);
         }
         CrossAcc<T> xacc;
         for (int l = tid; l <= k; l += CT) {
@@ -491,6 +520,7 @@ __global__ void __launch_bounds__(CT, 1)
             s_stop = stop;
             s_i = bc.idx;
         }
+        if (bc.a >= T(0)) greg_store(pu, k + 1);
         __syncthreads();
         ++k;
         if (s_stop) break;

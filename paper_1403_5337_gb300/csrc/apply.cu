@@ -27,7 +27,6 @@ namespace {
 
 constexpr int AP_THREADS = 256;
 constexpr int TR = 32;      // rows per tile
-constexpr int FA_RC = 8;    // right-hand sides per pass
 constexpr unsigned long long FA_SPIN_LIMIT = 1ull << 26;
 
 // Storage -> arithmetic type of the streamed factors (V, d): FP64, FP32, or a
@@ -66,11 +65,11 @@ struct FusedArgs {
 };
 
 // Lane-row / warp-split reduction helper: part[warp][lane][q] -> sum over warps.
-template <typename T>
+template <typename T, int RC>
 __device__ __forceinline__ T warp_parts_sum(const T *part, int lane_row, int q) {
     T v = T(0);
 #pragma unroll
-    for (int wv = 0; wv < AP_THREADS / 32; ++wv) v += part[(wv * TR + lane_row) * FA_RC + q];
+    for (int wv = 0; wv < AP_THREADS / 32; ++wv) v += part[(wv * TR + lane_row) * RC + q];
     return v;
 }
 
@@ -101,40 +100,71 @@ __device__ __forceinline__ void wait_node(const unsigned *cnt, unsigned target, 
 }
 
 // Partial V_c^T x over one tile's rows into w(c): the tile's block of V (32
-// rows x rp, coalesced column reads) and of x are staged in shared memory, then
-// one thread per column forms its 32-term dot products (padded stride: no bank
-// conflicts) and adds them to w with one atomic per (column, rhs).
-template <typename T, typename S>
+// rows x rp, coalesced column reads, four columns in flight per warp) and of x
+// are staged in shared memory, then one thread per column forms its 32-term dot
+// products (padded stride: no bank conflicts) and adds them to w with one
+// atomic per (column, rhs).
+template <typename T, typename S, int RC>
 __device__ void fa_vtx(const FusedArgs<T, S> &a, int c, int child, int64_t row0, int nrows, int r0, int rr,
                        T *sv, T *xs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = AP_THREADS / 32;
     const int rp = a.rp[c];
     const S *Vc = a.V + a.coff[c] * a.ldn;
     T *w = a.w[c];
     const float *vs = a.vscale[c];
-    for (int col = warp; col < rp; col += AP_THREADS / 32)
-        sv[col * (TR + 1) + lane] = (lane < nrows) ? to_t<T>(Vc[row0 + lane + (int64_t)col * a.ldn]) : T(0);
-    for (int e = threadIdx.x; e < TR * FA_RC; e += AP_THREADS) {
+    const int64_t row = row0 + lane;
+    int col = warp;
+    for (; col + 3 * NW < rp; col += 4 * NW) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (lane < nrows) ? to_t<T>(Vc[row + (int64_t)(col + u * NW) * a.ldn]) : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sv[(col + u * NW) * (TR + 1) + lane] = v[u];
+    }
+    for (; col < rp; col += NW) sv[col * (TR + 1) + lane] = (lane < nrows) ? to_t<T>(Vc[row + (int64_t)col * a.ldn]) : T(0);
+    for (int e = threadIdx.x; e < TR * RC; e += AP_THREADS) {
         const int li = e % TR, q = e / TR;
         xs[q * TR + li] = (li < nrows && q < rr) ? a.xt[row0 + li + (r0 + q) * a.ldn] : T(0);
     }
     __syncthreads();
-    for (int col = threadIdx.x; col < rp; col += AP_THREADS) {
-        T acc[FA_RC];
+    for (int cc = threadIdx.x; cc < rp; cc += AP_THREADS) {
+        T acc[RC];
 #pragma unroll
-        for (int q = 0; q < FA_RC; ++q) acc[q] = T(0);
+        for (int q = 0; q < RC; ++q) acc[q] = T(0);
 #pragma unroll 8
         for (int li = 0; li < TR; ++li) {
-            const T v = sv[col * (TR + 1) + li];
+            const T v = sv[cc * (TR + 1) + li];
 #pragma unroll
-            for (int q = 0; q < FA_RC; ++q) acc[q] = fma(v, xs[q * TR + li], acc[q]);
+            for (int q = 0; q < RC; ++q) acc[q] = fma(v, xs[q * TR + li], acc[q]);
         }
-        const T sc = vs ? (T)vs[(size_t)child * rp + col] : T(1);
+        const T sc = vs ? (T)vs[(size_t)child * rp + cc] : T(1);
 #pragma unroll
-        for (int q = 0; q < FA_RC; ++q)
-            if (q < rr) atomicAdd(&w[((size_t)child * rp + col) * a.s + r0 + q], acc[q] * sc);
+        for (int q = 0; q < RC; ++q)
+            if (q < rr) atomicAdd(&w[((size_t)child * rp + cc) * a.s + r0 + q], acc[q] * sc);
     }
     __syncthreads();
+}
+
+// acc[q] += sum_{k in [kb, ke)} M(k) y[k * RC + q] with M(k) = col[k * ldm] streamed
+// from global memory eight columns at a time (loads in flight before the FMAs).
+template <typename T, typename E, int RC>
+__device__ __forceinline__ void stream_dot(const E *col, int64_t ldm, const T *y, int kb, int ke, T (&acc)[RC]) {
+    int k = kb;
+    for (; k + 8 <= ke; k += 8) {
+        T m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m[u] = to_t<T>(col[(int64_t)(k + u) * ldm]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int q = 0; q < RC; ++q) acc[q] = fma(m[u], y[(k + u) * RC + q], acc[q]);
+    }
+    for (; k < ke; ++k) {
+        const T m = to_t<T>(col[(int64_t)k * ldm]);
+#pragma unroll
+        for (int q = 0; q < RC; ++q) acc[q] = fma(m, y[k * RC + q], acc[q]);
+    }
 }
 
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
@@ -174,16 +204,16 @@ __device__ void prefetch_tiles(const FusedArgs<T, S> &a) {
     }
 }
 
-template <typename T, typename S>
+template <typename T, typename S, int RC>
 __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs<T, S> a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     prefetch_tiles(a);
     extern __shared__ __align__(16) unsigned char smem[];
-    T *part = reinterpret_cast<T *>(smem);                          // 8 warps x 32 rows x FA_RC
-    T *ys = part + (AP_THREADS / 32) * TR * FA_RC;                  // this tile's half of y: rp x FA_RC
-    T *ws = ys + (size_t)a.rpmax * FA_RC;                           // w of the node: 2 rp x FA_RC
-    T *sv = ws + 2 * (size_t)a.rpmax * FA_RC;                       // V tile: rp x (32 + 1)
-    T *xs = sv + (size_t)a.rpmax * (TR + 1);                        // x tile: FA_RC x 32
+    T *part = reinterpret_cast<T *>(smem);                          // 8 warps x 32 rows x RC
+    T *ys = part + (AP_THREADS / 32) * TR * RC;                     // this tile's half of y: rp x RC
+    T *ws = ys + (size_t)a.rpmax * RC;                              // w of the node: 2 rp x RC; the leaf's x
+    T *sv = ws + (size_t)std::max(2 * a.rpmax, a.bmax) * RC;        // V tile: rp x (32 + 1)
+    T *xs = sv + (size_t)a.rpmax * (TR + 1);                        // x tile: RC x 32
     const int L = a.L;
     // ---- leaves: x = K_leaf^-1 x on the tile's rows, then the leaf level's V^T x
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -195,32 +225,31 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
         const T *K = a.Kinv + (size_t)leaf * a.bmax * a.bmax;
         const int il = (int)(row0 - l0) + lane;
         const int kper = (b + 7) / 8, kb = warp * kper, ke = min(b, kb + kper);
-        for (int r0 = 0; r0 < a.s; r0 += FA_RC) {
-            const int rr = min(FA_RC, a.s - r0);
-            T acc[FA_RC];
-#pragma unroll
-            for (int q = 0; q < FA_RC; ++q) acc[q] = T(0);
-            if (lane < nrows) {
-                for (int k = kb; k < ke; ++k) {
-                    const T kv = K[il + (size_t)k * a.bmax];
-#pragma unroll
-                    for (int q = 0; q < FA_RC; ++q)
-                        if (q < rr) acc[q] = fma(kv, dev::from_double<T>(a.Xin[l0 + k + (r0 + q) * a.ldxin]), acc[q]);
-                }
+        for (int r0 = 0; r0 < a.s; r0 += RC) {
+            const int rr = min(RC, a.s - r0);
+            // the leaf's rows of X, converted once
+            for (int e = threadIdx.x; e < b * RC; e += AP_THREADS) {
+                const int k = e / RC, q = e % RC;
+                ws[k * RC + q] = (q < rr) ? dev::from_double<T>(a.Xin[l0 + k + (int64_t)(r0 + q) * a.ldxin]) : T(0);
             }
+            __syncthreads();
+            T acc[RC];
 #pragma unroll
-            for (int q = 0; q < FA_RC; ++q) part[(warp * TR + lane) * FA_RC + q] = acc[q];
+            for (int q = 0; q < RC; ++q) acc[q] = T(0);
+            if (lane < nrows) stream_dot<T, T, RC>(K + il, a.bmax, ws, kb, ke, acc);
+#pragma unroll
+            for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
             __syncthreads();
             for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
                 const int li = e % TR, q = e / TR;
                 if (li < nrows) {
-                    const T v = warp_parts_sum(part, li, q);
+                    const T v = warp_parts_sum<T, RC>(part, li, q);
                     a.xt[row0 + li + (r0 + q) * a.ldn] = v;
                     if (L == 0) a.X[row0 + li + (r0 + q) * a.ldx] = (double)v;
                 }
             }
             __syncthreads();
-            if (L >= 1) fa_vtx(a, L, leaf, row0, nrows, r0, rr, sv, xs);
+            if (L >= 1) fa_vtx<T, S, RC>(a, L, leaf, row0, nrows, r0, rr, sv, xs);
         }
         if (L >= 1) arrive(a.cnt[L] + (leaf >> 1));
     }
@@ -244,61 +273,50 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
             const T *wn = a.w[c] + (size_t)node * s2 * a.s;
             const S *Dc = a.D + a.coff[c] * a.ldn;
             const float *ds = a.dscale[c];
-            for (int r0 = 0; r0 < a.s; r0 += FA_RC) {
-                const int rr = min(FA_RC, a.s - r0);
+            for (int r0 = 0; r0 < a.s; r0 += RC) {
+                const int rr = min(RC, a.s - r0);
                 if (rp > 0) {
                     // w of the node (complete: read past L1)
-                    for (int e = threadIdx.x; e < s2 * rr; e += AP_THREADS) {
-                        const int k = e / rr, q = e % rr;
-                        ws[k * FA_RC + q] = __ldcg(wn + (size_t)k * a.s + r0 + q);
+                    for (int e = threadIdx.x; e < s2 * RC; e += AP_THREADS) {
+                        const int k = e / RC, q = e % RC;
+                        ws[k * RC + q] = (q < rr) ? __ldcg(wn + (size_t)k * a.s + r0 + q) : T(0);
                     }
                     __syncthreads();
                     // ys = S^-1(half rows, :) w: lanes over rows, warps split the 2 rp columns
                     const int kper = (s2 + 7) / 8, kb = warp * kper, ke = min(s2, kb + kper);
                     for (int i0 = 0; i0 < rp; i0 += TR) {
                         const int i = i0 + lane;
-                        T acc[FA_RC];
+                        T acc[RC];
 #pragma unroll
-                        for (int q = 0; q < FA_RC; ++q) acc[q] = T(0);
-                        if (i < rp)
-                            for (int k = kb; k < ke; ++k) {
-                                const T sval = Sn[half + i + (size_t)k * s2];
+                        for (int q = 0; q < RC; ++q) acc[q] = T(0);
+                        if (i < rp) stream_dot<T, T, RC>(Sn + half + i, s2, ws, kb, ke, acc);
 #pragma unroll
-                                for (int q = 0; q < FA_RC; ++q) acc[q] = fma(sval, ws[k * FA_RC + q], acc[q]);
-                            }
-#pragma unroll
-                        for (int q = 0; q < FA_RC; ++q) part[(warp * TR + lane) * FA_RC + q] = acc[q];
+                        for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
                         __syncthreads();
-                        for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
+                        for (int e = threadIdx.x; e < TR * RC; e += AP_THREADS) {
                             const int li = e % TR, q = e / TR;
                             const int ii = i0 + li;
                             if (ii < rp) {
-                                const T yv = warp_parts_sum(part, li, q);
-                                ys[ii * FA_RC + q] = ds ? yv * (T)ds[(size_t)child * rp + ii] : yv;
+                                const T yv = warp_parts_sum<T, RC>(part, li, q);
+                                ys[ii * RC + q] = ds ? yv * (T)ds[(size_t)child * rp + ii] : yv;
                             }
                         }
                         __syncthreads();
                     }
                     // x -= d y on the tile's rows: lanes over rows, warps split the rp columns
                     const int uper = (rp + 7) / 8, ub = warp * uper, ue = min(rp, ub + uper);
-                    const int64_t row = row0 + lane;
-                    T acc[FA_RC];
+                    T acc[RC];
 #pragma unroll
-                    for (int q = 0; q < FA_RC; ++q) acc[q] = T(0);
-                    if (lane < nrows)
-                        for (int k = ub; k < ue; ++k) {
-                            const T dv = to_t<T>(Dc[row + (int64_t)k * a.ldn]);
+                    for (int q = 0; q < RC; ++q) acc[q] = T(0);
+                    if (lane < nrows) stream_dot<T, S, RC>(Dc + row0 + lane, a.ldn, ys, ub, ue, acc);
 #pragma unroll
-                            for (int q = 0; q < FA_RC; ++q) acc[q] = fma(dv, ys[k * FA_RC + q], acc[q]);
-                        }
-#pragma unroll
-                    for (int q = 0; q < FA_RC; ++q) part[(warp * TR + lane) * FA_RC + q] = acc[q];
+                    for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
                     __syncthreads();
                     for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
                         const int li = e % TR, q = e / TR;
                         if (li < nrows) {
                             const int64_t o = row0 + li + (int64_t)(r0 + q) * a.ldn;
-                            const T v = a.xt[o] - warp_parts_sum(part, li, q);
+                            const T v = a.xt[o] - warp_parts_sum<T, RC>(part, li, q);
                             a.xt[o] = v;
                             if (c == 1) a.X[row0 + li + (int64_t)(r0 + q) * a.ldx] = (double)v;
                         }
@@ -311,12 +329,15 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
                             a.X[row0 + li + (int64_t)(r0 + q) * a.ldx] = (double)a.xt[row0 + li + (int64_t)(r0 + q) * a.ldn];
                     }
                 }
-                if (c > 1) fa_vtx(a, c - 1, leaf >> (L - c + 1), row0, nrows, r0, rr, sv, xs);
+                if (c > 1) fa_vtx<T, S, RC>(a, c - 1, leaf >> (L - c + 1), row0, nrows, r0, rr, sv, xs);
             }
             if (c > 1) arrive(a.cnt[c - 1] + (leaf >> (L - c + 2)));
         }
     }
 }
+
+template <typename T, typename S, int RC>
+hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream_t st);
 
 template <typename T, typename S>
 hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st, const S *V, const S *Dm,
@@ -375,11 +396,21 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
         a.ldxin = h->ldn;
     }
     if (zp > z0) HODLR_TRY_CUDA(cudaMemsetAsync(z0, 0, (size_t)(zp - z0), st));
-    const size_t sm = ((size_t)(AP_THREADS / 32) * TR * FA_RC + 3 * (size_t)a.rpmax * FA_RC +
-                       (size_t)a.rpmax * (TR + 1) + (size_t)TR * FA_RC) * sizeof(T);
-    HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_fused_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (s <= 1) return launch_fused<T, S, 1>(h, a, st);
+    if (s <= 2) return launch_fused<T, S, 2>(h, a, st);
+    if (s <= 4) return launch_fused<T, S, 4>(h, a, st);
+    return launch_fused<T, S, 8>(h, a, st);
+}
+
+template <typename T, typename S, int RC>
+hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream_t st) {
+    const size_t sm = ((size_t)(AP_THREADS / 32) * TR * RC + (size_t)a.rpmax * RC +
+                       (size_t)std::max(2 * a.rpmax, a.bmax) * RC + (size_t)a.rpmax * (TR + 1) + (size_t)TR * RC) *
+                      sizeof(T);
+    HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_fused_kernel<T, S, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sm));
     int per_sm = 0;
-    HODLR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_fused_kernel<T, S>, AP_THREADS, sm));
+    HODLR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_fused_kernel<T, S, RC>, AP_THREADS, sm));
     if (per_sm <= 0) {
         set_error("fused apply: no resident CTA possible (%zu bytes of shared memory)", sm);
         return HODLR_RANGE;
@@ -395,7 +426,7 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, apply_fused_kernel<T, S>, a));
+    HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, apply_fused_kernel<T, S, RC>, a));
     note_launch();
     return HODLR_OK;
 }

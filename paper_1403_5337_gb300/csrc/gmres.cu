@@ -309,7 +309,7 @@ __global__ void count_active_kernel(const int *active, int s, int *nactive) {
 // After w = A z_j: classical Gram-Schmidt twice against v_0..v_j, the new basis
 // vector, the Givens update of the Hessenberg column and the loop test, in one
 // cooperative kernel with three software grid barriers (bounded waits).
-// Work units are (256-row chunk, rhs); thread t of a unit owns one row.
+// Work units are (128-row chunk, rhs); thread t of a unit owns one row.
 //   P1  Z(:, j) = z_j; h1 = V^T w                      (partial sums, atomics)
 //   P2  w -= V h1; h2 = V^T w
 //   P3  w -= V h2; ||w||^2;  CTA 0: H(:, j) = h1 + h2, h1 = 0
@@ -318,7 +318,7 @@ __global__ void count_active_kernel(const int *active, int s, int *nactive) {
 //       H(:, j), residual estimate, activity, loop condition
 // nrm is cleared by CTA 0 in P1 (it is only accumulated in P3).  The step j
 // and the activity of every rhs are fixed until CTA 0 advances them at the end.
-constexpr int TT = 256;
+constexpr int TT = 128;   // one warp per SM sub-partition: the FP64 reductions are pipe-bound
 constexpr int TW = TT / 32;
 constexpr unsigned long long TAIL_SPIN_LIMIT = 1ull << 26;
 
@@ -366,40 +366,61 @@ __device__ void tail_grid_sync(unsigned *bar, int *status) {
     __syncthreads();
 }
 
-// Butterfly sum of 32 values per lane over the warp: after five exchange rounds
-// (each lane keeps the half of its values selected by one bit of its lane
-// index) lane L holds the warp total of value L.  31 additions per lane instead
-// of 32 separate five-round reductions.
-__device__ __forceinline__ double warp_transpose_sum(double (&v)[32], int lane) {
+// Butterfly sum of G values per lane over the warp (G = 8, 16 or 32): rounds
+// with an xor distance of at least G add the partner's values; the later rounds
+// each keep the half of the values selected by one bit of the lane index.  Lane
+// L ends with the warp total of value L mod G, after 31 (G = 32), 31 (16) or
+// 23 (8) FP64 additions instead of five per value.
+template <int G>
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[G], int lane) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
+        if (o >= G) {
 #pragma unroll
-        for (int k = 0; k < o; ++k) {
-            const double send = up ? v[k] : v[k + o];
-            const double keep = up ? v[k + o] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            for (int k = 0; k < G; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        } else {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < o; ++k) {
+                const double send = up ? v[k] : v[k + o];
+                const double keep = up ? v[k + o] : v[k];
+                v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
         }
     }
     return v[0];
+}
+
+// h[i] += sum over the unit's rows of V(q, i) x(q), i in [g0, g0 + G) and i <= j.
+template <int G>
+__device__ __forceinline__ void unit_gram_group(const double *V, int64_t n, int64_t q, bool own, double x, int g0,
+                                                int j, double *h, double *part, int lane, int warp) {
+    double v[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) v[k] = (own && g0 + k <= j) ? V[(int64_t)(g0 + k) * n + q] * x : 0.0;
+    const double t = warp_transpose_sum<G>(v, lane);
+    if (lane < G) part[warp * 32 + lane] = t;
+    __syncthreads();
+    if (threadIdx.x < G && g0 + (int)threadIdx.x <= j) {
+        double u = 0.0;
+#pragma unroll
+        for (int wv = 0; wv < TW; ++wv) u += part[wv * 32 + threadIdx.x];
+        atomicAdd(h + g0 + threadIdx.x, u);
+    }
+    __syncthreads();
 }
 
 // h[i] += sum over the unit's rows of V(q, i) x(q), i <= j (one atomic per i).
 __device__ void unit_gram(const double *V, int64_t n, int64_t q, bool own, double x, int j, double *h,
                           double *part, int lane, int warp) {
     for (int g0 = 0; g0 <= j; g0 += 32) {
-        double v[32];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = (own && g0 + k <= j) ? V[(int64_t)(g0 + k) * n + q] * x : 0.0;
-        part[warp * 32 + lane] = warp_transpose_sum(v, lane);
-        __syncthreads();
-        if (threadIdx.x < 32 && g0 + (int)threadIdx.x <= j) {
-            double t = 0.0;
-#pragma unroll
-            for (int wv = 0; wv < TW; ++wv) t += part[wv * 32 + threadIdx.x];
-            atomicAdd(h + g0 + threadIdx.x, t);
-        }
-        __syncthreads();
+        const int left = j + 1 - g0;
+        if (left <= 8)
+            unit_gram_group<8>(V, n, q, own, x, g0, j, h, part, lane, warp);
+        else if (left <= 16)
+            unit_gram_group<16>(V, n, q, own, x, g0, j, h, part, lane, warp);
+        else
+            unit_gram_group<32>(V, n, q, own, x, g0, j, h, part, lane, warp);
     }
 }
 

@@ -429,3 +429,57 @@ def test_front4096_gmres(H, ctx, front4096, method, tol, prec):
         assert abs(int(info.iters[r]) - ref.iters) <= 2, (r, info.iters, ref.iters)
         assert np.linalg.norm(x[r] - ref.x) / np.linalg.norm(ref.x) < 1e-9
     h.close()
+
+
+@pytest.fixture(scope="module")
+def front16384():
+    return fg.make_front(**fg.WORKLOADS["checker16384"], device="cuda", cache=True)
+
+
+def test_front16384_bf16_high_contrast(H, ctx, front16384):
+    """The high-contrast n = 16384 front (checkerboard 1/1e6), BF16 storage of the
+    factors, ACA tol 1e-3, leaf 256, one right-hand side.  Checked at full size:
+    the ACA pivots and rank of the top-level block A(0:8192, 8192:16384) against
+    the oracle (FP32 decisions); FP64 GMRES reaches max(1e-12, 10 rho_LU), rho_LU
+    the dense FP64 LU solve's own residual (the contrast of 1e6 puts that floor
+    above 1e-12); and the BF16 preconditioner is
+    compared with the FP64 HODLR one, ||(P_bf16^-1 - P_fp64^-1) A Omega|| / ||Omega||."""
+    F = front16384
+    n = F.n
+    A = F.A if torch.is_tensor(F.A) else _dev(F.A)
+    h = H.hodlr_build(ctx, A, 256, 1e-3, "aca", precision="bf16", leaf_bounds=F.bounds)
+    # top-level block against the oracle, in FP32 decisions
+    Ah = A.cpu().numpy()
+    half = int(F.bounds[len(F.bounds) // 2])
+    blk = Ah[:half, half:]
+    ref = O.aca(lambda i: blk[i, :], lambda j: blk[:, j], blk.shape[0], blk.shape[1], 1e-3, 1 << 30, np.float32)
+    U, V, ranks, pr, pc = h.export_level(1)
+    k = ref.U.shape[1]
+    assert ranks[0] == k
+    assert list(pr[0][:k]) == list(ref.rows) and list(pc[0][:k]) == list(ref.cols)
+    H.hodlr_factor(h)
+    b = fg.rhs(n, 1, seed=1)
+    Bd = _dev(b.T)
+    # the attainable residual: FP64 dense LU's own, times 10 (and at most 1e-12)
+    xl = torch.linalg.solve(A, Bd.T)
+    rho = float(torch.linalg.norm(Bd.T - A @ xl) / torch.linalg.norm(Bd))
+    target = max(1e-12, 10 * rho)
+    del xl
+    X, info = H.gmres_solve(ctx, A, Bd, h, tol=target)
+    assert info.converged and info.true_relres[0] <= target, (info.iters, info.true_relres, rho)
+    # preconditioner error of the BF16 factors against the FP64 HODLR
+    h64 = H.hodlr_build(ctx, A, 256, 1e-3, "aca", precision="fp64", leaf_bounds=F.bounds)
+    H.hodlr_factor(h64)
+    g = torch.Generator(device="cpu").manual_seed(2)
+    Om = torch.randn(16, n, generator=g, dtype=torch.float64).cuda()
+    AOm = (A @ Om.T).T.contiguous()
+    Y1 = AOm.clone()
+    Y2 = AOm.clone()
+    H.hodlr_solve(h, Y1)
+    H.hodlr_solve(h64, Y2)
+    perr = float(torch.linalg.norm(Y1 - Y2) / torch.linalg.norm(Om))
+    print(f"checker16384 bf16: target {target:.2e} iters {info.iters.tolist()} true {info.true_relres.tolist()} rho_LU {rho:.2e} "
+          f"rank1 {k} precond-diff {perr:.3e}")
+    assert np.isfinite(perr) and perr < 1.0
+    h64.close()
+    h.close()
