@@ -75,6 +75,12 @@ void dfree(hodlr_ctx *c, void *p, size_t bytes, cudaStream_t s) {
         cudaFreeAsync(p, s);
 }
 
+size_t Arena::take(size_t b) {
+    const size_t o = bytes;
+    bytes += (std::max<size_t>(b, 1) + 255) & ~size_t(255);
+    return o;
+}
+
 void *own(hodlr_t *h, size_t bytes, cudaStream_t s) {
     void *p = dalloc(h->ctx, bytes, s);
     if (p) h->owned.push_back(DevBuf{p, bytes == 0 ? 256 : bytes});
@@ -217,7 +223,8 @@ hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn fr
     c->free_fn = free_fn;
     c->user = user;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_status, 65 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         set_error("hodlr_ctx_create: cannot allocate the status word");
@@ -225,6 +232,7 @@ hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn fr
     }
     cudaMemset(c->d_status, 0, sizeof(int));
     *c->h_status = 0;
+    c->h_scratch = c->h_status + 1;
     for (int i = 0; i < HODLR_SIDE_STREAMS; ++i)
         if (cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
@@ -253,7 +261,6 @@ hodlr_status hodlr_ctx_destroy(hodlr_ctx *c) {
 hodlr_status hodlr_destroy(hodlr_t *h) {
     if (!h) return HODLR_OK;
     cudaSetDevice(h->ctx->device);
-    cudaStreamSynchronize(nullptr);
     cudaDeviceSynchronize();
     free_plan(h, nullptr);
     for (auto &e : h->fev)
@@ -379,25 +386,22 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         hodlr_destroy(h);
         return s;
     };
-    h->d_bounds = (int64_t *)own(h, bounds.size() * sizeof(int64_t), st);
-    if (!h->d_bounds) return fail(HODLR_OUT_OF_MEMORY);
-    if (cudaMemcpyAsync(h->d_bounds, bounds.data(), bounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-        return fail(HODLR_CUDA_ERROR);
     auto nrange = [&](int l, int i, int64_t &r0, int64_t &m) {
         r0 = bounds[(size_t)i << (L - l)];
         m = bounds[(size_t)(i + 1) << (L - l)] - r0;
     };
-    // ---- compression staging
+    // ---- sizes of everything known before the ranks: the tree and pivot
+    // metadata, the apply's tiles and the leaf inverses (one owned allocation),
+    // and the compression staging (one temporary allocation)
     const size_t ce = elem_size(cprec);
-    std::vector<void *> Ust(L + 1, nullptr), Vst(L + 1, nullptr);
-    std::vector<std::pair<void *, size_t>> temp;
-    h->piv_rows.assign(L + 1, nullptr);
-    h->piv_cols.assign(L + 1, nullptr);
-    h->d_ranks.assign(L + 1, nullptr);
-    int32_t *caphit = (int32_t *)own(h, (size_t)(2 << L) * sizeof(int32_t), st);
-    if (!caphit) return fail(HODLR_OUT_OF_MEMORY);
-    std::vector<AcaBlockDesc> blocks;
+    std::vector<int4> tiles;
+    std::vector<int> tfirst(nleaf + 1);
+    for (int i = 0; i < nleaf; ++i) {
+        tfirst[i] = (int)tiles.size();
+        for (int64_t r = bounds[i]; r < bounds[i + 1]; r += 32)
+            tiles.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(32, bounds[i + 1] - r), 0));
+    }
+    tfirst[nleaf] = (int)tiles.size();
     int64_t max_m = 0;
     for (int l = 1; l <= L; ++l) {
         Level &lv = h->lv[l];
@@ -411,37 +415,63 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             max_m = std::max(max_m, m);
         }
         lv.cap = std::max(cap, 1);
-        const size_t sb = (size_t)h->ldn * lv.cap * ce;
-        Ust[l] = dalloc(c, sb, st);
-        Vst[l] = dalloc(c, sb, st);
-        if (!Ust[l] || !Vst[l]) {
-            for (int q = 1; q <= l; ++q) {
-                dfree(c, Ust[q], sb, st);
-                dfree(c, Vst[q], sb, st);
-            }
-            return fail(HODLR_OUT_OF_MEMORY);
-        }
-        temp.push_back({Ust[l], sb});
-        temp.push_back({Vst[l], sb});
-        h->piv_rows[l] = (int32_t *)own(h, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
-        h->piv_cols[l] = (int32_t *)own(h, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
-        h->d_ranks[l] = (int32_t *)own(h, (size_t)lv.nnodes * sizeof(int32_t), st);
-        if (!h->piv_rows[l] || !h->piv_cols[l] || !h->d_ranks[l]) return fail(HODLR_OUT_OF_MEMORY);
-        cudaMemsetAsync(h->piv_rows[l], 0xff, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
-        cudaMemsetAsync(h->piv_cols[l], 0xff, (size_t)lv.nnodes * lv.cap * sizeof(int32_t), st);
+    }
+    Arena meta, stage;
+    const size_t o_bounds = meta.take(bounds.size() * sizeof(int64_t));
+    const size_t o_caphit = meta.take((size_t)(2 << L) * sizeof(int32_t));
+    std::vector<size_t> o_prow(L + 1), o_pcol(L + 1), o_rank(L + 1), o_ust(L + 1), o_vst(L + 1);
+    const size_t o_piv0 = meta.bytes;
+    for (int l = 1; l <= L; ++l) o_prow[l] = meta.take((size_t)h->lv[l].nnodes * h->lv[l].cap * sizeof(int32_t));
+    for (int l = 1; l <= L; ++l) o_pcol[l] = meta.take((size_t)h->lv[l].nnodes * h->lv[l].cap * sizeof(int32_t));
+    const size_t piv_bytes = meta.bytes - o_piv0;
+    for (int l = 1; l <= L; ++l) o_rank[l] = meta.take((size_t)h->lv[l].nnodes * sizeof(int32_t));
+    const size_t o_tiles = meta.take(std::max<size_t>(tiles.size(), 1) * sizeof(int4));
+    const size_t o_tfirst = meta.take(tfirst.size() * sizeof(int));
+    const size_t o_leafinv = meta.take((size_t)nleaf * bmax * bmax * elem_size(h->prec));
+    for (int l = 1; l <= L; ++l) {
+        o_ust[l] = stage.take((size_t)h->ldn * h->lv[l].cap * ce);
+        o_vst[l] = stage.take((size_t)h->ldn * h->lv[l].cap * ce);
+    }
+    const size_t o_desc = stage.take((size_t)(2 << L) * sizeof(AcaBlockDesc));
+    char *mbase = (char *)own(h, meta.bytes, st);
+    if (!mbase) return fail(HODLR_OUT_OF_MEMORY);
+    char *sbase = (char *)dalloc(c, stage.bytes, st);
+    if (!sbase) return fail(HODLR_OUT_OF_MEMORY);
+    std::vector<std::pair<void *, size_t>> temp{{sbase, stage.bytes}};
+    h->d_bounds = (int64_t *)(mbase + o_bounds);
+    if (cudaMemcpyAsync(h->d_bounds, bounds.data(), bounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+        dfree(c, sbase, stage.bytes, st);
+        return fail(HODLR_CUDA_ERROR);
+    }
+    // ---- compression staging and per-block descriptors
+    std::vector<void *> Ust(L + 1, nullptr), Vst(L + 1, nullptr);
+    h->piv_rows.assign(L + 1, nullptr);
+    h->piv_cols.assign(L + 1, nullptr);
+    h->d_ranks.assign(L + 1, nullptr);
+    int32_t *caphit = (int32_t *)(mbase + o_caphit);
+    cudaMemsetAsync(mbase + o_piv0, 0xff, piv_bytes, st);
+    std::vector<AcaBlockDesc> blocks;
+    for (int l = 1; l <= L; ++l) {
+        Level &lv = h->lv[l];
+        Ust[l] = sbase + o_ust[l];
+        Vst[l] = sbase + o_vst[l];
+        h->piv_rows[l] = (int32_t *)(mbase + o_prow[l]);
+        h->piv_cols[l] = (int32_t *)(mbase + o_pcol[l]);
+        h->d_ranks[l] = (int32_t *)(mbase + o_rank[l]);
         for (int i = 0; i < lv.nnodes; ++i) {
-            AcaBlockDesc b;
-            nrange(l, i, b.r0, b.m);
-            nrange(l, i ^ 1, b.c0, b.nc);
-            b.ld = h->ldn;
-            b.U = Ust[l];
-            b.V = Vst[l];
-            b.cap = lv.cap;
-            b.rank = h->d_ranks[l] + i;
-            b.prow = h->piv_rows[l] + (size_t)i * lv.cap;
-            b.pcol = h->piv_cols[l] + (size_t)i * lv.cap;
-            b.cap_hit = caphit + blocks.size();
-            blocks.push_back(b);
+            AcaBlockDesc bd;
+            nrange(l, i, bd.r0, bd.m);
+            nrange(l, i ^ 1, bd.c0, bd.nc);
+            bd.ld = h->ldn;
+            bd.U = Ust[l];
+            bd.V = Vst[l];
+            bd.cap = lv.cap;
+            bd.rank = h->d_ranks[l] + i;
+            bd.prow = h->piv_rows[l] + (size_t)i * lv.cap;
+            bd.pcol = h->piv_cols[l] + (size_t)i * lv.cap;
+            bd.cap_hit = caphit + blocks.size();
+            blocks.push_back(bd);
         }
     }
     auto free_temp = [&]() {
@@ -450,34 +480,15 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     };
     // Row tiles of the fused apply (32 rows, never straddling a leaf) and the
     // first tile of every leaf.
-    {
-        std::vector<int4> tiles;
-        std::vector<int> first(nleaf + 1);
-        for (int i = 0; i < nleaf; ++i) {
-            first[i] = (int)tiles.size();
-            for (int64_t r = bounds[i]; r < bounds[i + 1]; r += 32)
-                tiles.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(32, bounds[i + 1] - r), 0));
-        }
-        first[nleaf] = (int)tiles.size();
-        int4 *dt = (int4 *)own(h, std::max<size_t>(tiles.size(), 1) * sizeof(int4), st);
-        h->d_tile_first = (int *)own(h, first.size() * sizeof(int), st);
-        if (!dt || !h->d_tile_first) {
-            free_temp();
-            return fail(HODLR_OUT_OF_MEMORY);
-        }
-        if (!tiles.empty())
-            cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(h->d_tile_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-        h->d_tiles = dt;
-        h->ntiles = (int)tiles.size();
-    }
+    h->d_tiles = (const int4 *)(mbase + o_tiles);
+    h->d_tile_first = (int *)(mbase + o_tfirst);
+    h->ntiles = (int)tiles.size();
+    if (!tiles.empty())
+        cudaMemcpyAsync((void *)h->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_tile_first, tfirst.data(), tfirst.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     // The leaf inverses depend on A only: they run on a side stream while the
     // off-diagonal blocks are compressed, and join the caller's stream after.
-    h->leafinv = own(h, (size_t)nleaf * bmax * bmax * elem_size(h->prec), st);
-    if (!h->leafinv) {
-        free_temp();
-        return fail(HODLR_OUT_OF_MEMORY);
-    }
+    h->leafinv = mbase + o_leafinv;
     cudaStream_t lstream = c->side[HODLR_SIDE_STREAMS - 1];
     cudaEvent_t lfork = nullptr, ljoin = nullptr;
     cudaEventCreateWithFlags(&lfork, cudaEventDisableTiming);
@@ -492,11 +503,7 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     cudaEventRecord(e0, st);
     hodlr_status rs = HODLR_OK;
     if (method == HODLR_ACA) {
-        AcaBlockDesc *db = (AcaBlockDesc *)dalloc(c, blocks.size() * sizeof(AcaBlockDesc) + 16, st);
-        if (!db) {
-            free_temp();
-            return fail(HODLR_OUT_OF_MEMORY);
-        }
+        AcaBlockDesc *db = (AcaBlockDesc *)(sbase + o_desc);
         cudaMemcpyAsync(db, blocks.data(), blocks.size() * sizeof(AcaBlockDesc), cudaMemcpyHostToDevice, st);
         std::vector<int> first;
         std::vector<int64_t> maxdim;
@@ -510,8 +517,6 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         }
         first.push_back(b0);
         rs = launch_aca_levels(c, A->data, A->ld, h->sym, cprec, db, first, maxdim, tol, st);
-        cudaStreamSynchronize(st);
-        dfree(c, db, blocks.size() * sizeof(AcaBlockDesc) + 16, st);
     } else {
         const int depth = o.bdlr_depth >= 0 ? o.bdlr_depth : (int)std::lround(-std::log10(tol));
         rs = run_bdlr(h, g, depth, st, Ust, Vst);
@@ -570,48 +575,48 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     h->Wtot = coff;
     const size_t pe = elem_size(h->prec);
     const size_t dvb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * pe;
-    h->U = own(h, dvb, st);
-    h->D = own(h, dvb, st);
-    h->V = own(h, dvb, st);
-    h->Sinv.assign(L, nullptr);
+    const bool q16 = (h->store == HODLR_BF16 || h->store == HODLR_FP16);
+    const size_t qb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * 2;
+    Arena fac;
+    const size_t o_U = fac.take(dvb), o_D = fac.take(dvb), o_V = fac.take(dvb);
+    std::vector<size_t> o_S(L), o_vs(L + 1), o_ds(L + 1);
     for (int l = 0; l < L; ++l) {
         const int64_t s2 = 2 * (int64_t)h->lv[l + 1].rp;
-        h->Sinv[l] = own(h, (size_t)(1 << l) * std::max<int64_t>(s2 * s2, 1) * pe, st);
-        if (!h->Sinv[l]) {
-            free_temp();
-            return fail(HODLR_OUT_OF_MEMORY);
-        }
+        o_S[l] = fac.take((size_t)(1 << l) * std::max<int64_t>(s2 * s2, 1) * pe);
     }
-    if (h->store == HODLR_BF16 || h->store == HODLR_FP16) {
-        const size_t qb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * 2;
-        h->Vq = own(h, qb, st);
-        h->Dq = own(h, qb, st);
-        if (!h->Vq || !h->Dq) {
-            free_temp();
-            return fail(HODLR_OUT_OF_MEMORY);
-        }
+    size_t o_Vq = 0, o_Dq = 0;
+    if (q16) {
+        o_Vq = fac.take(qb);
+        o_Dq = fac.take(qb);
+        if (h->store == HODLR_FP16)
+            for (int l = 1; l <= L; ++l) {
+                const size_t sb = (size_t)h->lv[l].nnodes * std::max(h->lv[l].rp, 1) * sizeof(float);
+                o_vs[l] = fac.take(sb);
+                o_ds[l] = fac.take(sb);
+            }
+    }
+    char *fbase = (char *)own(h, fac.bytes, st);
+    if (!fbase) {
+        free_temp();
+        return fail(HODLR_OUT_OF_MEMORY);
+    }
+    h->U = fbase + o_U;
+    h->D = fbase + o_D;
+    h->V = fbase + o_V;
+    h->Sinv.assign(L, nullptr);
+    for (int l = 0; l < L; ++l) h->Sinv[l] = fbase + o_S[l];
+    if (q16) {
+        h->Vq = fbase + o_Vq;
+        h->Dq = fbase + o_Dq;
         h->vscale.assign(L + 1, nullptr);
         h->dscale.assign(L + 1, nullptr);
         if (h->store == HODLR_FP16)
             for (int l = 1; l <= L; ++l) {
-                const size_t sb = (size_t)h->lv[l].nnodes * std::max(h->lv[l].rp, 1) * sizeof(float);
-                h->vscale[l] = (float *)own(h, sb, st);
-                h->dscale[l] = (float *)own(h, sb, st);
-                if (!h->vscale[l] || !h->dscale[l]) {
-                    free_temp();
-                    return fail(HODLR_OUT_OF_MEMORY);
-                }
+                h->vscale[l] = (float *)(fbase + o_vs[l]);
+                h->dscale[l] = (float *)(fbase + o_ds[l]);
             }
     }
-    if (!h->U || !h->D || !h->V || !h->leafinv) {
-        free_temp();
-        return fail(HODLR_OUT_OF_MEMORY);
-    }
-    if (h->Wtot > 0) {
-        cudaMemsetAsync(h->U, 0, dvb, st);
-        cudaMemsetAsync(h->D, 0, dvb, st);
-        cudaMemsetAsync(h->V, 0, dvb, st);
-    }
+    if (h->Wtot > 0) cudaMemsetAsync(h->U, 0, 3 * (o_D - o_U), st);   // U, D, V are adjacent
     for (int l = 1; l <= L; ++l) {
         Level &lv = h->lv[l];
         int64_t node_max = 0;

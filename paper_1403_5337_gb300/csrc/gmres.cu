@@ -760,43 +760,47 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     HODLR_TRY_CUDA(cudaSetDevice(c->device));
     const int64_t n = A->n;
     const int m = restart > 0 ? std::min(restart, max_iter) : max_iter;
+    const int64_t vstride = n * (m + 1), zstride = n * m;
+    const int hstride = m + 1;
+    // every work buffer in one allocation
+    Arena ar;
+    const size_t oVk = ar.take((size_t)vstride * s * 8), oZk = ar.take((size_t)zstride * s * 8),
+                 oWv = ar.take((size_t)n * s * 8), oh1 = ar.take((size_t)s * hstride * 8),
+                 oh2 = ar.take((size_t)s * hstride * 8), onrm = ar.take((size_t)s * 8),
+                 oH = ar.take((size_t)s * (m + 1) * m * 8), ocs = ar.take((size_t)s * m * 8),
+                 osn = ar.take((size_t)s * m * 8), og = ar.take((size_t)s * (m + 1) * 8), obn = ar.take((size_t)s * 8),
+                 oest = ar.take((size_t)s * 8), oib = ar.take((size_t)(4 * s + 4) * sizeof(int)),
+                 ozs = ar.take((size_t)n * s * sizeof(float2)), oZc = ar.take((size_t)n * s * 8), olp = ar.take(256);
     GmresBufs bufs;
     bufs.c = c;
     bufs.st = st;
-    const int64_t vstride = n * (m + 1), zstride = n * m;
-    double *Vk = (double *)bufs.get((size_t)vstride * s * 8);
-    double *Zk = (double *)bufs.get((size_t)zstride * s * 8);
-    double *Wv = (double *)bufs.get((size_t)n * s * 8);
-    const int hstride = m + 1;
-    double *h1 = (double *)bufs.get((size_t)s * hstride * 8);
-    double *h2 = (double *)bufs.get((size_t)s * hstride * 8);
-    double *nrm = (double *)bufs.get((size_t)s * 8);
-    GState gs;
-    gs.H = (double *)bufs.get((size_t)s * (m + 1) * m * 8);
-    gs.cs = (double *)bufs.get((size_t)s * m * 8);
-    gs.sn = (double *)bufs.get((size_t)s * m * 8);
-    gs.g = (double *)bufs.get((size_t)s * (m + 1) * 8);
-    gs.bnorm = (double *)bufs.get((size_t)s * 8);
-    gs.est = (double *)bufs.get((size_t)s * 8);
-    int *ibuf = (int *)bufs.get((size_t)(4 * s + 4) * sizeof(int));
-    void *zsw = bufs.get((size_t)n * s * sizeof(float2));
-    double *Zc = (double *)bufs.get((size_t)n * s * 8);
-    int *loops = (int *)bufs.get(256);
-    if (!Vk || !Zk || !Wv || !h1 || !h2 || !nrm || !gs.H || !gs.cs || !gs.sn || !gs.g || !gs.bnorm || !gs.est ||
-        !ibuf || !zsw || !Zc || !loops) {
-        set_error("gmres_solve: out of device memory");
+    char *base = (char *)bufs.get(ar.bytes);
+    if (!base) {
+        set_error("gmres_solve: out of device memory (%zu bytes)", ar.bytes);
         return HODLR_OUT_OF_MEMORY;
     }
+    double *Vk = (double *)(base + oVk);
+    double *Zk = (double *)(base + oZk);
+    double *Wv = (double *)(base + oWv);
+    double *h1 = (double *)(base + oh1);
+    double *h2 = (double *)(base + oh2);
+    double *nrm = (double *)(base + onrm);
+    GState gs;
+    gs.H = (double *)(base + oH);
+    gs.cs = (double *)(base + ocs);
+    gs.sn = (double *)(base + osn);
+    gs.g = (double *)(base + og);
+    gs.bnorm = (double *)(base + obn);
+    gs.est = (double *)(base + oest);
+    int *ibuf = (int *)(base + oib);
+    void *zsw = base + ozs;
+    double *Zc = (double *)(base + oZc);
+    int *loops = (int *)(base + olp);
     gs.iters = ibuf;
     gs.jcur = ibuf + s;
     gs.active = ibuf + 2 * s;
     gs.nactive = ibuf + 3 * s;
-    int *h_pin = nullptr;
-    HODLR_TRY_CUDA(cudaMallocHost(&h_pin, 64 * sizeof(int)));
-    struct PinFree {
-        int *p;
-        ~PinFree() { cudaFreeHost(p); }
-    } pf{h_pin};
+    int *h_pin = c->h_scratch;   // pinned, per context
     std::vector<double> hbuf(4 * (size_t)s);
     cudaEvent_t e0, e1;
     HODLR_TRY_CUDA(cudaEventCreate(&e0));
@@ -807,8 +811,6 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     // x0 = 0; iteration counters and per-rhs state start at zero
     HODLR_TRY_CUDA(cudaMemset2DAsync(X, ldx * 8, 0, n * 8, s, st));
     HODLR_TRY_CUDA(cudaMemsetAsync(ibuf, 0, (size_t)(4 * s + 4) * sizeof(int), st));
-    // R = B (first cycle): Wv = B
-    HODLR_TRY_CUDA(cudaMemcpy2DAsync(Wv, n * 8, B, ldb * 8, n * 8, s, cudaMemcpyDeviceToDevice, st));
     HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, s * 8, st));
     {
         // ||b||^2 via residual kernel with A X = 0: R = B - 0

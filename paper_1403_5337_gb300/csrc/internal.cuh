@@ -69,6 +69,7 @@ struct hodlr_ctx {
     void *user = nullptr;
     int *d_status = nullptr;      // device status word (one int)
     int *h_status = nullptr;      // pinned mirror
+    int *h_scratch = nullptr;     // pinned, 64 ints: small device-to-host reads of the solver
 };
 
 namespace hodlr {
@@ -155,6 +156,13 @@ namespace hodlr {
 inline size_t elem_size(int prec) { return prec == HODLR_FP64 ? 8 : 4; }
 
 void *own(hodlr_t *h, size_t bytes, cudaStream_t s);   // allocate and remember
+
+// Offsets of the pieces of one allocation (256-byte aligned): every allocation
+// goes through the caller's allocator, so related buffers share one.
+struct Arena {
+    size_t bytes = 0;
+    size_t take(size_t b);
+};
 hodlr_status ensure_work(hodlr_t *h, size_t bytes, cudaStream_t s);
 
 // ------------------------------------------------------------------ kernels (launchers)
