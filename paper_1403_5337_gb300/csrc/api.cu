@@ -663,7 +663,9 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         hodlr_status sp = plan_factor(h, st);
         if (sp != HODLR_OK) return fail(sp);
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
+    // (no synchronisation here: the factorisation that follows is stream-ordered
+    // after the compaction and the descriptor upload)
+    if (cudaGetLastError() != cudaSuccess) {
         set_error("hodlr_build: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(HODLR_CUDA_ERROR);
     }

@@ -229,11 +229,13 @@ struct GState {
     int *iters, *jcur, *active, *nactive;
 };
 
-// y = H(0:j,0:j)^-1 g(0:j) by back substitution, then X_r += Z_r y.  One CTA per rhs.
+// y = H(0:j,0:j)^-1 g(0:j) by back substitution, then X_r += Z_r y.  Grid
+// (row chunks, rhs): every CTA solves the small triangular system itself (j is
+// at most the restart length) and updates its own rows.
 __global__ void __launch_bounds__(KT)
     backsolve_kernel(GState st, int m, const double *__restrict__ Zk, int64_t zstride, int64_t n, double *__restrict__ X,
                      int64_t ldx) {
-    const int r = blockIdx.x;
+    const int r = blockIdx.y;
     const int j = st.jcur[r];
     if (j <= 0) return;
     extern __shared__ double ys[];
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(KT)
     }
     __syncthreads();
     const double *Z = Zk + r * zstride;
-    for (int64_t q = threadIdx.x; q < n; q += KT) {
+    for (int64_t q = blockIdx.x * (int64_t)KT + threadIdx.x; q < n; q += (int64_t)gridDim.x * KT) {
         double v = X[q + r * ldx];
         for (int k = 0; k < j; ++k) v = fma(Z[(int64_t)k * n + q], ys[k], v);
         X[q + r * ldx] = v;
@@ -930,7 +932,8 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         HODLR_TRY_CUDA(cudaGraphLaunch(iter.exec, st));
         HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin + 1, loops, sizeof(int), cudaMemcpyDeviceToHost, st));
         // x += Z y
-        backsolve_kernel<<<s, KT, (size_t)m * 8, st>>>(gs, m, Zk, zstride, n, X, ldx);
+        backsolve_kernel<<<dim3((unsigned)std::min<int64_t>((n + KT - 1) / KT, 64), s), KT, (size_t)m * 8, st>>>(
+            gs, m, Zk, zstride, n, X, ldx);
         note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
         // true residual R = B - A X
