@@ -245,13 +245,12 @@ __global__ void __launch_bounds__(CT, 1)
     __shared__ float xr_hi[CW], xr_lo[CW];
     __shared__ double xr_d[CW];
     __shared__ double s_norm2, s_uu, s_vv;
-    __shared__ int s_i, s_stop;
+    __shared__ int s_stop;
 
     for (int64_t e = tid; e < (int64_t)kcs * (smr + snr); e += CT) Us[e] = T(0);
     for (int64_t q = tid; q < mr; q += CT) used[q] = 0;
     if (tid == 0) {
         s_norm2 = 0.0;
-        s_i = 0;
         s_stop = 0;
     }
 
@@ -326,10 +325,17 @@ __global__ void __launch_bounds__(CT, 1)
     __syncthreads();
     cl.sync();
 
+    // The stop test of a step is made by the upper half of the warps while the
+    // lower half already runs the next step's row pass, when every column of
+    // the CTA's slice is owned by the lower half (the row pass writes nothing
+    // outside registers; the decision is read at its first barrier).
+    const bool split = (NPT == 1) && (nr <= CT / 2);
+    bool deferred = false;
+    int i_next = 0;
     int k = 0;
     while (k < kmax) {
         const int par = k & 1;
-        const int i = s_i;
+        const int i = i_next;
         // ---- row pass on own columns -> v_k (unscaled, kept in registers); U(i_k, :)
         // was gathered into pu at the end of the previous step
         const int kin = k < kcs ? k : kcs;
@@ -344,6 +350,16 @@ __global__ void __launch_bounds__(CT, 1)
                 const int64_t jl = j - j0;
                 r = dev::from_double<T>(arow_pf[t]);
                 int l = 0;
+                if constexpr (sizeof(T) == 4) {   // U(i_k, l..l+3) in one 16-byte broadcast load
+#pragma unroll 2
+                    for (; l + 4 <= kin; l += 4) {
+                        const float4 p4 = *reinterpret_cast<const float4 *>(pu + l);
+                        r = dev::sub_rn(r, dev::mul_rn(p4.x, Vs[(size_t)l * snr + jl]));
+                        r = dev::sub_rn(r, dev::mul_rn(p4.y, Vs[(size_t)(l + 1) * snr + jl]));
+                        r = dev::sub_rn(r, dev::mul_rn(p4.z, Vs[(size_t)(l + 2) * snr + jl]));
+                        r = dev::sub_rn(r, dev::mul_rn(p4.w, Vs[(size_t)(l + 3) * snr + jl]));
+                    }
+                }
 #pragma unroll 8
                 for (; l < kin; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vs[(size_t)l * snr + jl]));
                 for (; l < k; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vg[(int64_t)l * ld + j]));
@@ -358,6 +374,10 @@ __global__ void __launch_bounds__(CT, 1)
             rreg[t] = r;
         }
         const Cand<T> cr = cta_argmax(ba, bi, bv, red[0]);
+        if (deferred) {   // the previous step's stop test, made meanwhile by the upper warps
+            deferred = false;
+            if (s_stop) break;
+        }
         post_cand(cl, &slots[par][0][0], c, CL, cr);
         cl.sync();
         const Cand<T> best = best_of_slots(&slots[par][0][0], CL);
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(CT, 1)
             if (bf.a < T(0)) break;
             load_row(bf.idx);
             gather_pu(bf.idx, k);
-            if (tid == 0) s_i = bf.idx;
+            i_next = bf.idx;
             __syncthreads();
             continue;
         }
@@ -413,6 +433,16 @@ __global__ void __launch_bounds__(CT, 1)
                 const int64_t ql = q - i0;
                 T u = dev::from_double<T>(acol_pf[t]);
                 int l = 0;
+                if constexpr (sizeof(T) == 4) {   // V(j_k, l..l+3) in one 16-byte broadcast load
+#pragma unroll 2
+                    for (; l + 4 <= kin; l += 4) {
+                        const float4 p4 = *reinterpret_cast<const float4 *>(pv + l);
+                        u = dev::sub_rn(u, dev::mul_rn(p4.x, Us[(size_t)l * smr + ql]));
+                        u = dev::sub_rn(u, dev::mul_rn(p4.y, Us[(size_t)(l + 1) * smr + ql]));
+                        u = dev::sub_rn(u, dev::mul_rn(p4.z, Us[(size_t)(l + 2) * smr + ql]));
+                        u = dev::sub_rn(u, dev::mul_rn(p4.w, Us[(size_t)(l + 3) * smr + ql]));
+                    }
+                }
 #pragma unroll 8
                 for (; l < kin; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Us[(size_t)l * smr + ql]));
                 for (; l < k; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Ug[(int64_t)l * ld + q]));
@@ -463,65 +493,83 @@ __global__ void __launch_bounds__(CT, 1)
             load_row(bc.idx);          // the next pivot row and its U entries, while the stop test is made
             pu_load(bc.idx, k + 1);
         }
-        CrossAcc<T> xacc;
-        for (int l = tid; l <= k; l += CT) {
-            T pu_[MAX_CL], pv_[MAX_CL];
+        // dot products summed over the cluster in rank order, the cross term, the
+        // norm recurrence and the stop decision of step k, by warps [w0, w0 + nw)
+        auto stop_test = [&](int w0, int nw) {
+            const int t0 = 32 * w0, nt = 32 * nw;
+            CrossAcc<T> xacc;
+            for (int l = tid - t0; l <= k; l += nt) {
+                T pu_[MAX_CL], pv_[MAX_CL];
 #pragma unroll
-            for (int q = 0; q < MAX_CL; ++q)
-                if (q < CL) {
-                    const T *rp = cl.map_shared_rank(dots, q) + (size_t)par * 2 * (ACA_CAP + 1);
-                    pu_[q] = rp[l];
-                    pv_[q] = rp[ACA_CAP + 1 + l];
+                for (int q = 0; q < MAX_CL; ++q)
+                    if (q < CL) {
+                        const T *rp = cl.map_shared_rank(dots, q) + (size_t)par * 2 * (ACA_CAP + 1);
+                        pu_[q] = rp[l];
+                        pv_[q] = rp[ACA_CAP + 1 + l];
+                    }
+                T su = T(0), sv = T(0);
+#pragma unroll
+                for (int q = 0; q < MAX_CL; ++q)
+                    if (q < CL) {
+                        su += pu_[q];
+                        sv += pv_[q];
+                    }
+                if (l < k) {
+                    xacc.add_prod(su, sv);
+                } else {
+                    s_uu = (double)su;
+                    s_vv = (double)sv;
                 }
-            T su = T(0), sv = T(0);
-#pragma unroll
-            for (int q = 0; q < MAX_CL; ++q)
-                if (q < CL) {
-                    su += pu_[q];
-                    sv += pv_[q];
+            }
+            xacc.warp_reduce();
+            if (lane == 0) {
+                if constexpr (sizeof(T) == 4) {
+                    xr_hi[warp - w0] = (float)xacc.hi;
+                    xr_lo[warp - w0] = (float)xacc.lo;
+                } else {
+                    xr_d[warp - w0] = (double)xacc.hi;
                 }
-            if (l < k) {
-                xacc.add_prod(su, sv);
-            } else {
-                s_uu = (double)su;
-                s_vv = (double)sv;
             }
+            if (nw == CW)
+                __syncthreads();
+            else
+                asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+            if (tid == t0) {
+                CrossAcc<T> tot;
+                for (int w = 0; w < nw; ++w) {
+                    if constexpr (sizeof(T) == 4)
+                        tot.add_pair(xr_hi[w], xr_lo[w]);
+                    else
+                        tot.add_pair(xr_d[w], 0.0);
+                }
+                const double cross = tot.value(), uu = s_uu, vv = s_vv;
+                // ||S_k||^2 = ||S_{k-1}||^2 + 2 cross + ||u_k||^2 ||v_k||^2, evaluated left to right
+                s_norm2 = __dadd_rn(__dadd_rn(s_norm2, __dmul_rn(2.0, cross)), __dmul_rn(uu, vv));
+                if (c == 0) {
+                    B.prow[k] = i;
+                    B.pcol[k] = jk;
+                }
+                const double nrm = s_norm2 > 0.0 ? s_norm2 : 0.0;
+                int stop = (__dmul_rn(uu, vv) <= __dmul_rn(tol2, nrm));   // ||u|| ||v|| <= tol ||S||, squared
+                if ((int64_t)(k + 1) >= mn) stop = 1;
+                if (bc.a < T(0)) stop = 1;   // every row used
+                s_stop = stop;
+            }
+        };
+        const bool more = bc.a >= T(0) && (int64_t)(k + 1) < mn && k + 1 < kmax;
+        if (split && more) {
+            greg_store(pu, k + 1);
+            __syncthreads();   // U(i_{k+1}, :) in place for the next row pass
+            if (warp >= CW / 2) stop_test(CW / 2, CW / 2);
+            i_next = bc.idx;
+            ++k;
+            deferred = true;
+            continue;
         }
-        xacc.warp_reduce();
-        if (lane == 0) {
-            if constexpr (sizeof(T) == 4) {
-                xr_hi[warp] = (float)xacc.hi;
-                xr_lo[warp] = (float)xacc.lo;
-            } else {
-                xr_d[warp] = (double)xacc.hi;
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            CrossAcc<T> tot;
-#pragma unroll
-            for (int w = 0; w < CW; ++w) {
-                if constexpr (sizeof(T) == 4)
-                    tot.add_pair(xr_hi[w], xr_lo[w]);
-                else
-                    tot.add_pair(xr_d[w], 0.0);
-            }
-            const double cross = tot.value(), uu = s_uu, vv = s_vv;
-            // ||S_k||^2 = ||S_{k-1}||^2 + 2 cross + ||u_k||^2 ||v_k||^2, evaluated left to right
-            s_norm2 = __dadd_rn(__dadd_rn(s_norm2, __dmul_rn(2.0, cross)), __dmul_rn(uu, vv));
-            if (c == 0) {
-                B.prow[k] = i;
-                B.pcol[k] = jk;
-            }
-            const double nrm = s_norm2 > 0.0 ? s_norm2 : 0.0;
-            int stop = (__dmul_rn(uu, vv) <= __dmul_rn(tol2, nrm));   // ||u|| ||v|| <= tol ||S||, squared
-            if ((int64_t)(k + 1) >= mn) stop = 1;
-            if (bc.a < T(0)) stop = 1;   // every row used
-            s_stop = stop;
-            s_i = bc.idx;
-        }
+        stop_test(0, CW);
         if (bc.a >= T(0)) greg_store(pu, k + 1);
         __syncthreads();
+        i_next = bc.idx;
         ++k;
         if (s_stop) break;
     }
