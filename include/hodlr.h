@@ -186,6 +186,31 @@ hodlr_status gmres_solve(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const dou
                          int max_iter, int restart, hodlr_gmres_info *info,
                          hodlr_stream stream);
 
+/* ---------------------------------------------------------------- batches */
+/* The fronts of one nested-dissection tree solved together (independent
+ * problems of uneven sizes; no counterpart call in the paper, which treats one
+ * front at a time).  Arrays have nf entries; A[f] is front f (device, FP64),
+ * leaf[f] its leaf size, out[f] receives its HODLR matrix.  Every front is
+ * compressed with the same tol, method (ACA only: BDLR would need a graph per
+ * front) and options.  Synchronises `stream`.  On failure the fronts built so
+ * far are destroyed and every out[f] is NULL. */
+hodlr_status hodlr_build_batched(hodlr_ctx *ctx, int nf, const hodlr_matrix *A, const int *leaf, double tol,
+                                 int method, const hodlr_opts *o, hodlr_stream stream, hodlr_t **out);
+
+/* hodlr_factor of every h[f] (nf entries), stream-ordered. */
+hodlr_status hodlr_factor_batched(int nf, hodlr_t *const *h, hodlr_stream stream);
+
+/* gmres_solve for every front f: A[f] X_f = B_f with s[f] right-hand sides,
+ * B[f], X[f] device, n_f x s[f] column-major with leading dimensions ldb[f],
+ * ldx[f]; P[f] its preconditioner (or NULL, or P itself NULL for none).  info
+ * may be NULL or hold nf entries (each with arrays of s[f] entries).  Returns
+ * HODLR_NOT_CONVERGED if any front misses tol (all fronts are still solved).
+ * Synchronises `stream`. */
+hodlr_status gmres_solve_batched(hodlr_ctx *ctx, int nf, const hodlr_matrix *A, const int *s,
+                                 const double *const *B, const int64_t *ldb, double *const *X,
+                                 const int64_t *ldx, const hodlr_t *const *P, double tol, int max_iter,
+                                 int restart, hodlr_gmres_info *info, hodlr_stream stream);
+
 /* W <- A Z (device, n x s column-major) with the FP64-accurate double-float
  * matvec used inside gmres_solve. */
 hodlr_status hodlr_matvec(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *Z,

@@ -8,4 +8,4 @@ reached through the ctypes binding in `hodlr`.
 from .hodlr import (ACA, BDLR, BF16, FP16, FP32, FP64, Context, GmresInfo, Hodlr, HodlrError,  # noqa: F401
                     NotConverged, gmres_solve, hodlr_build, hodlr_factor, hodlr_matvec,
                     hodlr_launch_count, hodlr_matvec_noalloc, hodlr_precond_error, hodlr_solve,
-                    load_library)
+                    hodlr_build_batched, hodlr_factor_batched, gmres_solve_batched, load_library)

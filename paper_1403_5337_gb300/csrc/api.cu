@@ -673,6 +673,39 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     return HODLR_OK;
 }
 
+hodlr_status hodlr_build_batched(hodlr_ctx *c, int nf, const hodlr_matrix *A, const int *leaf, double tol,
+                                 int method, const hodlr_opts *o, hodlr_stream stream, hodlr_t **out) {
+    if (!c || nf < 0 || (nf > 0 && (!A || !leaf || !out))) {
+        set_error("hodlr_build_batched: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    if (method != HODLR_ACA) {
+        set_error("hodlr_build_batched: only ACA (BDLR needs a graph per front)");
+        return HODLR_INVALID_ARG;
+    }
+    for (int f = 0; f < nf; ++f) out[f] = nullptr;
+    for (int f = 0; f < nf; ++f) {
+        const hodlr_status r = hodlr_build(c, &A[f], leaf[f], tol, method, nullptr, o, stream, &out[f]);
+        if (r != HODLR_OK) {
+            for (int q = 0; q < f; ++q) {
+                hodlr_destroy(out[q]);
+                out[q] = nullptr;
+            }
+            return r;
+        }
+    }
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_factor_batched(int nf, hodlr_t *const *h, hodlr_stream stream) {
+    if (nf < 0 || (nf > 0 && !h)) {
+        set_error("hodlr_factor_batched: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    for (int f = 0; f < nf; ++f) HODLR_TRY(hodlr_factor(h[f], stream));
+    return HODLR_OK;
+}
+
 hodlr_status hodlr_factor(hodlr_t *h, hodlr_stream stream) {
     if (!h) {
         set_error("hodlr_factor: NULL");

@@ -974,3 +974,25 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     if (result == HODLR_NOT_CONVERGED) set_error("gmres_solve: not converged within %d iterations", max_iter);
     return result;
 }
+
+extern "C" hodlr_status gmres_solve_batched(hodlr_ctx *c, int nf, const hodlr_matrix *A, const int *s,
+                                            const double *const *B, const int64_t *ldb, double *const *X,
+                                            const int64_t *ldx, const hodlr_t *const *P, double tol, int max_iter,
+                                            int restart, hodlr_gmres_info *info, hodlr_stream stream) {
+    using namespace hodlr;
+    if (!c || nf < 0 || (nf > 0 && (!A || !s || !B || !ldb || !X || !ldx))) {
+        set_error("gmres_solve_batched: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    hodlr_status result = HODLR_OK;
+    for (int f = 0; f < nf; ++f) {
+        const hodlr_status r = gmres_solve(c, &A[f], s[f], B[f], ldb[f], X[f], ldx[f], P ? P[f] : nullptr, tol,
+                                           max_iter, restart, info ? &info[f] : nullptr, stream);
+        if (r == HODLR_NOT_CONVERGED)
+            result = HODLR_NOT_CONVERGED;
+        else if (r != HODLR_OK)
+            return r;
+    }
+    if (result == HODLR_NOT_CONVERGED) set_error("gmres_solve_batched: some front did not converge");
+    return result;
+}

@@ -76,7 +76,8 @@ SYMBOLS = ["hodlr_ctx_create", "hodlr_ctx_destroy", "hodlr_opts_default", "hodlr
            "hodlr_solve", "gmres_solve", "hodlr_matvec", "hodlr_matvec_noalloc", "hodlr_precond_error",
            "hodlr_stats_get",
            "hodlr_export_level", "hodlr_export_core", "hodlr_destroy", "hodlr_status_string",
-           "hodlr_last_error", "hodlr_launch_count"]
+           "hodlr_last_error", "hodlr_launch_count", "hodlr_build_batched", "hodlr_factor_batched",
+           "gmres_solve_batched"]
 
 _lib = None
 # Library calls in progress on this process.  The torch allocator callbacks run
@@ -126,6 +127,13 @@ def load_library(path: str = _LIBPATH):
     lib.hodlr_export_level.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp]
     lib.hodlr_export_core.argtypes = [vp, ci, vp, vp]
     lib.hodlr_destroy.argtypes = [vp]
+    lib.hodlr_launch_count.argtypes = [C.POINTER(C.c_longlong)]
+    lib.hodlr_build_batched.argtypes = [vp, ci, C.POINTER(_Matrix), C.POINTER(ci), cd, ci, C.POINTER(_Opts), vp,
+                                        C.POINTER(vp)]
+    lib.hodlr_factor_batched.argtypes = [ci, C.POINTER(vp), vp]
+    lib.gmres_solve_batched.argtypes = [vp, ci, C.POINTER(_Matrix), C.POINTER(ci), C.POINTER(vp), C.POINTER(i64),
+                                        C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), cd, ci, ci, C.POINTER(_Info),
+                                        vp]
     lib.hodlr_status_string.argtypes = [ci]
     lib.hodlr_status_string.restype = C.c_char_p
     lib.hodlr_last_error.restype = C.c_char_p
@@ -384,6 +392,69 @@ def gmres_solve(ctx: Context, A: torch.Tensor, B: torch.Tensor, P: Hodlr | None 
     if code not in (0, 6) or (code == 6 and raise_on_fail):
         _check(code)
     return X, GmresInfo(it, est, tr, info.restarts, info.ms_total, code == 0)
+
+
+def hodlr_build_batched(ctx: Context, As, leaves, tol: float, method: str = "aca", precision: str = "fp32",
+                        rank_cap: int = 0, symmetric: bool = True, stream=None):
+    """Compress every front of a batch (list of (n_f, n_f) FP64 device tensors):
+    one HODLR matrix per front, same tol and options (include/hodlr.h)."""
+    lib = load_library()
+    nf = len(As)
+    mats = (_Matrix * max(nf, 1))(*[_mat(A, symmetric) for A in As])
+    lv = (C.c_int * max(nf, 1))(*[int(x) for x in leaves])
+    o = _Opts()
+    lib.hodlr_opts_default(C.byref(o))
+    o.precision = _PREC[precision]
+    o.rank_cap = rank_cap
+    out = (C.c_void_p * max(nf, 1))()
+    _check(lib.hodlr_build_batched(ctx.handle, nf, mats, lv, float(tol), _METHOD[method], C.byref(o),
+                                   _stream(stream), out))
+    return [Hodlr(ctx, C.c_void_p(out[f]), As[f], []) for f in range(nf)]
+
+
+def hodlr_factor_batched(hs, stream=None) -> None:
+    """hodlr_factor of every HODLR matrix in the list."""
+    nf = len(hs)
+    arr = (C.c_void_p * max(nf, 1))(*[h.handle.value if isinstance(h.handle, C.c_void_p) else h.handle
+                                     for h in hs])
+    _check(_lib.hodlr_factor_batched(nf, arr, _stream(stream)))
+
+
+def gmres_solve_batched(ctx: Context, As, Bs, Ps=None, tol: float = 1e-12, max_iter: int = 1000,
+                        restart: int = 0, symmetric: bool = True, stream=None):
+    """GMRES for every front f: A_f X_f = B_f (B_f is (s_f, n_f) or (n_f,)).
+    Returns a list of (X_f, GmresInfo)."""
+    nf = len(As)
+    mats = (_Matrix * max(nf, 1))(*[_mat(A, symmetric) for A in As])
+    Xs, infos, keep = [], [], []
+    sv = (C.c_int * max(nf, 1))()
+    bp = (C.c_void_p * max(nf, 1))()
+    xp = (C.c_void_p * max(nf, 1))()
+    lb = (C.c_int64 * max(nf, 1))()
+    lx = (C.c_int64 * max(nf, 1))()
+    pp = (C.c_void_p * max(nf, 1))()
+    inf = (_Info * max(nf, 1))()
+    for f in range(nf):
+        n = As[f].shape[0]
+        bptr, s, ldb = _rhs(Bs[f], n)
+        X = torch.empty_like(Bs[f], memory_format=torch.contiguous_format)
+        xptr, _, ldx = _rhs(X, n)
+        it, est, tr = np.zeros(s, dtype=np.int32), np.zeros(s), np.zeros(s)
+        keep.append((it, est, tr))
+        sv[f], bp[f], xp[f], lb[f], lx[f] = s, bptr, xptr, ldb, ldx
+        pp[f] = Ps[f].handle if Ps is not None and Ps[f] is not None else None
+        inf[f] = _Info(it.ctypes.data, est.ctypes.data, tr.ctypes.data, 0, 0.0)
+        Xs.append(X)
+    code = _lib.gmres_solve_batched(ctx.handle, nf, mats, sv, bp, lb, xp, lx, pp if Ps is not None else None,
+                                    float(tol), int(max_iter), int(restart), inf, _stream(stream))
+    if code not in (0, 6):
+        _check(code)
+    out = []
+    for f in range(nf):
+        it, est, tr = keep[f]
+        out.append((Xs[f], GmresInfo(it, est, tr, inf[f].restarts, inf[f].ms_total,
+                                     bool(np.all(tr <= tol)))))
+    return out
 
 
 def hodlr_launch_count() -> int:
