@@ -113,6 +113,9 @@ typedef struct {
     const int64_t *leaf_bounds; /* host, optional: 2^L + 1 leaf boundary offsets     */
     int n_leaf_bounds;          /* length of leaf_bounds, or 0                       */
     uint64_t seed;              /* probe seed of hodlr_precond_error                 */
+    int defer_factor;           /* 0 (default): hodlr_build also factors, level by level
+                                   as the compression of each level completes; 1: only
+                                   hodlr_factor factors                               */
 } hodlr_opts;
 
 /* Per-call statistics of a built (and possibly factored) HODLR matrix. */
@@ -156,15 +159,21 @@ void hodlr_opts_default(hodlr_opts *o);
  * off-diagonal block of every level, A(alpha,beta) ~ U_alpha V_alpha,beta^T, by
  * ACA to relative tolerance `tol` or by BDLR with pivot threshold `tol` and the
  * graph `g`.  `leaf` is the maximum leaf size (>= 1; ignored when leaf_bounds is
- * given).  The result keeps a pointer to A.  Synchronises `stream`. */
+ * given).  The result keeps a pointer to A.  Unless opts->defer_factor is set, the
+ * factorisation of hodlr_factor is carried out too: each level's share of it is
+ * issued as soon as that level (and every deeper one) is compressed, while the
+ * compression of the upper levels still runs.  Returns once every level is
+ * compressed (the host waits for the ranks); the factorisation completes
+ * stream-ordered on `stream`. */
 hodlr_status hodlr_build(hodlr_ctx *ctx, const hodlr_matrix *A, int leaf, double tol,
                          int method, const hodlr_graph *g, const hodlr_opts *o,
                          hodlr_stream stream, hodlr_t **out);
 
 /* Recursive Woodbury factorisation (Sec. 4.3 Factorize steps 2-5), level by
  * level from the leaves: leaf inverses, d = K^-1 U for every node, and the core
- * S_i^(p) of every internal node, inverted.  Stream-ordered, no host sync; a
- * singular leaf or core is reported by the next synchronising call. */
+ * S_i^(p) of every internal node, inverted.  Nothing to do when hodlr_build has
+ * factored already (the default).  Stream-ordered, no host sync; a singular leaf
+ * or core is reported by the next synchronising call. */
 hodlr_status hodlr_factor(hodlr_t *h, hodlr_stream stream);
 
 /* X <- K~^-1 X in place (Sec. 4.3 Solve) for s right-hand sides: X device,
@@ -247,14 +256,15 @@ hodlr_status hodlr_precond_error(hodlr_t *h, int k, const double *Omega, int64_t
 hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *out);
 
 /* Copy one level's factors to host memory, for inspection and testing.
- * level = 1..L.  U_or_d, V: n x rank_pad[level-1] column-major FP64 (the U
- * columns before hodlr_factor, d = K_node^-1 U_node after it; rows of a node
- * beyond its rank are zero).  ranks: 2^level ints.  piv_rows / piv_cols:
+ * level = 1..L.  U, d, V: n x rank_pad[level-1] column-major FP64: the
+ * compressed columns U (Sec. 4.3 step 1), d = K_node^-1 U_node (Sec. 4.3
+ * step 3; HODLR_NOT_FACTORED before the factorisation) and V; rows of a node
+ * beyond its rank are zero.  ranks: 2^level ints.  piv_rows / piv_cols:
  * 2^level x cap[level-1] ints, the block-local pivot rows/columns of each
  * node's block A(node, sibling) in pivot order (ACA: i_k, j_k; BDLR: the kept
  * skeleton rows/columns), -1 past the rank.  Any output may be NULL.
  * Synchronises `stream`. */
-hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U_or_d, double *V,
+hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U, double *d, double *V,
                                 int32_t *ranks, int32_t *piv_rows, int32_t *piv_cols,
                                 hodlr_stream stream);
 

@@ -631,37 +631,33 @@ hodlr_status launch_level(hodlr_ctx *c, const double *A, int64_t lda, int sym, c
 
 hodlr_status launch_aca_levels(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
                                const AcaBlockDesc *d_blocks, const std::vector<int> &level_first,
-                               const std::vector<int64_t> &level_maxdim, double tol, cudaStream_t s) {
-    // level_first[l] .. level_first[l+1]: the blocks of level l (all of one size class)
+                               const std::vector<int64_t> &level_maxdim, double tol, cudaStream_t s,
+                               std::vector<cudaEvent_t> &done) {
+    // level_first[l] .. level_first[l+1]: the blocks of level l + 1 (all of one size class)
     const int nlev = (int)level_first.size() - 1;
+    done.assign(nlev, nullptr);
     cudaEvent_t fork;
     HODLR_TRY_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     HODLR_TRY_CUDA(cudaEventRecord(fork, s));
-    std::vector<cudaEvent_t> joins;
     hodlr_status rs = HODLR_OK;
     for (int l = 0; l < nlev && rs == HODLR_OK; ++l) {
         const int nb = level_first[l + 1] - level_first[l];
-        if (nb == 0) continue;
-        const int64_t dim = level_maxdim[l];
-        int CL = 1;
-        while (CL < 16 && dim > (int64_t)CL * 128) CL *= 2;
-        const int64_t mr = (dim + CL - 1) / CL;
         cudaStream_t ls = c->side[l % HODLR_SIDE_STREAMS];
         if (cudaStreamWaitEvent(ls, fork, 0) != cudaSuccess) {
             rs = HODLR_CUDA_ERROR;
             break;
         }
-        const AcaBlockDesc *db = d_blocks + level_first[l];
-        rs = (cprec == HODLR_FP64) ? launch_level<double>(c, A, lda, sym, db, nb, CL, mr, mr, tol, ls)
-                                   : launch_level<float>(c, A, lda, sym, db, nb, CL, mr, mr, tol, ls);
-        cudaEvent_t j;
-        cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
-        cudaEventRecord(j, ls);
-        joins.push_back(j);
-    }
-    for (auto j : joins) {
-        cudaStreamWaitEvent(s, j, 0);
-        cudaEventDestroy(j);
+        if (nb > 0) {
+            const int64_t dim = level_maxdim[l];
+            int CL = 1;
+            while (CL < 16 && dim > (int64_t)CL * 128) CL *= 2;
+            const int64_t mr = (dim + CL - 1) / CL;
+            const AcaBlockDesc *db = d_blocks + level_first[l];
+            rs = (cprec == HODLR_FP64) ? launch_level<double>(c, A, lda, sym, db, nb, CL, mr, mr, tol, ls)
+                                       : launch_level<float>(c, A, lda, sym, db, nb, CL, mr, mr, tol, ls);
+        }
+        cudaEventCreate(&done[l]);   // timed: the build reports the compression time
+        cudaEventRecord(done[l], ls);
     }
     cudaEventDestroy(fork);
     return rs;

@@ -497,11 +497,13 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     cudaStreamWaitEvent(lstream, lfork, 0);
     const hodlr_status rleaf = leaf_inverses(h, lstream);
     cudaEventRecord(ljoin, lstream);
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0;
     cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
     hodlr_status rs = HODLR_OK;
+    // done[c - 1]: level c compressed; rstream[c]: the stream its ranks are read on
+    std::vector<cudaEvent_t> done;
+    std::vector<cudaStream_t> rstream(L + 1, st);
     if (method == HODLR_ACA) {
         AcaBlockDesc *db = (AcaBlockDesc *)(sbase + o_desc);
         cudaMemcpyAsync(db, blocks.data(), blocks.size() * sizeof(AcaBlockDesc), cudaMemcpyHostToDevice, st);
@@ -516,50 +518,90 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             b0 += 1 << l;
         }
         first.push_back(b0);
-        rs = launch_aca_levels(c, A->data, A->ld, h->sym, cprec, db, first, maxdim, tol, st);
+        rs = launch_aca_levels(c, A->data, A->ld, h->sym, cprec, db, first, maxdim, tol, st, done);
+        for (int l = 1; l <= L; ++l) rstream[l] = c->side[(l - 1) % HODLR_SIDE_STREAMS];
     } else {
         const int depth = o.bdlr_depth >= 0 ? o.bdlr_depth : (int)std::lround(-std::log10(tol));
         rs = run_bdlr(h, g, depth, st, Ust, Vst);
+        done.assign(L, nullptr);
+        for (int l = 0; l < L; ++l) {
+            cudaEventCreate(&done[l]);
+            cudaEventRecord(done[l], st);
+        }
     }
-    cudaEventRecord(e1, st);
-    cudaStreamWaitEvent(st, ljoin, 0);
-    cudaEventDestroy(lfork);
-    cudaEventDestroy(ljoin);
+    auto drop_events = [&]() {
+        for (auto e : done)
+            if (e) cudaEventDestroy(e);
+        done.clear();
+        cudaEventDestroy(lfork);
+        cudaEventDestroy(ljoin);
+        cudaEventDestroy(e0);
+    };
     if (rs == HODLR_OK) rs = rleaf;
     if (rs != HODLR_OK) {
-        cudaStreamSynchronize(st);
+        cudaDeviceSynchronize();
+        drop_events();
         free_temp();
         return fail(rs);
     }
-    // ---- ranks -> padded layout
-    std::vector<int32_t> hr;
-    std::vector<int32_t> hcap(blocks.size());
+    // the leaf inverses are needed by every level's share of the factorisation
+    cudaStreamWaitEvent(st, ljoin, 0);
+    // ---- level by level from the leaves: ranks -> layout -> compaction -> the
+    // level's share of the factorisation, issued while the upper levels are
+    // still being compressed
+    const size_t pe = elem_size(h->prec);
+    const bool q16 = (h->store == HODLR_BF16 || h->store == HODLR_FP16);
+    const bool factor_now = o.defer_factor == 0;
+    h->Ul.assign(L + 1, nullptr);
+    h->Dl.assign(L + 1, nullptr);
+    h->Vl.assign(L + 1, nullptr);
+    h->Vql.assign(L + 1, nullptr);
+    h->Dql.assign(L + 1, nullptr);
+    h->Sinv.assign(L, nullptr);
+    h->vscale.assign(L + 1, nullptr);
+    h->dscale.assign(L + 1, nullptr);
+    if (factor_now && L > 0) {
+        if (!h->fev[0]) {
+            cudaEventCreate(&h->fev[0]);
+            cudaEventCreate(&h->fev[1]);
+        }
+        cudaEventRecord(h->fev[0], st);
+    }
+    // The factors the apply streams (d and V, or their 16-bit copies) of all
+    // levels share one region, filled from the leaves up as the ranks become
+    // known: a compact span (few pages) for the apply.  It is reserved for the
+    // rank caps; only the prefix the ranks need is ever touched.
+    const size_t se = q16 ? 2 : pe;
+    size_t dv_bound = 0;
     for (int l = 1; l <= L; ++l) {
+        const size_t rmax = std::max((h->lv[l].cap + 7) / 8 * 8, 8);   // the padded rank's bound
+        dv_bound += 2 * (((size_t)h->ldn * rmax * se + 255) & ~size_t(255));
+    }
+    char *dvbase = L > 0 ? (char *)own(h, dv_bound, st) : nullptr;
+    if (L > 0 && !dvbase) {
+        cudaDeviceSynchronize();
+        drop_events();
+        free_temp();
+        return fail(HODLR_OUT_OF_MEMORY);
+    }
+    size_t dv_used = 0;
+    std::vector<int32_t> hcap;
+    for (int l = L; l >= 1; --l) {
         Level &lv = h->lv[l];
         lv.ranks.resize(lv.nnodes);
-        if (cudaMemcpyAsync(lv.ranks.data(), h->d_ranks[l], lv.nnodes * sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess) {
+        hcap.resize(lv.nnodes);
+        // (pageable destination: the copies return once level l is compressed)
+        if (cudaMemcpyAsync(lv.ranks.data(), h->d_ranks[l], lv.nnodes * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            rstream[l]) != cudaSuccess ||
+            cudaMemcpyAsync(hcap.data(), caphit + ((1 << l) - 2), lv.nnodes * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, rstream[l]) != cudaSuccess ||
+            cudaStreamSynchronize(rstream[l]) != cudaSuccess) {
+            cudaDeviceSynchronize();
+            drop_events();
             free_temp();
             return fail(HODLR_CUDA_ERROR);
         }
-    }
-    cudaMemcpyAsync(hcap.data(), caphit, blocks.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    {
-        hodlr_status s2 = take_status(c, st);
-        if (s2 != HODLR_OK) {
-            free_temp();
-            return fail(s2);
-        }
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    h->ms_compress = ms;
-    for (auto v : hcap) h->cap_hit |= v;
-    int64_t coff = 0;
-    for (int l = 1; l <= L; ++l) {
-        Level &lv = h->lv[l];
+        for (auto v : hcap) h->cap_hit |= v;
         int mx = 0;
         double sum = 0;
         for (int r : lv.ranks) {
@@ -569,102 +611,138 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         lv.rank_max = mx;
         lv.rank_mean = sum / lv.nnodes;
         lv.rp = mx == 0 ? 0 : (mx + 7) / 8 * 8;
-        lv.coff = coff;
-        coff += lv.rp;
-    }
-    h->Wtot = coff;
-    const size_t pe = elem_size(h->prec);
-    const size_t dvb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * pe;
-    const bool q16 = (h->store == HODLR_BF16 || h->store == HODLR_FP16);
-    const size_t qb = (size_t)h->ldn * std::max<int64_t>(h->Wtot, 1) * 2;
-    Arena fac;
-    const size_t o_U = fac.take(dvb), o_D = fac.take(dvb), o_V = fac.take(dvb);
-    std::vector<size_t> o_S(L), o_vs(L + 1), o_ds(L + 1);
-    for (int l = 0; l < L; ++l) {
-        const int64_t s2 = 2 * (int64_t)h->lv[l + 1].rp;
-        o_S[l] = fac.take((size_t)(1 << l) * std::max<int64_t>(s2 * s2, 1) * pe);
-    }
-    size_t o_Vq = 0, o_Dq = 0;
-    if (q16) {
-        o_Vq = fac.take(qb);
-        o_Dq = fac.take(qb);
-        if (h->store == HODLR_FP16)
-            for (int l = 1; l <= L; ++l) {
-                const size_t sb = (size_t)h->lv[l].nnodes * std::max(h->lv[l].rp, 1) * sizeof(float);
-                o_vs[l] = fac.take(sb);
-                o_ds[l] = fac.take(sb);
+        // storage of level l: the streamed d and V in the shared region, and
+        // an arena with U, the cores of level l - 1 and (16-bit storage) the
+        // FP32 d and V with the FP16 scales
+        const size_t colb = (size_t)h->ldn * std::max(lv.rp, 1);
+        const size_t sb = ((colb * se) + 255) & ~size_t(255);
+        char *dv_d = dvbase + dv_used, *dv_v = dvbase + dv_used + sb;
+        dv_used += 2 * sb;
+        const int64_t s2 = 2 * (int64_t)lv.rp;
+        Arena la;
+        const size_t oU = la.take(colb * pe);
+        size_t oD = 0, oV = 0, ovs = 0, ods = 0;
+        if (q16) {
+            oD = la.take(colb * pe);
+            oV = la.take(colb * pe);
+        }
+        const size_t oS = la.take((size_t)(1 << (l - 1)) * std::max<int64_t>(s2 * s2, 1) * pe);
+        if (h->store == HODLR_FP16) {
+            const size_t scb = (size_t)lv.nnodes * std::max(lv.rp, 1) * sizeof(float);
+            ovs = la.take(scb);
+            ods = la.take(scb);
+        }
+        char *lb = (char *)own(h, la.bytes, st);
+        if (!lb || dv_used > dv_bound) {
+            cudaDeviceSynchronize();
+            drop_events();
+            free_temp();
+            return fail(lb ? HODLR_RANGE : HODLR_OUT_OF_MEMORY);
+        }
+        h->Ul[l] = lb + oU;
+        h->Sinv[l - 1] = lb + oS;
+        if (q16) {
+            h->Dl[l] = lb + oD;
+            h->Vl[l] = lb + oV;
+            h->Dql[l] = dv_d;
+            h->Vql[l] = dv_v;
+            if (h->store == HODLR_FP16) {
+                h->vscale[l] = (float *)(lb + ovs);
+                h->dscale[l] = (float *)(lb + ods);
             }
-    }
-    char *fbase = (char *)own(h, fac.bytes, st);
-    if (!fbase) {
-        free_temp();
-        return fail(HODLR_OUT_OF_MEMORY);
-    }
-    h->U = fbase + o_U;
-    h->D = fbase + o_D;
-    h->V = fbase + o_V;
-    h->Sinv.assign(L, nullptr);
-    for (int l = 0; l < L; ++l) h->Sinv[l] = fbase + o_S[l];
-    if (q16) {
-        h->Vq = fbase + o_Vq;
-        h->Dq = fbase + o_Dq;
-        h->vscale.assign(L + 1, nullptr);
-        h->dscale.assign(L + 1, nullptr);
-        if (h->store == HODLR_FP16)
-            for (int l = 1; l <= L; ++l) {
-                h->vscale[l] = (float *)(fbase + o_vs[l]);
-                h->dscale[l] = (float *)(fbase + o_ds[l]);
-            }
-    }
-    if (h->Wtot > 0) cudaMemsetAsync(h->U, 0, 3 * (o_D - o_U), st);   // U, D, V are adjacent
-    for (int l = 1; l <= L; ++l) {
-        Level &lv = h->lv[l];
+        } else {
+            h->Dl[l] = dv_d;
+            h->Vl[l] = dv_v;
+        }
+        if (lv.rp > 0) {
+            // compaction writes the ranks' columns only: zero U and V
+            cudaMemsetAsync(h->Ul[l], 0, colb * pe, st);
+            cudaMemsetAsync(h->Vl[l], 0, colb * pe, st);
+        }
+        // compaction of level l from the staging (written by its compression)
+        cudaStreamWaitEvent(st, done[l - 1], 0);
         int64_t node_max = 0;
         for (int i = 0; i < lv.nnodes; ++i) {
             int64_t r0, m;
             nrange(l, i, r0, m);
             node_max = std::max(node_max, m);
         }
-        const size_t off = (size_t)lv.coff * h->ldn * pe;
-        char *Dl = (char *)h->U + off, *Vl = (char *)h->V + off;
+        char *Uc = (char *)h->Ul[l], *Vc = (char *)h->Vl[l];
         hodlr_status s3 = HODLR_OK;
-        if (cprec == HODLR_FP64 && h->prec == HODLR_FP64) {
-            s3 = launch_compact<double, double>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                                node_max, st);
-            if (s3 == HODLR_OK)
-                s3 = launch_compact_v<double, double>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                                    node_max, st);
-        } else if (cprec == HODLR_FP64) {
-            s3 = launch_compact<double, float>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                               node_max, st);
-            if (s3 == HODLR_OK)
-                s3 = launch_compact_v<double, float>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                                   node_max, st);
-        } else if (h->prec == HODLR_FP64) {
-            s3 = launch_compact<float, double>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                               node_max, st);
-            if (s3 == HODLR_OK)
-                s3 = launch_compact_v<float, double>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                                   node_max, st);
-        } else {
-            s3 = launch_compact<float, float>(Ust[l], h->ldn, Dl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                              node_max, st);
-            if (s3 == HODLR_OK)
-                s3 = launch_compact_v<float, float>(Vst[l], h->ldn, Vl, h->ldn, h->d_bounds, L, l, h->d_ranks[l], lv.rp,
-                                                  node_max, st);
+        if (lv.rp > 0) {
+            if (cprec == HODLR_FP64 && h->prec == HODLR_FP64) {
+                s3 = launch_compact<double, double>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
+                                                    lv.rp, node_max, st);
+                if (s3 == HODLR_OK)
+                    s3 = launch_compact_v<double, double>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
+                                                          h->d_ranks[l], lv.rp, node_max, st);
+            } else if (cprec == HODLR_FP64) {
+                s3 = launch_compact<double, float>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
+                                                   lv.rp, node_max, st);
+                if (s3 == HODLR_OK)
+                    s3 = launch_compact_v<double, float>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
+                                                         h->d_ranks[l], lv.rp, node_max, st);
+            } else if (h->prec == HODLR_FP64) {
+                s3 = launch_compact<float, double>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
+                                                   lv.rp, node_max, st);
+                if (s3 == HODLR_OK)
+                    s3 = launch_compact_v<float, double>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
+                                                         h->d_ranks[l], lv.rp, node_max, st);
+            } else {
+                s3 = launch_compact<float, float>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
+                                                  lv.rp, node_max, st);
+                if (s3 == HODLR_OK)
+                    s3 = launch_compact_v<float, float>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
+                                                        h->d_ranks[l], lv.rp, node_max, st);
+            }
         }
+        if (s3 == HODLR_OK) s3 = plan_level(h, l, st);
+        if (s3 == HODLR_OK && factor_now) s3 = run_level(h, l, st);
         if (s3 != HODLR_OK) {
+            cudaDeviceSynchronize();
+            drop_events();
             free_temp();
             return fail(s3);
         }
     }
-    free_temp();
-    {
-        hodlr_status sp = plan_factor(h, st);
-        if (sp != HODLR_OK) return fail(sp);
+    if (factor_now) {
+        if (L > 0) cudaEventRecord(h->fev[1], st);
+        h->factored = true;
     }
-    // (no synchronisation here: the factorisation that follows is stream-ordered
-    // after the compaction and the descriptor upload)
+    int64_t coff = 0;
+    for (int l = 1; l <= L; ++l) {
+        h->lv[l].coff = coff;
+        coff += h->lv[l].rp;
+    }
+    h->Wtot = coff;
+    // compression time: from the launch to the last level's completion
+    float ms = 0.f;
+    for (auto e : done) {
+        float t = 0.f;
+        if (e && cudaEventElapsedTime(&t, e0, e) == cudaSuccess) ms = std::max(ms, t);
+    }
+    h->ms_compress = ms;
+    // non-finite entries met by the compression (every level is complete here;
+    // a factorisation fault is reported by the next synchronising call)
+    {
+        int w = 0;
+        cudaStream_t ss = rstream[L > 0 ? 1 : 0];
+        if (cudaMemcpyAsync(&w, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, ss) != cudaSuccess ||
+            cudaStreamSynchronize(ss) != cudaSuccess) {
+            cudaDeviceSynchronize();
+            drop_events();
+            free_temp();
+            return fail(HODLR_CUDA_ERROR);
+        }
+        if (w & (ST_NONFINITE | ST_RANGE | ST_TIMEOUT)) {
+            cudaDeviceSynchronize();
+            drop_events();
+            free_temp();
+            return fail(take_status(c, st));
+        }
+    }
+    free_temp();
+    drop_events();
     if (cudaGetLastError() != cudaSuccess) {
         set_error("hodlr_build: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(HODLR_CUDA_ERROR);
@@ -713,7 +791,7 @@ hodlr_status hodlr_factor(hodlr_t *h, hodlr_stream stream) {
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
-    h->factored = false;
+    if (h->factored) return HODLR_OK;   // factored during the build
     if (!h->fev[0]) {
         HODLR_TRY_CUDA(cudaEventCreate(&h->fev[0]));
         HODLR_TRY_CUDA(cudaEventCreate(&h->fev[1]));
@@ -784,30 +862,34 @@ hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {
     return HODLR_OK;
 }
 
-hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U_or_d, double *V, int32_t *ranks,
+hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U, double *d, double *V, int32_t *ranks,
                                 int32_t *piv_rows, int32_t *piv_cols, hodlr_stream stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!h || level < 1 || level > h->L) {
         set_error("hodlr_export_level: level out of range");
         return HODLR_INVALID_ARG;
     }
+    if (d && !h->factored) {
+        set_error("hodlr_export_level: d requested before hodlr_factor");
+        return HODLR_NOT_FACTORED;
+    }
     HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
     const Level &lv = h->lv[level];
     const int64_t n = h->n, rp = lv.rp;
-    if ((U_or_d || V) && rp > 0) {
+    if ((U || d || V) && rp > 0) {
         double *tmp = (double *)dalloc(h->ctx, (size_t)n * rp * 8, st);
         if (!tmp) return HODLR_OUT_OF_MEMORY;
-        for (int which = 0; which < 2; ++which) {
-            double *dst = which == 0 ? U_or_d : V;
+        double *dst3[3] = {U, d, V};
+        const void *src3[3] = {h->Ul[level], h->Dl[level], h->Vl[level]};
+        for (int which = 0; which < 3; ++which) {
+            double *dst = dst3[which];
             if (!dst) continue;
-            const void *src = which == 0 ? (h->factored ? h->D : h->U) : h->V;
+            const void *src = src3[which];
             int blocks = (int)std::min<int64_t>((n * rp + 255) / 256, 4096);
             if (h->prec == HODLR_FP64)
-                to_double_kernel<double><<<blocks, 256, 0, st>>>((const double *)src + lv.coff * h->ldn, h->ldn, tmp, n,
-                                                                 n, rp);
+                to_double_kernel<double><<<blocks, 256, 0, st>>>((const double *)src, h->ldn, tmp, n, n, rp);
             else
-                to_double_kernel<float><<<blocks, 256, 0, st>>>((const float *)src + lv.coff * h->ldn, h->ldn, tmp, n, n,
-                                                                rp);
+                to_double_kernel<float><<<blocks, 256, 0, st>>>((const float *)src, h->ldn, tmp, n, n, rp);
             note_launch();
             HODLR_TRY_CUDA(cudaMemcpyAsync(dst, tmp, (size_t)n * rp * 8, cudaMemcpyDeviceToHost, st));
         }

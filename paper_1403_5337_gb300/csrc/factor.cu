@@ -1,19 +1,20 @@
-// Recursive Woodbury factorisation of a HODLR matrix, level-synchronous
-// (Sec. 4.3, Factorize steps 2-5; Sec. 4.2 eqs. Schur and y).
+// Recursive Woodbury factorisation of a HODLR matrix, level by level from the
+// leaves (Sec. 4.3, Factorize steps 2-5; Sec. 4.2 eqs. Schur and y).
 //
-// Layout: D and V are ldn x Wtot column-major; the columns of level l occupy
-// [coff(l), coff(l) + rp(l)).  Row block "node" of level l in D first holds
-// U_node (the Z stack of the paper: every row carries the U columns of all its
-// ancestors' blocks), and after factorisation d_node = K_node^-1 U_node.
+// Layout: per level c, U_c, d_c and V_c are ldn x rp(c) column-major.  Row
+// block "node" of U_c holds U_node (the Z stack of the paper, one level at a
+// time); after factorisation d_c(node rows) = K_node^-1 U_node.
 //
-//  1. leaves:  D(leaf rows, :) <- K_leaf^-1 Z(leaf rows, :)          (explicit inverse)
-//  2. for l = L-1 .. 0, children c = l + 1:
-//       Y_child = V(child rows, blk c)^T D(child rows, 0 : coff(c)+rp(c))
-//       S_node  = [[I, P], [Q, I]],  P = Y_alpha(:, blk c) = V_ba^T d_alpha,
-//                                     Q = Y_beta (:, blk c) = V_ab^T d_beta
-//       S^-1    = [[M^-1, -M^-1 P], [-Q M^-1, I + Q M^-1 P]],  M = I - P Q
-//       (l >= 1) D(alpha, 0:coff(c)) -= d_alpha * (S^-1 [Y_alpha; Y_beta])(rp:2rp, :)
-//                D(beta,  0:coff(c)) -= d_beta  * (S^-1 [Y_alpha; Y_beta])(0:rp, :)
+// The share of level c, issued as soon as levels c..L are compressed:
+//  1. d_c <- K_leaf^-1 U_c on every leaf                            (explicit inverses)
+//  2. for l = L-1 .. c (parents of level l + 1, deepest first):
+//       Y = [V_ba^T d_c(alpha); V_ab^T d_c(beta)],  [y1; y2] = S_l^-1 Y,
+//       d_c(alpha) -= d_alpha y2,  d_c(beta) -= d_beta y1      (d_alpha: final d of level l+1)
+//  3. the cores of level c - 1: P = V_ba^T d_alpha, Q = V_ab^T d_beta (now final),
+//       S = [[I, P], [Q, I]],  M = I - P Q,
+//       S^-1 = [[M^-1, -M^-1 P], [-Q M^-1, I + Q M^-1 P]]
+// Summed over c this is the level-synchronous sweep of the paper's recursion:
+// each d column receives the updates of the deeper levels in the same order.
 // The 2x2 block inverse through M = I - P Q is the same algebra as solving with
 // S; it halves the size of the dense inversion.
 #include <cuda_bf16.h>
@@ -624,12 +625,11 @@ hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, c
 
 }  // namespace
 
-// The factorisation is planned once, when the HODLR matrix is built: every
-// launch of the level-synchronous sweep is recorded with its arguments, and all
-// batched-GEMM and inversion descriptors are laid out in one blob that is
-// uploaded in a single copy.  hodlr_factor then only replays the launches, with
-// no host-device transfer on the stream.
-struct FactorPlan {
+// The factorisation is recorded level by level when the HODLR matrix is built:
+// the launches of each level's share (see plan_level) with their arguments, and
+// that share's batched-GEMM and inversion descriptors laid out in one blob
+// uploaded in a single copy.  Replaying needs no host-device transfer.
+struct LevelPlan {
     std::vector<std::function<hodlr_status(cudaStream_t)>> ops;
     std::vector<char> blob;
     char *dblob = nullptr;
@@ -645,12 +645,16 @@ struct FactorPlan {
     }
 };
 
+struct FactorPlan {
+    std::vector<LevelPlan> lv;   // index 1..L
+};
+
 namespace {
 
 template <typename T>
 struct Rec {
     hodlr_ctx *c;
-    FactorPlan *P;
+    LevelPlan *P;
     void gj(const std::vector<GJDesc<T>> &hd) {
         if (hd.empty()) return;
         int bmax = 0;
@@ -658,7 +662,7 @@ struct Rec {
         const size_t off = P->put(hd.data(), hd.size() * sizeof(GJDesc<T>));
         const int cnt = (int)hd.size();
         hodlr_ctx *cc = c;
-        FactorPlan *PP = P;
+        LevelPlan *PP = P;
         P->ops.push_back([=](cudaStream_t s) {
             return launch_gj<T>(cc, reinterpret_cast<const GJDesc<T> *>(PP->dblob + off), cnt, bmax, s);
         });
@@ -675,7 +679,7 @@ struct Rec {
         const size_t off = P->put(hd.data(), hd.size() * sizeof(GemmDesc<T>));
         const int cnt = (int)hd.size();
         hodlr_ctx *cc = c;
-        FactorPlan *PP = P;
+        LevelPlan *PP = P;
         P->ops.push_back([=](cudaStream_t s) {
             return gemm_batched<T>(cc, reinterpret_cast<const GemmDesc<T> *>(PP->dblob + off), cnt, maxM, maxN,
                                    maxK, transA, alpha, s);
@@ -688,7 +692,7 @@ struct Rec {
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(512, (most + 2047) / 2048));
         const size_t off = P->put(hd.data(), hd.size() * sizeof(FillDesc<T>));
         const int cnt = (int)hd.size();
-        FactorPlan *PP = P;
+        LevelPlan *PP = P;
         P->ops.push_back([=](cudaStream_t s) {
             fill_kernel<T><<<dim3(gx, cnt), 256, 0, s>>>(reinterpret_cast<const FillDesc<T> *>(PP->dblob + off));
             note_launch();
@@ -699,214 +703,186 @@ struct Rec {
 };
 
 template <typename T>
-hodlr_status plan_typed(hodlr_t *h, FactorPlan *Pl, cudaStream_t s) {
-    hodlr_ctx *c = h->ctx;
+hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) {
+    hodlr_ctx *cx = h->ctx;
     const int L = h->L;
-    const int64_t ldn = h->ldn, W = h->Wtot;
-    T *D = reinterpret_cast<T *>(h->D);
-    T *V = reinterpret_cast<T *>(h->V);
+    const int64_t ldn = h->ldn;
     const int nleaf = 1 << L;
+    const int64_t bmax = h->bmax;
     auto node_range = [&](int l, int i, int64_t &r0, int64_t &m) {
         r0 = h->bounds[(size_t)i << (L - l)];
         m = h->bounds[(size_t)(i + 1) << (L - l)] - r0;
     };
-    // ---- workspace: every level has its own Y, S^-1 W and M areas, so one
-    // fill launch at the start prepares all of them (zeros, identities)
-    const int64_t bmax = h->bmax;
-    struct LvlWs {
-        size_t y = 0, yv = 0, m = 0, gw = 0;
-    };
-    std::vector<LvlWs> ws(L);
-    size_t need = 0;
-    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    for (int l = 0; l < L; ++l) {
-        const int cch = l + 1;
-        const int rp = h->lv[cch].rp;
-        const int64_t Wc = h->lv[cch].coff + rp;
-        const int nn = 1 << l;
-        ws[l].y = al((size_t)nn * 2 * rp * Wc * sizeof(T));                                   // [Y_a; Y_b] per node
-        ws[l].yv = al((size_t)nn * 2 * rp * std::max<int64_t>(h->lv[cch].coff, 1) * sizeof(T)); // S^-1 [Y_a; Y_b]
-        ws[l].m = al((size_t)nn * rp * rp * sizeof(T));                                       // M per node
-        ws[l].gw = gj_needs_work<T>(rp) ? al((size_t)nn * 2 * rp * rp * sizeof(T)) : 0;      // GJ work
-        need += ws[l].y + ws[l].yv + ws[l].m + ws[l].gw;
+    const int rc = h->lv[c].rp;
+    T *Uc = reinterpret_cast<T *>(h->Ul[c]);
+    T *Dc = reinterpret_cast<T *>(h->Dl[c]);
+    T *Vc = reinterpret_cast<T *>(h->Vl[c]);
+    const T *Kinv = reinterpret_cast<const T *>(h->leafinv);
+    // ---- workspace: per deeper level l the children's V^T d_c and its S^-1
+    // image, then the cores of level c - 1 (one allocation)
+    Arena ws;
+    std::vector<size_t> oY(L), oYv(L);
+    for (int l = L - 1; l >= c; --l) {
+        const size_t bytes = (size_t)(1 << l) * 2 * h->lv[l + 1].rp * std::max(rc, 1) * sizeof(T);
+        oY[l] = ws.take(bytes);
+        oYv[l] = ws.take(bytes);
     }
-    need += 4096;
-    Pl->work = dalloc(c, need, s);
+    const int nn0 = 1 << (c - 1);
+    const int64_t s2c = 2 * (int64_t)rc;
+    const size_t oYo = ws.take((size_t)nn0 * s2c * std::max(rc, 1) * sizeof(T));
+    const size_t oM = ws.take((size_t)nn0 * rc * rc * sizeof(T));
+    const bool gwn = gj_needs_work<T>(rc);
+    const size_t oGW = gwn ? ws.take((size_t)nn0 * 2 * rc * rc * sizeof(T)) : 0;
+    Pl->work = dalloc(cx, ws.bytes, s);
     if (!Pl->work) {
-        set_error("factor plan: out of device memory (%zu bytes)", need);
+        set_error("factor plan: out of device memory (%zu bytes)", ws.bytes);
         return HODLR_OUT_OF_MEMORY;
     }
-    Pl->work_bytes = need;
-    char *wp = reinterpret_cast<char *>(Pl->work);
-    auto carve = [&](size_t bytes) {
-        char *p = wp;
-        wp += al(bytes);
-        return p;
-    };
-    Rec<T> rec{c, Pl};
-    const T *U = reinterpret_cast<const T *>(h->U);
+    Pl->work_bytes = ws.bytes;
+    char *wb = reinterpret_cast<char *>(Pl->work);
+    Rec<T> rec{cx, Pl};
+    // ---- zeros and identities this share starts from
     std::vector<FillDesc<T>> fills;
-    struct LvlPtr {
-        T *Y, *Yv, *M, *gw;
-    };
-    std::vector<LvlPtr> lp(L);
-    for (int l = 0; l < L; ++l) {
-        const int cch = l + 1;
-        const int rp = h->lv[cch].rp;
-        const int nn = 1 << l;
-        lp[l].Y = reinterpret_cast<T *>(carve(ws[l].y));
-        lp[l].Yv = reinterpret_cast<T *>(carve(ws[l].yv));
-        lp[l].M = reinterpret_cast<T *>(carve(ws[l].m));
-        lp[l].gw = ws[l].gw ? reinterpret_cast<T *>(carve(ws[l].gw)) : nullptr;
-        if (rp == 0) continue;
-        const int64_t s2 = 2 * (int64_t)rp;
-        fills.push_back(FillDesc<T>{lp[l].Y, 0, (int64_t)(ws[l].y / sizeof(T)), 1, INT_MAX, 1, 0});
-        fills.push_back(FillDesc<T>{lp[l].Yv, 0, (int64_t)(ws[l].yv / sizeof(T)), 1, INT_MAX, 1, 0});
-        fills.push_back(FillDesc<T>{lp[l].M, rp, rp, rp, 0, nn, (int64_t)rp * rp});               // I
-        fills.push_back(FillDesc<T>{reinterpret_cast<T *>(h->Sinv[l]), s2, s2, s2, rp, nn, s2 * s2});  // [0 0; 0 I]
-    }
-    // ---- 1. leaf inverses: computed by hodlr_build (they depend on A only), while
-    // the off-diagonal blocks are being compressed
-    T *Kinv = reinterpret_cast<T *>(h->leafinv);
-    if (W > 0) fills.push_back(FillDesc<T>{D, 0, ldn * W, 1, INT_MAX, 1, 0});
-    rec.fill(fills);
-    // ---- 2. leaf stack: D = Kinv_leaf * U (all columns).  U is left intact, so
-    // the factorisation can be repeated.
-    if (W > 0) {
-        std::vector<GemmDesc<T>> gd(nleaf);
-        for (int i = 0; i < nleaf; ++i) {
-            int64_t r0, m;
-            node_range(L, i, r0, m);
-            gd[i] = GemmDesc<T>{Kinv + (size_t)i * bmax * bmax, U + r0, D + r0, bmax, ldn, ldn,
-                                (int)m, (int)W, (int)m};
+    if (rc > 0) {
+        fills.push_back(FillDesc<T>{Dc, 0, ldn * rc, 1, INT_MAX, 1, 0});
+        for (int l = L - 1; l >= c; --l) {
+            const int64_t e = (int64_t)(1 << l) * 2 * h->lv[l + 1].rp * rc;
+            if (e == 0) continue;
+            fills.push_back(FillDesc<T>{reinterpret_cast<T *>(wb + oY[l]), 0, e, 1, INT_MAX, 1, 0});
+            fills.push_back(FillDesc<T>{reinterpret_cast<T *>(wb + oYv[l]), 0, e, 1, INT_MAX, 1, 0});
         }
-        rec.gemm(gd, 0, T(1));
+        fills.push_back(FillDesc<T>{reinterpret_cast<T *>(wb + oYo), 0, (int64_t)nn0 * s2c * rc, 1, INT_MAX, 1, 0});
+        fills.push_back(FillDesc<T>{reinterpret_cast<T *>(wb + oM), rc, rc, rc, 0, nn0, (int64_t)rc * rc});   // I
+        fills.push_back(FillDesc<T>{reinterpret_cast<T *>(h->Sinv[c - 1]), s2c, s2c, s2c, rc, nn0,
+                                    s2c * s2c});   // [0 0; 0 I]
     }
-    // ---- 3. levels, bottom-up.  Node i of level l has children a = 2i, b = 2i+1
-    // at level l+1, whose blocks V(a, blk)^T D(a, :) and V(b, blk)^T D(b, :) are
-    // stacked as Y_i = [Y_a; Y_b] (2 rp x Wc, ld 2 rp).  P = Y_a(:, own block),
-    // Q = Y_b(:, own block); S = [[I, P], [Q, I]], M = I - P Q,
-    // S^-1 = [[M^-1, -M^-1 P], [-Q M^-1, I + Q M^-1 P]].
-    for (int l = L - 1; l >= 0; --l) {
-        const int cch = l + 1;
-        const int rp = h->lv[cch].rp;
-        const int64_t coffc = h->lv[cch].coff;
-        const int64_t Wc = coffc + rp;
-        const int nn = 1 << l;
-        const int nch = 2 * nn;
-        T *Sinv = reinterpret_cast<T *>(h->Sinv[l]);
-        const int64_t s2 = 2 * (int64_t)rp;
-        if (rp == 0) continue;
-        T *Y = lp[l].Y, *Yv = lp[l].Yv, *M = lp[l].M, *gw = lp[l].gw;
-        auto Yi = [&](int i) { return Y + (size_t)i * s2 * Wc; };
-        // (a) Y_child = V(child, blk)^T D(child, 0:Wc)
+    rec.fill(fills);
+    if (rc > 0) {
+        // ---- d_c = K_leaf^-1 U_c on every leaf
         {
-            std::vector<GemmDesc<T>> gd(nch);
-            for (int i = 0; i < nch; ++i) {
+            std::vector<GemmDesc<T>> gd(nleaf);
+            for (int i = 0; i < nleaf; ++i) {
                 int64_t r0, m;
-                node_range(cch, i, r0, m);
-                gd[i] = GemmDesc<T>{V + coffc * ldn + r0, D + r0, Yi(i / 2) + (i & 1) * rp, ldn, ldn,
-                                    s2, rp, (int)Wc, (int)m};
+                node_range(L, i, r0, m);
+                gd[i] = GemmDesc<T>{Kinv + (size_t)i * bmax * bmax, Uc + r0, Dc + r0, bmax, ldn, ldn, (int)m, rc,
+                                    (int)m};
+            }
+            rec.gemm(gd, 0, T(1));
+        }
+        // ---- the Woodbury update of every deeper level, deepest first: for
+        // the parents of level l + 1, [y1; y2] = S^-1 [V_ba^T d_c(a); V_ab^T d_c(b)],
+        // d_c(a) -= d_a y2, d_c(b) -= d_b y1
+        for (int l = L - 1; l >= c; --l) {
+            const int rl = h->lv[l + 1].rp;
+            if (rl == 0) continue;
+            const int nn = 1 << l;
+            const int64_t s2 = 2 * (int64_t)rl;
+            const T *Vn = reinterpret_cast<const T *>(h->Vl[l + 1]);
+            const T *Dn = reinterpret_cast<const T *>(h->Dl[l + 1]);
+            const T *Sn = reinterpret_cast<const T *>(h->Sinv[l]);
+            T *Y = reinterpret_cast<T *>(wb + oY[l]);
+            T *Yv = reinterpret_cast<T *>(wb + oYv[l]);
+            std::vector<GemmDesc<T>> gy(2 * nn), gv(nn), gu(2 * nn);
+            for (int ch = 0; ch < 2 * nn; ++ch) {
+                int64_t r0, m;
+                node_range(l + 1, ch, r0, m);
+                gy[ch] = GemmDesc<T>{Vn + r0, Dc + r0, Y + (size_t)(ch / 2) * s2 * rc + (ch & 1) * rl, ldn, ldn, s2,
+                                     rl, rc, (int)m};
+            }
+            for (int i = 0; i < nn; ++i)
+                gv[i] = GemmDesc<T>{Sn + (size_t)i * s2 * s2, Y + (size_t)i * s2 * rc, Yv + (size_t)i * s2 * rc, s2, s2,
+                                    s2, (int)s2, rc, (int)s2};
+            for (int i = 0; i < nn; ++i) {
+                int64_t ra, ma, rb, mb;
+                node_range(l + 1, 2 * i, ra, ma);
+                node_range(l + 1, 2 * i + 1, rb, mb);
+                const T *yv = Yv + (size_t)i * s2 * rc;
+                gu[2 * i] = GemmDesc<T>{Dn + ra, yv + rl, Dc + ra, ldn, s2, ldn, (int)ma, rc, rl};
+                gu[2 * i + 1] = GemmDesc<T>{Dn + rb, yv, Dc + rb, ldn, s2, ldn, (int)mb, rc, rl};
+            }
+            rec.gemm(gy, 1, T(1));
+            rec.gemm(gv, 0, T(1));
+            rec.gemm(gu, 0, T(-1));
+        }
+        // ---- the cores of level c - 1: Y_i = [V_ba^T d_a; V_ab^T d_b] (2 rc x rc),
+        // P = Y_a, Q = Y_b, S = [[I, P], [Q, I]], M = I - P Q,
+        // S^-1 = [[M^-1, -M^-1 P], [-Q M^-1, I + Q M^-1 P]]
+        T *Yo = reinterpret_cast<T *>(wb + oYo);
+        T *M = reinterpret_cast<T *>(wb + oM);
+        T *gw = gwn ? reinterpret_cast<T *>(wb + oGW) : nullptr;
+        T *Sinv = reinterpret_cast<T *>(h->Sinv[c - 1]);
+        auto Yi = [&](int i) { return Yo + (size_t)i * s2c * rc; };
+        {
+            std::vector<GemmDesc<T>> gd(2 * nn0);
+            for (int ch = 0; ch < 2 * nn0; ++ch) {
+                int64_t r0, m;
+                node_range(c, ch, r0, m);
+                gd[ch] = GemmDesc<T>{Vc + r0, Dc + r0, Yi(ch / 2) + (ch & 1) * rc, ldn, ldn, s2c, rc, rc, (int)m};
             }
             rec.gemm(gd, 1, T(1));
         }
-        // (b) M = I - P Q per node
         {
-            std::vector<GemmDesc<T>> gd(nn);
-            for (int i = 0; i < nn; ++i) {
-                const T *P = Yi(i) + coffc * s2;
-                const T *Q = Yi(i) + rp + coffc * s2;
-                gd[i] = GemmDesc<T>{P, Q, M + (size_t)i * rp * rp, s2, s2, rp, rp, rp, rp};
-            }
+            std::vector<GemmDesc<T>> gd(nn0);
+            for (int i = 0; i < nn0; ++i)
+                gd[i] = GemmDesc<T>{Yi(i), Yi(i) + rc, M + (size_t)i * rc * rc, s2c, s2c, rc, rc, rc, rc};
             rec.gemm(gd, 0, T(-1));
         }
-        // (c) M^-1 into the top-left block of S^-1
         {
-            std::vector<GJDesc<T>> gd(nn);
-            for (int i = 0; i < nn; ++i)
-                gd[i] = GJDesc<T>{nullptr, 0, M + (size_t)i * rp * rp, rp, gw ? gw + (size_t)i * 2 * rp * rp : nullptr,
-                                  Sinv + (size_t)i * s2 * s2, s2, rp};
+            std::vector<GJDesc<T>> gd(nn0);
+            for (int i = 0; i < nn0; ++i)
+                gd[i] = GJDesc<T>{nullptr, 0, M + (size_t)i * rc * rc, rc, gw ? gw + (size_t)i * 2 * rc * rc : nullptr,
+                                  Sinv + (size_t)i * s2c * s2c, s2c, rc};
             rec.gj(gd);
         }
-        // (d) TR = -M^-1 P and BL = -Q M^-1 (one launch), then BR = I - Q TR
         {
-            std::vector<GemmDesc<T>> g12(2 * nn), g3(nn);
-            for (int i = 0; i < nn; ++i) {
-                T *S = Sinv + (size_t)i * s2 * s2;
-                const T *P = Yi(i) + coffc * s2;
-                const T *Q = Yi(i) + rp + coffc * s2;
-                g12[2 * i] = GemmDesc<T>{S, P, S + rp * s2, s2, s2, s2, rp, rp, rp};
-                g12[2 * i + 1] = GemmDesc<T>{Q, S, S + rp, s2, s2, s2, rp, rp, rp};
-                g3[i] = GemmDesc<T>{Q, S + rp * s2, S + rp + rp * s2, s2, s2, s2, rp, rp, rp};
+            std::vector<GemmDesc<T>> g12(2 * nn0), g3(nn0);
+            for (int i = 0; i < nn0; ++i) {
+                T *S = Sinv + (size_t)i * s2c * s2c;
+                const T *P = Yi(i), *Q = Yi(i) + rc;
+                g12[2 * i] = GemmDesc<T>{S, P, S + rc * s2c, s2c, s2c, s2c, rc, rc, rc};        // TR -= M^-1 P
+                g12[2 * i + 1] = GemmDesc<T>{Q, S, S + rc, s2c, s2c, s2c, rc, rc, rc};          // BL -= Q M^-1
+                g3[i] = GemmDesc<T>{Q, S + rc * s2c, S + rc + rc * s2c, s2c, s2c, s2c, rc, rc, rc};   // BR -= Q TR
             }
             rec.gemm(g12, 0, T(-1));
             rec.gemm(g3, 0, T(-1));
         }
-        // (e) update the ancestor columns (levels 1..l) for l >= 1:
-        // [y1; y2] = S^-1 [Y_a; Y_b](:, 0:coffc), D(a) -= d_a y2, D(b) -= d_b y1
-        if (l >= 1 && coffc > 0) {
-            std::vector<GemmDesc<T>> gs(nn);
-            for (int i = 0; i < nn; ++i)
-                gs[i] = GemmDesc<T>{Sinv + (size_t)i * s2 * s2, Yi(i), Yv + (size_t)i * s2 * coffc, s2, s2, s2,
-                                    (int)s2, (int)coffc, (int)s2};
-            rec.gemm(gs, 0, T(1));
-            std::vector<GemmDesc<T>> gu(nch);
-            for (int i = 0; i < nn; ++i) {
-                int64_t ra, ma, rb, mb;
-                node_range(cch, 2 * i, ra, ma);
-                node_range(cch, 2 * i + 1, rb, mb);
-                const T *yv = Yv + (size_t)i * s2 * coffc;
-                gu[2 * i] = GemmDesc<T>{D + coffc * ldn + ra, yv + rp, D + ra, ldn, s2, ldn,
-                                        (int)ma, (int)coffc, rp};
-                gu[2 * i + 1] = GemmDesc<T>{D + coffc * ldn + rb, yv, D + rb, ldn, s2, ldn,
-                                            (int)mb, (int)coffc, rp};
-            }
-            rec.gemm(gu, 0, T(-1));
-        }
     }
-    // 16-bit copies of V and d for the apply (BF16 / FP16 storage)
+    // ---- 16-bit copies of V_c and d_c for the apply (BF16 / FP16 storage)
     if constexpr (sizeof(T) == 4) {
-        if (h->store == HODLR_BF16 || h->store == HODLR_FP16) {
-            for (int l = 1; l <= L; ++l) {
-                const int rp = h->lv[l].rp;
-                if (rp == 0) continue;
-                const int64_t coff = h->lv[l].coff;
-                const int nn = 1 << l;
-                const float *Vf = reinterpret_cast<const float *>(h->V);
-                const float *Df = reinterpret_cast<const float *>(h->D);
-                const int64_t *bd = h->d_bounds;
-                if (h->store == HODLR_BF16) {
-                    __nv_bfloat16 *Vq = reinterpret_cast<__nv_bfloat16 *>(h->Vq);
-                    __nv_bfloat16 *Dq = reinterpret_cast<__nv_bfloat16 *>(h->Dq);
-                    Pl->ops.push_back([=](cudaStream_t s) {
-                        quantize_kernel<__nv_bfloat16><<<dim3(nn, rp), 256, 0, s>>>(Vf, Vq, ldn, coff, rp, bd, L, l,
-                                                                                     nullptr);
-                        note_launch();
-                        quantize_kernel<__nv_bfloat16><<<dim3(nn, rp), 256, 0, s>>>(Df, Dq, ldn, coff, rp, bd, L, l,
-                                                                                     nullptr);
-                        note_launch();
-                        HODLR_TRY_CUDA(cudaGetLastError());
-                        return HODLR_OK;
-                    });
-                } else {
-                    __half *Vq = reinterpret_cast<__half *>(h->Vq);
-                    __half *Dq = reinterpret_cast<__half *>(h->Dq);
-                    float *vs = h->vscale[l], *ds = h->dscale[l];
-                    Pl->ops.push_back([=](cudaStream_t s) {
-                        quantize_kernel<__half><<<dim3(nn, rp), 256, 0, s>>>(Vf, Vq, ldn, coff, rp, bd, L, l, vs);
-                        note_launch();
-                        quantize_kernel<__half><<<dim3(nn, rp), 256, 0, s>>>(Df, Dq, ldn, coff, rp, bd, L, l, ds);
-                        note_launch();
-                        HODLR_TRY_CUDA(cudaGetLastError());
-                        return HODLR_OK;
-                    });
-                }
+        if ((h->store == HODLR_BF16 || h->store == HODLR_FP16) && rc > 0) {
+            const int nn = 1 << c;
+            const float *Vf = reinterpret_cast<const float *>(h->Vl[c]);
+            const float *Df = reinterpret_cast<const float *>(h->Dl[c]);
+            const int64_t *bd = h->d_bounds;
+            if (h->store == HODLR_BF16) {
+                __nv_bfloat16 *Vq = reinterpret_cast<__nv_bfloat16 *>(h->Vql[c]);
+                __nv_bfloat16 *Dq = reinterpret_cast<__nv_bfloat16 *>(h->Dql[c]);
+                Pl->ops.push_back([=](cudaStream_t st) {
+                    quantize_kernel<__nv_bfloat16><<<dim3(nn, rc), 256, 0, st>>>(Vf, Vq, ldn, 0, rc, bd, L, c, nullptr);
+                    note_launch();
+                    quantize_kernel<__nv_bfloat16><<<dim3(nn, rc), 256, 0, st>>>(Df, Dq, ldn, 0, rc, bd, L, c, nullptr);
+                    note_launch();
+                    HODLR_TRY_CUDA(cudaGetLastError());
+                    return HODLR_OK;
+                });
+            } else {
+                __half *Vq = reinterpret_cast<__half *>(h->Vql[c]);
+                __half *Dq = reinterpret_cast<__half *>(h->Dql[c]);
+                float *vs = h->vscale[c], *ds = h->dscale[c];
+                Pl->ops.push_back([=](cudaStream_t st) {
+                    quantize_kernel<__half><<<dim3(nn, rc), 256, 0, st>>>(Vf, Vq, ldn, 0, rc, bd, L, c, vs);
+                    note_launch();
+                    quantize_kernel<__half><<<dim3(nn, rc), 256, 0, st>>>(Df, Dq, ldn, 0, rc, bd, L, c, ds);
+                    note_launch();
+                    HODLR_TRY_CUDA(cudaGetLastError());
+                    return HODLR_OK;
+                });
             }
         }
     }
-    // one upload of every descriptor (the caller synchronises before factor runs)
+    // one upload of this share's descriptors
     Pl->dbytes = std::max<size_t>(Pl->blob.size(), 256);
-    Pl->dblob = reinterpret_cast<char *>(dalloc(c, Pl->dbytes, s));
+    Pl->dblob = reinterpret_cast<char *>(dalloc(cx, Pl->dbytes, s));
     if (!Pl->dblob) {
         set_error("factor plan: out of device memory for descriptors");
         return HODLR_OUT_OF_MEMORY;
@@ -983,25 +959,37 @@ hodlr_status leaf_inverses(hodlr_t *h, cudaStream_t s) {
     return leaf_inverses_typed<float>(h, s);
 }
 
-hodlr_status plan_factor(hodlr_t *h, cudaStream_t s) {
-    if (h->plan) return HODLR_OK;
-    FactorPlan *P = new FactorPlan();
-    hodlr_status st = (h->prec == HODLR_FP64) ? plan_typed<double>(h, P, s) : plan_typed<float>(h, P, s);
-    h->plan = P;   // owned even on failure, released by free_plan
-    return st;
+hodlr_status plan_level(hodlr_t *h, int c, cudaStream_t s) {
+    if (!h->plan) {
+        h->plan = new FactorPlan();
+        h->plan->lv.resize(h->L + 1);
+    }
+    LevelPlan *P = &h->plan->lv[c];
+    if (!P->ops.empty()) return HODLR_OK;
+    return (h->prec == HODLR_FP64) ? plan_level_typed<double>(h, P, c, s) : plan_level_typed<float>(h, P, c, s);
+}
+
+hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s) {
+    if (!h->plan || c >= (int)h->plan->lv.size()) {
+        set_error("factor: level %d was not planned", c);
+        return HODLR_INVALID_ARG;
+    }
+    for (auto &op : h->plan->lv[c].ops) HODLR_TRY(op(s));
+    return HODLR_OK;
 }
 
 void free_plan(hodlr_t *h, cudaStream_t s) {
     if (!h->plan) return;
-    if (h->plan->work) dfree(h->ctx, h->plan->work, h->plan->work_bytes, s);
-    if (h->plan->dblob) dfree(h->ctx, h->plan->dblob, h->plan->dbytes, s);
+    for (auto &P : h->plan->lv) {
+        if (P.work) dfree(h->ctx, P.work, P.work_bytes, s);
+        if (P.dblob) dfree(h->ctx, P.dblob, P.dbytes, s);
+    }
     delete h->plan;
     h->plan = nullptr;
 }
 
 hodlr_status factor_impl(hodlr_t *h, cudaStream_t s) {
-    HODLR_TRY(plan_factor(h, s));
-    for (auto &op : h->plan->ops) HODLR_TRY(op(s));
+    for (int c = h->L; c >= 1; --c) HODLR_TRY(run_level(h, c, s));
     return HODLR_OK;
 }
 

@@ -93,8 +93,8 @@ hodlr_status take_status(hodlr_ctx *c, cudaStream_t s);
 // sibling's rows (A(node, sibling) ~ U_node V_sibling^T).
 struct Level {
     int nnodes = 0;
-    int rp = 0;               // padded rank (columns of this level in D and V)
-    int64_t coff = 0;         // first column of this level in D and V
+    int rp = 0;               // padded rank (columns of this level's U, d and V)
+    int64_t coff = 0;         // sum of rp over the levels above (storage accounting)
     int cap = 0;              // staging columns for compression
     std::vector<int> ranks;   // per node
     int rank_max = 0;
@@ -116,7 +116,6 @@ struct hodlr_s {
     int64_t *d_bounds = nullptr;
     int prec = HODLR_FP32;            // factorisation arithmetic (FP64 or FP32)
     int store = HODLR_FP32;           // storage of the streamed factors V, d in the apply
-    void *Vq = nullptr, *Dq = nullptr;   // 16-bit copies of V and d (BF16 / FP16 storage)
     std::vector<float *> vscale, dscale; // FP16: per level 0..L, [nnodes * rp] dequantisation factors
     int cprec = HODLR_FP32;           // compression precision
     int method = HODLR_ACA;
@@ -124,11 +123,13 @@ struct hodlr_s {
     int rank_cap = 1024;
     int cap_hit = 0;
     std::vector<hodlr::Level> lv;     // index 1..L used
-    int64_t ldn = 0;                  // leading dimension of D, V (n rounded up to 32)
-    int64_t Wtot = 0;                 // total columns of D, V
-    void *U = nullptr;                // elem[ldn * Wtot]: the compressed U columns (kept: re-factorable)
-    void *D = nullptr;                // elem[ldn * Wtot]: d = K_node^-1 U_node after factorisation
-    void *V = nullptr;                // elem[ldn * Wtot]
+    int64_t ldn = 0;                  // leading dimension of U, D, V (n rounded up to 32)
+    int64_t Wtot = 0;                 // sum of rp over the levels
+    // Per level c = 1..L (index 0 unused), each ldn x rp(c) column-major:
+    std::vector<void *> Ul;           // the compressed U columns (kept: re-factorable)
+    std::vector<void *> Dl;           // d = K_node^-1 U_node after factorisation
+    std::vector<void *> Vl;           // rows of node nu: V of the sibling's block
+    std::vector<void *> Vql, Dql;     // 16-bit copies of V and d (BF16 / FP16 storage)
     void *leafinv = nullptr;          // elem[2^L * bmax * bmax], column-major per leaf
     std::vector<void *> Sinv;         // level l = 0..L-1: elem[2^l * (2 rp(l+1))^2]
     std::vector<int32_t *> piv_rows;  // per level 1..L: [nnodes][cap] pivot rows (ACA) / kept rows (BDLR)
@@ -180,11 +181,14 @@ struct AcaBlockDesc {
     int32_t *cap_hit;   // out
 };
 // Partial-pivoting ACA, one thread-block cluster per block, one launch per level on the context's side
-// streams (forked from and joined back into s).  level_first: first block of each
-// level in d_blocks (size nlev + 1); level_maxdim: largest block side per level.
+// streams (forked from s; level l + 1 on side[l mod HODLR_SIDE_STREAMS]).  level_first: first block of
+// each level in d_blocks (size nlev + 1); level_maxdim: largest block side per level.
+// done[l] (created here, destroyed by the caller) completes with level l + 1's
+// compression; s itself does not wait for the levels.
 hodlr_status launch_aca_levels(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
                                const AcaBlockDesc *d_blocks, const std::vector<int> &level_first,
-                               const std::vector<int64_t> &level_maxdim, double tol, cudaStream_t s);
+                               const std::vector<int64_t> &level_maxdim, double tol, cudaStream_t s,
+                               std::vector<cudaEvent_t> &done);
 
 struct BdlrHost;   // defined in bdlr.cu
 hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t s,
@@ -204,9 +208,12 @@ hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T> *d_desc, int nbatch, i
                           int maxN, int maxK, int transA, T alpha, cudaStream_t s);
 
 hodlr_status factor_impl(hodlr_t *h, cudaStream_t s);
-// Record the factorisation's launches and upload its descriptors (stream-ordered
-// on s; the caller synchronises before the first factor_impl).
-hodlr_status plan_factor(hodlr_t *h, cudaStream_t s);
+// Record level c's share of the factorisation (its d columns through every
+// deeper level's update, then the cores of level c - 1) and upload its
+// descriptors; levels are recorded from c = L down to 1.  run_level issues the
+// recorded launches of level c on s; factor_impl replays every level.
+hodlr_status plan_level(hodlr_t *h, int c, cudaStream_t s);
+hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s);
 // Explicit inverses of the leaf blocks of A (stream-ordered; h->leafinv allocated).
 hodlr_status leaf_inverses(hodlr_t *h, cudaStream_t s);
 void free_plan(hodlr_t *h, cudaStream_t s);

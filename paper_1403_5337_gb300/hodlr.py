@@ -52,7 +52,8 @@ class _Graph(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("compress_precision", C.c_int), ("rank_cap", C.c_int),
                 ("bdlr_depth", C.c_int), ("core_cond_threshold", C.c_double),
-                ("leaf_bounds", C.c_void_p), ("n_leaf_bounds", C.c_int), ("seed", C.c_uint64)]
+                ("leaf_bounds", C.c_void_p), ("n_leaf_bounds", C.c_int), ("seed", C.c_uint64),
+                ("defer_factor", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -124,7 +125,7 @@ def load_library(path: str = _LIBPATH):
     lib.hodlr_matvec_noalloc.argtypes = [C.POINTER(_Matrix), ci, vp, i64, vp, i64, vp]
     lib.hodlr_precond_error.argtypes = [vp, ci, vp, i64, C.POINTER(cd), vp]
     lib.hodlr_stats_get.argtypes = [vp, C.POINTER(_Stats)]
-    lib.hodlr_export_level.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp]
+    lib.hodlr_export_level.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp, vp]
     lib.hodlr_export_core.argtypes = [vp, ci, vp, vp]
     lib.hodlr_destroy.argtypes = [vp]
     lib.hodlr_launch_count.argtypes = [C.POINTER(C.c_longlong)]
@@ -268,7 +269,7 @@ class Hodlr:
                     ms_compress=st.ms_compress, ms_factor=st.ms_factor)
 
     def export_level(self, level: int, stream=None):
-        """(U or d, V, ranks, piv_rows, piv_cols) of level `level` as numpy arrays."""
+        """(U, V, ranks, piv_rows, piv_cols) of level `level` as numpy arrays."""
         s = self.stats()
         n, rp, cap = s["n"], s["rank_pad"][level - 1], s["cap"][level - 1]
         U = np.zeros((rp, n))
@@ -276,9 +277,18 @@ class Hodlr:
         ranks = np.zeros(1 << level, dtype=np.int32)
         pr = np.zeros((1 << level, cap), dtype=np.int32)
         pc = np.zeros((1 << level, cap), dtype=np.int32)
-        _check(_lib.hodlr_export_level(self.handle, level, U.ctypes.data, V.ctypes.data, ranks.ctypes.data,
+        _check(_lib.hodlr_export_level(self.handle, level, U.ctypes.data, None, V.ctypes.data, ranks.ctypes.data,
                                        pr.ctypes.data, pc.ctypes.data, _stream(stream)))
         return U.T.copy(), V.T.copy(), ranks, pr, pc
+
+    def export_d(self, level: int, stream=None):
+        """d = K_node^-1 U_node of level `level` (n x rank_pad), after the factorisation."""
+        s = self.stats()
+        n, rp = s["n"], s["rank_pad"][level - 1]
+        d = np.zeros((rp, n))
+        _check(_lib.hodlr_export_level(self.handle, level, None, d.ctypes.data, None, None, None, None,
+                                       _stream(stream)))
+        return d.T.copy()
 
     def export_core(self, level: int, stream=None):
         s = self.stats()
@@ -305,8 +315,10 @@ class Hodlr:
 
 def hodlr_build(ctx: Context, A: torch.Tensor, leaf: int, tol: float, method: str = "aca", graph=None,
                 precision: str = "fp32", compress_precision: str | None = None, rank_cap: int = 0,
-                bdlr_depth: int = -1, leaf_bounds=None, symmetric: bool = True, stream=None) -> Hodlr:
-    """Compress A into HODLR form (Sec. 4.3 step 1, Sec. 5): see include/hodlr.h."""
+                bdlr_depth: int = -1, leaf_bounds=None, symmetric: bool = True, stream=None,
+                defer_factor: bool = False) -> Hodlr:
+    """Compress A into HODLR form (Sec. 4.3 step 1, Sec. 5) and, unless
+    defer_factor, factor it level by level meanwhile: see include/hodlr.h."""
     lib = load_library()
     mat = _mat(A, symmetric)
     o = _Opts()
@@ -315,6 +327,7 @@ def hodlr_build(ctx: Context, A: torch.Tensor, leaf: int, tol: float, method: st
     o.compress_precision = -1 if compress_precision is None else _PREC[compress_precision]
     o.rank_cap = rank_cap
     o.bdlr_depth = bdlr_depth
+    o.defer_factor = 1 if defer_factor else 0
     keep = []
     if leaf_bounds is not None:
         lb = np.ascontiguousarray(np.asarray(leaf_bounds, dtype=np.int64))
