@@ -129,7 +129,7 @@ typedef struct {
     double rank_mean[HODLR_MAX_LEVELS];
     int cap[HODLR_MAX_LEVELS];           /* pivot-list stride of level 1..L       */
     int cap_hit;                        /* 1 if a block stopped at rank_cap       */
-    int64_t bytes_factors;               /* device bytes of V, d, leaf and core factors */
+    int64_t bytes_factors;               /* device bytes of U, V, d, E, leaf and core factors */
     int factored;
     double ms_compress, ms_factor;       /* device time of the last build / factor */
 } hodlr_stats;

@@ -529,10 +529,19 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             cudaEventRecord(done[l], st);
         }
     }
+    // share_done[l]: level l's compaction and (unless deferred) its share of the
+    // factorisation are complete
+    std::vector<cudaEvent_t> share_done(L + 1, nullptr);
+    cudaEvent_t st_mark = nullptr;
     auto drop_events = [&]() {
+        if (st_mark) cudaEventDestroy(st_mark);
+        st_mark = nullptr;
         for (auto e : done)
             if (e) cudaEventDestroy(e);
         done.clear();
+        for (auto e : share_done)
+            if (e) cudaEventDestroy(e);
+        share_done.clear();
         cudaEventDestroy(lfork);
         cudaEventDestroy(ljoin);
         cudaEventDestroy(e0);
@@ -544,22 +553,26 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         free_temp();
         return fail(rs);
     }
-    // the leaf inverses are needed by every level's share of the factorisation
-    cudaStreamWaitEvent(st, ljoin, 0);
     // ---- level by level from the leaves: ranks -> layout -> compaction -> the
     // level's share of the factorisation, issued while the upper levels are
-    // still being compressed
+    // still being compressed.  Level l's compaction and share run on its own
+    // stream (the one its ranks are read on); the share waits for a deeper
+    // level's share only where it starts reading that level's factors, so the
+    // shares of different levels overlap.
+    cudaEventCreateWithFlags(&st_mark, cudaEventDisableTiming);
+    cudaEventRecord(st_mark, st);   // everything allocated so far is ordered before this
     const size_t pe = elem_size(h->prec);
     const bool q16 = (h->store == HODLR_BF16 || h->store == HODLR_FP16);
     const bool factor_now = o.defer_factor == 0;
     h->Ul.assign(L + 1, nullptr);
     h->Dl.assign(L + 1, nullptr);
     h->Vl.assign(L + 1, nullptr);
+    h->El.assign(L + 1, nullptr);
     h->Vql.assign(L + 1, nullptr);
-    h->Dql.assign(L + 1, nullptr);
+    h->Eql.assign(L + 1, nullptr);
     h->Sinv.assign(L, nullptr);
     h->vscale.assign(L + 1, nullptr);
-    h->dscale.assign(L + 1, nullptr);
+    h->escale.assign(L + 1, nullptr);
     if (factor_now && L > 0) {
         if (!h->fev[0]) {
             cudaEventCreate(&h->fev[0]);
@@ -567,15 +580,16 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         }
         cudaEventRecord(h->fev[0], st);
     }
-    // The factors the apply streams (d and V, or their 16-bit copies) of all
-    // levels share one region, filled from the leaves up as the ranks become
-    // known: a compact span (few pages) for the apply.  It is reserved for the
-    // rank caps; only the prefix the ranks need is ever touched.
+    // The factors the apply streams (E = d S^-1(half) and V, or their 16-bit
+    // copies) of all levels share one region, filled from the leaves up as the
+    // ranks become known: a compact span (few pages) for the apply.  It is
+    // reserved for the rank caps; only the prefix the ranks need is touched.
     const size_t se = q16 ? 2 : pe;
     size_t dv_bound = 0;
     for (int l = 1; l <= L; ++l) {
         const size_t rmax = std::max((h->lv[l].cap + 7) / 8 * 8, 8);   // the padded rank's bound
-        dv_bound += 2 * (((size_t)h->ldn * rmax * se + 255) & ~size_t(255));
+        dv_bound += (((size_t)h->ldn * 2 * rmax * se + 255) & ~size_t(255)) +
+                    (((size_t)h->ldn * rmax * se + 255) & ~size_t(255));
     }
     char *dvbase = L > 0 ? (char *)own(h, dv_bound, st) : nullptr;
     if (L > 0 && !dvbase) {
@@ -586,6 +600,7 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     }
     size_t dv_used = 0;
     std::vector<int32_t> hcap;
+    int hstat = 0, aca_status = 0;   // the status word after each level's compression
     for (int l = L; l >= 1; --l) {
         Level &lv = h->lv[l];
         lv.ranks.resize(lv.nnodes);
@@ -593,6 +608,7 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         // (pageable destination: the copies return once level l is compressed)
         if (cudaMemcpyAsync(lv.ranks.data(), h->d_ranks[l], lv.nnodes * sizeof(int32_t), cudaMemcpyDeviceToHost,
                             rstream[l]) != cudaSuccess ||
+            cudaMemcpyAsync(&hstat, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, rstream[l]) != cudaSuccess ||
             cudaMemcpyAsync(hcap.data(), caphit + ((1 << l) - 2), lv.nnodes * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, rstream[l]) != cudaSuccess ||
             cudaStreamSynchronize(rstream[l]) != cudaSuccess) {
@@ -602,6 +618,7 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             return fail(HODLR_CUDA_ERROR);
         }
         for (auto v : hcap) h->cap_hit |= v;
+        aca_status |= hstat;
         int mx = 0;
         double sum = 0;
         for (int r : lv.ranks) {
@@ -611,26 +628,26 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         lv.rank_max = mx;
         lv.rank_mean = sum / lv.nnodes;
         lv.rp = mx == 0 ? 0 : (mx + 7) / 8 * 8;
-        // storage of level l: the streamed d and V in the shared region, and
-        // an arena with U, the cores of level l - 1 and (16-bit storage) the
-        // FP32 d and V with the FP16 scales
+        // storage of level l: the streamed E and V in the shared region, and
+        // an arena with U, d, the cores of level l - 1 and (16-bit storage) the
+        // FP32 E and V with the FP16 scales
         const size_t colb = (size_t)h->ldn * std::max(lv.rp, 1);
-        const size_t sb = ((colb * se) + 255) & ~size_t(255);
-        char *dv_d = dvbase + dv_used, *dv_v = dvbase + dv_used + sb;
-        dv_used += 2 * sb;
+        const size_t sbe = ((2 * colb * se) + 255) & ~size_t(255), sbv = ((colb * se) + 255) & ~size_t(255);
+        char *dv_e = dvbase + dv_used, *dv_v = dvbase + dv_used + sbe;
+        dv_used += sbe + sbv;
         const int64_t s2 = 2 * (int64_t)lv.rp;
         Arena la;
-        const size_t oU = la.take(colb * pe);
-        size_t oD = 0, oV = 0, ovs = 0, ods = 0;
+        const size_t oU = la.take(colb * pe), oD = la.take(colb * pe);
+        size_t oE = 0, oV = 0, ovs = 0, oes = 0;
         if (q16) {
-            oD = la.take(colb * pe);
+            oE = la.take(2 * colb * pe);
             oV = la.take(colb * pe);
         }
         const size_t oS = la.take((size_t)(1 << (l - 1)) * std::max<int64_t>(s2 * s2, 1) * pe);
         if (h->store == HODLR_FP16) {
             const size_t scb = (size_t)lv.nnodes * std::max(lv.rp, 1) * sizeof(float);
             ovs = la.take(scb);
-            ods = la.take(scb);
+            oes = la.take(2 * scb);
         }
         char *lb = (char *)own(h, la.bytes, st);
         if (!lb || dv_used > dv_bound) {
@@ -640,27 +657,30 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             return fail(lb ? HODLR_RANGE : HODLR_OUT_OF_MEMORY);
         }
         h->Ul[l] = lb + oU;
+        h->Dl[l] = lb + oD;
         h->Sinv[l - 1] = lb + oS;
         if (q16) {
-            h->Dl[l] = lb + oD;
+            h->El[l] = lb + oE;
             h->Vl[l] = lb + oV;
-            h->Dql[l] = dv_d;
+            h->Eql[l] = dv_e;
             h->Vql[l] = dv_v;
             if (h->store == HODLR_FP16) {
                 h->vscale[l] = (float *)(lb + ovs);
-                h->dscale[l] = (float *)(lb + ods);
+                h->escale[l] = (float *)(lb + oes);
             }
         } else {
-            h->Dl[l] = dv_d;
+            h->El[l] = dv_e;
             h->Vl[l] = dv_v;
         }
+        const cudaStream_t sl = c->side[(l - 1) % HODLR_SIDE_STREAMS];
+        cudaStreamWaitEvent(sl, st_mark, 0);
+        cudaStreamWaitEvent(sl, ljoin, 0);        // the leaf inverses (read by the share)
+        cudaStreamWaitEvent(sl, done[l - 1], 0);  // level l compressed into the staging
         if (lv.rp > 0) {
             // compaction writes the ranks' columns only: zero U and V
-            cudaMemsetAsync(h->Ul[l], 0, colb * pe, st);
-            cudaMemsetAsync(h->Vl[l], 0, colb * pe, st);
+            cudaMemsetAsync(h->Ul[l], 0, colb * pe, sl);
+            cudaMemsetAsync(h->Vl[l], 0, colb * pe, sl);
         }
-        // compaction of level l from the staging (written by its compression)
-        cudaStreamWaitEvent(st, done[l - 1], 0);
         int64_t node_max = 0;
         for (int i = 0; i < lv.nnodes; ++i) {
             int64_t r0, m;
@@ -672,32 +692,36 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         if (lv.rp > 0) {
             if (cprec == HODLR_FP64 && h->prec == HODLR_FP64) {
                 s3 = launch_compact<double, double>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
-                                                    lv.rp, node_max, st);
+                                                    lv.rp, node_max, sl);
                 if (s3 == HODLR_OK)
                     s3 = launch_compact_v<double, double>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
-                                                          h->d_ranks[l], lv.rp, node_max, st);
+                                                          h->d_ranks[l], lv.rp, node_max, sl);
             } else if (cprec == HODLR_FP64) {
                 s3 = launch_compact<double, float>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
-                                                   lv.rp, node_max, st);
+                                                   lv.rp, node_max, sl);
                 if (s3 == HODLR_OK)
                     s3 = launch_compact_v<double, float>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
-                                                         h->d_ranks[l], lv.rp, node_max, st);
+                                                         h->d_ranks[l], lv.rp, node_max, sl);
             } else if (h->prec == HODLR_FP64) {
                 s3 = launch_compact<float, double>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
-                                                   lv.rp, node_max, st);
+                                                   lv.rp, node_max, sl);
                 if (s3 == HODLR_OK)
                     s3 = launch_compact_v<float, double>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
-                                                         h->d_ranks[l], lv.rp, node_max, st);
+                                                         h->d_ranks[l], lv.rp, node_max, sl);
             } else {
                 s3 = launch_compact<float, float>(Ust[l], h->ldn, Uc, h->ldn, h->d_bounds, L, l, h->d_ranks[l],
-                                                  lv.rp, node_max, st);
+                                                  lv.rp, node_max, sl);
                 if (s3 == HODLR_OK)
                     s3 = launch_compact_v<float, float>(Vst[l], h->ldn, Vc, h->ldn, h->d_bounds, L, l,
-                                                        h->d_ranks[l], lv.rp, node_max, st);
+                                                        h->d_ranks[l], lv.rp, node_max, sl);
             }
         }
-        if (s3 == HODLR_OK) s3 = plan_level(h, l, st);
-        if (s3 == HODLR_OK && factor_now) s3 = run_level(h, l, st);
+        if (s3 == HODLR_OK) s3 = plan_level(h, l, sl);
+        if (s3 == HODLR_OK && factor_now) s3 = run_level(h, l, sl, share_done.data());
+        if (s3 == HODLR_OK) {
+            cudaEventCreateWithFlags(&share_done[l], cudaEventDisableTiming);
+            cudaEventRecord(share_done[l], sl);
+        }
         if (s3 != HODLR_OK) {
             cudaDeviceSynchronize();
             drop_events();
@@ -705,6 +729,10 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             return fail(s3);
         }
     }
+    // join on the caller's stream: the leaf inverses (a tree of one leaf has no
+    // level to wait for them) and every level's share
+    cudaStreamWaitEvent(st, ljoin, 0);
+    for (int l = 1; l <= L; ++l) cudaStreamWaitEvent(st, share_done[l], 0);
     if (factor_now) {
         if (L > 0) cudaEventRecord(h->fev[1], st);
         h->factored = true;
@@ -722,13 +750,13 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         if (e && cudaEventElapsedTime(&t, e0, e) == cudaSuccess) ms = std::max(ms, t);
     }
     h->ms_compress = ms;
-    // non-finite entries met by the compression (every level is complete here;
-    // a factorisation fault is reported by the next synchronising call)
+    // non-finite entries met by the compression (read with each level's ranks,
+    // after its compression; a factorisation fault is reported by the next
+    // synchronising call)
     {
-        int w = 0;
-        cudaStream_t ss = rstream[L > 0 ? 1 : 0];
-        if (cudaMemcpyAsync(&w, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, ss) != cudaSuccess ||
-            cudaStreamSynchronize(ss) != cudaSuccess) {
+        int w = aca_status;
+        if (L == 0 && (cudaMemcpyAsync(&w, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                       cudaStreamSynchronize(st) != cudaSuccess)) {
             cudaDeviceSynchronize();
             drop_events();
             free_temp();
@@ -848,7 +876,8 @@ hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {
     }
     o->cap_hit = h->cap_hit;
     const size_t pe = elem_size(h->prec);
-    int64_t b = (int64_t)2 * h->ldn * h->Wtot * pe + ((int64_t)1 << h->L) * h->bmax * h->bmax * pe;
+    // U, d, V (ldn x rp each) and E (ldn x 2 rp) per level, the leaf inverses, the cores
+    int64_t b = (int64_t)5 * h->ldn * h->Wtot * pe + ((int64_t)1 << h->L) * h->bmax * h->bmax * pe;
     for (int l = 0; l < h->L; ++l) b += ((int64_t)1 << l) * 4 * (int64_t)h->lv[l + 1].rp * h->lv[l + 1].rp * pe;
     o->bytes_factors = b;
     o->factored = h->factored ? 1 : 0;

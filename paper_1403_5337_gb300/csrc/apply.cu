@@ -2,8 +2,11 @@
 //   leaves:  x_leaf <- K_leaf^-1 x_leaf
 //   for c = L .. 1 (children level), every parent node (alpha, beta):
 //       w = [V_ba^T x_alpha ; V_ab^T x_beta]         (segmented reductions)
-//       y = S^-1 w                                   (one GEMV per node)
-//       x_alpha -= d_alpha y2,  x_beta -= d_beta y1  (rank-rp updates)
+//       y = S^-1 w,  x_alpha -= d_alpha y2,  x_beta -= d_beta y1
+// The last line is applied as x_alpha -= E_alpha w, x_beta -= E_beta w with
+// E_alpha = d_alpha S^-1(rows rp..2rp-1, :) and E_beta = d_beta S^-1(rows
+// 0..rp-1, :), formed once by the factorisation: the same product, associated
+// differently, so no tile has to form y from the node's core.
 // X is FP64 in and out; the arithmetic runs in the factor's precision T on a
 // private copy of X.
 //
@@ -12,9 +15,9 @@
 // is the reduction w of each node: every tile adds its partial V^T x to w of
 // its node and then bumps the node's arrival counter; a tile of that node
 // waits for the counter to reach the node's tile count (a bounded spin: all
-// CTAs are co-resident), forms its own half of y = S^-1 w, updates its rows and
-// immediately adds its partial of the next level's w.  There is no grid-wide
-// barrier: deep levels wait only for the few tiles of their own node.
+// CTAs are co-resident), updates its rows with E w and immediately adds its
+// partial of the next level's w.  There is no grid-wide barrier: deep levels
+// wait only for the few tiles of their own node.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -46,15 +49,14 @@ struct FusedArgs {
     const T *Kinv;
     int bmax, L, s, rpmax;
     int64_t n, ldn, ldx, ldxin;
-    // per level c: V and d (ldn x rp(c)) at Vb + voff[c], Db + doff[c]; one
-    // base and element offsets (a dynamically indexed array of pointers in
-    // the kernel arguments measured ~15% slower here)
-    const S *Vb, *Db;
-    int64_t voff[HODLR_MAX_LEVELS], doff[HODLR_MAX_LEVELS];
+    // per level c: V (ldn x rp(c)) and E (ldn x 2 rp(c)) at Vb + voff[c],
+    // Eb + eoff[c]; one base and element offsets (a dynamically indexed array
+    // of pointers in the kernel arguments measured ~15% slower here)
+    const S *Vb, *Eb;
+    int64_t voff[HODLR_MAX_LEVELS], eoff[HODLR_MAX_LEVELS];
     int rp[HODLR_MAX_LEVELS];
-    const T *Sinv[HODLR_MAX_LEVELS];       // by parent level l = c - 1
     const float *vscale[HODLR_MAX_LEVELS];
-    const float *dscale[HODLR_MAX_LEVELS];
+    const float *escale[HODLR_MAX_LEVELS];
     T *w[HODLR_MAX_LEVELS];                // w(c): [parent node][2 rp(c)][s], zeroed before the launch
     unsigned *cnt[HODLR_MAX_LEVELS];       // arrivals per parent node of level c, zeroed before the launch
     T *xt;
@@ -173,8 +175,8 @@ __device__ __forceinline__ void stream_dot(const E *col, int64_t ldm, const T *y
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Pull everything this CTA's tiles will read into L2 up front (the leaf inverse
-// rows, every level's d and V rows of the tiles, a 1/gridDim share of the S^-1
-// cores), so that the dependent phases later hit L2 instead of HBM.
+// rows, every level's E and V rows of the tiles), so that the dependent phases
+// later hit L2 instead of HBM.
 template <typename T, typename S>
 __device__ void prefetch_tiles(const FusedArgs<T, S> &a) {
     constexpr int LINE = 128;
@@ -190,20 +192,14 @@ __device__ void prefetch_tiles(const FusedArgs<T, S> &a) {
         const int lines = (nrows + per_line - 1) / per_line;   // every line starts inside the tile
         for (int c = 1; c <= a.L; ++c) {
             const int rp = a.rp[c];
-            for (int e = threadIdx.x; e < 2 * rp * lines; e += AP_THREADS) {
-                const int col = e / (2 * lines), r = e % (2 * lines);
-                const S *base = (r < lines ? a.Db + a.doff[c] : a.Vb + a.voff[c]) + (int64_t)col * a.ldn + row0;
-                prefetch_l2(base + (int64_t)(r % lines) * per_line);
+            // columns 0 .. 2 rp - 1: E, 2 rp .. 3 rp - 1: V
+            for (int e = threadIdx.x; e < 3 * rp * lines; e += AP_THREADS) {
+                const int col = e / lines, r = e % lines;
+                const S *base = col < 2 * rp ? a.Eb + a.eoff[c] + (int64_t)col * a.ldn
+                                             : a.Vb + a.voff[c] + (int64_t)(col - 2 * rp) * a.ldn;
+                prefetch_l2(base + row0 + (int64_t)r * per_line);
             }
         }
-    }
-    for (int c = 1; c <= a.L; ++c) {
-        const int64_t s2 = 2 * (int64_t)a.rp[c];
-        const int64_t bytes = (int64_t)(1 << (c - 1)) * s2 * s2 * sizeof(T);
-        const char *p = reinterpret_cast<const char *>(a.Sinv[c - 1]);
-        for (int64_t o = ((int64_t)blockIdx.x * AP_THREADS + threadIdx.x) * LINE; o < bytes;
-             o += (int64_t)gridDim.x * AP_THREADS * LINE)
-            prefetch_l2(p + o);
     }
 }
 
@@ -213,8 +209,7 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
     prefetch_tiles(a);
     extern __shared__ __align__(16) unsigned char smem[];
     T *part = reinterpret_cast<T *>(smem);                          // 8 warps x 32 rows x RC
-    T *ys = part + (AP_THREADS / 32) * TR * RC;                     // this tile's half of y: rp x RC
-    T *ws = ys + (size_t)a.rpmax * RC;                              // w of the node: 2 rp x RC; the leaf's x
+    T *ws = part + (AP_THREADS / 32) * TR * RC;                     // w of the node: 2 rp x RC; the leaf's x
     T *sv = ws + (size_t)std::max(2 * a.rpmax, a.bmax) * RC;        // V tile: rp x (32 + 1)
     T *xs = sv + (size_t)a.rpmax * (TR + 1);                        // x tile: RC x 32
     const int L = a.L;
@@ -256,8 +251,8 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
         }
         if (L >= 1) arrive(a.cnt[L] + (leaf >> 1));
     }
-    // ---- levels c = L .. 1: y = S^-1 w for the node, x -= d y on the tile's rows,
-    // then the next level's V^T x (or the store)
+    // ---- levels c = L .. 1: x -= E w(node) on the tile's rows (E = d S^-1(half)
+    // formed by the factorisation), then the next level's V^T x (or the store)
     for (int c = L; c >= 1; --c) {
         const int rp = a.rp[c];
         const int s2 = 2 * rp;
@@ -268,50 +263,29 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
             const int64_t row0 = tl.y;
             const int node = leaf >> shift;
             const int child = leaf >> (L - c);
-            const int half = (child & 1) ? 0 : rp;   // the first child takes y2
             const unsigned target =
                 (unsigned)(a.tile_first[(node + 1) << shift] - a.tile_first[node << shift]);
             wait_node(a.cnt[c] + node, target, a.status);
-            const T *Sn = a.Sinv[c - 1] + (size_t)node * s2 * s2;
             const T *wn = a.w[c] + (size_t)node * s2 * a.s;
-            const S *Dc = a.Db + a.doff[c];
-            const float *ds = a.dscale[c];
+            const S *Ec = a.Eb + a.eoff[c];
+            const float *es = a.escale[c];
             for (int r0 = 0; r0 < a.s; r0 += RC) {
                 const int rr = min(RC, a.s - r0);
                 if (rp > 0) {
-                    // w of the node (complete: read past L1)
+                    // w of the node (complete: read past L1), times E's FP16 column factors
                     for (int e = threadIdx.x; e < s2 * RC; e += AP_THREADS) {
                         const int k = e / RC, q = e % RC;
-                        ws[k * RC + q] = (q < rr) ? __ldcg(wn + (size_t)k * a.s + r0 + q) : T(0);
+                        T v = (q < rr) ? __ldcg(wn + (size_t)k * a.s + r0 + q) : T(0);
+                        if (es) v *= (T)es[(size_t)child * s2 + k];
+                        ws[k * RC + q] = v;
                     }
                     __syncthreads();
-                    // ys = S^-1(half rows, :) w: lanes over rows, warps split the 2 rp columns
-                    const int kper = (s2 + 7) / 8, kb = warp * kper, ke = min(s2, kb + kper);
-                    for (int i0 = 0; i0 < rp; i0 += TR) {
-                        const int i = i0 + lane;
-                        T acc[RC];
-#pragma unroll
-                        for (int q = 0; q < RC; ++q) acc[q] = T(0);
-                        if (i < rp) stream_dot<T, T, RC>(Sn + half + i, s2, ws, kb, ke, acc);
-#pragma unroll
-                        for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
-                        __syncthreads();
-                        for (int e = threadIdx.x; e < TR * RC; e += AP_THREADS) {
-                            const int li = e % TR, q = e / TR;
-                            const int ii = i0 + li;
-                            if (ii < rp) {
-                                const T yv = warp_parts_sum<T, RC>(part, li, q);
-                                ys[ii * RC + q] = ds ? yv * (T)ds[(size_t)child * rp + ii] : yv;
-                            }
-                        }
-                        __syncthreads();
-                    }
-                    // x -= d y on the tile's rows: lanes over rows, warps split the rp columns
-                    const int uper = (rp + 7) / 8, ub = warp * uper, ue = min(rp, ub + uper);
+                    // x -= E w on the tile's rows: lanes over rows, warps split the 2 rp columns
+                    const int uper = (s2 + 7) / 8, ub = warp * uper, ue = min(s2, ub + uper);
                     T acc[RC];
 #pragma unroll
                     for (int q = 0; q < RC; ++q) acc[q] = T(0);
-                    if (lane < nrows) stream_dot<T, S, RC>(Dc + row0 + lane, a.ldn, ys, ub, ue, acc);
+                    if (lane < nrows) stream_dot<T, S, RC>(Ec + row0 + lane, a.ldn, ws, ub, ue, acc);
 #pragma unroll
                     for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
                     __syncthreads();
@@ -344,8 +318,8 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream
 
 template <typename T, typename S>
 hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st,
-                         const std::vector<void *> &V, const std::vector<void *> &Dm, const float *const *vsc,
-                         const float *const *dsc) {
+                         const std::vector<void *> &V, const std::vector<void *> &E, const float *const *vsc,
+                         const float *const *esc) {
     hodlr_t *hm = const_cast<hodlr_t *>(h);
     HODLR_TRY(solve_prepare(h, s, st));
     const int L = h->L;
@@ -366,14 +340,13 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
     char *z0 = wp + al((size_t)h->ldn * s * sizeof(T));
     char *zp = z0;
     a.Vb = L >= 1 ? reinterpret_cast<const S *>(V[1]) : nullptr;
-    a.Db = L >= 1 ? reinterpret_cast<const S *>(Dm[1]) : nullptr;
+    a.Eb = L >= 1 ? reinterpret_cast<const S *>(E[1]) : nullptr;
     for (int c = 1; c <= L; ++c) {
         a.rp[c] = h->lv[c].rp;
         a.voff[c] = reinterpret_cast<const S *>(V[c]) - a.Vb;
-        a.doff[c] = reinterpret_cast<const S *>(Dm[c]) - a.Db;
-        a.Sinv[c - 1] = reinterpret_cast<const T *>(h->Sinv[c - 1]);
+        a.eoff[c] = reinterpret_cast<const S *>(E[c]) - a.Eb;
         a.vscale[c] = vsc ? vsc[c] : nullptr;
-        a.dscale[c] = dsc ? dsc[c] : nullptr;
+        a.escale[c] = esc ? esc[c] : nullptr;
         a.w[c] = reinterpret_cast<T *>(zp);
         zp += al((size_t)(1 << c) * h->lv[c].rp * s * sizeof(T));
     }
@@ -409,8 +382,8 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
 
 template <typename T, typename S, int RC>
 hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream_t st) {
-    const size_t sm = ((size_t)(AP_THREADS / 32) * TR * RC + (size_t)a.rpmax * RC +
-                       (size_t)std::max(2 * a.rpmax, a.bmax) * RC + (size_t)a.rpmax * (TR + 1) + (size_t)TR * RC) *
+    const size_t sm = ((size_t)(AP_THREADS / 32) * TR * RC + (size_t)std::max(2 * a.rpmax, a.bmax) * RC +
+                       (size_t)a.rpmax * (TR + 1) + (size_t)TR * RC) *
                       sizeof(T);
     HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_fused_kernel<T, S, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sm));
@@ -439,12 +412,12 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream
 }  // namespace
 
 hodlr_status solve_impl(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st) {
-    if (h->prec == HODLR_FP64) return solve_fused<double, double>(h, s, X, ldx, st, h->Vl, h->Dl, nullptr, nullptr);
+    if (h->prec == HODLR_FP64) return solve_fused<double, double>(h, s, X, ldx, st, h->Vl, h->El, nullptr, nullptr);
     if (h->store == HODLR_BF16)
-        return solve_fused<float, __nv_bfloat16>(h, s, X, ldx, st, h->Vql, h->Dql, nullptr, nullptr);
+        return solve_fused<float, __nv_bfloat16>(h, s, X, ldx, st, h->Vql, h->Eql, nullptr, nullptr);
     if (h->store == HODLR_FP16)
-        return solve_fused<float, __half>(h, s, X, ldx, st, h->Vql, h->Dql, h->vscale.data(), h->dscale.data());
-    return solve_fused<float, float>(h, s, X, ldx, st, h->Vl, h->Dl, nullptr, nullptr);
+        return solve_fused<float, __half>(h, s, X, ldx, st, h->Vql, h->Eql, h->vscale.data(), h->escale.data());
+    return solve_fused<float, float>(h, s, X, ldx, st, h->Vl, h->El, nullptr, nullptr);
 }
 
 // Allocate the apply's workspace for s right-hand sides ahead of time (the

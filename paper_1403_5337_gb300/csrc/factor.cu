@@ -536,6 +536,227 @@ hodlr_status launch_gj_reg(hodlr_ctx *c, const GJDesc<T> *dd, int count, cudaStr
     return HODLR_OK;
 }
 
+// Blocked form of the register Gauss-Jordan above (FP32, b = 65 .. 160):
+// the pivots are taken in panels of NB columns.  Warp 0 sweeps a panel's
+// columns on all rows by itself (the same implicit pivoting and tie rule: the
+// largest |a(i, k)| over unused rows, lowest row first, found with two warp
+// reductions on the bit patterns of |a|), then all warps apply the panel to
+// the other columns at once.  With R the panel's pivot rows, C its columns and
+// P the swept panel (P(R, :) = B^-1, P(i, :) = -a(i, C) B^-1 otherwise, B =
+// a(R, C)), sweeping the panel's pivots one after another is, on a column j
+// outside C,
+//   a(i, j) <- [i not in R] a(i, j) + sum_t P(i, t) a_old(r_t, j),
+// r_t the pivot row of the panel's column t.  Three CTA barriers per panel
+// instead of two per column.
+template <typename T, int MR, int MC, int NB>
+__global__ void __launch_bounds__(GJR_THREADS, 1) gj_blocked_kernel(const GJDesc<T> *__restrict__ descs,
+                                                                   int *status) {
+    static_assert(sizeof(T) == 4, "FP32 only (pivot keys are 32-bit patterns)");
+    static_assert(32 % NB == 0 && NB % 4 == 0, "panels of 4k columns within a 32-column slot");
+    constexpr int BR = MR * GJR_TY;           // row capacity
+    constexpr int MW = (BR + 31) / 32;        // panel rows per lane of warp 0
+    const GJDesc<T> g = descs[blockIdx.x];
+    const int b = g.b;
+    if (b <= 0) return;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    __shared__ __align__(16) T P[2][BR][NB];  // the panel, by panel parity
+    __shared__ T Rold[NB][MC * GJR_TX];       // the panel's pivot rows before its sweeps
+    __shared__ int piv[NB];
+    __shared__ int prow[BR];                  // pivot row of step k
+    __shared__ int krow[BR];                  // step at which row i was the pivot
+    __shared__ unsigned char rused[BR];
+    __shared__ int s_fail;
+    __shared__ T *s_out;                      // the output's address and stride, parked here
+    __shared__ int64_t s_ldo;                 // for the final store (registers are the limit)
+    T a[MR][MC];
+#pragma unroll
+    for (int p = 0; p < MR; ++p) {
+        const int i = ty + GJR_TY * p;
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int j = tx + GJR_TX * q;
+            T v = T(0);
+            if (i < b && j < b)
+                v = g.srcA ? dev::from_double<T>(g.srcA[(int64_t)i * g.lda + j]) : g.srcM[i + (int64_t)j * g.ldm];
+            a[p][q] = v;
+        }
+    }
+    for (int i = tid; i < BR; i += GJR_THREADS) rused[i] = i >= b ? 1 : 0;
+    for (int e = tid; e < 2 * BR * NB; e += GJR_THREADS) (&P[0][0][0])[e] = T(0);
+    if (tid == 0) {
+        s_fail = 0;
+        s_out = g.out;
+        s_ldo = g.ldo;
+    }
+    __syncthreads();
+    bool fail = false;
+    // one copy of the panel's code (the slot kq of the panel's columns is a
+    // runtime value; unrolling over it multiplied the code beyond the
+    // instruction cache)
+    for (int k0 = 0, panel = 0; k0 < b && !fail; k0 += NB, ++panel) {
+        const int kq = k0 / GJR_TX, kx0 = k0 % GJR_TX;
+        const int nbp = min(NB, b - k0);
+        const int par = panel & 1;
+        const bool inpanel = tx >= kx0 && tx < kx0 + nbp;
+        // 1. the owners of the panel's columns post them
+        if (inpanel) {
+#pragma unroll
+            for (int p = 0; p < MR; ++p) {
+                T v = a[p][0];
+#pragma unroll
+                for (int q = 1; q < MC; ++q)
+                    if (q == kq) v = a[p][q];
+                P[par][ty + GJR_TY * p][tx - kx0] = v;
+            }
+        }
+        __syncthreads();
+        // 2. warp 0 sweeps the panel's pivots on the panel
+        if (ty == 0) {
+            T v[MW][NB];
+            unsigned ub = 0;   // bit m: row tx + 32 m is not a candidate
+#pragma unroll
+            for (int m = 0; m < MW; ++m) {
+                const int i = tx + 32 * m;
+                if (i < BR) {
+                    if (rused[i]) ub |= 1u << m;
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) v[m][t] = P[par][i][t];
+                } else {
+                    ub |= 1u << m;
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) v[m][t] = T(0);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                if (t >= nbp) break;
+                unsigned best = 0u;
+                int bi = INT_MAX;
+#pragma unroll
+                for (int m = 0; m < MW; ++m) {
+                    const T av = fabsf(v[m][t]);
+                    const unsigned key = (av > T(0)) ? __float_as_uint(av) : 0u;   // NaN: no candidate
+                    if (!((ub >> m) & 1u) && key > best) {
+                        best = key;
+                        bi = tx + 32 * m;
+                    }
+                }
+                const unsigned wmax = __reduce_max_sync(0xffffffffu, best);
+                if (wmax == 0u) {   // uniform: no usable pivot in this column
+                    if (tx == 0) s_fail = 1;
+                    break;
+                }
+                const int pr = (int)__reduce_min_sync(0xffffffffu, best == wmax ? (unsigned)bi : 0xffffffffu);
+                const int o = pr & 31, mo = pr >> 5;
+                T rr[NB];
+#pragma unroll
+                for (int m = 0; m < MW; ++m)
+                    if (m == mo) {
+#pragma unroll
+                        for (int t2 = 0; t2 < NB; ++t2) rr[t2] = __shfl_sync(0xffffffffu, v[m][t2], o);
+                    }
+                const T pv = rr[t];
+                const T d = T(1) / pv;
+                rr[t] = pv + T(1);
+#pragma unroll
+                for (int m = 0; m < MW; ++m) {
+                    const bool isp = (tx + 32 * m) == pr;
+                    const T f = (isp ? pv - T(1) : v[m][t]) * d;
+#pragma unroll
+                    for (int t2 = 0; t2 < NB; ++t2) v[m][t2] = fmaf(-f, rr[t2], v[m][t2]);
+                    if (isp) ub |= 1u << m;
+                }
+                if (tx == 0) {
+                    piv[t] = pr;
+                    prow[k0 + t] = pr;
+                    krow[pr] = k0 + t;
+                    rused[pr] = 1;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < MW; ++m) {
+                const int i = tx + 32 * m;
+                if (i < BR) {
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) P[par][i][t] = (t < nbp) ? v[m][t] : T(0);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            fail = true;
+            break;
+        }
+        // 3. the owners of the panel's pivot rows post them as they were before the panel
+        unsigned cur = 0;   // bit p: row ty + 8 p is one of this panel's pivot rows
+        for (int t = 0; t < nbp; ++t) {
+            const int r = piv[t];
+            if ((r & (GJR_TY - 1)) == ty) {
+                const int pp = r / GJR_TY;
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == pp) {
+                        cur |= 1u << p;
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) Rold[t][tx + GJR_TX * q] = a[p][q];
+                    }
+            }
+        }
+        __syncthreads();
+        // 4. the panel's update of every other column; the panel's columns take
+        // P.  Column slots outermost with their NB pivot-row entries in
+        // registers and the panel rows read as 16-byte vectors (holding all
+        // slots' entries at once measured 2.5x slower at this register budget).
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            T rk[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) rk[t] = (t < nbp) ? Rold[t][tx + GJR_TX * q] : T(0);
+            const bool pcol = (q == kq) && inpanel;
+#pragma unroll
+            for (int p = 0; p < MR; ++p) {
+                const int i = ty + GJR_TY * p;
+                T pn[NB];
+#pragma unroll
+                for (int t = 0; t < NB; t += 4) {
+                    const float4 w = *reinterpret_cast<const float4 *>(&P[par][i][t]);
+                    pn[t] = w.x;
+                    pn[t + 1] = w.y;
+                    pn[t + 2] = w.z;
+                    pn[t + 3] = w.w;
+                }
+                T acc = ((cur >> p) & 1u) ? T(0) : a[p][q];
+#pragma unroll
+                for (int t = 0; t < NB; ++t) acc = fmaf(pn[t], rk[t], acc);
+                a[p][q] = pcol ? P[par][i][tx - kx0] : acc;
+            }
+        }
+    }
+    if (fail) {
+        if (tid == 0) atomicOr(status, ST_SINGULAR);
+        return;
+    }
+    __syncthreads();
+    // M^-1(krow[i], prow[j]) = a(i, j)
+    T *out = s_out;
+    const int64_t ldo = s_ldo;
+#pragma unroll
+    for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int i = ty + GJR_TY * p, j = tx + GJR_TX * q;
+            if (i < b && j < b) out[krow[i] + (int64_t)prow[j] * ldo] = a[p][q];
+        }
+}
+
+template <typename T, int MR, int MC, int NB = 4>
+hodlr_status launch_gj_blocked(hodlr_ctx *c, const GJDesc<T> *dd, int count, cudaStream_t s) {
+    gj_blocked_kernel<T, MR, MC, NB><<<count, GJR_THREADS, 0, s>>>(dd, c->d_status);
+    note_launch();
+    HODLR_TRY_CUDA(cudaGetLastError());
+    return HODLR_OK;
+}
+
 template <typename T>
 size_t gjs_smem(int b) {
     return ((size_t)(b + 1) * b + 2 * (size_t)b) * sizeof(T) + (size_t)b * sizeof(int) + 16;
@@ -598,12 +819,15 @@ template <typename T>
 hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, cudaStream_t s) {
     if (bmax <= 32) return launch_gj_reg<T, 4, 1>(c, dd, count, s);
     if (bmax <= 64) return launch_gj_reg<T, 8, 2>(c, dd, count, s);
-    if (bmax <= 96) return launch_gj_reg<T, 12, 3>(c, dd, count, s);
-    if (bmax <= 128) return launch_gj_reg<T, 16, 4>(c, dd, count, s);
-    if constexpr (sizeof(T) == 4) {   // FP64 tiles beyond 128 would spill registers
-        if (bmax <= 144) return launch_gj_reg<T, 18, 5>(c, dd, count, s);
-        if (bmax <= 160) return launch_gj_reg<T, 20, 5>(c, dd, count, s);
-        if (bmax <= 192) return launch_gj_reg<T, 24, 6>(c, dd, count, s);
+    if constexpr (sizeof(T) == 4) {   // blocked from 65 to 160; FP64 tiles beyond 128 would spill registers
+        if (bmax <= 96) return launch_gj_blocked<T, 12, 3>(c, dd, count, s);
+        if (bmax <= 128) return launch_gj_blocked<T, 16, 4>(c, dd, count, s);
+        if (bmax <= 144) return launch_gj_blocked<T, 18, 5>(c, dd, count, s);
+        if (bmax <= 160) return launch_gj_blocked<T, 20, 5>(c, dd, count, s);
+        if (bmax <= 192) return launch_gj_reg<T, 24, 6>(c, dd, count, s);   // the blocked tile would spill
+    } else {
+        if (bmax <= 96) return launch_gj_reg<T, 12, 3>(c, dd, count, s);
+        if (bmax <= 128) return launch_gj_reg<T, 16, 4>(c, dd, count, s);
     }
     if (gjs_smem<T>(bmax) <= GJS_SMEM_MAX) {
         const size_t sm = gjs_smem<T>(bmax);
@@ -631,6 +855,9 @@ hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, c
 // uploaded in a single copy.  Replaying needs no host-device transfer.
 struct LevelPlan {
     std::vector<std::function<hodlr_status(cudaStream_t)>> ops;
+    // (op index, level l): ops from that index on read level l's share (its d,
+    // V and the cores of level l - 1); a replay on its own stream waits there
+    std::vector<std::pair<size_t, int>> waits;
     std::vector<char> blob;
     char *dblob = nullptr;
     size_t dbytes = 0;
@@ -717,6 +944,7 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
     T *Uc = reinterpret_cast<T *>(h->Ul[c]);
     T *Dc = reinterpret_cast<T *>(h->Dl[c]);
     T *Vc = reinterpret_cast<T *>(h->Vl[c]);
+    T *Ec = reinterpret_cast<T *>(h->El[c]);
     const T *Kinv = reinterpret_cast<const T *>(h->leafinv);
     // ---- workspace: per deeper level l the children's V^T d_c and its S^-1
     // image, then the cores of level c - 1 (one allocation)
@@ -745,6 +973,7 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
     std::vector<FillDesc<T>> fills;
     if (rc > 0) {
         fills.push_back(FillDesc<T>{Dc, 0, ldn * rc, 1, INT_MAX, 1, 0});
+        fills.push_back(FillDesc<T>{Ec, 0, ldn * 2 * rc, 1, INT_MAX, 1, 0});
         for (int l = L - 1; l >= c; --l) {
             const int64_t e = (int64_t)(1 << l) * 2 * h->lv[l + 1].rp * rc;
             if (e == 0) continue;
@@ -780,6 +1009,7 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
             const T *Vn = reinterpret_cast<const T *>(h->Vl[l + 1]);
             const T *Dn = reinterpret_cast<const T *>(h->Dl[l + 1]);
             const T *Sn = reinterpret_cast<const T *>(h->Sinv[l]);
+            Pl->waits.push_back({Pl->ops.size(), l + 1});
             T *Y = reinterpret_cast<T *>(wb + oY[l]);
             T *Yv = reinterpret_cast<T *>(wb + oYv[l]);
             std::vector<GemmDesc<T>> gy(2 * nn), gv(nn), gu(2 * nn);
@@ -846,33 +1076,47 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
             rec.gemm(g12, 0, T(-1));
             rec.gemm(g3, 0, T(-1));
         }
+        // ---- E = d_child S^-1(half, :) on every child's rows: the apply's
+        // x_child -= d_child y_half with y = S^-1 w becomes x_child -= E w (the
+        // first child takes the second half y2, the second child y1)
+        {
+            std::vector<GemmDesc<T>> gd(2 * nn0);
+            for (int ch = 0; ch < 2 * nn0; ++ch) {
+                int64_t r0, m;
+                node_range(c, ch, r0, m);
+                const T *Sh = Sinv + (size_t)(ch / 2) * s2c * s2c + ((ch & 1) ? 0 : rc);
+                gd[ch] = GemmDesc<T>{Dc + r0, Sh, Ec + r0, ldn, s2c, ldn, (int)m, (int)s2c, rc};
+            }
+            rec.gemm(gd, 0, T(1));
+        }
     }
-    // ---- 16-bit copies of V_c and d_c for the apply (BF16 / FP16 storage)
+    // ---- 16-bit copies of V_c and E_c for the apply (BF16 / FP16 storage)
     if constexpr (sizeof(T) == 4) {
         if ((h->store == HODLR_BF16 || h->store == HODLR_FP16) && rc > 0) {
             const int nn = 1 << c;
             const float *Vf = reinterpret_cast<const float *>(h->Vl[c]);
-            const float *Df = reinterpret_cast<const float *>(h->Dl[c]);
+            const float *Ef = reinterpret_cast<const float *>(h->El[c]);
             const int64_t *bd = h->d_bounds;
             if (h->store == HODLR_BF16) {
                 __nv_bfloat16 *Vq = reinterpret_cast<__nv_bfloat16 *>(h->Vql[c]);
-                __nv_bfloat16 *Dq = reinterpret_cast<__nv_bfloat16 *>(h->Dql[c]);
+                __nv_bfloat16 *Eq = reinterpret_cast<__nv_bfloat16 *>(h->Eql[c]);
                 Pl->ops.push_back([=](cudaStream_t st) {
                     quantize_kernel<__nv_bfloat16><<<dim3(nn, rc), 256, 0, st>>>(Vf, Vq, ldn, 0, rc, bd, L, c, nullptr);
                     note_launch();
-                    quantize_kernel<__nv_bfloat16><<<dim3(nn, rc), 256, 0, st>>>(Df, Dq, ldn, 0, rc, bd, L, c, nullptr);
+                    quantize_kernel<__nv_bfloat16><<<dim3(nn, 2 * rc), 256, 0, st>>>(Ef, Eq, ldn, 0, 2 * rc, bd, L, c,
+                                                                                  nullptr);
                     note_launch();
                     HODLR_TRY_CUDA(cudaGetLastError());
                     return HODLR_OK;
                 });
             } else {
                 __half *Vq = reinterpret_cast<__half *>(h->Vql[c]);
-                __half *Dq = reinterpret_cast<__half *>(h->Dql[c]);
-                float *vs = h->vscale[c], *ds = h->dscale[c];
+                __half *Eq = reinterpret_cast<__half *>(h->Eql[c]);
+                float *vs = h->vscale[c], *es = h->escale[c];
                 Pl->ops.push_back([=](cudaStream_t st) {
                     quantize_kernel<__half><<<dim3(nn, rc), 256, 0, st>>>(Vf, Vq, ldn, 0, rc, bd, L, c, vs);
                     note_launch();
-                    quantize_kernel<__half><<<dim3(nn, rc), 256, 0, st>>>(Df, Dq, ldn, 0, rc, bd, L, c, ds);
+                    quantize_kernel<__half><<<dim3(nn, 2 * rc), 256, 0, st>>>(Ef, Eq, ldn, 0, 2 * rc, bd, L, c, es);
                     note_launch();
                     HODLR_TRY_CUDA(cudaGetLastError());
                     return HODLR_OK;
@@ -969,12 +1213,18 @@ hodlr_status plan_level(hodlr_t *h, int c, cudaStream_t s) {
     return (h->prec == HODLR_FP64) ? plan_level_typed<double>(h, P, c, s) : plan_level_typed<float>(h, P, c, s);
 }
 
-hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s) {
+hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s, const cudaEvent_t *share_done) {
     if (!h->plan || c >= (int)h->plan->lv.size()) {
         set_error("factor: level %d was not planned", c);
         return HODLR_INVALID_ARG;
     }
-    for (auto &op : h->plan->lv[c].ops) HODLR_TRY(op(s));
+    const LevelPlan &P = h->plan->lv[c];
+    size_t w = 0;
+    for (size_t i = 0; i < P.ops.size(); ++i) {
+        for (; w < P.waits.size() && P.waits[w].first == i; ++w)
+            if (share_done) HODLR_TRY_CUDA(cudaStreamWaitEvent(s, share_done[P.waits[w].second], 0));
+        HODLR_TRY(P.ops[i](s));
+    }
     return HODLR_OK;
 }
 
@@ -989,7 +1239,7 @@ void free_plan(hodlr_t *h, cudaStream_t s) {
 }
 
 hodlr_status factor_impl(hodlr_t *h, cudaStream_t s) {
-    for (int c = h->L; c >= 1; --c) HODLR_TRY(run_level(h, c, s));
+    for (int c = h->L; c >= 1; --c) HODLR_TRY(run_level(h, c, s, nullptr));
     return HODLR_OK;
 }
 

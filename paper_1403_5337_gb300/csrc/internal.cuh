@@ -116,7 +116,7 @@ struct hodlr_s {
     int64_t *d_bounds = nullptr;
     int prec = HODLR_FP32;            // factorisation arithmetic (FP64 or FP32)
     int store = HODLR_FP32;           // storage of the streamed factors V, d in the apply
-    std::vector<float *> vscale, dscale; // FP16: per level 0..L, [nnodes * rp] dequantisation factors
+    std::vector<float *> vscale, escale; // FP16: per level 0..L, [nnodes * rp] (V) and [nnodes * 2 rp] (E) dequantisation factors
     int cprec = HODLR_FP32;           // compression precision
     int method = HODLR_ACA;
     double tol = 0.0;
@@ -128,8 +128,9 @@ struct hodlr_s {
     // Per level c = 1..L (index 0 unused), each ldn x rp(c) column-major:
     std::vector<void *> Ul;           // the compressed U columns (kept: re-factorable)
     std::vector<void *> Dl;           // d = K_node^-1 U_node after factorisation
+    std::vector<void *> El;           // ldn x 2 rp(c): E = d S^-1(half of the parent's core), the apply's update
     std::vector<void *> Vl;           // rows of node nu: V of the sibling's block
-    std::vector<void *> Vql, Dql;     // 16-bit copies of V and d (BF16 / FP16 storage)
+    std::vector<void *> Vql, Eql;     // 16-bit copies of V and E (BF16 / FP16 storage)
     void *leafinv = nullptr;          // elem[2^L * bmax * bmax], column-major per leaf
     std::vector<void *> Sinv;         // level l = 0..L-1: elem[2^l * (2 rp(l+1))^2]
     std::vector<int32_t *> piv_rows;  // per level 1..L: [nnodes][cap] pivot rows (ACA) / kept rows (BDLR)
@@ -211,9 +212,12 @@ hodlr_status factor_impl(hodlr_t *h, cudaStream_t s);
 // Record level c's share of the factorisation (its d columns through every
 // deeper level's update, then the cores of level c - 1) and upload its
 // descriptors; levels are recorded from c = L down to 1.  run_level issues the
-// recorded launches of level c on s; factor_impl replays every level.
+// recorded launches of level c on s; factor_impl replays every level.  With
+// share_done (indexed by level), s waits for share_done[l] where level c's
+// share starts reading level l's factors, so that the shares of different
+// levels can run on different streams.
 hodlr_status plan_level(hodlr_t *h, int c, cudaStream_t s);
-hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s);
+hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s, const cudaEvent_t *share_done);
 // Explicit inverses of the leaf blocks of A (stream-ordered; h->leafinv allocated).
 hodlr_status leaf_inverses(hodlr_t *h, cudaStream_t s);
 void free_plan(hodlr_t *h, cudaStream_t s);

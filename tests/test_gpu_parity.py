@@ -416,6 +416,27 @@ def test_singular_leaf_is_reported(H, ctx):
 
 
 # ---------------------------------------------------------------- the 4096 front
+def test_cores_fp32_vs_fp64_front4096(H, ctx, front4096):
+    """The FP32 factorisation (blocked Gauss-Jordan for the cores wider than
+    64) against the FP64 one on the same FP32 compression: every inverted core
+    agrees to FP32 accuracy."""
+    F = front4096
+    A = _dev(F.A)
+    g = (F.rowptr, F.colind)
+    h32 = H.hodlr_build(ctx, A, 128, 1e-4, "aca", graph=g, precision="fp32", compress_precision="fp32")
+    h64 = H.hodlr_build(ctx, A, 128, 1e-4, "aca", graph=g, precision="fp64", compress_precision="fp32")
+    s32, s64 = h32.stats(), h64.stats()
+    assert s32["rank_max"] == s64["rank_max"]
+    assert max(s32["rank_pad"]) > 128   # cores of several widths above 64
+    for l in range(s32["levels"]):
+        S32, S64 = h32.export_core(l), h64.export_core(l)
+        for i in range(len(S64)):
+            err = np.abs(S32[i] - S64[i]).max() / np.abs(S64[i]).max()
+            assert err < 1e-4, (l, i, err)
+    h32.close()
+    h64.close()
+
+
 @pytest.mark.parametrize("method,tol,prec", [("aca", 1e-4, "fp32"), ("aca", 1e-4, "fp64"),
                                              ("bdlr", 1e-4, "fp32"), ("aca", 1e-8, "fp32")])
 def test_front4096_gmres(H, ctx, front4096, method, tol, prec):
