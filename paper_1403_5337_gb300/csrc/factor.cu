@@ -5,7 +5,8 @@
 // block "node" of U_c holds U_node (the Z stack of the paper, one level at a
 // time); after factorisation d_c(node rows) = K_node^-1 U_node.
 //
-// The share of level c, issued as soon as levels c..L are compressed:
+// The share of level c, issued as soon as level c is compressed (on that
+// level's stream; step 2 for level l waits for the share of level l + 1):
 //  1. d_c <- K_leaf^-1 U_c on every leaf                            (explicit inverses)
 //  2. for l = L-1 .. c (parents of level l + 1, deepest first):
 //       Y = [V_ba^T d_c(alpha); V_ab^T d_c(beta)],  [y1; y2] = S_l^-1 Y,
@@ -13,6 +14,8 @@
 //  3. the cores of level c - 1: P = V_ba^T d_alpha, Q = V_ab^T d_beta (now final),
 //       S = [[I, P], [Q, I]],  M = I - P Q,
 //       S^-1 = [[M^-1, -M^-1 P], [-Q M^-1, I + Q M^-1 P]]
+//  4. the apply's update E_alpha = d_alpha S^-1(rows rp..2rp-1, :),
+//       E_beta = d_beta S^-1(rows 0..rp-1, :)   (x_alpha -= d_alpha y2 = E_alpha w)
 // Summed over c this is the level-synchronous sweep of the paper's recursion:
 // each d column receives the updates of the deeper levels in the same order.
 // The 2x2 block inverse through M = I - P Q is the same algebra as solving with
