@@ -471,7 +471,8 @@ def main():
     hp.close()
     ew = 8 if args.precision == "fp64" else (2 if args.precision in ("bf16", "fp16") else 4)
     wtot = sum(pst["rank_pad"])
-    ap_bytes = (2.0 * n * wtot * ew + n * WORKLOADS[args.workload]["leaf"] * (8 if args.precision == "fp64" else 4)
+    # V (n x rp) and E (n x 2 rp) of every level, the leaf inverses' rows, X in and out
+    ap_bytes = (3.0 * n * wtot * ew + n * WORKLOADS[args.workload]["leaf"] * (8 if args.precision == "fp64" else 4)
                 + 16.0 * n * Z.shape[0])
     n_ap = int(np.max(info.iters)) + info.restarts
     kernels = {
