@@ -63,6 +63,11 @@ struct FusedArgs {
     const int4 *tiles;                     // (leaf, first row, rows, 0)
     const int *tile_first;                 // first tile of each leaf, 2^L + 1 entries
     int ntiles;
+    // stage = 1: one tile per CTA, whose leaf-inverse rows and E, V rows of every
+    // level are copied into shared memory at the start (byte offsets of each
+    // level's block in the staging area; columns of 32 rows each)
+    int stage, stage_at;
+    int sofE[HODLR_MAX_LEVELS], sofV[HODLR_MAX_LEVELS];
     const int64_t *bounds;
     const double *Xin;
     double *X;
@@ -111,23 +116,32 @@ __device__ __forceinline__ void wait_node(const unsigned *cnt, unsigned target, 
 // atomic per (column, rhs).
 template <typename T, typename S, int RC>
 __device__ void fa_vtx(const FusedArgs<T, S> &a, int c, int child, int64_t row0, int nrows, int r0, int rr,
-                       T *sv, T *xs) {
+                       T *sv, T *xs, const unsigned char *stg) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = AP_THREADS / 32;
     const int rp = a.rp[c];
     const S *Vc = a.Vb + a.voff[c];
     T *w = a.w[c];
     const float *vs = a.vscale[c];
-    const int64_t row = row0 + lane;
-    int col = warp;
-    for (; col + 3 * NW < rp; col += 4 * NW) {
-        T v[4];
+    if (stg) {
+        // the tile's V rows are staged (column-major, 32 rows per column)
+        const S *Vs = reinterpret_cast<const S *>(stg + a.sofV[c]);
+        for (int col = warp; col < rp; col += NW)
+            sv[col * (TR + 1) + lane] = (lane < nrows) ? to_t<T>(Vs[col * TR + lane]) : T(0);
+    } else {
+        const int64_t row = row0 + lane;
+        int col = warp;
+        for (; col + 3 * NW < rp; col += 4 * NW) {
+            T v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (lane < nrows) ? to_t<T>(Vc[row + (int64_t)(col + u * NW) * a.ldn]) : T(0);
+            for (int u = 0; u < 4; ++u)
+                v[u] = (lane < nrows) ? to_t<T>(Vc[row + (int64_t)(col + u * NW) * a.ldn]) : T(0);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sv[(col + u * NW) * (TR + 1) + lane] = v[u];
+            for (int u = 0; u < 4; ++u) sv[(col + u * NW) * (TR + 1) + lane] = v[u];
+        }
+        for (; col < rp; col += NW)
+            sv[col * (TR + 1) + lane] = (lane < nrows) ? to_t<T>(Vc[row + (int64_t)col * a.ldn]) : T(0);
     }
-    for (; col < rp; col += NW) sv[col * (TR + 1) + lane] = (lane < nrows) ? to_t<T>(Vc[row + (int64_t)col * a.ldn]) : T(0);
     for (int e = threadIdx.x; e < TR * RC; e += AP_THREADS) {
         const int li = e % TR, q = e / TR;
         xs[q * TR + li] = (li < nrows && q < rr) ? a.xt[row0 + li + (r0 + q) * a.ldn] : T(0);
@@ -203,16 +217,67 @@ __device__ void prefetch_tiles(const FusedArgs<T, S> &a) {
     }
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Copy `cols` columns of the tile's `nrows` (<= 32) rows, column j at src + j ld,
+// to dst + 32 j: 16-byte asynchronous copies when the tile is full and every
+// column starts on a 16-byte boundary, element copies otherwise.
+template <typename X>
+__device__ void stage_cols(X *dst, const X *src, int64_t ld, int cols, int nrows) {
+    const bool vec = nrows == TR && (reinterpret_cast<uintptr_t>(src) & 15) == 0 && ((ld * sizeof(X)) & 15) == 0;
+    if (vec) {
+        constexpr int P = TR * (int)sizeof(X) / 16;   // 16-byte pieces per column
+        for (int e = threadIdx.x; e < cols * P; e += AP_THREADS) {
+            const int j = e / P, p = e % P;
+            cp_async16(reinterpret_cast<char *>(dst + (size_t)j * TR) + 16 * p,
+                       reinterpret_cast<const char *>(src + j * ld) + 16 * p);
+        }
+    } else {
+        for (int e = threadIdx.x; e < cols * TR; e += AP_THREADS) {
+            const int j = e / TR, r = e % TR;
+            if (r < nrows) dst[(size_t)j * TR + r] = src[j * ld + r];
+        }
+    }
+}
+
 template <typename T, typename S, int RC>
 __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs<T, S> a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    prefetch_tiles(a);
     extern __shared__ __align__(16) unsigned char smem[];
     T *part = reinterpret_cast<T *>(smem);                          // 8 warps x 32 rows x RC
     T *ws = part + (AP_THREADS / 32) * TR * RC;                     // w of the node: 2 rp x RC; the leaf's x
     T *sv = ws + (size_t)std::max(2 * a.rpmax, a.bmax) * RC;        // V tile: rp x (32 + 1)
     T *xs = sv + (size_t)a.rpmax * (TR + 1);                        // x tile: RC x 32
     const int L = a.L;
+    // The tile's leaf-inverse rows, then E and V rows of every level, in shared
+    // memory (one CTA per tile), or pulled into L2 for the phases below.
+    const unsigned char *stg = nullptr;
+    if (a.stage) {
+        unsigned char *st = smem + a.stage_at;
+        if ((int)blockIdx.x < a.ntiles) {
+            const int4 tl = a.tiles[blockIdx.x];
+            const int leaf = tl.x, nrows = tl.z;
+            const int64_t row0 = tl.y;
+            const int64_t l0 = a.bounds[leaf];
+            const int b = (int)(a.bounds[leaf + 1] - l0);
+            stage_cols<T>(reinterpret_cast<T *>(st), a.Kinv + (size_t)leaf * a.bmax * a.bmax + (row0 - l0), a.bmax, b,
+                          nrows);
+            for (int c = 1; c <= L; ++c) {
+                stage_cols<S>(reinterpret_cast<S *>(st + a.sofE[c]), a.Eb + a.eoff[c] + row0, a.ldn, 2 * a.rp[c],
+                              nrows);
+                stage_cols<S>(reinterpret_cast<S *>(st + a.sofV[c]), a.Vb + a.voff[c] + row0, a.ldn, a.rp[c], nrows);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        stg = st;
+    } else {
+        prefetch_tiles(a);
+    }
     // ---- leaves: x = K_leaf^-1 x on the tile's rows, then the leaf level's V^T x
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = a.tiles[t];
@@ -234,7 +299,12 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
             T acc[RC];
 #pragma unroll
             for (int q = 0; q < RC; ++q) acc[q] = T(0);
-            if (lane < nrows) stream_dot<T, T, RC>(K + il, a.bmax, ws, kb, ke, acc);
+            if (lane < nrows) {
+                if (stg)
+                    stream_dot<T, T, RC>(reinterpret_cast<const T *>(stg) + lane, TR, ws, kb, ke, acc);
+                else
+                    stream_dot<T, T, RC>(K + il, a.bmax, ws, kb, ke, acc);
+            }
 #pragma unroll
             for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
             __syncthreads();
@@ -247,7 +317,7 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
                 }
             }
             __syncthreads();
-            if (L >= 1) fa_vtx<T, S, RC>(a, L, leaf, row0, nrows, r0, rr, sv, xs);
+            if (L >= 1) fa_vtx<T, S, RC>(a, L, leaf, row0, nrows, r0, rr, sv, xs, stg);
         }
         if (L >= 1) arrive(a.cnt[L] + (leaf >> 1));
     }
@@ -285,7 +355,13 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
                     T acc[RC];
 #pragma unroll
                     for (int q = 0; q < RC; ++q) acc[q] = T(0);
-                    if (lane < nrows) stream_dot<T, S, RC>(Ec + row0 + lane, a.ldn, ws, ub, ue, acc);
+                    if (lane < nrows) {
+                        if (stg)
+                            stream_dot<T, S, RC>(reinterpret_cast<const S *>(stg + a.sofE[c]) + lane, TR, ws, ub, ue,
+                                                 acc);
+                        else
+                            stream_dot<T, S, RC>(Ec + row0 + lane, a.ldn, ws, ub, ue, acc);
+                    }
 #pragma unroll
                     for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
                     __syncthreads();
@@ -306,7 +382,7 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
                             a.X[row0 + li + (int64_t)(r0 + q) * a.ldx] = (double)a.xt[row0 + li + (int64_t)(r0 + q) * a.ldn];
                     }
                 }
-                if (c > 1) fa_vtx<T, S, RC>(a, c - 1, leaf >> (L - c + 1), row0, nrows, r0, rr, sv, xs);
+                if (c > 1) fa_vtx<T, S, RC>(a, c - 1, leaf >> (L - c + 1), row0, nrows, r0, rr, sv, xs, stg);
             }
             if (c > 1) arrive(a.cnt[c - 1] + (leaf >> (L - c + 2)));
         }
@@ -381,10 +457,38 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
 }
 
 template <typename T, typename S, int RC>
-hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream_t st) {
-    const size_t sm = ((size_t)(AP_THREADS / 32) * TR * RC + (size_t)std::max(2 * a.rpmax, a.bmax) * RC +
-                       (size_t)a.rpmax * (TR + 1) + (size_t)TR * RC) *
-                      sizeof(T);
+hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a0, cudaStream_t st) {
+    FusedArgs<T, S> a = a0;
+    const size_t sm0 = (((size_t)(AP_THREADS / 32) * TR * RC + (size_t)std::max(2 * a.rpmax, a.bmax) * RC +
+                         (size_t)a.rpmax * (TR + 1) + (size_t)TR * RC) *
+                            sizeof(T) +
+                        15) & ~size_t(15);
+    // staging area of one tile: the leaf inverse's rows, then per level E (2 rp
+    // columns) and V (rp columns), 32 rows per column
+    auto al16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+    size_t sbytes = al16((size_t)a.bmax * TR * sizeof(T));
+    for (int c = 1; c <= a.L; ++c) {
+        a.sofE[c] = (int)sbytes;
+        sbytes += al16((size_t)2 * a.rp[c] * TR * sizeof(S));
+        a.sofV[c] = (int)sbytes;
+        sbytes += al16((size_t)a.rp[c] * TR * sizeof(S));
+    }
+    int optin = 0;
+    HODLR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->ctx->device));
+    size_t sm = sm0;
+    a.stage = 0;
+    a.stage_at = (int)sm0;
+    if (h->ntiles <= h->ctx->num_sms && sm0 + sbytes <= (size_t)optin) {
+        HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_fused_kernel<T, S, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sm0 + sbytes)));
+        int per = 0;
+        HODLR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_fused_kernel<T, S, RC>, AP_THREADS,
+                                                                     sm0 + sbytes));
+        if (per >= 1) {
+            a.stage = 1;
+            sm = sm0 + sbytes;
+        }
+    }
     HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_fused_kernel<T, S, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sm));
     int per_sm = 0;
@@ -393,7 +497,9 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream
         set_error("fused apply: no resident CTA possible (%zu bytes of shared memory)", sm);
         return HODLR_RANGE;
     }
-    const int grid = std::max(1, std::min(h->ctx->num_sms * std::min(per_sm, 2), std::max(h->ntiles, 1)));
+    // staging needs one CTA per tile (ntiles <= SMs <= resident CTAs)
+    const int grid = a.stage ? std::max(h->ntiles, 1)
+                             : std::max(1, std::min(h->ctx->num_sms * std::min(per_sm, 2), std::max(h->ntiles, 1)));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(AP_THREADS);
