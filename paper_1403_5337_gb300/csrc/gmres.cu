@@ -92,10 +92,16 @@ __global__ void split_vec_kernel(const double *__restrict__ Z, int64_t ldz, int6
 // most 32 terms per row in the float pair before it is converted to FP64, so
 // the compensation term's own FP32 rounding never accumulates further.
 // VEC: A rows are 16-byte aligned (even lda, aligned base) -> double2 loads.
+// With a split buffer Asp (n x n FP32 pairs, ld n, VEC only): while *split_state
+// is 0 the kernel splits A as usual and also stores the pairs to Asp; once it
+// is 1 (set by the Arnoldi step that follows the first product of a solve)
+// it reads the pairs instead of A and skips the split -- the same FP32 parts,
+// so the same products.
 template <bool VEC>
 __global__ void __launch_bounds__(MV_THREADS, 4)
     df_matvec_kernel(const double *__restrict__ A, int64_t n, int64_t lda, const float2 *__restrict__ zs,
-                     int s, int r0, double *__restrict__ W, int64_t ldw, int *status) {
+                     int s, int r0, double *__restrict__ W, int64_t ldw, int *status, float2 *__restrict__ Asp,
+                     const int *__restrict__ split_state) {
     __shared__ __align__(16) float2 zsm[MV_S][MV_KC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k0 = (int64_t)blockIdx.y * MV_KC;
@@ -113,7 +119,50 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
 #pragma unroll
         for (int q = 0; q < MV_S; ++q) acc[a][q] = DF{0.f, 0.f};
     int bad = 0;
-    if (VEC) {
+    // 1: write the pairs, 2: read them (a later launch of the same product reads
+    // what the launch for the first right-hand sides wrote)
+    const int smode = (VEC && Asp) ? ((*split_state || r0 > 0) ? 2 : 1) : 0;
+    if (VEC && smode == 2) {
+        const int np = kc >> 1;
+        for (int p0 = lane; p0 < np; p0 += 32 * MV_U) {
+            float4 hv[MV_RPW][MV_U];   // (h0, l0, h1, l1) of a column pair
+#pragma unroll
+            for (int u = 0; u < MV_U; ++u) {
+                const int p = p0 + 32 * u;
+#pragma unroll
+                for (int a = 0; a < MV_RPW; ++a) {
+                    const int64_t row = row0 + a;
+                    hv[a][u] = (p < np && row < n) ? __ldg(reinterpret_cast<const float4 *>(Asp + row * n + k0) + p)
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < MV_U; ++u) {
+                const int p = p0 + 32 * u;
+                if (p >= np) break;
+#pragma unroll
+                for (int q = 0; q < MV_S; ++q) {
+                    const float4 z = reinterpret_cast<const float4 *>(zsm[q])[p];
+#pragma unroll
+                    for (int a = 0; a < MV_RPW; ++a) {
+                        df_acc(acc[a][q], hv[a][u].x, hv[a][u].y, z.x, z.y);
+                        df_acc(acc[a][q], hv[a][u].z, hv[a][u].w, z.z, z.w);
+                    }
+                }
+            }
+        }
+        if ((kc & 1) && lane == 0) {   // odd tail column
+            const int kk = kc - 1;
+#pragma unroll
+            for (int a = 0; a < MV_RPW; ++a) {
+                const int64_t row = row0 + a;
+                if (row >= n) continue;
+                const float2 hl = Asp[row * n + k0 + kk];
+#pragma unroll
+                for (int q = 0; q < MV_S; ++q) df_acc(acc[a][q], hl.x, hl.y, zsm[q][kk].x, zsm[q][kk].y);
+            }
+        }
+    } else if (VEC) {
         const int np = kc >> 1;   // column pairs
         for (int p0 = lane; p0 < np; p0 += 32 * MV_U) {
             double2 av[MV_RPW][MV_U];
@@ -137,6 +186,8 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
                     float h0, l0, h1, l1;
                     split_entry(av[a][u].x, h0, l0, bad);
                     split_entry(av[a][u].y, h1, l1, bad);
+                    if (smode == 1 && row0 + a < n)
+                        reinterpret_cast<float4 *>(Asp + (row0 + a) * n + k0)[p] = make_float4(h0, l0, h1, l1);
 #pragma unroll
                     for (int q = 0; q < MV_S; ++q) {
                         const float4 z = reinterpret_cast<const float4 *>(zsm[q])[p];
@@ -154,6 +205,7 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
                 if (row >= n) continue;
                 float h0, l0;
                 split_entry(A[row * lda + k0 + kk], h0, l0, bad);
+                if (smode == 1) Asp[row * n + k0 + kk] = make_float2(h0, l0);
 #pragma unroll
                 for (int q = 0; q < MV_S; ++q) df_acc(acc[a][q], h0, l0, zsm[q][kk].x, zsm[q][kk].y);
             }
@@ -340,6 +392,7 @@ struct TailArgs {
     int *status;
     int *loops;
     int limit;
+    int *split_state;   // set to 1: A's FP32 pairs are in place for the next products
     cudaGraphConditionalHandle handle;
 };
 
@@ -584,6 +637,7 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
         *a.gs.nactive = s_cnt;
+        if (a.split_state) *a.split_state = 1;
         const int it = ++(*a.loops);
         cudaGraphSetConditional(a.handle, (s_cnt > 0 && it < a.limit) ? 1u : 0u);
     }
@@ -592,7 +646,8 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
 }  // namespace
 
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s, const double *Z, int64_t ldz,
-                         double *W, int64_t ldw, cudaStream_t st, void *work, bool w_zeroed) {
+                         double *W, int64_t ldw, cudaStream_t st, void *work, bool w_zeroed, float2 *Asp,
+                         const int *split_state) {
     if (n == 0 || s == 0) return HODLR_OK;
     float2 *zs = work ? reinterpret_cast<float2 *>(work)
                       : reinterpret_cast<float2 *>(dalloc(c, (size_t)n * s * sizeof(float2), st));
@@ -603,11 +658,14 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
     cudaError_t e = w_zeroed ? cudaSuccess : cudaMemset2DAsync(W, ldw * sizeof(double), 0, n * sizeof(double), s, st);
     const dim3 grid((unsigned)((n + MV_ROWS - 1) / MV_ROWS), (unsigned)((n + MV_KC - 1) / MV_KC));
     const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    if (!vec || n % 2 != 0) Asp = nullptr;   // the split buffer is read as 16-byte pairs of columns
     for (int r0 = 0; r0 < s && e == cudaSuccess; r0 += MV_S) {
         if (vec)
-            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
+            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status, Asp,
+                                                                split_state);
         else
-            df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status);
+            df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status, nullptr,
+                                                                 nullptr);
         note_launch();
         e = cudaGetLastError();
     }
@@ -698,10 +756,11 @@ extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const
     const bool vec = (A->ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(A->data) & 15) == 0);
     for (int r0 = 0; r0 < s; r0 += MV_S) {
         if (vec)
-            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw, slot.status);
+            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw, slot.status,
+                                                                nullptr, nullptr);
         else
             df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw,
-                                                                 slot.status);
+                                                                 slot.status, nullptr, nullptr);
         note_launch();
     }
     HODLR_TRY_CUDA(cudaGetLastError());
@@ -772,7 +831,8 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
                  oH = ar.take((size_t)s * (m + 1) * m * 8), ocs = ar.take((size_t)s * m * 8),
                  osn = ar.take((size_t)s * m * 8), og = ar.take((size_t)s * (m + 1) * 8), obn = ar.take((size_t)s * 8),
                  oest = ar.take((size_t)s * 8), oib = ar.take((size_t)(4 * s + 4) * sizeof(int)),
-                 ozs = ar.take((size_t)n * s * sizeof(float2)), oZc = ar.take((size_t)n * s * 8), olp = ar.take(256);
+                 ozs = ar.take((size_t)n * s * sizeof(float2)), oZc = ar.take((size_t)n * s * 8), olp = ar.take(256),
+                 osst = ar.take(256);
     GmresBufs bufs;
     bufs.c = c;
     bufs.st = st;
@@ -798,6 +858,17 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     void *zsw = base + ozs;
     double *Zc = (double *)(base + oZc);
     int *loops = (int *)(base + olp);
+    // A's FP32 (hi, lo) pairs for the products after the first (ld n; skipped
+    // when A's rows are not 16-byte aligned, n is odd, the buffer would exceed
+    // 16 GiB or cannot be allocated: the products then split A every time)
+    int *split_state = (int *)(base + osst);
+    float2 *Asp = nullptr;
+    if (n % 2 == 0 && A->ld % 2 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
+        (double)n * (double)n * 8.0 <= 16.0 * 1024 * 1024 * 1024) {
+        Asp = reinterpret_cast<float2 *>(bufs.get((size_t)n * n * sizeof(float2)));
+        cudaGetLastError();
+    }
+    HODLR_TRY_CUDA(cudaMemsetAsync(split_state, 0, sizeof(int), st));
     gs.iters = ibuf;
     gs.jcur = ibuf + s;
     gs.active = ibuf + 2 * s;
@@ -852,6 +923,7 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     ta.status = c->d_status;
     ta.loops = loops;
     ta.limit = m + 1;
+    ta.split_state = Asp ? split_state : nullptr;
     const size_t tail_smem = (size_t)(m + 1) * sizeof(double) + 2 * (size_t)s * sizeof(int);
     HODLR_TRY_CUDA(cudaFuncSetAttribute(arnoldi_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)tail_smem));
@@ -884,7 +956,7 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         HODLR_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         auto record = [&]() -> hodlr_status {
             if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs));
-            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true));
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state));
             ta.handle = handle;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)tail_grid);
@@ -937,7 +1009,7 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
         // true residual R = B - A X
-        HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, X, ldx, Wv, n, st, zsw));
+        HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, X, ldx, Wv, n, st, zsw, false, Asp, split_state));
         HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, st));
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
         note_launch();
