@@ -46,7 +46,10 @@ hodlr_status take_status(hodlr_ctx *c, cudaStream_t s) {
     HODLR_TRY_CUDA(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     HODLR_TRY_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
     HODLR_TRY_CUDA(cudaStreamSynchronize(s));
-    const int w = *c->h_status;
+    return status_word(*c->h_status);
+}
+
+hodlr_status status_word(int w) {
     if (w) {
         set_error("device status word 0x%x (%s%s%s%s)", w, (w & ST_NONFINITE) ? "non-finite value " : "",
                   (w & ST_SINGULAR) ? "zero pivot " : "", (w & ST_TIMEOUT) ? "wait budget exceeded " : "",
@@ -55,8 +58,15 @@ hodlr_status take_status(hodlr_ctx *c, cudaStream_t s) {
     return status_from_word(w);
 }
 
-void *dalloc(hodlr_ctx *c, size_t bytes, cudaStream_t s) {
-    if (bytes == 0) bytes = 256;
+// Device memory of the library: the context's allocator (or the CUDA pool) for
+// new blocks; released blocks are kept in the context's cache and handed out
+// again for requests of the same rounded size, so repeated solves of one
+// problem allocate nothing.  A cached block carries an event recorded on the
+// stream that released it; a request on another stream waits for it.
+namespace {
+size_t round_block(size_t bytes) { return (std::max<size_t>(bytes, 1) + 255) & ~size_t(255); }
+
+void *raw_alloc(hodlr_ctx *c, size_t bytes, cudaStream_t s) {
     if (c->alloc) return c->alloc(bytes, c->user, reinterpret_cast<hodlr_stream>(s));
     void *p = nullptr;
     if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
@@ -66,13 +76,106 @@ void *dalloc(hodlr_ctx *c, size_t bytes, cudaStream_t s) {
     return p;
 }
 
-void dfree(hodlr_ctx *c, void *p, size_t bytes, cudaStream_t s) {
-    if (!p) return;
-    if (bytes == 0) bytes = 256;
+void raw_free(hodlr_ctx *c, void *p, size_t bytes, cudaStream_t s) {
     if (c->free_fn)
         c->free_fn(p, bytes, c->user, reinterpret_cast<hodlr_stream>(s));
     else
         cudaFreeAsync(p, s);
+}
+}  // namespace
+
+void *dalloc(hodlr_ctx *c, size_t bytes, cudaStream_t s) {
+    const size_t sz = round_block(bytes);
+    hodlr_cached_block b{nullptr, 0, nullptr, nullptr};
+    {
+        std::lock_guard<std::mutex> lock(c->cache_mu);
+        auto it = c->cache.find(sz);
+        if (it != c->cache.end() && !it->second.empty()) {
+            auto &v = it->second;
+            size_t k = v.size() - 1;
+            for (size_t q = v.size(); q-- > 0;)
+                if (v[q].stream == s) {   // prefer a block released on this stream
+                    k = q;
+                    break;
+                }
+            b = v[k];
+            v[k] = v.back();
+            v.pop_back();
+            c->cache_bytes -= sz;
+            --c->cache_count;
+        }
+    }
+    if (b.p) {
+        // wait first, then recycle the event (a later record of it does not
+        // affect a wait already issued)
+        if (b.stream != s) cudaStreamWaitEvent(s, b.ev, 0);
+        std::lock_guard<std::mutex> lock(c->cache_mu);
+        c->spare_events.push_back(b.ev);
+        return b.p;
+    }
+    return raw_alloc(c, sz, s);
+}
+
+void dfree(hodlr_ctx *c, void *p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    const size_t sz = round_block(bytes);
+    cudaEvent_t ev = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(c->cache_mu);
+        if (!c->spare_events.empty()) {
+            ev = c->spare_events.back();
+            c->spare_events.pop_back();
+        }
+    }
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        raw_free(c, p, sz, s);
+        return;
+    }
+    cudaEventRecord(ev, s);
+    std::vector<hodlr_cached_block> evict;
+    {
+        std::lock_guard<std::mutex> lock(c->cache_mu);
+        c->cache[sz].push_back(hodlr_cached_block{p, sz, s, ev});
+        c->fifo.push_back({p, sz});
+        c->cache_bytes += sz;
+        ++c->cache_count;
+        while (c->cache_bytes > HODLR_CACHE_LIMIT && !c->fifo.empty()) {
+            const auto f = c->fifo.front();
+            c->fifo.pop_front();
+            auto &v = c->cache[f.second];
+            for (size_t q = 0; q < v.size(); ++q)
+                if (v[q].p == f.first) {
+                    evict.push_back(v[q]);
+                    v[q] = v.back();
+                    v.pop_back();
+                    c->cache_bytes -= f.second;
+                    --c->cache_count;
+                    break;
+                }
+        }
+        if (c->fifo.size() > 2 * c->cache_count + 64) {
+            // drop the entries of blocks handed out again
+            std::deque<std::pair<void *, size_t>> keep;
+            for (const auto &f : c->fifo) {
+                const auto it = c->cache.find(f.second);
+                if (it == c->cache.end()) continue;
+                for (const auto &q : it->second)
+                    if (q.p == f.first) {
+                        keep.push_back(f);
+                        break;
+                    }
+            }
+            c->fifo.swap(keep);
+        }
+    }
+    for (auto &b : evict) {
+        // the block may have been used on streams its allocator does not know
+        // about: hand it back only once that use is complete
+        cudaEventSynchronize(b.ev);
+        raw_free(c, b.p, b.bytes, b.stream);
+        cudaEventDestroy(b.ev);
+    }
 }
 
 size_t Arena::take(size_t b) {
@@ -230,6 +333,14 @@ hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn fr
         set_error("hodlr_ctx_create: cannot allocate the status word");
         return HODLR_OUT_OF_MEMORY;
     }
+    if (cudaMallocHost(&c->h_report, HODLR_REPORT_BYTES) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->d_status);
+        cudaFreeHost(c->h_status);
+        delete c;
+        set_error("hodlr_ctx_create: cannot allocate the pinned report buffer");
+        return HODLR_OUT_OF_MEMORY;
+    }
     cudaMemset(c->d_status, 0, sizeof(int));
     *c->h_status = 0;
     c->h_scratch = c->h_status + 1;
@@ -239,6 +350,7 @@ hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn fr
             for (int q = 0; q < i; ++q) cudaStreamDestroy(c->side[q]);
             cudaFree(c->d_status);
             cudaFreeHost(c->h_status);
+            cudaFreeHost(c->h_report);
             delete c;
             set_error("hodlr_ctx_create: cannot create streams");
             return HODLR_CUDA_ERROR;
@@ -250,10 +362,27 @@ hodlr_status hodlr_ctx_create(int device, hodlr_alloc_fn alloc, hodlr_free_fn fr
 hodlr_status hodlr_ctx_destroy(hodlr_ctx *c) {
     if (!c) return HODLR_OK;
     cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &g : c->graph_trash) {
+        if (g.first) cudaGraphExecDestroy(g.first);
+        if (g.second) cudaGraphDestroy(g.second);
+    }
+    c->graph_trash.clear();
+    for (auto &kv : c->cache)
+        for (auto &b : kv.second) {
+            raw_free(c, b.p, b.bytes, nullptr);
+            cudaEventDestroy(b.ev);
+        }
+    c->cache.clear();
+    c->fifo.clear();
+    for (auto e : c->spare_events) cudaEventDestroy(e);
+    c->spare_events.clear();
+    cudaDeviceSynchronize();
     for (int i = 0; i < HODLR_SIDE_STREAMS; ++i)
         if (c->side[i]) cudaStreamDestroy(c->side[i]);
     cudaFree(c->d_status);
     cudaFreeHost(c->h_status);
+    if (c->h_report) cudaFreeHost(c->h_report);
     delete c;
     return HODLR_OK;
 }
@@ -267,7 +396,6 @@ hodlr_status hodlr_destroy(hodlr_t *h) {
         if (e) cudaEventDestroy(e);
     for (auto &b : h->owned) dfree(h->ctx, b.p, b.bytes, nullptr);
     if (h->work) dfree(h->ctx, h->work, h->work_bytes, nullptr);
-    cudaDeviceSynchronize();
     delete h;
     return HODLR_OK;
 }
@@ -439,11 +567,6 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     if (!sbase) return fail(HODLR_OUT_OF_MEMORY);
     std::vector<std::pair<void *, size_t>> temp{{sbase, stage.bytes}};
     h->d_bounds = (int64_t *)(mbase + o_bounds);
-    if (cudaMemcpyAsync(h->d_bounds, bounds.data(), bounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st) !=
-        cudaSuccess) {
-        dfree(c, sbase, stage.bytes, st);
-        return fail(HODLR_CUDA_ERROR);
-    }
     // ---- compression staging and per-block descriptors
     std::vector<void *> Ust(L + 1, nullptr), Vst(L + 1, nullptr);
     h->piv_rows.assign(L + 1, nullptr);
@@ -478,25 +601,9 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
         for (auto &q : temp) dfree(c, q.first, q.second, st);
         temp.clear();
     };
-    // Row tiles of the fused apply (32 rows, never straddling a leaf) and the
-    // first tile of every leaf.
-    h->d_tiles = (const int4 *)(mbase + o_tiles);
-    h->d_tile_first = (int *)(mbase + o_tfirst);
-    h->ntiles = (int)tiles.size();
-    if (!tiles.empty())
-        cudaMemcpyAsync((void *)h->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(h->d_tile_first, tfirst.data(), tfirst.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-    // The leaf inverses depend on A only: they run on a side stream while the
-    // off-diagonal blocks are compressed, and join the caller's stream after.
-    h->leafinv = mbase + o_leafinv;
-    cudaStream_t lstream = c->side[HODLR_SIDE_STREAMS - 1];
     cudaEvent_t lfork = nullptr, ljoin = nullptr;
     cudaEventCreateWithFlags(&lfork, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&ljoin, cudaEventDisableTiming);
-    cudaEventRecord(lfork, st);
-    cudaStreamWaitEvent(lstream, lfork, 0);
-    const hodlr_status rleaf = leaf_inverses(h, lstream);
-    cudaEventRecord(ljoin, lstream);
     cudaEvent_t e0;
     cudaEventCreate(&e0);
     cudaEventRecord(e0, st);
@@ -529,6 +636,24 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
             cudaEventRecord(done[l], st);
         }
     }
+    // ---- what the compression does not need, issued after its launch: the
+    // leaf bounds, the apply's row tiles (32 rows, never straddling a leaf) and
+    // the first tile of every leaf, and the leaf inverses, which depend on A
+    // only and run on a side stream while the off-diagonal blocks are
+    // compressed (they join the levels' streams and the caller's stream later)
+    cudaMemcpyAsync(h->d_bounds, bounds.data(), bounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    h->d_tiles = (const int4 *)(mbase + o_tiles);
+    h->d_tile_first = (int *)(mbase + o_tfirst);
+    h->ntiles = (int)tiles.size();
+    if (!tiles.empty())
+        cudaMemcpyAsync((void *)h->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_tile_first, tfirst.data(), tfirst.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    h->leafinv = mbase + o_leafinv;
+    cudaStream_t lstream = c->side[HODLR_SIDE_STREAMS - 1];
+    cudaEventRecord(lfork, st);
+    cudaStreamWaitEvent(lstream, lfork, 0);
+    const hodlr_status rleaf = leaf_inverses(h, lstream);
+    cudaEventRecord(ljoin, lstream);
     // share_done[l]: level l's compaction and (unless deferred) its share of the
     // factorisation are complete
     std::vector<cudaEvent_t> share_done(L + 1, nullptr);

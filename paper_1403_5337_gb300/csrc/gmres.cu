@@ -359,6 +359,36 @@ __global__ void count_active_kernel(const int *active, int s, int *nactive) {
     *nactive = c;
 }
 
+// The host's view of a cycle, gathered for one copy: ints [active rhs, device
+// status word (read and cleared), replays of the last cycle's iteration, iters
+// per rhs], then from report_doff(s) on doubles [est, ||r||^2, ||b||] per rhs.
+__host__ __device__ inline size_t report_doff(int s) { return ((size_t)(3 + s) * sizeof(int) + 7) & ~size_t(7); }
+__host__ __device__ inline size_t report_bytes(int s) { return report_doff(s) + (size_t)3 * s * sizeof(double); }
+
+__global__ void cycle_report_kernel(GState st, int s, const double *nrm, int *status, const int *loops, char *rep) {
+    if (threadIdx.x != 0) return;
+    int c = 0;
+    for (int r = 0; r < s; ++r) c += st.active[r];
+    *st.nactive = c;
+    int *ri = reinterpret_cast<int *>(rep);
+    ri[0] = c;
+    ri[1] = atomicExch(status, 0);
+    ri[2] = *loops;
+    for (int r = 0; r < s; ++r) ri[3 + r] = st.iters[r];
+    double *rd = reinterpret_cast<double *>(rep + report_doff(s));
+    for (int r = 0; r < s; ++r) {
+        rd[r] = st.est[r];
+        rd[s + r] = nrm[r];
+        rd[2 * s + r] = st.bnorm[r];
+    }
+}
+
+// First node of a cycle's graph: the while loop runs only if some right-hand
+// side is active (so the host need not wait for the count before launching).
+__global__ void cond_init_kernel(const int *nactive, cudaGraphConditionalHandle handle) {
+    cudaGraphSetConditional(handle, *nactive > 0 ? 1u : 0u);
+}
+
 // ------------------------------------------------------------------ fused Arnoldi step
 // After w = A z_j: classical Gram-Schmidt twice against v_0..v_j, the new basis
 // vector, the Givens update of the Hessenberg column and the loop test, in one
@@ -777,13 +807,28 @@ extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const
 namespace {
 
 struct IterGraph {
+    hodlr_ctx *c = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    ~IterGraph() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
+    ~IterGraph() {   // handed to the context: torn down by the next solve
+        if (exec || graph) {
+            std::lock_guard<std::mutex> lock(c->cache_mu);
+            c->graph_trash.push_back({exec, graph});
+        }
     }
 };
+
+void empty_graph_trash(hodlr_ctx *c) {
+    std::vector<std::pair<cudaGraphExec_t, cudaGraph_t>> t;
+    {
+        std::lock_guard<std::mutex> lock(c->cache_mu);
+        t.swap(c->graph_trash);
+    }
+    for (auto &g : t) {
+        if (g.first) cudaGraphExecDestroy(g.first);
+        if (g.second) cudaGraphDestroy(g.second);
+    }
+}
 
 struct GmresBufs {
     hodlr_ctx *c = nullptr;
@@ -832,7 +877,7 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
                  osn = ar.take((size_t)s * m * 8), og = ar.take((size_t)s * (m + 1) * 8), obn = ar.take((size_t)s * 8),
                  oest = ar.take((size_t)s * 8), oib = ar.take((size_t)(4 * s + 4) * sizeof(int)),
                  ozs = ar.take((size_t)n * s * sizeof(float2)), oZc = ar.take((size_t)n * s * 8), olp = ar.take(256),
-                 osst = ar.take(256);
+                 osst = ar.take(256), orep = ar.take(report_bytes(s));
     GmresBufs bufs;
     bufs.c = c;
     bufs.st = st;
@@ -862,6 +907,7 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     // when A's rows are not 16-byte aligned, n is odd, the buffer would exceed
     // 16 GiB or cannot be allocated: the products then split A every time)
     int *split_state = (int *)(base + osst);
+    char *rep_dev = base + orep;
     float2 *Asp = nullptr;
     if (n % 2 == 0 && A->ld % 2 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
         (double)n * (double)n * 8.0 <= 16.0 * 1024 * 1024 * 1024) {
@@ -873,8 +919,6 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
     gs.jcur = ibuf + s;
     gs.active = ibuf + 2 * s;
     gs.nactive = ibuf + 3 * s;
-    int *h_pin = c->h_scratch;   // pinned, per context
-    std::vector<double> hbuf(4 * (size_t)s);
     cudaEvent_t e0, e1;
     HODLR_TRY_CUDA(cudaEventCreate(&e0));
     HODLR_TRY_CUDA(cudaEventCreate(&e1));
@@ -939,6 +983,7 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         tail_grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->num_sms * per_sm));
     }
     IterGraph iter;
+    iter.c = c;
     long long body_kernels = 0;   // kernels of one recorded iteration
     {
         cudaStream_t cs = c->side[HODLR_SIDE_STREAMS - 1];
@@ -950,8 +995,18 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         cp.conditional.handle = handle;
         cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
-        cudaGraphNode_t cnode;
-        HODLR_TRY_CUDA(cudaGraphAddNode(&cnode, iter.graph, nullptr, nullptr, 0, &cp));
+        cudaGraphNode_t knode, cnode;
+        {
+            const int *na = gs.nactive;
+            void *kargs[] = {(void *)&na, (void *)&handle};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void *)cond_init_kernel;
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(1);
+            kp.kernelParams = kargs;
+            HODLR_TRY_CUDA(cudaGraphAddKernelNode(&knode, iter.graph, nullptr, 0, &kp));
+        }
+        HODLR_TRY_CUDA(cudaGraphAddNode(&cnode, iter.graph, &knode, nullptr, 1, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         HODLR_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         auto record = [&]() -> hodlr_status {
@@ -987,22 +1042,50 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         }
         HODLR_TRY_CUDA(cudaGraphInstantiate(&iter.exec, iter.graph, 0));
     }
+    // the host's view of each cycle comes in one copy (pinned unless s is huge)
+    const size_t rbytes = report_bytes(s);
+    std::vector<char> rep_pageable;
+    char *rep_host = reinterpret_cast<char *>(c->h_report);
+    if (rbytes > HODLR_REPORT_BYTES) {
+        rep_pageable.resize(rbytes);
+        rep_host = rep_pageable.data();
+    }
+    const int *rep_i = reinterpret_cast<const int *>(rep_host);
+    const double *rep_d = reinterpret_cast<const double *>(rep_host + report_doff(s));
+    auto read_report = [&]() -> hodlr_status {
+        cycle_report_kernel<<<1, 32, 0, st>>>(gs, s, nrm, c->d_status, loops, rep_dev);
+        note_launch();
+        HODLR_TRY_CUDA(cudaMemcpyAsync(rep_host, rep_dev, rbytes, cudaMemcpyDeviceToHost, st));
+        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+        return HODLR_OK;
+    };
     int restarts = 0;
     hodlr_status result = HODLR_OK;
+    bool reported = false;
     for (int cycle = 0;; ++cycle) {
         start_cycle_kernel<<<vgrid, KT, 0, st>>>(gs, m, s, Wv, n, n, nrm, Vk, vstride, tol, max_iter, cycle == 0, Zc);
         note_launch();
-        count_active_kernel<<<1, 1, 0, st>>>(gs.active, s, gs.nactive);
-        note_launch();
-        HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin, gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
-        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
-        if (cycle > 0) note_launch((long long)h_pin[1] * body_kernels);   // replays of the previous cycle
-        HODLR_TRY(take_status(c, st));
-        if (h_pin[0] == 0) break;
-        if (cycle > 0) ++restarts;
+        if (cycle > 0) {
+            // the first cycle is launched without waiting (its graph tests the
+            // count itself); later cycles read the report and stop here once
+            // every rhs has converged, with the results already on the host
+            HODLR_TRY_CUDA(cudaEventRecord(e1, st));
+            HODLR_TRY(read_report());
+            note_launch((long long)rep_i[2] * body_kernels);   // replays of the previous cycle
+            HODLR_TRY(status_word(rep_i[1]));
+            if (rep_i[0] == 0) {
+                reported = true;
+                break;
+            }
+            ++restarts;
+        } else {
+            count_active_kernel<<<1, 1, 0, st>>>(gs.active, s, gs.nactive);
+            note_launch();
+        }
         HODLR_TRY_CUDA(cudaMemsetAsync(loops, 0, sizeof(int), st));
         HODLR_TRY_CUDA(cudaGraphLaunch(iter.exec, st));
-        HODLR_TRY_CUDA(cudaMemcpyAsync(h_pin + 1, loops, sizeof(int), cudaMemcpyDeviceToHost, st));
+        note_launch();   // the graph's test of the count
+        if (cycle == 0) empty_graph_trash(c);   // earlier solves' graphs, while this one runs
         // x += Z y
         backsolve_kernel<<<dim3((unsigned)std::min<int64_t>((n + KT - 1) / KT, 64), s), KT, (size_t)m * 8, st>>>(
             gs, m, Zk, zstride, n, X, ldx);
@@ -1016,26 +1099,22 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         HODLR_TRY_CUDA(cudaGetLastError());
         if (cycle > 10000) break;
     }
-    HODLR_TRY_CUDA(cudaEventRecord(e1, st));
-    // final info
-    std::vector<int> iters(s);
-    HODLR_TRY_CUDA(cudaMemcpyAsync(iters.data(), gs.iters, s * sizeof(int), cudaMemcpyDeviceToHost, st));
-    HODLR_TRY_CUDA(cudaMemcpyAsync(hbuf.data(), gs.est, s * 8, cudaMemcpyDeviceToHost, st));
-    HODLR_TRY_CUDA(cudaMemcpyAsync(hbuf.data() + s, nrm, s * 8, cudaMemcpyDeviceToHost, st));
-    HODLR_TRY_CUDA(cudaMemcpyAsync(hbuf.data() + 2 * s, gs.bnorm, s * 8, cudaMemcpyDeviceToHost, st));
-    HODLR_TRY_CUDA(cudaStreamSynchronize(st));
-    HODLR_TRY(take_status(c, st));
+    if (!reported) {
+        HODLR_TRY_CUDA(cudaEventRecord(e1, st));
+        HODLR_TRY(read_report());
+        HODLR_TRY(status_word(rep_i[1]));
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int r = 0; r < s; ++r) {
-        const double bn = hbuf[2 * s + r];
-        const double tr = bn > 0.0 ? std::sqrt(hbuf[s + r]) / bn : 0.0;
+        const double bn = rep_d[2 * s + r];
+        const double tr = bn > 0.0 ? std::sqrt(rep_d[s + r]) / bn : 0.0;
         if (!(tr <= tol)) result = HODLR_NOT_CONVERGED;
         if (info) {
-            if (info->iters) info->iters[r] = iters[r];
-            if (info->est_relres) info->est_relres[r] = hbuf[r];
+            if (info->iters) info->iters[r] = rep_i[3 + r];
+            if (info->est_relres) info->est_relres[r] = rep_d[r];
             if (info->true_relres) info->true_relres[r] = tr;
         }
     }

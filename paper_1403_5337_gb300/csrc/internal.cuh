@@ -5,6 +5,9 @@
 #include <stdint.h>
 
 #include <string>
+#include <deque>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "hodlr.h"
@@ -60,6 +63,16 @@ struct LaunchCapture {
 
 #define HODLR_SIDE_STREAMS 8
 
+// A device block kept by the context after the library released it: reused by
+// the next request of the same rounded size (after an event wait when the new
+// stream differs from the one it was released on).
+struct hodlr_cached_block {
+    void *p;
+    size_t bytes;
+    cudaStream_t stream;
+    cudaEvent_t ev;
+};
+
 struct hodlr_ctx {
     int device = 0;
     int num_sms = 0;
@@ -70,7 +83,21 @@ struct hodlr_ctx {
     int *d_status = nullptr;      // device status word (one int)
     int *h_status = nullptr;      // pinned mirror
     int *h_scratch = nullptr;     // pinned, 64 ints: small device-to-host reads of the solver
+    void *h_report = nullptr;     // pinned, HODLR_REPORT_BYTES: the solver's per-cycle report
+    // cache of released device blocks by rounded size (bounded; flushed by
+    // hodlr_ctx_destroy); fifo: release order for eviction (entries of blocks
+    // handed out again are skipped)
+    std::unordered_map<size_t, std::vector<hodlr_cached_block>> cache;
+    std::deque<std::pair<void *, size_t>> fifo;
+    size_t cache_bytes = 0, cache_count = 0;
+    std::vector<cudaEvent_t> spare_events;
+    std::mutex cache_mu;
+    // executable graphs of finished solves, destroyed by the next solve once
+    // it has work queued (their teardown is host time) or by hodlr_ctx_destroy
+    std::vector<std::pair<cudaGraphExec_t, cudaGraph_t>> graph_trash;
 };
+#define HODLR_REPORT_BYTES 65536
+#define HODLR_CACHE_LIMIT (size_t(16) << 30)
 
 namespace hodlr {
 
@@ -85,6 +112,8 @@ struct DevBuf {
 
 // Read and clear the context's device status word (synchronises the stream).
 hodlr_status take_status(hodlr_ctx *c, cudaStream_t s);
+// The status (and error message) of a device status word already read.
+hodlr_status status_word(int w);
 
 // ------------------------------------------------------------------ tree
 // Level l (1..L) of the tree holds 2^l nodes; node i covers leaves

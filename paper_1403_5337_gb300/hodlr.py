@@ -171,10 +171,28 @@ def _check(code):
         raise HodlrError(code, msg)
 
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream):
     if stream is None:
+        if _raw_stream is not None:   # the current stream's handle without a Stream object
+            return C.c_void_p(_raw_stream(torch.cuda.current_device()))
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+_default_opts = None
+
+
+def _opts() -> "_Opts":
+    """A fresh copy of the library's default options (read from it once)."""
+    global _default_opts
+    if _default_opts is None:
+        o = _Opts()
+        load_library().hodlr_opts_default(C.byref(o))
+        _default_opts = bytes(o)
+    return _Opts.from_buffer_copy(_default_opts)
 
 
 def _mat(A: torch.Tensor, symmetric: bool) -> _Matrix:
@@ -321,8 +339,7 @@ def hodlr_build(ctx: Context, A: torch.Tensor, leaf: int, tol: float, method: st
     defer_factor, factor it level by level meanwhile: see include/hodlr.h."""
     lib = load_library()
     mat = _mat(A, symmetric)
-    o = _Opts()
-    lib.hodlr_opts_default(C.byref(o))
+    o = _opts()
     o.precision = _PREC[precision]
     o.compress_precision = -1 if compress_precision is None else _PREC[compress_precision]
     o.rank_cap = rank_cap
@@ -335,7 +352,7 @@ def hodlr_build(ctx: Context, A: torch.Tensor, leaf: int, tol: float, method: st
         o.leaf_bounds = lb.ctypes.data
         o.n_leaf_bounds = lb.shape[0]
     gp = None
-    if graph is not None:
+    if graph is not None and method == "bdlr":   # only BDLR reads the graph
         rp = np.ascontiguousarray(np.asarray(graph[0], dtype=np.int32))
         ci = np.ascontiguousarray(np.asarray(graph[1], dtype=np.int32))
         keep += [rp, ci]
@@ -415,8 +432,7 @@ def hodlr_build_batched(ctx: Context, As, leaves, tol: float, method: str = "aca
     nf = len(As)
     mats = (_Matrix * max(nf, 1))(*[_mat(A, symmetric) for A in As])
     lv = (C.c_int * max(nf, 1))(*[int(x) for x in leaves])
-    o = _Opts()
-    lib.hodlr_opts_default(C.byref(o))
+    o = _opts()
     o.precision = _PREC[precision]
     o.rank_cap = rank_cap
     out = (C.c_void_p * max(nf, 1))()
