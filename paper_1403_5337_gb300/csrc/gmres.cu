@@ -392,16 +392,19 @@ __global__ void cond_init_kernel(const int *nactive, cudaGraphConditionalHandle 
 // ------------------------------------------------------------------ fused Arnoldi step
 // After w = A z_j: classical Gram-Schmidt twice against v_0..v_j, the new basis
 // vector, the Givens update of the Hessenberg column and the loop test, in one
-// cooperative kernel with three software grid barriers (bounded waits).
+// cooperative kernel with two software grid barriers (bounded waits).
 // Work units are (128-row chunk, rhs); thread t of a unit owns one row.
 //   P1  Z(:, j) = z_j; h1 = V^T w                      (partial sums, atomics)
-//   P2  w -= V h1; h2 = V^T w
-//   P3  w -= V h2; ||w||^2;  CTA 0: H(:, j) = h1 + h2, h1 = 0
-//   P4  v_{j+1} = w / ||w|| (also the next apply's input), w = 0 (the next
-//       product accumulates into it); CTA 0: h2 = 0, Givens rotation of
-//       H(:, j), residual estimate, activity, loop condition
-// nrm is cleared by CTA 0 in P1 (it is only accumulated in P3).  The step j
-// and the activity of every rhs are fixed until CTA 0 advances them at the end.
+//   P2  w -= V h1; h2 = V^T w; ||w||^2
+//   P3  w -= V h2; v_{j+1} = w / ||w|| (also the next apply's input), w = 0
+//       (the next product accumulates into it), with ||w - V h2||^2 =
+//       ||w||^2 - ||h2||^2 (V orthonormal to working precision after the first
+//       pass; ||h2|| << ||w||, so the difference loses nothing); CTA 0 first
+//       H(:, j) = h1 + h2, h1 = 0, then the Givens rotation of H(:, j), the
+//       residual estimate, activity and the loop condition
+// nrm and h2 are cleared by CTA 0 in P1 (they are only accumulated in P2).  The
+// step j and the activity of every rhs are fixed until CTA 0 advances them at
+// the end.
 constexpr int TT = 128;   // one warp per SM sub-partition: the FP64 reductions are pipe-bound
 constexpr int TW = TT / 32;
 constexpr unsigned long long TAIL_SPIN_LIMIT = 1ull << 26;
@@ -524,8 +527,11 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
     }
     __syncthreads();
     // ---- P1: Z(:, j) = z_j; h1 = V^T w
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int r = threadIdx.x; r < a.s; r += TT) a.nrm[r] = 0.0;
+        for (int r = 0; r < a.s; ++r)
+            for (int i = threadIdx.x; i <= sj[r]; i += TT) a.h2[(int64_t)r * a.hstride + i] = 0.0;
+    }
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int r = (int)(u / chunks);
         if (!sa[r]) continue;
@@ -540,7 +546,7 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
         unit_gram(a.Vk + r * a.vstride, a.n, q, own, x, j, a.h1 + (int64_t)r * a.hstride, part, lane, warp);
     }
     tail_grid_sync(a.bar, a.status);
-    // ---- P2: w -= V h1; h2 = V^T w
+    // ---- P2: w -= V h1; h2 = V^T w; ||w||^2
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int r = (int)(u / chunks);
         if (!sa[r]) continue;
@@ -557,23 +563,6 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
             a.w[q + r * a.n] = x;
         }
         unit_gram(V, a.n, q, own, x, j, a.h2 + (int64_t)r * a.hstride, part, lane, warp);
-    }
-    tail_grid_sync(a.bar, a.status);
-    // ---- P3: w -= V h2; ||w||^2
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-        const int r = (int)(u / chunks);
-        if (!sa[r]) continue;
-        const int j = sj[r];
-        const int64_t q = (u % chunks) * TT + threadIdx.x;
-        const double *V = a.Vk + r * a.vstride;
-        for (int i = threadIdx.x; i <= j; i += TT) hs[i] = __ldcg(a.h2 + (int64_t)r * a.hstride + i);
-        __syncthreads();
-        double x = 0.0;
-        if (q < a.n) {
-            x = a.w[q + r * a.n];
-            for (int i = 0; i <= j; ++i) x = fma(-hs[i], V[(int64_t)i * a.n + q], x);
-            a.w[q + r * a.n] = x;
-        }
         double p = x * x;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
@@ -587,8 +576,9 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
         }
         __syncthreads();
     }
+    tail_grid_sync(a.bar, a.status);
     if (blockIdx.x == 0) {
-        // H(:, j) = h1 + h2 (h2 is complete: P2 ended at the barrier); h1 is no longer read
+        // H(:, j) = h1 + h2 (both complete); h1 is no longer read
         for (int r = 0; r < a.s; ++r) {
             if (!sa[r]) continue;
             const int j = sj[r];
@@ -599,21 +589,26 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
             }
         }
     }
-    tail_grid_sync(a.bar, a.status);
-    // ---- P4: v_{j+1} = w / ||w||; w = 0
+    // ---- P3: w -= V h2; v_{j+1} = w / ||w||; w = 0
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int r = (int)(u / chunks);
         if (!sa[r]) continue;
         const int j = sj[r];
         const int64_t q = (u % chunks) * TT + threadIdx.x;
+        const double *V = a.Vk + r * a.vstride;
+        for (int i = threadIdx.x; i <= j; i += TT) hs[i] = __ldcg(a.h2 + (int64_t)r * a.hstride + i);
+        __syncthreads();
         if (threadIdx.x == 0) {
-            const double nr = sqrt(__ldcg(a.nrm + r));
-            s_inv = nr > 0.0 ? 1.0 / nr : 0.0;
+            double h2n = 0.0;
+            for (int i = 0; i <= j; ++i) h2n += hs[i] * hs[i];
+            const double nw2 = __ldcg(a.nrm + r) - h2n;
+            s_inv = nw2 > 0.0 ? 1.0 / sqrt(nw2) : 0.0;
         }
         __syncthreads();
         const double inv = s_inv;
         if (q < a.n) {
-            const double x = a.w[q + r * a.n];
+            double x = a.w[q + r * a.n];
+            for (int i = 0; i <= j; ++i) x = fma(-hs[i], V[(int64_t)i * a.n + q], x);
             if (inv > 0.0) {
                 const double v = x * inv;
                 a.Vk[r * a.vstride + (int64_t)(j + 1) * a.n + q] = v;
@@ -631,12 +626,14 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
     for (int r = threadIdx.x; r < a.s; r += TT) {
         if (!sa[r]) continue;
         const int j = sj[r];
-        double *h2r = a.h2 + (int64_t)r * a.hstride;
-        for (int i = 0; i <= j; ++i) h2r[i] = 0.0;
+        const double *h2r = a.h2 + (int64_t)r * a.hstride;
+        double h2n = 0.0;
+        for (int i = 0; i <= j; ++i) h2n += __ldcg(h2r + i) * __ldcg(h2r + i);
         double *Hc = a.gs.H + (int64_t)r * (a.m + 1) * a.m + (int64_t)j * (a.m + 1);
         double *cs = a.gs.cs + (int64_t)r * a.m, *sn = a.gs.sn + (int64_t)r * a.m;
         double *g = a.gs.g + (int64_t)r * (a.m + 1);
-        const double hn = sqrt(__ldcg(a.nrm + r));
+        const double nw2 = __ldcg(a.nrm + r) - h2n;
+        const double hn = nw2 > 0.0 ? sqrt(nw2) : 0.0;
         Hc[j + 1] = hn;
         for (int i = 0; i < j; ++i) {
             const double t = cs[i] * Hc[i] + sn[i] * Hc[i + 1];
