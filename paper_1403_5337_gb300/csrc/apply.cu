@@ -71,6 +71,7 @@ struct FusedArgs {
     const int64_t *bounds;
     const double *Xin;
     double *X;
+    float2 *Xs;        // optional: X also as FP32 (hi, lo) pairs, ld ldx (the product's split input)
     int *status;
 };
 
@@ -243,6 +244,17 @@ __device__ void stage_cols(X *dst, const X *src, int64_t ld, int cols, int nrows
     }
 }
 
+// X(o) = v in FP64, and (if requested) its FP32 (hi, lo) split for the product
+// that follows: exact for an FP32 v (lo = 0), round-to-nearest parts for FP64.
+template <typename T, typename S>
+__device__ __forceinline__ void store_x(const FusedArgs<T, S> &a, int64_t o, T v) {
+    a.X[o] = (double)v;
+    if (a.Xs) {
+        const float hi = (float)v;
+        a.Xs[o] = make_float2(hi, (float)((double)v - (double)hi));
+    }
+}
+
 template <typename T, typename S, int RC>
 __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs<T, S> a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -313,7 +325,7 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
                 if (li < nrows) {
                     const T v = warp_parts_sum<T, RC>(part, li, q);
                     a.xt[row0 + li + (r0 + q) * a.ldn] = v;
-                    if (L == 0) a.X[row0 + li + (r0 + q) * a.ldx] = (double)v;
+                    if (L == 0) store_x(a, row0 + li + (r0 + q) * a.ldx, v);
                 }
             }
             __syncthreads();
@@ -371,7 +383,7 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
                             const int64_t o = row0 + li + (int64_t)(r0 + q) * a.ldn;
                             const T v = a.xt[o] - warp_parts_sum<T, RC>(part, li, q);
                             a.xt[o] = v;
-                            if (c == 1) a.X[row0 + li + (int64_t)(r0 + q) * a.ldx] = (double)v;
+                            if (c == 1) store_x(a, row0 + li + (int64_t)(r0 + q) * a.ldx, v);
                         }
                     }
                     __syncthreads();
@@ -379,7 +391,8 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
                     for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
                         const int li = e % TR, q = e / TR;
                         if (li < nrows)
-                            a.X[row0 + li + (int64_t)(r0 + q) * a.ldx] = (double)a.xt[row0 + li + (int64_t)(r0 + q) * a.ldn];
+                            store_x(a, row0 + li + (int64_t)(r0 + q) * a.ldx,
+                                    a.xt[row0 + li + (int64_t)(r0 + q) * a.ldn]);
                     }
                 }
                 if (c > 1) fa_vtx<T, S, RC>(a, c - 1, leaf >> (L - c + 1), row0, nrows, r0, rr, sv, xs, stg);
@@ -395,7 +408,7 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a, cudaStream
 template <typename T, typename S>
 hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st,
                          const std::vector<void *> &V, const std::vector<void *> &E, const float *const *vsc,
-                         const float *const *esc) {
+                         const float *const *esc, float2 *Xs) {
     hodlr_t *hm = const_cast<hodlr_t *>(h);
     HODLR_TRY(solve_prepare(h, s, st));
     const int L = h->L;
@@ -442,6 +455,7 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
     // single leaf (L = 0) reads its input from a copy.
     a.Xin = X;
     a.ldxin = ldx;
+    a.Xs = Xs;
     if (L == 0) {
         double *cp = reinterpret_cast<double *>(zp);
         HODLR_TRY_CUDA(cudaMemcpy2DAsync(cp, h->ldn * sizeof(double), X, ldx * sizeof(double), h->n * sizeof(double),
@@ -517,13 +531,13 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a0, cudaStrea
 
 }  // namespace
 
-hodlr_status solve_impl(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st) {
-    if (h->prec == HODLR_FP64) return solve_fused<double, double>(h, s, X, ldx, st, h->Vl, h->El, nullptr, nullptr);
+hodlr_status solve_impl(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st, float2 *Xs) {
+    if (h->prec == HODLR_FP64) return solve_fused<double, double>(h, s, X, ldx, st, h->Vl, h->El, nullptr, nullptr, Xs);
     if (h->store == HODLR_BF16)
-        return solve_fused<float, __nv_bfloat16>(h, s, X, ldx, st, h->Vql, h->Eql, nullptr, nullptr);
+        return solve_fused<float, __nv_bfloat16>(h, s, X, ldx, st, h->Vql, h->Eql, nullptr, nullptr, Xs);
     if (h->store == HODLR_FP16)
-        return solve_fused<float, __half>(h, s, X, ldx, st, h->Vql, h->Eql, h->vscale.data(), h->escale.data());
-    return solve_fused<float, float>(h, s, X, ldx, st, h->Vl, h->El, nullptr, nullptr);
+        return solve_fused<float, __half>(h, s, X, ldx, st, h->Vql, h->Eql, h->vscale.data(), h->escale.data(), Xs);
+    return solve_fused<float, float>(h, s, X, ldx, st, h->Vl, h->El, nullptr, nullptr, Xs);
 }
 
 // Allocate the apply's workspace for s right-hand sides ahead of time (the

@@ -674,14 +674,16 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
 
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s, const double *Z, int64_t ldz,
                          double *W, int64_t ldw, cudaStream_t st, void *work, bool w_zeroed, float2 *Asp,
-                         const int *split_state) {
+                         const int *split_state, bool z_split) {
     if (n == 0 || s == 0) return HODLR_OK;
     float2 *zs = work ? reinterpret_cast<float2 *>(work)
                       : reinterpret_cast<float2 *>(dalloc(c, (size_t)n * s * sizeof(float2), st));
     if (!zs) return HODLR_OUT_OF_MEMORY;
-    int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
-    split_vec_kernel<<<blocks, 256, 0, st>>>(Z, ldz, n, s, zs);
-    note_launch();
+    if (!(z_split && work)) {
+        int blocks = (int)std::min<int64_t>((n * s + 255) / 256, 4096);
+        split_vec_kernel<<<blocks, 256, 0, st>>>(Z, ldz, n, s, zs);
+        note_launch();
+    }
     cudaError_t e = w_zeroed ? cudaSuccess : cudaMemset2DAsync(W, ldw * sizeof(double), 0, n * sizeof(double), s, st);
     const dim3 grid((unsigned)((n + MV_ROWS - 1) / MV_ROWS), (unsigned)((n + MV_KC - 1) / MV_KC));
     const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
@@ -1007,8 +1009,9 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         HODLR_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         auto record = [&]() -> hodlr_status {
-            if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs));
-            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state));
+            // the apply also leaves z split into FP32 pairs for the product
+            if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs, reinterpret_cast<float2 *>(zsw)));
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state, P != nullptr));
             ta.handle = handle;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)tail_grid);

@@ -250,14 +250,17 @@ hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s, const cudaEvent_t *sha
 // Explicit inverses of the leaf blocks of A (stream-ordered; h->leafinv allocated).
 hodlr_status leaf_inverses(hodlr_t *h, cudaStream_t s);
 void free_plan(hodlr_t *h, cudaStream_t s);
-hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s);
+// Xs (optional): also store the result as FP32 (hi, lo) pairs (ld ldx), the
+// split the product reads.
+hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s, float2 *Xs = nullptr);
 hodlr_status solve_prepare(const hodlr_t *h, int s_rhs, cudaStream_t s);
 // Asp / split_state: optional n x n buffer of A's FP32 (hi, lo) pairs, written by
 // the first product while *split_state is 0 and read by later ones.
+// z_split: work already holds the FP32 split of Z (ld n), written by the apply.
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s_rhs,
                          const double *Z, int64_t ldz, double *W, int64_t ldw, cudaStream_t s,
                          void *work = nullptr, bool w_zeroed = false, float2 *Asp = nullptr,
-                         const int *split_state = nullptr);
+                         const int *split_state = nullptr, bool z_split = false);
 
 // Convert / pad kernels
 hodlr_status copy_columns(int prec_src, int prec_dst, const void *src, int64_t ld_src,

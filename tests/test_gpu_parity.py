@@ -200,10 +200,10 @@ def test_launch_count_covers_replayed_iterations(H, ctx, front576):
     c1 = H.hodlr_launch_count()
     it = int(info.iters.max())
     assert info.converged and it >= 2
-    # per replayed iteration: the apply, the split of z, the product, the fused
-    # Arnoldi step; per cycle at least the start, the back substitution, the
-    # true-residual product and the residual
-    assert c1 - c0 >= 4 * it + 4
+    # per replayed iteration: the apply (which also splits z for the product),
+    # the product, the fused Arnoldi step; per cycle at least the start, the
+    # back substitution, the true-residual product and the residual
+    assert c1 - c0 >= 3 * it + 4
     h.close()
 
 
