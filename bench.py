@@ -36,6 +36,8 @@ DTYPE = {"fp32": "f32+f64", "bf16": "bf16+f32+f64", "fp16": "f16+f32+f64", "fp64
 WORKLOADS = {
     "plane4096": dict(nx=64, ny=64, below=32, above=32, field="lognormal", sigma=0.5, leaf=128, seed=0, nrhs=4),
     "plane576": dict(nx=24, ny=24, below=8, above=8, field="lognormal", sigma=0.5, leaf=64, seed=0, nrhs=1),
+    # the large front (run with --precision fp16 --tol 1e-3 --no-cpu-baseline)
+    "plane32768": dict(nx=128, ny=256, below=4, above=4, field="lognormal", sigma=0.5, leaf=256, seed=0, nrhs=32),
 }
 
 
