@@ -66,6 +66,25 @@ __device__ __forceinline__ void df_acc(DF &acc, float ah, float al, float zh, fl
     acc.c += err + t;
 }
 
+// The same with zl = 0 (z exactly an FP32 value: the output of an FP32 apply).
+__device__ __forceinline__ void df_acc_z(DF &acc, float ah, float al, float zh) {
+    const float p = ah * zh;
+    const float t = fmaf(al, zh, fmaf(ah, zh, -p));
+    const float s = acc.s + p;
+    const float bp = s - acc.s;
+    const float err = (acc.s - (s - bp)) + (p - bp);
+    acc.s = s;
+    acc.c += err + t;
+}
+
+template <bool ZF>
+__device__ __forceinline__ void df_term(DF &acc, float ah, float al, float zh, float zl) {
+    if constexpr (ZF)
+        df_acc_z(acc, ah, al, zh);
+    else
+        df_acc(acc, ah, al, zh, zl);
+}
+
 constexpr int MV_THREADS = 256;
 constexpr int MV_WARPS = MV_THREADS / 32;
 constexpr int MV_RPW = 2;            // rows per warp
@@ -97,7 +116,8 @@ __global__ void split_vec_kernel(const double *__restrict__ Z, int64_t ldz, int6
 // is 1 (set by the Arnoldi step that follows the first product of a solve)
 // it reads the pairs instead of A and skips the split -- the same FP32 parts,
 // so the same products.
-template <bool VEC>
+// ZF: every z of this launch has a zero low part (z is exactly FP32).
+template <bool VEC, bool ZF>
 __global__ void __launch_bounds__(MV_THREADS, 4)
     df_matvec_kernel(const double *__restrict__ A, int64_t n, int64_t lda, const float2 *__restrict__ zs,
                      int s, int r0, double *__restrict__ W, int64_t ldw, int *status, float2 *__restrict__ Asp,
@@ -145,8 +165,8 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
                     const float4 z = reinterpret_cast<const float4 *>(zsm[q])[p];
 #pragma unroll
                     for (int a = 0; a < MV_RPW; ++a) {
-                        df_acc(acc[a][q], hv[a][u].x, hv[a][u].y, z.x, z.y);
-                        df_acc(acc[a][q], hv[a][u].z, hv[a][u].w, z.z, z.w);
+                        df_term<ZF>(acc[a][q], hv[a][u].x, hv[a][u].y, z.x, z.y);
+                        df_term<ZF>(acc[a][q], hv[a][u].z, hv[a][u].w, z.z, z.w);
                     }
                 }
             }
@@ -159,7 +179,7 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
                 if (row >= n) continue;
                 const float2 hl = Asp[row * n + k0 + kk];
 #pragma unroll
-                for (int q = 0; q < MV_S; ++q) df_acc(acc[a][q], hl.x, hl.y, zsm[q][kk].x, zsm[q][kk].y);
+                for (int q = 0; q < MV_S; ++q) df_term<ZF>(acc[a][q], hl.x, hl.y, zsm[q][kk].x, zsm[q][kk].y);
             }
         }
     } else if (VEC) {
@@ -191,8 +211,8 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
 #pragma unroll
                     for (int q = 0; q < MV_S; ++q) {
                         const float4 z = reinterpret_cast<const float4 *>(zsm[q])[p];
-                        df_acc(acc[a][q], h0, l0, z.x, z.y);
-                        df_acc(acc[a][q], h1, l1, z.z, z.w);
+                        df_term<ZF>(acc[a][q], h0, l0, z.x, z.y);
+                        df_term<ZF>(acc[a][q], h1, l1, z.z, z.w);
                     }
                 }
             }
@@ -207,7 +227,7 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
                 split_entry(A[row * lda + k0 + kk], h0, l0, bad);
                 if (smode == 1) Asp[row * n + k0 + kk] = make_float2(h0, l0);
 #pragma unroll
-                for (int q = 0; q < MV_S; ++q) df_acc(acc[a][q], h0, l0, zsm[q][kk].x, zsm[q][kk].y);
+                for (int q = 0; q < MV_S; ++q) df_term<ZF>(acc[a][q], h0, l0, zsm[q][kk].x, zsm[q][kk].y);
             }
         }
     } else {
@@ -230,7 +250,7 @@ __global__ void __launch_bounds__(MV_THREADS, 4)
                     float h0, l0;
                     split_entry(av[a][u], h0, l0, bad);
 #pragma unroll
-                    for (int q = 0; q < MV_S; ++q) df_acc(acc[a][q], h0, l0, zsm[q][kk].x, zsm[q][kk].y);
+                    for (int q = 0; q < MV_S; ++q) df_term<ZF>(acc[a][q], h0, l0, zsm[q][kk].x, zsm[q][kk].y);
                 }
             }
         }
@@ -674,7 +694,7 @@ __global__ void __launch_bounds__(TT) arnoldi_tail_kernel(TailArgs a) {
 
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s, const double *Z, int64_t ldz,
                          double *W, int64_t ldw, cudaStream_t st, void *work, bool w_zeroed, float2 *Asp,
-                         const int *split_state, bool z_split) {
+                         const int *split_state, bool z_split, bool z_fp32) {
     if (n == 0 || s == 0) return HODLR_OK;
     float2 *zs = work ? reinterpret_cast<float2 *>(work)
                       : reinterpret_cast<float2 *>(dalloc(c, (size_t)n * s * sizeof(float2), st));
@@ -690,11 +710,15 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
     if (!vec || n % 2 != 0) Asp = nullptr;   // the split buffer is read as 16-byte pairs of columns
     for (int r0 = 0; r0 < s && e == cudaSuccess; r0 += MV_S) {
         if (vec)
-            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status, Asp,
-                                                                split_state);
+            if (z_fp32)
+                df_matvec_kernel<true, true><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status,
+                                                                          Asp, split_state);
+            else
+                df_matvec_kernel<true, false><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status,
+                                                                           Asp, split_state);
         else
-            df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status, nullptr,
-                                                                 nullptr);
+            df_matvec_kernel<false, false><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status,
+                                                                        nullptr, nullptr);
         note_launch();
         e = cudaGetLastError();
     }
@@ -785,11 +809,11 @@ extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_matrix *A, int s, const
     const bool vec = (A->ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(A->data) & 15) == 0);
     for (int r0 = 0; r0 < s; r0 += MV_S) {
         if (vec)
-            df_matvec_kernel<true><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw, slot.status,
-                                                                nullptr, nullptr);
+            df_matvec_kernel<true, false><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw,
+                                                                       slot.status, nullptr, nullptr);
         else
-            df_matvec_kernel<false><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw,
-                                                                 slot.status, nullptr, nullptr);
+            df_matvec_kernel<false, false><<<grid, MV_THREADS, 0, st>>>(A->data, n, A->ld, slot.split, s, r0, W, ldw,
+                                                                        slot.status, nullptr, nullptr);
         note_launch();
     }
     HODLR_TRY_CUDA(cudaGetLastError());
@@ -1011,7 +1035,8 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         auto record = [&]() -> hodlr_status {
             // the apply also leaves z split into FP32 pairs for the product
             if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs, reinterpret_cast<float2 *>(zsw)));
-            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state, P != nullptr));
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state, P != nullptr,
+                                  P != nullptr && P->prec != HODLR_FP64));
             ta.handle = handle;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)tail_grid);

@@ -256,11 +256,12 @@ hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cud
 hodlr_status solve_prepare(const hodlr_t *h, int s_rhs, cudaStream_t s);
 // Asp / split_state: optional n x n buffer of A's FP32 (hi, lo) pairs, written by
 // the first product while *split_state is 0 and read by later ones.
-// z_split: work already holds the FP32 split of Z (ld n), written by the apply.
+// z_split: work already holds the FP32 split of Z (ld n), written by the apply;
+// z_fp32: every entry of Z is exactly an FP32 value (zero low parts).
 hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, int s_rhs,
                          const double *Z, int64_t ldz, double *W, int64_t ldw, cudaStream_t s,
                          void *work = nullptr, bool w_zeroed = false, float2 *Asp = nullptr,
-                         const int *split_state = nullptr, bool z_split = false);
+                         const int *split_state = nullptr, bool z_split = false, bool z_fp32 = false);
 
 // Convert / pad kernels
 hodlr_status copy_columns(int prec_src, int prec_dst, const void *src, int64_t ld_src,
