@@ -305,6 +305,43 @@ def test_gmres_multi_rhs_on_dirty_memory(H, ctx, front576):
     h.close()
 
 
+def test_gmres_restarts_six_rhs(H, ctx, front576):
+    """Restarted GMRES (several cycles: the per-cycle report, the stored split
+    of A kept across cycles) with six right-hand sides (two launches per
+    product): same solution as the unrestarted solve."""
+    F = front576
+    A = _dev(F.A)
+    b = fg.rhs(F.n, 6, seed=8)
+    h = H.hodlr_build(ctx, A, 64, 1e-3, "aca", precision="fp32")
+    X1, i1 = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    X2, i2 = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12, restart=2)
+    assert i1.converged and i2.converged
+    assert i2.restarts >= 1 and np.all(i2.true_relres <= 1e-12)
+    ref = np.linalg.solve(F.A, b)
+    for X in (X1, X2):
+        assert np.linalg.norm(X.cpu().numpy().T - ref) / np.linalg.norm(ref) < 1e-9
+    h.close()
+
+
+def test_streams_and_block_reuse(H, ctx, front576):
+    """Build, solve and destroy on alternating streams: released blocks are
+    reused across streams (ordered by their events); every solve is exact."""
+    F = front576
+    A = _dev(F.A)
+    b = fg.rhs(F.n, 2, seed=9)
+    ref = np.linalg.solve(F.A, b)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for st in (s1, s2, s1, s2):
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            h = H.hodlr_build(ctx, A, 64, 1e-6, "aca", precision="fp32")
+            X, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+            h.close()
+        st.synchronize()
+        assert info.converged
+        assert np.linalg.norm(X.cpu().numpy().T - ref) / np.linalg.norm(ref) < 1e-9
+
+
 def test_gmres_unpreconditioned_and_nonconvergence(H, ctx, front576):
     F = front576
     b = fg.rhs(F.n, 1, seed=1)
