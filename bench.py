@@ -214,10 +214,16 @@ def run_batch(args):
     ctx = H.Context(0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def step():
+    def step(marks=None):
         hs = H.hodlr_build_batched(ctx, As, leaves, args.tol, "aca", precision=args.precision)
+        if marks:
+            marks[0].record()
         H.hodlr_factor_batched(hs)
+        if marks:
+            marks[1].record()
         res = H.gmres_solve_batched(ctx, As, Bs, hs, tol=1e-12)
+        if marks:
+            marks[2].record()
         for h in hs:
             h.close()
         return res
@@ -227,17 +233,22 @@ def run_batch(args):
     torch.cuda.synchronize()
     l0 = H.hodlr_launch_count()
     tot = 0.0
+    ph = np.zeros(4)
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e0.record()
-        res = step()
+        res = step(marks)
         e1.record()
         torch.cuda.synchronize()
         tot += e0.elapsed_time(e1)
+        ev = [e0] + marks + [e1]
+        ph += [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
     l1 = H.hodlr_launch_count()
     ms = tot / args.steps
+    ph /= args.steps
     its = np.array([int(r[1].iters[0]) for r in res])
     tr = np.array([float(r[1].true_relres[0]) for r in res])
     line = {"metric": METRIC, "value": ms / len(As), "unit": "ms", "n_gpus": 1, "steps": args.steps,
@@ -249,7 +260,9 @@ def run_batch(args):
                        "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas x1"},
             "converged": bool(np.all(tr <= 1e-12)), "iters_max": int(its.max()), "iters_mean": float(its.mean()),
             "true_relres_max": float(tr.max()), "gpu_launches": l1 - l0,
-            "gpu_launches_per_step": (l1 - l0) / args.steps}
+            "gpu_launches_per_step": (l1 - l0) / args.steps,
+            "phases_ms": {"build_batched": ph[0], "factor_batched": ph[1], "gmres_solve_batched": ph[2],
+                          "close": ph[3]}}
     print(json.dumps(line))
 
 

@@ -214,7 +214,9 @@ hodlr_status hodlr_factor_batched(int nf, hodlr_t *const *h, hodlr_stream stream
  * ldx[f]; P[f] its preconditioner (or NULL, or P itself NULL for none).  info
  * may be NULL or hold nf entries (each with arrays of s[f] entries).  Returns
  * HODLR_NOT_CONVERGED if any front misses tol (all fronts are still solved).
- * Synchronises `stream`. */
+ * Fronts are set up and their first cycles enqueued in windows with one host
+ * wait per window, so a front that restarts has an info.ms_total that also spans
+ * later fronts' first cycles.  Synchronises `stream`. */
 hodlr_status gmres_solve_batched(hodlr_ctx *ctx, int nf, const hodlr_matrix *A, const int *s,
                                  const double *const *B, const int64_t *ldb, double *const *X,
                                  const int64_t *ldx, const hodlr_t *const *P, double tol, int max_iter,

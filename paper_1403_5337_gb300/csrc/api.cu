@@ -400,8 +400,12 @@ hodlr_status hodlr_destroy(hodlr_t *h) {
     return HODLR_OK;
 }
 
-hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double tol, int method, const hodlr_graph *g,
-                         const hodlr_opts *o_in, hodlr_stream stream, hodlr_t **out) {
+// One front.  With sync_leaf_status false a single-leaf front returns without
+// reading the status word (its compression is empty); the caller reads it once
+// for a whole batch.
+static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double tol, int method,
+                              const hodlr_graph *g, const hodlr_opts *o_in, hodlr_stream stream, hodlr_t **out,
+                              bool sync_leaf_status) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!c || !out) {
         set_error("hodlr_build: NULL context or output");
@@ -880,7 +884,8 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     // synchronising call)
     {
         int w = aca_status;
-        if (L == 0 && (cudaMemcpyAsync(&w, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (L == 0 && sync_leaf_status &&
+            (cudaMemcpyAsync(&w, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                        cudaStreamSynchronize(st) != cudaSuccess)) {
             cudaDeviceSynchronize();
             drop_events();
@@ -904,6 +909,11 @@ hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double t
     return HODLR_OK;
 }
 
+hodlr_status hodlr_build(hodlr_ctx *c, const hodlr_matrix *A, int leaf, double tol, int method, const hodlr_graph *g,
+                         const hodlr_opts *o_in, hodlr_stream stream, hodlr_t **out) {
+    return build_one(c, A, leaf, tol, method, g, o_in, stream, out, true);
+}
+
 hodlr_status hodlr_build_batched(hodlr_ctx *c, int nf, const hodlr_matrix *A, const int *leaf, double tol,
                                  int method, const hodlr_opts *o, hodlr_stream stream, hodlr_t **out) {
     if (!c || nf < 0 || (nf > 0 && (!A || !leaf || !out))) {
@@ -915,13 +925,32 @@ hodlr_status hodlr_build_batched(hodlr_ctx *c, int nf, const hodlr_matrix *A, co
         return HODLR_INVALID_ARG;
     }
     for (int f = 0; f < nf; ++f) out[f] = nullptr;
+    auto destroy_all = [&](int upto) {
+        for (int q = 0; q < upto; ++q) {
+            hodlr_destroy(out[q]);
+            out[q] = nullptr;
+        }
+    };
     for (int f = 0; f < nf; ++f) {
-        const hodlr_status r = hodlr_build(c, &A[f], leaf[f], tol, method, nullptr, o, stream, &out[f]);
+        const hodlr_status r = build_one(c, &A[f], leaf[f], tol, method, nullptr, o, stream, &out[f], false);
         if (r != HODLR_OK) {
-            for (int q = 0; q < f; ++q) {
-                hodlr_destroy(out[q]);
-                out[q] = nullptr;
-            }
+            destroy_all(f);
+            return r;
+        }
+    }
+    if (nf > 0) {
+        // the single-leaf fronts' non-finite / range checks, for the batch at once
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        int w = 0;
+        if (cudaMemcpyAsync(&w, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("hodlr_build_batched: %s", cudaGetErrorString(cudaGetLastError()));
+            destroy_all(nf);
+            return HODLR_CUDA_ERROR;
+        }
+        if (w & (ST_NONFINITE | ST_RANGE | ST_TIMEOUT)) {
+            const hodlr_status r = take_status(c, st);
+            destroy_all(nf);
             return r;
         }
     }

@@ -16,6 +16,7 @@
 // about 2^-48, comparable to an FP64 dot product's accumulated rounding.
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -867,148 +868,197 @@ struct GmresBufs {
     }
 };
 
-}  // namespace
+// One GMRES solve (one front): its buffers, the recorded iteration graph and
+// the host's view of the last cycle report.  setup() validates and launches
+// nothing that depends on the host; first_cycle() and next_cycle() enqueue a
+// cycle and its report without waiting, take_report() reads the report once
+// the stream has passed it, finish() fills the info and gives the result.
+struct GmresJob {
+    hodlr_ctx *c = nullptr;
+    const hodlr_matrix *A = nullptr;
+    int s = 0;
+    const double *B = nullptr;
+    int64_t ldb = 0;
+    double *X = nullptr;
+    int64_t ldx = 0;
+    const hodlr_t *P = nullptr;
+    double tol = 0.0;
+    int max_iter = 0, m = 0;
+    cudaStream_t st = nullptr;
 
-extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, const double *B, int64_t ldb,
-                                    double *X, int64_t ldx, const hodlr_t *P, double tol, int max_iter, int restart,
-                                    hodlr_gmres_info *info, hodlr_stream stream) {
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!c || !A || !A->data || !B || !X || s <= 0 || A->n <= 0 || A->ld < A->n || ldb < A->n || ldx < A->n ||
-        max_iter <= 0 || !(tol > 0.0) || restart < 0) {
-        set_error("gmres_solve: invalid argument");
-        return HODLR_INVALID_ARG;
-    }
-    if (P && (P->n != A->n)) {
-        set_error("gmres_solve: preconditioner size %lld != %lld", (long long)P->n, (long long)A->n);
-        return HODLR_INVALID_ARG;
-    }
-    if (P && !P->factored) {
-        set_error("gmres_solve: preconditioner not factored");
-        return HODLR_NOT_FACTORED;
-    }
-    HODLR_TRY_CUDA(cudaSetDevice(c->device));
-    const int64_t n = A->n;
-    const int m = restart > 0 ? std::min(restart, max_iter) : max_iter;
-    const int64_t vstride = n * (m + 1), zstride = n * m;
-    const int hstride = m + 1;
-    // every work buffer in one allocation
-    Arena ar;
-    const size_t oVk = ar.take((size_t)vstride * s * 8), oZk = ar.take((size_t)zstride * s * 8),
-                 oWv = ar.take((size_t)n * s * 8), oh1 = ar.take((size_t)s * hstride * 8),
-                 oh2 = ar.take((size_t)s * hstride * 8), onrm = ar.take((size_t)s * 8),
-                 oH = ar.take((size_t)s * (m + 1) * m * 8), ocs = ar.take((size_t)s * m * 8),
-                 osn = ar.take((size_t)s * m * 8), og = ar.take((size_t)s * (m + 1) * 8), obn = ar.take((size_t)s * 8),
-                 oest = ar.take((size_t)s * 8), oib = ar.take((size_t)(4 * s + 4) * sizeof(int)),
-                 ozs = ar.take((size_t)n * s * sizeof(float2)), oZc = ar.take((size_t)n * s * 8), olp = ar.take(256),
-                 osst = ar.take(256), orep = ar.take(report_bytes(s));
+    int64_t n = 0, vstride = 0, zstride = 0;
+    int hstride = 0;
     GmresBufs bufs;
-    bufs.c = c;
-    bufs.st = st;
-    char *base = (char *)bufs.get(ar.bytes);
-    if (!base) {
-        set_error("gmres_solve: out of device memory (%zu bytes)", ar.bytes);
-        return HODLR_OUT_OF_MEMORY;
-    }
-    double *Vk = (double *)(base + oVk);
-    double *Zk = (double *)(base + oZk);
-    double *Wv = (double *)(base + oWv);
-    double *h1 = (double *)(base + oh1);
-    double *h2 = (double *)(base + oh2);
-    double *nrm = (double *)(base + onrm);
-    GState gs;
-    gs.H = (double *)(base + oH);
-    gs.cs = (double *)(base + ocs);
-    gs.sn = (double *)(base + osn);
-    gs.g = (double *)(base + og);
-    gs.bnorm = (double *)(base + obn);
-    gs.est = (double *)(base + oest);
-    int *ibuf = (int *)(base + oib);
-    void *zsw = base + ozs;
-    double *Zc = (double *)(base + oZc);
-    int *loops = (int *)(base + olp);
-    // A's FP32 (hi, lo) pairs for the products after the first (ld n; skipped
-    // when A's rows are not 16-byte aligned, n is odd, the buffer would exceed
-    // 16 GiB or cannot be allocated: the products then split A every time)
-    int *split_state = (int *)(base + osst);
-    char *rep_dev = base + orep;
+    IterGraph iter;
+    GState gs{};
+    TailArgs ta{};
+    double *Vk = nullptr, *Zk = nullptr, *Wv = nullptr, *nrm = nullptr, *Zc = nullptr;
+    void *zsw = nullptr;
+    int *loops = nullptr, *split_state = nullptr;
+    char *rep_dev = nullptr;
     float2 *Asp = nullptr;
-    if (n % 2 == 0 && A->ld % 2 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
-        (double)n * (double)n * 8.0 <= 16.0 * 1024 * 1024 * 1024) {
-        Asp = reinterpret_cast<float2 *>(bufs.get((size_t)n * n * sizeof(float2)));
-        cudaGetLastError();
-    }
-    HODLR_TRY_CUDA(cudaMemsetAsync(split_state, 0, sizeof(int), st));
-    gs.iters = ibuf;
-    gs.jcur = ibuf + s;
-    gs.active = ibuf + 2 * s;
-    gs.nactive = ibuf + 3 * s;
-    cudaEvent_t e0, e1;
-    HODLR_TRY_CUDA(cudaEventCreate(&e0));
-    HODLR_TRY_CUDA(cudaEventCreate(&e1));
-    HODLR_TRY_CUDA(cudaEventRecord(e0, st));
+    dim3 vgrid;
+    int tail_grid = 0;
+    size_t tail_smem = 0;
+    long long body_kernels = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    size_t rbytes = 0;
+    std::vector<char> rep_pageable;
+    char *rep_host = nullptr;
+    int restarts = 0;
 
-    const dim3 vgrid((unsigned)std::min<int64_t>((n + KT - 1) / KT, 1024), s);
-    // x0 = 0; iteration counters and per-rhs state start at zero
-    HODLR_TRY_CUDA(cudaMemset2DAsync(X, ldx * 8, 0, n * 8, s, st));
-    HODLR_TRY_CUDA(cudaMemsetAsync(ibuf, 0, (size_t)(4 * s + 4) * sizeof(int), st));
-    HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, s * 8, st));
-    {
-        // ||b||^2 via residual kernel with A X = 0: R = B - 0
-        double *zero = h1;   // reuse as zero source
-        HODLR_TRY_CUDA(cudaMemsetAsync(zero, 0, (size_t)s * hstride * 8, st));
+    ~GmresJob() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
     }
-    // nrm = ||Wv||^2
-    {
-        // R := B - 0 computed as residual_kernel(B, Wv=0): zero Wv first
+    const int *rep_i() const { return reinterpret_cast<const int *>(rep_host); }
+    const double *rep_d() const { return reinterpret_cast<const double *>(rep_host + report_doff(s)); }
+
+    // Work-buffer bytes of a solve of order n with s right-hand sides and
+    // restart length m (the stored split of A included).
+    static size_t device_bytes(int64_t n, int s, int m) {
+        const double v = (double)n * (m + 1) * s * 8 + (double)n * m * s * 8 + (double)n * s * 24 +
+                         (double)s * (m + 1) * (m + 8) * 8 + 8192.0 + (double)n * n * 8;
+        return (size_t)std::min(v, 1e18);
+    }
+
+    hodlr_status setup(char *host_slot) {
+        if (!c || !A || !A->data || !B || !X || s <= 0 || A->n <= 0 || A->ld < A->n || ldb < A->n || ldx < A->n ||
+            max_iter <= 0 || !(tol > 0.0) || m < 0) {
+            set_error("gmres_solve: invalid argument");
+            return HODLR_INVALID_ARG;
+        }
+        if (P && (P->n != A->n)) {
+            set_error("gmres_solve: preconditioner size %lld != %lld", (long long)P->n, (long long)A->n);
+            return HODLR_INVALID_ARG;
+        }
+        if (P && !P->factored) {
+            set_error("gmres_solve: preconditioner not factored");
+            return HODLR_NOT_FACTORED;
+        }
+        HODLR_TRY_CUDA(cudaSetDevice(c->device));
+        n = A->n;
+        m = m > 0 ? std::min(m, max_iter) : max_iter;
+        vstride = n * (m + 1);
+        zstride = n * m;
+        hstride = m + 1;
+        // every work buffer in one allocation
+        Arena ar;
+        const size_t oVk = ar.take((size_t)vstride * s * 8), oZk = ar.take((size_t)zstride * s * 8),
+                     oWv = ar.take((size_t)n * s * 8), oh1 = ar.take((size_t)s * hstride * 8),
+                     oh2 = ar.take((size_t)s * hstride * 8), onrm = ar.take((size_t)s * 8),
+                     oH = ar.take((size_t)s * (m + 1) * m * 8), ocs = ar.take((size_t)s * m * 8),
+                     osn = ar.take((size_t)s * m * 8), og = ar.take((size_t)s * (m + 1) * 8),
+                     obn = ar.take((size_t)s * 8), oest = ar.take((size_t)s * 8),
+                     oib = ar.take((size_t)(4 * s + 4) * sizeof(int)), ozs = ar.take((size_t)n * s * sizeof(float2)),
+                     oZc = ar.take((size_t)n * s * 8), olp = ar.take(256), osst = ar.take(256),
+                     orep = ar.take(report_bytes(s));
+        bufs.c = c;
+        bufs.st = st;
+        iter.c = c;
+        char *base = (char *)bufs.get(ar.bytes);
+        if (!base) {
+            set_error("gmres_solve: out of device memory (%zu bytes)", ar.bytes);
+            return HODLR_OUT_OF_MEMORY;
+        }
+        Vk = (double *)(base + oVk);
+        Zk = (double *)(base + oZk);
+        Wv = (double *)(base + oWv);
+        double *h1 = (double *)(base + oh1);
+        double *h2 = (double *)(base + oh2);
+        nrm = (double *)(base + onrm);
+        gs.H = (double *)(base + oH);
+        gs.cs = (double *)(base + ocs);
+        gs.sn = (double *)(base + osn);
+        gs.g = (double *)(base + og);
+        gs.bnorm = (double *)(base + obn);
+        gs.est = (double *)(base + oest);
+        int *ibuf = (int *)(base + oib);
+        zsw = base + ozs;
+        Zc = (double *)(base + oZc);
+        loops = (int *)(base + olp);
+        // A's FP32 (hi, lo) pairs for the products after the first (ld n; skipped
+        // when A's rows are not 16-byte aligned, n is odd, the buffer would exceed
+        // 16 GiB or cannot be allocated: the products then split A every time)
+        split_state = (int *)(base + osst);
+        rep_dev = base + orep;
+        if (n % 2 == 0 && A->ld % 2 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
+            (double)n * (double)n * 8.0 <= 16.0 * 1024 * 1024 * 1024) {
+            Asp = reinterpret_cast<float2 *>(bufs.get((size_t)n * n * sizeof(float2)));
+            cudaGetLastError();
+        }
+        HODLR_TRY_CUDA(cudaMemsetAsync(split_state, 0, sizeof(int), st));
+        gs.iters = ibuf;
+        gs.jcur = ibuf + s;
+        gs.active = ibuf + 2 * s;
+        gs.nactive = ibuf + 3 * s;
+        HODLR_TRY_CUDA(cudaEventCreate(&e0));
+        HODLR_TRY_CUDA(cudaEventCreate(&e1));
+        HODLR_TRY_CUDA(cudaEventRecord(e0, st));
+
+        vgrid = dim3((unsigned)std::min<int64_t>((n + KT - 1) / KT, 1024), s);
+        // x0 = 0; iteration counters and per-rhs state start at zero
+        HODLR_TRY_CUDA(cudaMemset2DAsync(X, ldx * 8, 0, n * 8, s, st));
+        HODLR_TRY_CUDA(cudaMemsetAsync(ibuf, 0, (size_t)(4 * s + 4) * sizeof(int), st));
+        HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, s * 8, st));
+        HODLR_TRY_CUDA(cudaMemsetAsync(h1, 0, (size_t)s * hstride * 8, st));
+        // R := B - 0 and nrm = ||R||^2 (W starts at zero)
         HODLR_TRY_CUDA(cudaMemset2DAsync(Wv, n * 8, 0, n * 8, s, st));
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
         note_launch();
-    }
-    // ---- one Arnoldi iteration, recorded once and replayed by a device-side
-    // while loop (a conditional graph node) until no right-hand side is active:
-    // z = P^-1 v_j, w = A z, then the fused Gram-Schmidt / Givens step
-    if (P) HODLR_TRY(solve_prepare(P, s, st));
-    HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, st));
-    TailArgs ta{};
-    ta.Vk = Vk;
-    ta.vstride = vstride;
-    ta.n = n;
-    ta.w = Wv;
-    ta.Zc = Zc;
-    ta.Zk = Zk;
-    ta.zstride = zstride;
-    ta.h1 = h1;
-    ta.h2 = h2;
-    ta.nrm = nrm;
-    ta.hstride = hstride;
-    ta.gs = gs;
-    ta.m = m;
-    ta.s = s;
-    ta.max_iter = max_iter;
-    ta.tol = tol;
-    ta.bar = reinterpret_cast<unsigned *>(ibuf + 3 * s + 2);
-    ta.status = c->d_status;
-    ta.loops = loops;
-    ta.limit = m + 1;
-    ta.split_state = Asp ? split_state : nullptr;
-    const size_t tail_smem = (size_t)(m + 1) * sizeof(double) + 2 * (size_t)s * sizeof(int);
-    HODLR_TRY_CUDA(cudaFuncSetAttribute(arnoldi_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tail_smem));
-    int tail_grid = 0;
-    {
-        int per_sm = 0;
-        HODLR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_tail_kernel, TT, tail_smem));
-        if (per_sm <= 0) {
-            set_error("gmres_solve: restart length %d needs too much shared memory", m);
-            return HODLR_INVALID_ARG;
+        // ---- one Arnoldi iteration, recorded once and replayed by a device-side
+        // while loop (a conditional graph node) until no right-hand side is active:
+        // z = P^-1 v_j, w = A z, then the fused Gram-Schmidt / Givens step
+        if (P) HODLR_TRY(solve_prepare(P, s, st));
+        HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, st));
+        ta.Vk = Vk;
+        ta.vstride = vstride;
+        ta.n = n;
+        ta.w = Wv;
+        ta.Zc = Zc;
+        ta.Zk = Zk;
+        ta.zstride = zstride;
+        ta.h1 = h1;
+        ta.h2 = h2;
+        ta.nrm = nrm;
+        ta.hstride = hstride;
+        ta.gs = gs;
+        ta.m = m;
+        ta.s = s;
+        ta.max_iter = max_iter;
+        ta.tol = tol;
+        ta.bar = reinterpret_cast<unsigned *>(ibuf + 3 * s + 2);
+        ta.status = c->d_status;
+        ta.loops = loops;
+        ta.limit = m + 1;
+        ta.split_state = Asp ? split_state : nullptr;
+        tail_smem = (size_t)(m + 1) * sizeof(double) + 2 * (size_t)s * sizeof(int);
+        HODLR_TRY_CUDA(cudaFuncSetAttribute(arnoldi_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)tail_smem));
+        {
+            int per_sm = 0;
+            HODLR_TRY_CUDA(
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_tail_kernel, TT, tail_smem));
+            if (per_sm <= 0) {
+                set_error("gmres_solve: restart length %d needs too much shared memory", m);
+                return HODLR_INVALID_ARG;
+            }
+            const int64_t units = ((n + TT - 1) / TT) * s;
+            tail_grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->num_sms * per_sm));
         }
-        const int64_t units = ((n + TT - 1) / TT) * s;
-        tail_grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)c->num_sms * per_sm));
+        HODLR_TRY(record_graph());
+        // the host's view of each cycle comes in one copy (pinned unless the
+        // caller's slot is missing or too small)
+        rbytes = report_bytes(s);
+        rep_host = host_slot;
+        if (!rep_host) {
+            rep_pageable.resize(rbytes);
+            rep_host = rep_pageable.data();
+        }
+        return HODLR_OK;
     }
-    IterGraph iter;
-    iter.c = c;
-    long long body_kernels = 0;   // kernels of one recorded iteration
-    {
+
+    hodlr_status record_graph() {
         cudaStream_t cs = c->side[HODLR_SIDE_STREAMS - 1];
         HODLR_TRY_CUDA(cudaGraphCreate(&iter.graph, 0));
         cudaGraphConditionalHandle handle;
@@ -1035,8 +1085,8 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
         auto record = [&]() -> hodlr_status {
             // the apply also leaves z split into FP32 pairs for the product
             if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs, reinterpret_cast<float2 *>(zsw)));
-            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state, P != nullptr,
-                                  P != nullptr && P->prec != HODLR_FP64));
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state,
+                                  P != nullptr, P != nullptr && P->prec != HODLR_FP64));
             ta.handle = handle;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)tail_grid);
@@ -1066,91 +1116,139 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
             return HODLR_CUDA_ERROR;
         }
         HODLR_TRY_CUDA(cudaGraphInstantiate(&iter.exec, iter.graph, 0));
-    }
-    // the host's view of each cycle comes in one copy (pinned unless s is huge)
-    const size_t rbytes = report_bytes(s);
-    std::vector<char> rep_pageable;
-    char *rep_host = reinterpret_cast<char *>(c->h_report);
-    if (rbytes > HODLR_REPORT_BYTES) {
-        rep_pageable.resize(rbytes);
-        rep_host = rep_pageable.data();
-    }
-    const int *rep_i = reinterpret_cast<const int *>(rep_host);
-    const double *rep_d = reinterpret_cast<const double *>(rep_host + report_doff(s));
-    auto read_report = [&]() -> hodlr_status {
-        cycle_report_kernel<<<1, 32, 0, st>>>(gs, s, nrm, c->d_status, loops, rep_dev);
-        note_launch();
-        HODLR_TRY_CUDA(cudaMemcpyAsync(rep_host, rep_dev, rbytes, cudaMemcpyDeviceToHost, st));
-        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
         return HODLR_OK;
-    };
-    int restarts = 0;
-    hodlr_status result = HODLR_OK;
-    bool reported = false;
-    for (int cycle = 0;; ++cycle) {
-        start_cycle_kernel<<<vgrid, KT, 0, st>>>(gs, m, s, Wv, n, n, nrm, Vk, vstride, tol, max_iter, cycle == 0, Zc);
-        note_launch();
-        if (cycle > 0) {
-            // the first cycle is launched without waiting (its graph tests the
-            // count itself); later cycles read the report and stop here once
-            // every rhs has converged, with the results already on the host
-            HODLR_TRY_CUDA(cudaEventRecord(e1, st));
-            HODLR_TRY(read_report());
-            note_launch((long long)rep_i[2] * body_kernels);   // replays of the previous cycle
-            HODLR_TRY(status_word(rep_i[1]));
-            if (rep_i[0] == 0) {
-                reported = true;
-                break;
-            }
-            ++restarts;
-        } else {
+    }
+
+    // One cycle from the current start vector: the Arnoldi iterations (graph),
+    // x += Z y and the true residual R = B - A X.
+    hodlr_status launch_cycle(bool first) {
+        if (first) {
             count_active_kernel<<<1, 1, 0, st>>>(gs.active, s, gs.nactive);
             note_launch();
         }
         HODLR_TRY_CUDA(cudaMemsetAsync(loops, 0, sizeof(int), st));
         HODLR_TRY_CUDA(cudaGraphLaunch(iter.exec, st));
         note_launch();   // the graph's test of the count
-        if (cycle == 0) empty_graph_trash(c);   // earlier solves' graphs, while this one runs
+        if (first) empty_graph_trash(c);   // earlier solves' graphs, while this one runs
         // x += Z y
         backsolve_kernel<<<dim3((unsigned)std::min<int64_t>((n + KT - 1) / KT, 64), s), KT, (size_t)m * 8, st>>>(
             gs, m, Zk, zstride, n, X, ldx);
         note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
-        // true residual R = B - A X
         HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, X, ldx, Wv, n, st, zsw, false, Asp, split_state));
         HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, st));
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
         note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
-        if (cycle > 10000) break;
+        return HODLR_OK;
     }
-    if (!reported) {
+
+    // The first cycle (the graph tests the count itself, so it is launched
+    // without a host round trip), then the restart test and its report.
+    hodlr_status first_cycle() {
+        start_cycle_kernel<<<vgrid, KT, 0, st>>>(gs, m, s, Wv, n, n, nrm, Vk, vstride, tol, max_iter, true, Zc);
+        note_launch();
+        HODLR_TRY(launch_cycle(true));
+        return enqueue_report();
+    }
+    hodlr_status next_cycle() {
+        ++restarts;
+        HODLR_TRY(launch_cycle(false));
+        return enqueue_report();
+    }
+    // Restart test from the true residual (a right-hand side stays active
+    // while its residual is above tol), then the report copy.
+    hodlr_status enqueue_report() {
+        start_cycle_kernel<<<vgrid, KT, 0, st>>>(gs, m, s, Wv, n, n, nrm, Vk, vstride, tol, max_iter, false, Zc);
+        note_launch();
         HODLR_TRY_CUDA(cudaEventRecord(e1, st));
-        HODLR_TRY(read_report());
-        HODLR_TRY(status_word(rep_i[1]));
+        cycle_report_kernel<<<1, 32, 0, st>>>(gs, s, nrm, c->d_status, loops, rep_dev);
+        note_launch();
+        HODLR_TRY_CUDA(cudaMemcpyAsync(rep_host, rep_dev, rbytes, cudaMemcpyDeviceToHost, st));
+        return HODLR_OK;
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    for (int r = 0; r < s; ++r) {
-        const double bn = rep_d[2 * s + r];
-        const double tr = bn > 0.0 ? std::sqrt(rep_d[s + r]) / bn : 0.0;
-        if (!(tr <= tol)) result = HODLR_NOT_CONVERGED;
-        if (info) {
-            if (info->iters) info->iters[r] = rep_i[3 + r];
-            if (info->est_relres) info->est_relres[r] = rep_d[r];
-            if (info->true_relres) info->true_relres[r] = tr;
+    // After the stream has passed the report: false once every rhs is done.
+    hodlr_status take_report(bool &more) {
+        note_launch((long long)rep_i()[2] * body_kernels);   // replays of the last cycle
+        HODLR_TRY(status_word(rep_i()[1]));
+        more = rep_i()[0] != 0 && restarts < 10000;
+        return HODLR_OK;
+    }
+
+    hodlr_status finish(hodlr_gmres_info *info) {
+        hodlr_status result = HODLR_OK;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const int *ri = rep_i();
+        const double *rd = rep_d();
+        for (int r = 0; r < s; ++r) {
+            const double bn = rd[2 * s + r];
+            const double tr = bn > 0.0 ? std::sqrt(rd[s + r]) / bn : 0.0;
+            if (!(tr <= tol)) result = HODLR_NOT_CONVERGED;
+            if (info) {
+                if (info->iters) info->iters[r] = ri[3 + r];
+                if (info->est_relres) info->est_relres[r] = rd[r];
+                if (info->true_relres) info->true_relres[r] = tr;
+            }
         }
+        if (info) {
+            info->restarts = restarts;
+            info->ms_total = ms;
+        }
+        if (result == HODLR_NOT_CONVERGED) set_error("gmres_solve: not converged within %d iterations", max_iter);
+        return result;
     }
-    if (info) {
-        info->restarts = restarts;
-        info->ms_total = ms;
+
+    // Restarted cycles, each waited for, until every rhs is done.
+    hodlr_status run_to_end(hodlr_gmres_info *info) {
+        bool more = false;
+        HODLR_TRY(take_report(more));
+        while (more) {
+            HODLR_TRY(next_cycle());
+            HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+            HODLR_TRY(take_report(more));
+        }
+        return finish(info);
     }
-    if (result == HODLR_NOT_CONVERGED) set_error("gmres_solve: not converged within %d iterations", max_iter);
-    return result;
+};
+
+size_t report_slot(int s) { return (report_bytes(s) + 63) & ~size_t(63); }
+
+}  // namespace
+
+extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, const double *B, int64_t ldb,
+                                    double *X, int64_t ldx, const hodlr_t *P, double tol, int max_iter, int restart,
+                                    hodlr_gmres_info *info, hodlr_stream stream) {
+    if (!c) {
+        set_error("gmres_solve: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    GmresJob j;
+    j.c = c;
+    j.A = A;
+    j.s = s;
+    j.B = B;
+    j.ldb = ldb;
+    j.X = X;
+    j.ldx = ldx;
+    j.P = P;
+    j.tol = tol;
+    j.max_iter = max_iter;
+    j.m = restart;
+    j.st = reinterpret_cast<cudaStream_t>(stream);
+    const bool pinned = s > 0 && report_bytes(s) <= HODLR_REPORT_BYTES;
+    HODLR_TRY(j.setup(pinned ? reinterpret_cast<char *>(c->h_report) : nullptr));
+    HODLR_TRY(j.first_cycle());
+    HODLR_TRY_CUDA(cudaStreamSynchronize(j.st));
+    return j.run_to_end(info);
 }
 
+// Fronts are taken in windows: every front of a window is set up and its first
+// cycle and report enqueued on the stream without a host wait (each report in
+// its own slot of the context's pinned buffer); one synchronisation then covers
+// the window, and only fronts that need a restart wait again.  A window holds
+// at most HODLR_REPORT_BYTES of reports, about 8 GiB of work buffers and each
+// preconditioner once.
 extern "C" hodlr_status gmres_solve_batched(hodlr_ctx *c, int nf, const hodlr_matrix *A, const int *s,
                                             const double *const *B, const int64_t *ldb, double *const *X,
                                             const int64_t *ldx, const hodlr_t *const *P, double tol, int max_iter,
@@ -1160,14 +1258,60 @@ extern "C" hodlr_status gmres_solve_batched(hodlr_ctx *c, int nf, const hodlr_ma
         set_error("gmres_solve_batched: invalid argument");
         return HODLR_INVALID_ARG;
     }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t mem_window = (size_t)8 << 30;
     hodlr_status result = HODLR_OK;
-    for (int f = 0; f < nf; ++f) {
-        const hodlr_status r = gmres_solve(c, &A[f], s[f], B[f], ldb[f], X[f], ldx[f], P ? P[f] : nullptr, tol,
-                                           max_iter, restart, info ? &info[f] : nullptr, stream);
-        if (r == HODLR_NOT_CONVERGED)
-            result = HODLR_NOT_CONVERGED;
-        else if (r != HODLR_OK)
-            return r;
+    for (int f0 = 0; f0 < nf;) {
+        std::vector<std::unique_ptr<GmresJob>> jobs;
+        std::vector<const hodlr_t *> seen;
+        size_t rep_used = 0, mem_used = 0;
+        int f = f0;
+        for (; f < nf; ++f) {
+            const int sf = s[f] > 0 ? s[f] : 1;
+            const int64_t nn = A[f].n > 0 ? A[f].n : 1;
+            const int mf = restart > 0 ? std::min(restart, std::max(max_iter, 1)) : std::max(max_iter, 1);
+            const size_t rb = report_slot(sf), mb = GmresJob::device_bytes(nn, sf, mf);
+            // a preconditioner met again in the window ends it: its work buffers
+            // may be resized for the new front while an earlier graph uses them
+            const hodlr_t *pf = P ? P[f] : nullptr;
+            if (f > f0 && (rep_used + rb > HODLR_REPORT_BYTES || mem_used + mb > mem_window ||
+                           (pf && std::find(seen.begin(), seen.end(), pf) != seen.end())))
+                break;
+            if (pf) seen.push_back(pf);
+            auto j = std::make_unique<GmresJob>();
+            j->c = c;
+            j->A = &A[f];
+            j->s = s[f];
+            j->B = B[f];
+            j->ldb = ldb[f];
+            j->X = X[f];
+            j->ldx = ldx[f];
+            j->P = pf;
+            j->tol = tol;
+            j->max_iter = max_iter;
+            j->m = restart;
+            j->st = st;
+            char *slot = rep_used + rb <= HODLR_REPORT_BYTES ? reinterpret_cast<char *>(c->h_report) + rep_used
+                                                             : nullptr;
+            rep_used += rb;
+            mem_used += mb;
+            hodlr_status r = j->setup(slot);
+            if (r == HODLR_OK) r = j->first_cycle();
+            if (r != HODLR_OK) {
+                cudaStreamSynchronize(st);
+                return r;
+            }
+            jobs.push_back(std::move(j));
+        }
+        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+        for (size_t k = 0; k < jobs.size(); ++k) {
+            const hodlr_status r = jobs[k]->run_to_end(info ? &info[f0 + k] : nullptr);
+            if (r == HODLR_NOT_CONVERGED)
+                result = HODLR_NOT_CONVERGED;
+            else if (r != HODLR_OK)
+                return r;
+        }
+        f0 = f;
     }
     if (result == HODLR_NOT_CONVERGED) set_error("gmres_solve_batched: some front did not converge");
     return result;
