@@ -944,15 +944,17 @@ struct GmresJob {
         hstride = m + 1;
         // every work buffer in one allocation
         Arena ar;
+        // W, h1, h2, nrm, the integer block and the split flag are adjacent:
+        // one memset clears them
         const size_t oVk = ar.take((size_t)vstride * s * 8), oZk = ar.take((size_t)zstride * s * 8),
                      oWv = ar.take((size_t)n * s * 8), oh1 = ar.take((size_t)s * hstride * 8),
                      oh2 = ar.take((size_t)s * hstride * 8), onrm = ar.take((size_t)s * 8),
+                     oib = ar.take((size_t)(4 * s + 4) * sizeof(int)), osst = ar.take(256), ozero_end = ar.bytes,
                      oH = ar.take((size_t)s * (m + 1) * m * 8), ocs = ar.take((size_t)s * m * 8),
                      osn = ar.take((size_t)s * m * 8), og = ar.take((size_t)s * (m + 1) * 8),
                      obn = ar.take((size_t)s * 8), oest = ar.take((size_t)s * 8),
-                     oib = ar.take((size_t)(4 * s + 4) * sizeof(int)), ozs = ar.take((size_t)n * s * sizeof(float2)),
-                     oZc = ar.take((size_t)n * s * 8), olp = ar.take(256), osst = ar.take(256),
-                     orep = ar.take(report_bytes(s));
+                     ozs = ar.take((size_t)n * s * sizeof(float2)), oZc = ar.take((size_t)n * s * 8),
+                     olp = ar.take(256), orep = ar.take(report_bytes(s));
         bufs.c = c;
         bufs.st = st;
         iter.c = c;
@@ -987,7 +989,6 @@ struct GmresJob {
             Asp = reinterpret_cast<float2 *>(bufs.get((size_t)n * n * sizeof(float2)));
             cudaGetLastError();
         }
-        HODLR_TRY_CUDA(cudaMemsetAsync(split_state, 0, sizeof(int), st));
         gs.iters = ibuf;
         gs.jcur = ibuf + s;
         gs.active = ibuf + 2 * s;
@@ -997,20 +998,17 @@ struct GmresJob {
         HODLR_TRY_CUDA(cudaEventRecord(e0, st));
 
         vgrid = dim3((unsigned)std::min<int64_t>((n + KT - 1) / KT, 1024), s);
-        // x0 = 0; iteration counters and per-rhs state start at zero
+        // x0 = 0; W, h1, h2, nrm, the iteration counters, per-rhs state and
+        // the split flag start at zero
         HODLR_TRY_CUDA(cudaMemset2DAsync(X, ldx * 8, 0, n * 8, s, st));
-        HODLR_TRY_CUDA(cudaMemsetAsync(ibuf, 0, (size_t)(4 * s + 4) * sizeof(int), st));
-        HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, s * 8, st));
-        HODLR_TRY_CUDA(cudaMemsetAsync(h1, 0, (size_t)s * hstride * 8, st));
-        // R := B - 0 and nrm = ||R||^2 (W starts at zero)
-        HODLR_TRY_CUDA(cudaMemset2DAsync(Wv, n * 8, 0, n * 8, s, st));
+        HODLR_TRY_CUDA(cudaMemsetAsync(base + oWv, 0, ozero_end - oWv, st));
+        // R := B - 0 and nrm = ||R||^2
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
         note_launch();
         // ---- one Arnoldi iteration, recorded once and replayed by a device-side
         // while loop (a conditional graph node) until no right-hand side is active:
         // z = P^-1 v_j, w = A z, then the fused Gram-Schmidt / Givens step
         if (P) HODLR_TRY(solve_prepare(P, s, st));
-        HODLR_TRY_CUDA(cudaMemsetAsync(h2, 0, (size_t)s * hstride * 8, st));
         ta.Vk = Vk;
         ta.vstride = vstride;
         ta.n = n;
@@ -1244,9 +1242,10 @@ extern "C" hodlr_status gmres_solve(hodlr_ctx *c, const hodlr_matrix *A, int s, 
 }
 
 // Fronts are taken in windows: every front of a window is set up and its first
-// cycle and report enqueued on the stream without a host wait (each report in
-// its own slot of the context's pinned buffer); one synchronisation then covers
-// the window, and only fronts that need a restart wait again.  A window holds
+// cycle and report enqueued without a host wait (each report in its own slot of
+// the context's pinned buffer), the fronts spread over several streams so that
+// their small dependent kernels overlap; one synchronisation then covers the
+// window, and only fronts that need a restart wait again.  A window holds
 // at most HODLR_REPORT_BYTES of reports, about 8 GiB of work buffers and each
 // preconditioner once.
 extern "C" hodlr_status gmres_solve_batched(hodlr_ctx *c, int nf, const hodlr_matrix *A, const int *s,
@@ -1259,7 +1258,24 @@ extern "C" hodlr_status gmres_solve_batched(hodlr_ctx *c, int nf, const hodlr_ma
         return HODLR_INVALID_ARG;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    HODLR_TRY_CUDA(cudaSetDevice(c->device));
     const size_t mem_window = (size_t)8 << 30;
+    // fronts are independent: they go round-robin onto the context's side
+    // streams (all but the one graphs are captured on), which start after the
+    // work already on `stream` and are waited for by the host before return
+    constexpr int NS = HODLR_SIDE_STREAMS - 1;
+    cudaEvent_t ready = nullptr;
+    HODLR_TRY_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    struct EventGuard {
+        cudaEvent_t e;
+        ~EventGuard() { cudaEventDestroy(e); }
+    } ready_guard{ready};
+    HODLR_TRY_CUDA(cudaEventRecord(ready, st));
+    for (int q = 0; q < NS; ++q) HODLR_TRY_CUDA(cudaStreamWaitEvent(c->side[q], ready, 0));
+    auto sync_side = [&]() -> hodlr_status {
+        for (int q = 0; q < NS; ++q) HODLR_TRY_CUDA(cudaStreamSynchronize(c->side[q]));
+        return HODLR_OK;
+    };
     hodlr_status result = HODLR_OK;
     for (int f0 = 0; f0 < nf;) {
         std::vector<std::unique_ptr<GmresJob>> jobs;
@@ -1290,7 +1306,7 @@ extern "C" hodlr_status gmres_solve_batched(hodlr_ctx *c, int nf, const hodlr_ma
             j->tol = tol;
             j->max_iter = max_iter;
             j->m = restart;
-            j->st = st;
+            j->st = c->side[(f - f0) % NS];
             char *slot = rep_used + rb <= HODLR_REPORT_BYTES ? reinterpret_cast<char *>(c->h_report) + rep_used
                                                              : nullptr;
             rep_used += rb;
@@ -1298,21 +1314,25 @@ extern "C" hodlr_status gmres_solve_batched(hodlr_ctx *c, int nf, const hodlr_ma
             hodlr_status r = j->setup(slot);
             if (r == HODLR_OK) r = j->first_cycle();
             if (r != HODLR_OK) {
-                cudaStreamSynchronize(st);
+                sync_side();
                 return r;
             }
             jobs.push_back(std::move(j));
         }
-        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+        HODLR_TRY(sync_side());
         for (size_t k = 0; k < jobs.size(); ++k) {
             const hodlr_status r = jobs[k]->run_to_end(info ? &info[f0 + k] : nullptr);
             if (r == HODLR_NOT_CONVERGED)
                 result = HODLR_NOT_CONVERGED;
-            else if (r != HODLR_OK)
+            else if (r != HODLR_OK) {
+                sync_side();
                 return r;
+            }
         }
         f0 = f;
     }
+    // every side stream idle on return: work queued next on `stream` sees X
+    HODLR_TRY(sync_side());
     if (result == HODLR_NOT_CONVERGED) set_error("gmres_solve_batched: some front did not converge");
     return result;
 }

@@ -323,6 +323,22 @@ def test_gmres_restarts_six_rhs(H, ctx, front576):
     h.close()
 
 
+def test_batched_shared_preconditioner_restarts(H, ctx, front576):
+    """Batched GMRES with one preconditioner shared by three fronts of 1, 2 and
+    3 right-hand sides (a window ends where the preconditioner repeats) and
+    restarted cycles: every solution is exact and converged."""
+    F = front576
+    A = _dev(F.A)
+    h = H.hodlr_build(ctx, A, 64, 1e-3, "aca", precision="fp32")
+    bs = [fg.rhs(F.n, k + 1, seed=20 + k) for k in range(3)]
+    res = H.gmres_solve_batched(ctx, [A] * 3, [_dev(b.T) for b in bs], [h] * 3, tol=1e-12, restart=2)
+    for b, (X, info) in zip(bs, res):
+        assert info.converged and info.restarts >= 1 and np.all(info.true_relres <= 1e-12)
+        ref = np.linalg.solve(F.A, b)
+        assert np.linalg.norm(X.cpu().numpy().T - ref) / np.linalg.norm(ref) < 1e-9
+    h.close()
+
+
 def test_streams_and_block_reuse(H, ctx, front576):
     """Build, solve and destroy on alternating streams: released blocks are
     reused across streams (ordered by their events); every solve is exact."""
