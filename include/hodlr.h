@@ -188,8 +188,9 @@ hodlr_status hodlr_solve(hodlr_t *h, int s, double *X, int64_t ldx, hodlr_stream
  * when the estimated residual <= tol ||b||; the true residual is then
  * recomputed and the solve restarts from x while it misses tol.  restart = 0
  * means one cycle of up to max_iter steps.  Returns HODLR_NOT_CONVERGED with X
- * = the last iterate if some column misses tol within max_iter steps.
- * Synchronises `stream`. */
+ * = the last iterate if some column misses tol within max_iter steps.  The
+ * products with A are those of hodlr_matvec; with s >= 16 (n >= 256) A's digit
+ * slices are made once per call.  Synchronises `stream`. */
 hodlr_status gmres_solve(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *B,
                          int64_t ldb, double *X, int64_t ldx, const hodlr_t *P, double tol,
                          int max_iter, int restart, hodlr_gmres_info *info,
@@ -222,8 +223,14 @@ hodlr_status gmres_solve_batched(hodlr_ctx *ctx, int nf, const hodlr_matrix *A, 
                                  const int64_t *ldx, const hodlr_t *const *P, double tol, int max_iter,
                                  int restart, hodlr_gmres_info *info, hodlr_stream stream);
 
-/* W <- A Z (device, n x s column-major) with the FP64-accurate double-float
- * matvec used inside gmres_solve. */
+/* W <- A Z (device, n x s column-major), FP64-accurate, with the products used
+ * inside gmres_solve: for s < 16 or n < 256 the double-float product on the FP32
+ * pipes (each entry split into FP32 pairs); otherwise every row of A and column
+ * of Z is split exactly into seven base-256 digit slices relative to a power of
+ * two of its own, the slice products run on the BF16 tensor cores, and the
+ * error per term is a few units of 2^-56 max|A(i,:)| max|Z(:,j)| (that path
+ * allocates about 14 n^2 bytes for A's slices per call, and falls back to the
+ * double-float product when they cannot be allocated). */
 hodlr_status hodlr_matvec(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *Z,
                           int64_t ldz, double *W, int64_t ldw, hodlr_stream stream);
 

@@ -1010,7 +1010,23 @@ hodlr_status hodlr_matvec(hodlr_ctx *c, const hodlr_matrix *A, int s, const doub
         return HODLR_INVALID_ARG;
     }
     HODLR_TRY_CUDA(cudaSetDevice(c->device));
-    return matvec_impl(c, A->data, A->n, A->ld, s, Z, ldz, W, ldw, reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (oz_eligible(A->n, s)) {
+        // many right-hand sides: split A for this call and use the tensor cores
+        const size_t ab = oz_a_bytes(A->n), zb = oz_z_bytes(A->n, s);
+        void *abuf = dalloc(c, ab, st);
+        void *zbuf = abuf ? dalloc(c, zb, st) : nullptr;
+        if (zbuf) {
+            hodlr_status r = oz_split_a(c, A->data, A->n, A->ld, abuf, st);
+            if (r == HODLR_OK) r = oz_matvec(c, abuf, A->n, s, Z, ldz, W, ldw, zbuf, st);
+            dfree(c, zbuf, zb, st);
+            dfree(c, abuf, ab, st);
+            return r;
+        }
+        if (abuf) dfree(c, abuf, ab, st);
+        cudaGetLastError();   // too large for the slices: the double-float product
+    }
+    return matvec_impl(c, A->data, A->n, A->ld, s, Z, ldz, W, ldw, st);
 }
 
 hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {

@@ -897,6 +897,8 @@ struct GmresJob {
     int *loops = nullptr, *split_state = nullptr;
     char *rep_dev = nullptr;
     float2 *Asp = nullptr;
+    // tensor-core product (many right-hand sides): A's digit slices, Z's
+    void *oza = nullptr, *ozz = nullptr;
     dim3 vgrid;
     int tail_grid = 0;
     size_t tail_smem = 0;
@@ -917,8 +919,9 @@ struct GmresJob {
     // Work-buffer bytes of a solve of order n with s right-hand sides and
     // restart length m (the stored split of A included).
     static size_t device_bytes(int64_t n, int s, int m) {
+        const double prod = oz_eligible(n, s) ? (double)oz_a_bytes(n) + (double)oz_z_bytes(n, s) : (double)n * n * 8;
         const double v = (double)n * (m + 1) * s * 8 + (double)n * m * s * 8 + (double)n * s * 24 +
-                         (double)s * (m + 1) * (m + 8) * 8 + 8192.0 + (double)n * n * 8;
+                         (double)s * (m + 1) * (m + 8) * 8 + 8192.0 + prod;
         return (size_t)std::min(v, 1e18);
     }
 
@@ -984,7 +987,13 @@ struct GmresJob {
         // 16 GiB or cannot be allocated: the products then split A every time)
         split_state = (int *)(base + osst);
         rep_dev = base + orep;
-        if (n % 2 == 0 && A->ld % 2 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
+        if (oz_eligible(n, s)) {
+            oza = bufs.get(oz_a_bytes(n));
+            ozz = oza ? bufs.get(oz_z_bytes(n, s)) : nullptr;
+            if (!ozz) oza = nullptr;   // the double-float product instead
+            cudaGetLastError();
+        }
+        if (!oza && n % 2 == 0 && A->ld % 2 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
             (double)n * (double)n * 8.0 <= 16.0 * 1024 * 1024 * 1024) {
             Asp = reinterpret_cast<float2 *>(bufs.get((size_t)n * n * sizeof(float2)));
             cudaGetLastError();
@@ -1005,6 +1014,7 @@ struct GmresJob {
         // R := B - 0 and nrm = ||R||^2
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
         note_launch();
+        if (oza) HODLR_TRY(oz_split_a(c, A->data, n, A->ld, oza, st));
         // ---- one Arnoldi iteration, recorded once and replayed by a device-side
         // while loop (a conditional graph node) until no right-hand side is active:
         // z = P^-1 v_j, w = A z, then the fused Gram-Schmidt / Givens step
@@ -1081,10 +1091,15 @@ struct GmresJob {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         HODLR_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         auto record = [&]() -> hodlr_status {
-            // the apply also leaves z split into FP32 pairs for the product
-            if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs, reinterpret_cast<float2 *>(zsw)));
-            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state,
-                                  P != nullptr, P != nullptr && P->prec != HODLR_FP64));
+            if (oza) {
+                if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs));
+                HODLR_TRY(oz_matvec(c, oza, n, s, Zc, n, Wv, n, ozz, cs));
+            } else {
+                // the apply also leaves z split into FP32 pairs for the product
+                if (P) HODLR_TRY(solve_impl(P, s, Zc, n, cs, reinterpret_cast<float2 *>(zsw)));
+                HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, Zc, n, Wv, n, cs, zsw, true, Asp, split_state,
+                                      P != nullptr, P != nullptr && P->prec != HODLR_FP64));
+            }
             ta.handle = handle;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)tail_grid);
@@ -1133,7 +1148,10 @@ struct GmresJob {
             gs, m, Zk, zstride, n, X, ldx);
         note_launch();
         HODLR_TRY_CUDA(cudaGetLastError());
-        HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, X, ldx, Wv, n, st, zsw, false, Asp, split_state));
+        if (oza)
+            HODLR_TRY(oz_matvec(c, oza, n, s, X, ldx, Wv, n, ozz, st));
+        else
+            HODLR_TRY(matvec_impl(c, A->data, n, A->ld, s, X, ldx, Wv, n, st, zsw, false, Asp, split_state));
         HODLR_TRY_CUDA(cudaMemsetAsync(nrm, 0, (size_t)s * 8, st));
         residual_kernel<<<vgrid, KT, 0, st>>>(B, ldb, Wv, n, n, nrm);
         note_launch();

@@ -263,6 +263,22 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
                          void *work = nullptr, bool w_zeroed = false, float2 *Asp = nullptr,
                          const int *split_state = nullptr, bool z_split = false, bool z_fp32 = false);
 
+// FP64-accurate product on the BF16 tensor cores for many right-hand sides
+// (ozaki.cu): A's rows and Z's columns split exactly into OZ_SLICES base-256
+// digit slices.  oz_split_a writes A's slices into abuf (oz_a_bytes(n) bytes,
+// once per A); oz_matvec splits Z into zbuf (oz_z_bytes(n, s) bytes) and
+// writes W = A Z (every entry; W need not be zeroed).  Used where
+// oz_eligible(n, s).
+constexpr int OZ_SLICES = 7;
+constexpr int OZ_MIN_RHS = 16;
+constexpr int64_t OZ_MIN_N = 256;
+bool oz_eligible(int64_t n, int s_rhs);
+size_t oz_a_bytes(int64_t n);
+size_t oz_z_bytes(int64_t n, int s_rhs);
+hodlr_status oz_split_a(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, void *abuf, cudaStream_t s);
+hodlr_status oz_matvec(hodlr_ctx *c, const void *abuf, int64_t n, int s_rhs, const double *Z, int64_t ldz,
+                       double *W, int64_t ldw, void *zbuf, cudaStream_t s);
+
 // Convert / pad kernels
 hodlr_status copy_columns(int prec_src, int prec_dst, const void *src, int64_t ld_src,
                           void *dst, int64_t ld_dst, int64_t rows, int64_t cols,

@@ -376,7 +376,9 @@ def hodlr_solve(h: Hodlr, X: torch.Tensor, stream=None) -> torch.Tensor:
 
 
 def hodlr_matvec(ctx: Context, A: torch.Tensor, Z: torch.Tensor, symmetric: bool = True, stream=None):
-    """W = A Z with the FP64-accurate double-float matvec; Z is (s, n) or (n,)."""
+    """W = A Z, FP64-accurate; Z is (s, n) or (n,).  Fewer than 16 right-hand
+    sides (or n < 256): the double-float product on the FP32 pipes; otherwise the
+    exact digit-slice product on the BF16 tensor cores."""
     mat = _mat(A, symmetric)
     ptr, s, ld = _rhs(Z, A.shape[0])
     W = torch.empty_like(Z, memory_format=torch.contiguous_format)

@@ -261,6 +261,67 @@ def test_matvec_is_fp64_accurate(H, ctx, front576):
     assert np.median(np.abs(W - ref) / (np.abs(F.A) @ np.abs(z.T)).T) < 2.0 ** -48
 
 
+def _row_exponents(M):
+    """Least e with max |M(i, :)| < 2^e per row (np.frexp's exponent)."""
+    return np.frexp(np.abs(M).max(axis=1))[1].astype(np.float64)
+
+
+@pytest.mark.parametrize("n,s", [(576, 32), (300, 20), (576, 45)])
+def test_tensor_core_product_fp64_accurate(H, ctx, front576, n, s):
+    """hodlr_matvec with 16 or more right-hand sides takes the digit-slice
+    product on the tensor cores: seven base-256 digits per entry relative to a
+    power of two per row of A and per column of Z (the last one rounded), slice
+    pairs up to level 6 kept.  Per entry of A Z the digit and dropped-pair
+    errors are at most n (2^-57 + 2^-57 + 6 * 256^2 2^-72) 2^(e_i + f_j)
+    < 8 n 2^(e_i + f_j - 56); the float-pair and FP32 sums add at most about
+    n 2^-51 of (|A||Z|)(i, j), the FP64 reference n 2^-53.  Statistically the
+    error is far below the double-float product's 2^-48 per term.  Ragged sizes (n = 300: 384 padded rows, 320
+    padded k; s = 20, 45: padded columns), a zero column and a column spanning
+    30 orders of magnitude are included."""
+    rng = np.random.default_rng(11)
+    if n == 576:
+        A = front576.A
+    else:
+        A = rng.standard_normal((n, n)) * np.exp(rng.uniform(-8, 8, (n, n)))
+    Z = rng.standard_normal((s, n))
+    Z[1] = 0.0
+    Z[2] *= np.exp(rng.uniform(-35, 35, n))
+    W = H.hodlr_matvec(ctx, _dev(A), _dev(Z)).cpu().numpy()
+    ref = (A @ Z.T).T
+    scale = np.ldexp(1.0, (_row_exponents(Z)[:, None] + _row_exponents(A)[None, :]).astype(int))
+    scale[1] = 0.0
+    absz = (np.abs(A) @ np.abs(Z.T)).T
+    err = np.abs(W - ref)
+    assert np.all(err <= 8 * n * 2.0 ** -56 * scale + n * 2.0 ** -50 * absz)
+    assert np.all(W[1] == 0.0)
+    nz = absz > 0
+    assert np.median(err[nz] / absz[nz]) < 2.0 ** -48
+
+
+def test_gmres_many_rhs_tensor_core_product(H, ctx, front576):
+    """GMRES with 20 right-hand sides (products on the tensor cores) gives the
+    same solutions as two solves of 10 (double-float products), each to a true
+    relative residual below 1e-12."""
+    F = front576
+    A = _dev(F.A)
+    b = fg.rhs(F.n, 20, seed=12)
+    h = H.hodlr_build(ctx, A, 64, 1e-4, "aca", precision="fp32")
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    assert info.converged and np.all(info.true_relres <= 1e-12)
+    x = X.cpu().numpy()
+    true = np.linalg.norm(b - F.A @ x.T, axis=0) / np.linalg.norm(b, axis=0)
+    assert np.all(true <= 1.5e-12)
+    for r0 in (0, 10):
+        X2, i2 = H.gmres_solve(ctx, A, _dev(b[:, r0:r0 + 10].T), h, tol=1e-12)
+        assert i2.converged
+        assert np.abs(info.iters[r0:r0 + 10] - i2.iters).max() <= 1
+        x2 = X2.cpu().numpy()
+        assert np.linalg.norm(x[r0:r0 + 10] - x2) / np.linalg.norm(x2) < 1e-10
+    ref = np.linalg.solve(F.A, b)
+    assert np.linalg.norm(x.T - ref) / np.linalg.norm(ref) < 1e-9
+    h.close()
+
+
 @pytest.mark.parametrize("prec,itol", [("fp64", 1), ("fp32", 2)])
 def test_gmres_matches_oracle(H, ctx, front576, prec, itol):
     F = front576
