@@ -60,3 +60,54 @@ def test_ctx_create_without_gpu_fails_cleanly(lib):
 def test_cuda_sources_target_sm103a_only():
     from paper_1403_5337_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_invalid_arguments_are_rejected_before_any_device_call():
+    """Every entry point checks its arguments before it touches the device:
+    NULL handles, negative counts and sizes beyond a fixed limit come back as
+    status codes with a message (no GPU is needed to see them)."""
+    from paper_1403_5337_gb300 import build
+    from paper_1403_5337_gb300 import hodlr as B
+    build.build()
+    L = B.load_library()
+    C = ctypes
+    INVALID, RANGE = 1, 9
+
+    def msg():
+        return L.hodlr_last_error().decode()
+
+    dummy = C.create_string_buffer(64)   # a non-NULL pointer that is never dereferenced
+    mat = B._Matrix(C.cast(dummy, C.c_void_p), 64, 64, 1)
+    out = C.c_void_p()
+    assert L.hodlr_build(None, C.byref(mat), 16, 1e-4, 0, None, None, None, C.byref(out)) == INVALID
+    assert "hodlr_build" in msg()
+    assert L.hodlr_factor(None, None) == INVALID
+    assert L.hodlr_solve(None, 1, None, 64, None) == INVALID
+    info = B._Info()
+    assert L.gmres_solve(None, C.byref(mat), 1, None, 64, None, 64, None, 1e-12, 10, 0, C.byref(info),
+                         None) == INVALID
+    assert "gmres_solve" in msg()
+    assert L.hodlr_matvec(None, C.byref(mat), 1, None, 64, None, 64, None) == INVALID
+    assert L.hodlr_factor_batched(-1, None, None) == INVALID
+    assert L.gmres_solve_batched(None, 1, None, None, None, None, None, None, None, 1e-12, 10, 0, None,
+                                 None) == INVALID
+    outs = (C.c_void_p * 1)()
+    assert L.hodlr_build_batched(None, 1, None, None, 1e-4, 0, None, None, outs) == INVALID
+    # BDLR needs one graph per front: refused for batches before the context is used
+    assert L.hodlr_build_batched(C.cast(dummy, C.c_void_p), 0, None, None, 1e-4, 1, None, None, outs) == INVALID
+    assert "BDLR" in msg()
+    st = B._Stats()
+    assert L.hodlr_stats_get(None, C.byref(st)) == INVALID
+    assert L.hodlr_export_level(None, 1, None, None, None, None, None, None, None) == INVALID
+    assert L.hodlr_export_core(None, 0, None, None) == INVALID
+    val = C.c_double()
+    assert L.hodlr_precond_error(None, 4, None, 64, C.byref(val), None) == INVALID
+    assert L.hodlr_launch_count(None) == INVALID
+    # the allocation-free product's static scratch holds n s <= 2^19 entries
+    big = B._Matrix(C.cast(dummy, C.c_void_p), 1 << 16, 1 << 16, 1)
+    assert L.hodlr_matvec_noalloc(C.byref(big), 16, C.cast(dummy, C.c_void_p), 1 << 16,
+                                  C.cast(dummy, C.c_void_p), 1 << 16, None) == RANGE
+    assert "static scratch" in msg()
+    # releasing nothing is not an error
+    assert L.hodlr_destroy(None) == 0
+    assert L.hodlr_ctx_destroy(None) == 0
