@@ -387,6 +387,46 @@ def test_gmres_iterate_is_krylov_least_squares():
                             rel_tol=1e-6)
 
 
+def test_gmres_restart_one_is_minimal_residual_iteration():
+    """GMRES(1) (restart = 1) is the minimal residual iteration:
+    x_{k+1} = x_k + a_k M r_k, a_k = (r_k . A M r_k) / ||A M r_k||^2."""
+    rng = np.random.default_rng(4)
+    n = 20
+    A = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    M = np.diag(rng.uniform(0.5, 2.0, n))
+    b = rng.standard_normal(n)
+    x = np.zeros(n)
+    for k in range(1, 6):
+        r = b - A @ x
+        q = A @ (M @ r)
+        x = x + (r @ q) / (q @ q) * (M @ r)
+        res = O.gmres(A, b, prec=lambda v: M @ v, tol=1e-30, max_iter=k, restart=1)
+        assert res.iters == k and not res.converged
+        assert np.allclose(res.x, x, rtol=1e-10, atol=1e-12)
+
+
+def test_gmres_two_restart_cycles_are_two_least_squares_solves():
+    """GMRES(m) over two cycles: each cycle minimises ||b - A x|| over
+    x_prev + M K_m(A M, r_prev), r_prev the true residual of the previous iterate."""
+    rng = np.random.default_rng(5)
+    n, m = 30, 4
+    A = rng.standard_normal((n, n)) + 5 * np.eye(n)
+    M = np.diag(rng.uniform(0.5, 2.0, n))
+    b = rng.standard_normal(n)
+    x = np.zeros(n)
+    for _ in range(2):
+        r = b - A @ x
+        Kry = [r]
+        for _ in range(m - 1):
+            Kry.append(A @ (M @ Kry[-1]))
+        Kmat = M @ np.stack(Kry, axis=1)
+        c, *_ = np.linalg.lstsq(A @ Kmat, r, rcond=None)
+        x = x + Kmat @ c
+    res = O.gmres(A, b, prec=lambda v: M @ v, tol=1e-30, max_iter=2 * m, restart=m)
+    assert res.iters == 2 * m
+    assert np.allclose(res.x, x, rtol=1e-8, atol=1e-10)
+
+
 def test_gmres_zero_rhs_and_max_iter():
     A = np.eye(5) * 2
     r = O.gmres(A, np.zeros(5))
