@@ -2,6 +2,7 @@
 hand-derived worked examples, closed forms, identities, brute force on tiny inputs.
 CPU only."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -457,3 +458,36 @@ def test_precond_error_limits():
     assert O.precond_error(A, lambda v: np.linalg.solve(A, v), Om) < 1e-14
     e = O.precond_error(A, lambda v: v, Om)
     assert math.isclose(e, np.linalg.norm(Om - A @ Om) / np.linalg.norm(Om))
+
+
+def _golden(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = []
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            rows.append(line)
+    return rows
+
+
+def test_default_bdlr_depth_follows_table3():
+    """Without an explicit depth the oracle's BDLR build takes the depth the
+    paper pairs with the tolerance (Table 3 caption, tests/golden): the blocks
+    and the candidate row / column sets equal those of the explicit depth, and
+    the candidate sets differ from those of the next depth."""
+    F = fg.make_front(16, 16, 4, 4, "lognormal", 0.5, leaf=16, seed=0)
+    tree = O.make_tree(F.n, 16, F.bounds)
+    graph = (F.rowptr, F.colind)
+    rows = _golden("bdlr_depth_per_tolerance.txt")
+    assert [(float(t), int(d)) for t, d in rows] == [(1e-1, 1), (1e-3, 3), (1e-5, 5)]
+    for t, d in rows:
+        tol, depth = float(t), int(d)
+        auto = O.build(F.A, tree, "bdlr", tol, graph=graph)
+        expl = O.build(F.A, tree, "bdlr", tol, graph=graph, depth=depth)
+        other = O.build(F.A, tree, "bdlr", tol, graph=graph, depth=depth + 1)
+        assert auto.keys() == expl.keys()
+        for key in auto:
+            assert np.array_equal(O.assemble(F.A, tree, {key: auto[key]}), O.assemble(F.A, tree, {key: expl[key]}))
+            assert auto[key].info_ab.I == expl[key].info_ab.I and auto[key].info_ba.J == expl[key].info_ba.J
+        assert any(auto[k].info_ab.I != other[k].info_ab.I for k in auto)
+
