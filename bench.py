@@ -164,6 +164,20 @@ def _save_inputs(F, B):
     return path
 
 
+def job_time(total_ms, steps, world, device):
+    """The timed region's length over the whole job: the maximum over ranks (an
+    all-reduce when world > 1), the time per step, and the value, time per
+    frontal solve, every rank solving its own front in each step."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return total_ms, ms_per_step, ms_per_step / world
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -431,12 +445,7 @@ def main():
     total_ms, infos, X = timed(args.precision, args.steps, args.warmup)
     clk = clocks.stop()
     n_launches = launches[1] - launches[0]
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = ms_per_step / world
+    total_ms, ms_per_step, value = job_time(total_ms, args.steps, world, "cuda")
     info, st = infos[-1]
     converged = bool(info.converged and np.all(info.true_relres <= 1e-12))
 
