@@ -30,6 +30,16 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
+# generated fronts and scratch files stay inside the repository unless the
+# caller points HODLR_FRONT_CACHE elsewhere
+os.environ.setdefault("HODLR_FRONT_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), ".front_cache"))
+
+
+def _scratch_dir():
+    d = os.environ["HODLR_FRONT_CACHE"]
+    os.makedirs(d, exist_ok=True)
+    return d
+
 METRIC = "time to 1e-12 relative residual per frontal solve"
 # arithmetic of the path per --precision: preconditioner storage + factor, then the FP64 Krylov loop
 DTYPE = {"fp32": "f32+f64", "bf16": "bf16+f32+f64", "fp16": "f16+f32+f64", "fp64": "f64"}
@@ -64,7 +74,7 @@ class Clocks:
 
     def start(self):
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            fd, self.path = tempfile.mkstemp(suffix=".csv", dir=_scratch_dir())
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -157,7 +167,7 @@ def _oracle_subprocess(path, leaf, method, tol, reps):
 
 
 def _save_inputs(F, B):
-    fd, path = tempfile.mkstemp(suffix=".npz")
+    fd, path = tempfile.mkstemp(suffix=".npz", dir=_scratch_dir())
     os.close(fd)
     A = F.A if isinstance(F.A, np.ndarray) else F.A.cpu().numpy()
     np.savez(path, A=A, B=B, bounds=F.bounds, rowptr=F.rowptr, colind=F.colind)
