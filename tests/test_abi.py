@@ -111,3 +111,45 @@ def test_invalid_arguments_are_rejected_before_any_device_call():
     # releasing nothing is not an error
     assert L.hodlr_destroy(None) == 0
     assert L.hodlr_ctx_destroy(None) == 0
+
+
+_C_CHECK = r"""
+#include "hodlr.h"
+#include <stdio.h>
+#include <string.h>
+int main(void) {
+    hodlr_opts o;
+    long long launches = -1;
+    hodlr_opts_default(&o);
+    if (strcmp(hodlr_status_string(HODLR_OK), "ok") != 0) return 1;
+    if (hodlr_launch_count(&launches) != HODLR_OK || launches < 0) return 2;
+    if (hodlr_factor(NULL, NULL) != HODLR_INVALID_ARG) return 3;
+    if (hodlr_last_error()[0] == '\0') return 4;
+    if (hodlr_destroy(NULL) != HODLR_OK) return 5;
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_boundary_is_plain_c():
+    """The boundary is usable from C: a C99 program including include/hodlr.h
+    compiles with -Wall -Wextra -Werror, links against libhodlr.so and calls
+    the entry points that need no device (status strings, option defaults,
+    launch count, argument checks)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1403_5337_gb300 import build
+    libpath = build.build()
+    d = os.path.join(ROOT, "paper_1403_5337_gb300", "_build", "ctest")
+    os.makedirs(d, exist_ok=True)
+    src, exe = os.path.join(d, "abi_check.c"), os.path.join(d, "abi_check")
+    with open(src, "w") as f:
+        f.write(_C_CHECK)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), src,
+                    "-o", exe, libpath, "-Wl,-rpath," + os.path.dirname(libpath)], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
