@@ -217,7 +217,9 @@ hodlr_status hodlr_factor_batched(int nf, hodlr_t *const *h, hodlr_stream stream
  * HODLR_NOT_CONVERGED if any front misses tol (all fronts are still solved).
  * Fronts are set up and their first cycles enqueued in windows with one host
  * wait per window, so a front that restarts has an info.ms_total that also spans
- * later fronts' first cycles.  Synchronises `stream`. */
+ * later fronts' first cycles.  The fronts run on the context's internal streams,
+ * after the work already queued on `stream`; all of it is complete when the call
+ * returns.  Synchronises `stream`. */
 hodlr_status gmres_solve_batched(hodlr_ctx *ctx, int nf, const hodlr_matrix *A, const int *s,
                                  const double *const *B, const int64_t *ldb, double *const *X,
                                  const int64_t *ldx, const hodlr_t *const *P, double tol, int max_iter,
