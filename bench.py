@@ -30,13 +30,14 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-# generated fronts and scratch files stay inside the repository unless the
-# caller points HODLR_FRONT_CACHE elsewhere
-os.environ.setdefault("HODLR_FRONT_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), ".front_cache"))
 
 
 def _scratch_dir():
-    d = os.environ["HODLR_FRONT_CACHE"]
+    """Where the benchmark's scratch files go: $HODLR_FRONT_CACHE (the front
+    cache's directory) when set, else the system's temporary directory."""
+    d = os.environ.get("HODLR_FRONT_CACHE")
+    if not d:
+        return tempfile.gettempdir()
     os.makedirs(d, exist_ok=True)
     return d
 

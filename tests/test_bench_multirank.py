@@ -15,13 +15,13 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, totals, steps, out):
+def _worker(rank, world, port, totals, steps, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    out[rank] = bench.job_time(totals[rank], steps, world, "cpu")
+    q.put((rank, bench.job_time(totals[rank], steps, world, "cpu")))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -31,10 +31,9 @@ def test_job_time_is_the_slowest_rank_over_the_whole_job():
     frontal solve of the job (per-step time / number of ranks, each rank solving
     one front per step)."""
     world, steps = 2, 4
-    with mp.Manager() as mgr:
-        out = mgr.dict()
-        mp.spawn(_worker, args=(world, _free_port(), [10.0, 14.0], steps, out), nprocs=world, join=True)
-        res = dict(out)
+    q = mp.get_context("spawn").SimpleQueue()
+    mp.spawn(_worker, args=(world, _free_port(), [10.0, 14.0], steps, q), nprocs=world, join=True)
+    res = dict(q.get() for _ in range(world))
     for r in range(world):
         total, per_step, value = res[r]
         assert total == 14.0 and per_step == 3.5 and value == 1.75
