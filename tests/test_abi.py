@@ -153,3 +153,48 @@ def test_boundary_is_plain_c():
                     "-o", exe, libpath, "-Wl,-rpath," + os.path.dirname(libpath)], check=True)
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
+
+
+def _ptxas_report(src):
+    """(kernel, stack bytes, spill store bytes, spill load bytes, registers) for
+    every entry function of one source, from ptxas -v (the library's flags)."""
+    import subprocess
+    from paper_1403_5337_gb300 import build
+    d = os.path.join(ROOT, "paper_1403_5337_gb300", "_build", "ptxas")
+    os.makedirs(d, exist_ok=True)
+    obj = os.path.join(d, os.path.basename(src) + ".o")
+    cmd = [build.nvcc(), "-c", os.path.join(build.CSRC, src), "-o", obj, "-I", build.INCLUDE, "-I", build.CSRC,
+           "-Xptxas", "-v"] + build.NVCC_FLAGS + build.ARCH
+    out = subprocess.run(cmd, capture_output=True, text=True, check=True).stderr
+    rows, name = [], None
+    for line in out.splitlines():
+        m = re.search(r"Compiling entry function '([^']+)'", line)
+        if m:
+            name = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes stack frame, (\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m and name:
+            rows.append([name, int(m.group(1)), int(m.group(2)), int(m.group(3)), None])
+            continue
+        m = re.search(r"Used (\d+) registers", line)
+        if m and rows and rows[-1][0] == name and rows[-1][4] is None:
+            rows[-1][4] = int(m.group(1))
+    return rows
+
+
+@pytest.mark.parametrize("src,kernels,allowed", [
+    ("ozaki.cu", ("oz_gemm_kernel", "oz_split_rows_kernel", "oz_split_cols_kernel"), 0),
+    ("gmres.cu", ("arnoldi_tail_kernel", "residual_kernel", "start_cycle_kernel", "backsolve_kernel"), 0),
+    # the double-float product at its 64-register cap (four CTAs of 256 threads
+    # per SM): the variant for a general FP64 z spills 12 bytes
+    ("gmres.cu", ("df_matvec_kernel",), 16),
+])
+def test_product_and_gmres_kernels_do_not_spill(src, kernels, allowed):
+    """The products' and the GMRES kernels keep their state in registers for
+    sm_103a: spill stores, spill loads and stack frame within `allowed` bytes."""
+    rows = _ptxas_report(src)
+    for k in kernels:
+        found = [r for r in rows if k in r[0]]
+        assert found, (k, [r[0] for r in rows])
+        for name, stack, st, ld, regs in found:
+            assert max(st, ld, stack) <= allowed, (name, stack, st, ld, regs)
