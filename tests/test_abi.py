@@ -1,6 +1,7 @@
 """The C-ABI library builds for sm_103a, loads, and exports every declared symbol
 (CPU only: no compute call is made here)."""
 import ctypes
+import functools
 import os
 import re
 
@@ -155,7 +156,22 @@ def test_boundary_is_plain_c():
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
 
 
+_PTXAS_SOURCES = ("ozaki.cu", "gmres.cu", "apply.cu", "factor.cu", "aca_cluster.cu")
+
+
+@functools.lru_cache(maxsize=None)
+def _ptxas_all():
+    """ptxas reports of the checked sources, compiled in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(len(_PTXAS_SOURCES)) as ex:
+        return dict(zip(_PTXAS_SOURCES, ex.map(_ptxas_compile, _PTXAS_SOURCES)))
+
+
 def _ptxas_report(src):
+    return _ptxas_all()[src]
+
+
+def _ptxas_compile(src):
     """(kernel, stack bytes, spill store bytes, spill load bytes, registers) for
     every entry function of one source, from ptxas -v (the library's flags)."""
     import subprocess
@@ -188,6 +204,16 @@ def _ptxas_report(src):
     # the double-float product at its 64-register cap (four CTAs of 256 threads
     # per SM): the variant for a general FP64 z spills 12 bytes
     ("gmres.cu", ("df_matvec_kernel",), 16),
+    # the apply in chunks of 4 and 1 right-hand sides (FP32 factors, every
+    # storage type); the chunk-of-2 variants and the FP64 apply spill (at most
+    # 48 stores / 80 loads, 24-byte frames) and are bounded below
+    ("apply.cu", ("apply_fused_kernelIffLi4", "apply_fused_kernelIf6__halfLi4",
+                  "apply_fused_kernelIf13__nv_bfloat16Li4", "apply_fused_kernelIffLi1"), 0),
+    ("apply.cu", ("apply_fused_kernel",), 80),
+    # register-tiled Gauss-Jordan: the 161-192 FP32 instance spills 48 bytes at 255 registers
+    ("factor.cu", ("gj_blocked_kernel", "gemm_batched_kernel"), 0),
+    ("factor.cu", ("gj_inverse_reg_kernel",), 48),
+    ("aca_cluster.cu", ("aca_cluster_kernel",), 0),
 ])
 def test_product_and_gmres_kernels_do_not_spill(src, kernels, allowed):
     """The products' and the GMRES kernels keep their state in registers for
