@@ -13,8 +13,8 @@ CUDA path, the tests and the benchmark:
 * a counter-based normal generator (SplitMix64 finaliser + Box-Muller), so that
   every coefficient and right-hand side is a pure function of (seed, index);
 * the coefficient fields (lognormal and checkerboard);
-* the exact FP64 plane-by-plane block-tridiagonal elimination of the box onto
-  its middle plane;
+* the exact FP64 block-tridiagonal elimination of the box onto its middle
+  plane (across the planes, or across the lines of thin slabs);
 * the recursive-bisection ordering of the plane (every HODLR node is then a
   rectangle of the plane and a contiguous index range), the plane's 5-point
   adjacency graph in that order (the sparse graph the BDLR row/column selection
@@ -123,15 +123,131 @@ def face_coefficients(a: np.ndarray):
 
 
 # --------------------------------------------------------------------------- front
-def plane_front(a: np.ndarray, n_below: int, device="cpu") -> np.ndarray:
+def _plane_matrix(fx, fy, fz, k, dev):
+    """T_k: the 2D block of plane k of the box operator (x-fastest order); its
+    diagonal carries all six face coefficients of each node."""
+    import torch
+    f64 = torch.float64
+    ny, nx = fx.shape[1], fx.shape[2] - 1
+    n = nx * ny
+    diag = (fx[k, :, :-1] + fx[k, :, 1:] + fy[k, :-1, :] + fy[k, 1:, :]
+            + fz[k] + fz[k + 1]).reshape(-1)
+    t = torch.diag(torch.as_tensor(diag, dtype=f64, device=dev))
+    idx = np.arange(n).reshape(ny, nx)
+    for r_, c_, v_ in ((idx[:, :-1], idx[:, 1:], fx[k, :, 1:-1]),      # x-neighbours
+                       (idx[:-1, :], idx[1:, :], fy[k, 1:-1, :])):     # y-neighbours
+        r = torch.as_tensor(r_.reshape(-1), device=dev)
+        c = torch.as_tensor(c_.reshape(-1), device=dev)
+        v = torch.as_tensor(v_.reshape(-1), dtype=f64, device=dev)
+        t[r, c] = -v
+        t[c, r] = -v
+    return t
+
+
+def _slab_inverse_planes(fx, fy, fz, planes, dev):
+    """(A_slab^-1) on the last plane of `planes` (ordered away from the front):
+    S_0 = T_first, S_{k+1} = T_{k+1} - C_k S_k^-1 C_k, result S_last^-1."""
+    import torch
+    f64 = torch.float64
+    s = None
+    for step, k in enumerate(planes):
+        t = _plane_matrix(fx, fy, fz, k, dev)
+        if s is not None:
+            prev = planes[step - 1]
+            c = torch.as_tensor(fz[max(prev, k)].reshape(-1), dtype=f64, device=dev)
+            t -= c[:, None] * torch.cholesky_inverse(torch.linalg.cholesky(s)) * c[None, :]
+        s = t
+    return torch.cholesky_inverse(torch.linalg.cholesky(s))
+
+
+def _slab_inverse_rows(fx, fy, fz, planes, adj, dev):
+    """The same block, (A_slab^-1) on plane `adj`, by a block-tridiagonal
+    elimination across the y-lines of the slab instead of across its planes.
+
+    Block j holds the slab's nodes with y = j (local order q*nx + x, q the
+    plane's position in sorted `planes`), nb = p*nx of them; neighbouring blocks
+    couple through the diagonal y-face coefficients F_j.  With the block pivots
+    Sigma_0 = B_0, Sigma_j = B_j - F_{j-1} Sigma_{j-1}^-1 F_{j-1}, the columns
+    E of the identity on plane `adj` are solved for by
+      forward   W_j = Sigma_j^-1 (E_j + F_{j-1} W_{j-1})
+      backward  X_j = W_j + Sigma_j^-1 F_j X_{j+1}
+    and the result is X restricted to the rows of plane `adj`.  Only the first
+    nx*(j+1) columns of W_j are non-zero (E_j is non-zero in the columns of line
+    j alone), which the forward sweep exploits.  About 3 ny nb^2 n flops against
+    p n^3 for the plane recursion: the cheaper one for thin slabs."""
+    import torch
+    f64 = torch.float64
+    planes = sorted(planes)
+    p = len(planes)
+    ny, nx = fx.shape[1], fx.shape[2] - 1
+    n = nx * ny
+    nb = p * nx
+    zl = planes.index(adj)
+    q = np.repeat(np.arange(p), nx)          # local plane of each block row
+    x = np.tile(np.arange(nx), p)
+    z = np.asarray(planes)[q]
+
+    def block(j):
+        d = (fx[z, j, x] + fx[z, j, x + 1] + fy[z, j, x] + fy[z, j + 1, x] + fz[z, j, x] + fz[z + 1, j, x])
+        b = np.diag(d)
+        r = np.nonzero(x < nx - 1)[0]                      # x-neighbours
+        b[r, r + 1] = b[r + 1, r] = -fx[z[r], j, x[r] + 1]
+        r = np.nonzero((q < p - 1))[0]                     # z-neighbours, consecutive planes only
+        r = r[np.asarray(planes)[q[r] + 1] == z[r] + 1]
+        b[r, r + nx] = b[r + nx, r] = -fz[z[r] + 1, j, x[r]]
+        return torch.as_tensor(b, dtype=f64, device=dev)
+
+    def couple(j):                                         # F_j between lines j and j+1
+        return torch.as_tensor(fy[z, j + 1, x], dtype=f64, device=dev)
+
+    sinv, W = [], []
+    for j in range(ny):
+        b = block(j)
+        if j > 0:
+            f = couple(j - 1)
+            b -= f[:, None] * sinv[-1] * f[None, :]
+        si = torch.cholesky_inverse(torch.linalg.cholesky(b))
+        rhs = torch.zeros(nb, nx * (j + 1), dtype=f64, device=dev)
+        if j > 0:
+            rhs[:, :nx * j] = couple(j - 1)[:, None] * W[-1]
+        rhs[zl * nx + np.arange(nx), nx * j + np.arange(nx)] += 1.0
+        W.append(si @ rhs)
+        sinv.append(si)
+    G = torch.empty(n, n, dtype=f64, device=dev)
+    X = None
+    for j in range(ny - 1, -1, -1):
+        Xj = torch.zeros(nb, n, dtype=f64, device=dev)
+        Xj[:, :nx * (j + 1)] = W[j]
+        if X is not None:
+            Xj += sinv[j] @ (couple(j)[:, None] * X)
+        W[j] = None
+        X = Xj
+        G[j * nx:(j + 1) * nx] = X[zl * nx:(zl + 1) * nx]
+    return G
+
+
+def _transpose_faces(fx, fy, fz):
+    """Faces of the box with x and y exchanged (so that lines run along the
+    other axis)."""
+    return (np.ascontiguousarray(fy.transpose(0, 2, 1)), np.ascontiguousarray(fx.transpose(0, 2, 1)),
+            np.ascontiguousarray(fz.transpose(0, 2, 1)))
+
+
+def plane_front(a: np.ndarray, n_below: int, device="cpu", method="auto") -> np.ndarray:
     """Exact FP64 Schur complement of the box operator onto plane k = n_below.
 
-    Planes 0..n_below-1 and n_below+1..nz-1 are eliminated one plane at a time:
-    S_0 = T_0, S_{k+1} = T_{k+1} - C_k S_k^{-1} C_k, where T_k is the 2D block of
-    plane k (its diagonal carries all six face coefficients) and C_k is the
-    diagonal matrix of z-face coefficients between planes k and k+1.  The front is
-    T_m - C_below S_below^{-1} C_below - C_above S_above^{-1} C_above, returned in
-    the plane's natural x-fastest order, symmetrised exactly."""
+    The front is T_m - C_below G_below C_below - C_above G_above C_above, where
+    T_m is the 2D block of the middle plane, C the diagonal z-face coefficients
+    to its neighbouring planes and G the block, on the neighbouring plane, of the
+    inverse of the operator restricted to the slab of planes on that side.
+    G comes from one of two exact eliminations of the slab (same values up to
+    rounding):
+      "planes": one plane at a time, S_0 = T_0, S_{k+1} = T_{k+1} - C_k S_k^-1 C_k,
+                G = S_last^-1 (about p n^3 flops for p planes);
+      "rows":   block-tridiagonal across the lines of the slab along its longer
+                side (about 3 ny nb^2 n flops, nb = p * shorter side);
+      "auto":   "rows" when it is at least four times cheaper, else "planes".
+    Returned in the plane's natural x-fastest order, symmetrised exactly."""
     import torch
 
     nz, ny, nx = a.shape
@@ -141,53 +257,31 @@ def plane_front(a: np.ndarray, n_below: int, device="cpu") -> np.ndarray:
     dev = torch.device(device)
     f64 = torch.float64
 
-    def T(k):
-        diag = (fx[k, :, :-1] + fx[k, :, 1:] + fy[k, :-1, :] + fy[k, 1:, :]
-                + fz[k] + fz[k + 1]).reshape(-1)
-        t = torch.diag(torch.as_tensor(diag, dtype=f64, device=dev))
-        idx = np.arange(n).reshape(ny, nx)
-        # x-neighbours
-        r = torch.as_tensor(idx[:, :-1].reshape(-1), device=dev)
-        c = torch.as_tensor(idx[:, 1:].reshape(-1), device=dev)
-        v = torch.as_tensor(fx[k, :, 1:-1].reshape(-1), dtype=f64, device=dev)
-        t[r, c] = -v
-        t[c, r] = -v
-        # y-neighbours
-        r = torch.as_tensor(idx[:-1, :].reshape(-1), device=dev)
-        c = torch.as_tensor(idx[1:, :].reshape(-1), device=dev)
-        v = torch.as_tensor(fy[k, 1:-1, :].reshape(-1), dtype=f64, device=dev)
-        t[r, c] = -v
-        t[c, r] = -v
-        return t
+    def side(planes, adj):
+        p = len(planes)
+        lines, short = max(nx, ny), min(nx, ny)
+        rows_cost = 3.0 * lines * (p * short) ** 2 * n
+        use_rows = method == "rows" or (method == "auto" and 4.0 * rows_cost < p * float(n) ** 3)
+        if not use_rows:
+            return _slab_inverse_planes(fx, fy, fz, planes, dev)
+        if ny >= nx:
+            return _slab_inverse_rows(fx, fy, fz, planes, adj, dev)
+        # lines along x: exchange the axes, eliminate, and map back to x-fastest order
+        G = _slab_inverse_rows(*_transpose_faces(fx, fy, fz), planes, adj, dev)
+        t = torch.as_tensor(np.arange(n).reshape(nx, ny).T.reshape(-1), device=dev)   # natural -> exchanged
+        return G.index_select(0, t).index_select(1, t)
 
-    def cz(k):  # z-faces between plane k and k+1
-        return torch.as_tensor(fz[k + 1].reshape(-1), dtype=f64, device=dev)
-
-    def eliminate(planes, links):
-        s = None
-        for step, k in enumerate(planes):
-            t = T(k)
-            if s is not None:
-                c = links[step - 1]
-                sinv = torch.cholesky_inverse(torch.linalg.cholesky(s))
-                t -= c[:, None] * sinv * c[None, :]
-                del sinv
-            s = t
-        return s
-
-    front = T(m)
+    front = _plane_matrix(fx, fy, fz, m, dev)
     if m > 0:
-        below = list(range(0, m))
-        s = eliminate(below, [cz(k) for k in below[:-1]])
-        c = cz(m - 1)
-        front -= c[:, None] * torch.cholesky_inverse(torch.linalg.cholesky(s)) * c[None, :]
-        del s
+        G = side(list(range(0, m)), m - 1)
+        c = torch.as_tensor(fz[m].reshape(-1), dtype=f64, device=dev)
+        front -= c[:, None] * G * c[None, :]
+        del G
     if m < nz - 1:
-        above = list(range(nz - 1, m, -1))
-        s = eliminate(above, [cz(k - 1) for k in above[:-1]])
-        c = cz(m)
-        front -= c[:, None] * torch.cholesky_inverse(torch.linalg.cholesky(s)) * c[None, :]
-        del s
+        G = side(list(range(nz - 1, m, -1)), m + 1)
+        c = torch.as_tensor(fz[m + 1].reshape(-1), dtype=f64, device=dev)
+        front -= c[:, None] * G * c[None, :]
+        del G
     front = 0.5 * (front + front.T)
     return front.cpu().numpy() if dev.type == "cpu" else front
 

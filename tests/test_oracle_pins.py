@@ -47,6 +47,30 @@ def test_front_is_brute_force_schur_complement(field):
     assert np.allclose(F, S, rtol=1e-12, atol=1e-12 * np.abs(S).max())
 
 
+@pytest.mark.parametrize("field", ["lognormal", "checkerboard"])
+@pytest.mark.parametrize("shape", [(4, 5, 2, 2), (5, 4, 3, 1), (3, 4, 1, 0)])
+def test_line_elimination_is_brute_force_schur_complement(field, shape):
+    """The elimination across the lines of the slabs (the one the thin n = 32768
+    front takes) against the dense Schur complement, both line directions."""
+    nx, ny, below, above = shape
+    nz = below + 1 + above
+    a = (fg.coefficient_lognormal(nx, ny, nz, 0.7, seed=5) if field == "lognormal"
+         else fg.coefficient_checkerboard(nx, ny, nz, cell=2, contrast=1e3))
+    M = _dense_3d_operator(a)
+    s = np.arange(nx * ny) + nx * ny * below
+    i = np.setdiff1d(np.arange(M.shape[0]), s)
+    S = M[np.ix_(s, s)] - M[np.ix_(s, i)] @ np.linalg.solve(M[np.ix_(i, i)], M[np.ix_(i, s)])
+    F = fg.plane_front(a, below, method="rows")
+    assert np.allclose(F, S, rtol=1e-12, atol=1e-12 * np.abs(S).max())
+
+
+def test_line_and_plane_eliminations_agree():
+    a = fg.coefficient_lognormal(12, 20, 9, 0.5, seed=0)
+    F1 = fg.plane_front(a, 4, method="planes")
+    F2 = fg.plane_front(a, 4, method="rows")
+    assert np.abs(F1 - F2).max() <= 1e-13 * np.abs(F1).max()
+
+
 def test_front_invariants():
     F = fg.make_front(8, 6, 3, 2, "lognormal", 0.5, leaf=8, seed=0)
     A = F.A
@@ -190,6 +214,98 @@ def test_aca_rank_cap():
 def test_aca_zero_block():
     r = _aca_matrix(np.zeros((4, 6)), 1e-6)
     assert r.U.shape == (4, 0) and r.V.shape == (6, 0)
+
+
+# ------------------------------------------------- ACA and LU in FP32 arithmetic
+# The single-precision compression mode rounds the block entries to FP32 and
+# forms every residual entry term by term, one FP32 multiply and one FP32
+# subtract per term, every pivot scaling and LU update in FP32.  The values
+# below are worked out by hand from IEEE round-to-nearest-even:
+#   fl32(1/3) = 11184811 * 2^-25, fl32(2/3) = 11184811 * 2^-24,
+#   fl32(3 * fl32(1/3)) = fl32(1 + 2^-25) = 1, fl32(3 * fl32(2/3)) = fl32(2 + 2^-24) = 2,
+#   fl32(1 - fl32(1/3)) = fl32(11184810.5 * 2^-24) = 11184810 * 2^-24 (tie to even).
+THIRD32 = 11184811 * 2.0 ** -25
+
+
+def _aca_dense(A, tol, dtype, cap=100):
+    m, n = A.shape
+    return O.aca(lambda i: A[i, :], lambda j: A[:, j], m, n, tol, cap, dtype)
+
+
+def test_aca_fp32_rounds_entries_first():
+    # 1 and 1 + 2^-30 are the same FP32 number: a tie, so the lowest column wins;
+    # in FP64 the larger entry wins.
+    A = np.array([[1.0, 1.0 + 2.0 ** -30, 0.5], [0.25, 0.5, 2.0], [0.5, 0.125, 1.0]])
+    assert _aca_dense(A, 1e-12, np.float32).cols[0] == 0
+    assert _aca_dense(A, 1e-12, np.float64).cols[0] == 1
+
+
+def test_aca_fp32_hand_run_rounding_points():
+    """Step 1 pivots on the 3 of row 0, v_1 = [1, fl32(1/3), fl32(2/3)], u_1 = [3, 3, 1].
+    Step 2 takes row 1: per-term FP32 gives r = [0, 2^-22, -2^-22], a tie, so j_2 = 1
+    and v_2 = [0, 1, -1], u_2 = [0, 2^-22, -fl32(1/3)].  Forming the products
+    u_1[1] v_1 exactly and rounding the residual once would give
+    r = [0, 7 * 2^-25, -10 * 2^-25] and j_2 = 2 instead."""
+    A = np.array([[3.0, 1.0, 2.0],
+                  [3.0, 1.0 + 2.0 ** -22, 2.0 - 2.0 ** -22],
+                  [1.0, 0.0, 0.0]])
+    r = _aca_dense(A, 1e-12, np.float32)
+    assert r.rows[:2] == [0, 1] and r.cols[:2] == [0, 1]
+    assert r.V[:, 0].tolist() == [1.0, THIRD32, 2 * THIRD32]
+    assert r.U[:, 0].tolist() == [3.0, 3.0, 1.0]
+    assert r.V[:, 1].tolist() == [0.0, 1.0, -1.0]
+    assert r.U[:, 1].tolist() == [0.0, 2.0 ** -22, -THIRD32]
+    # the wrong rounding point changes the decision (the reading is not vacuous)
+    rr = np.float32(A[1, 1]) - np.float32(np.float64(3.0) * THIRD32)
+    r_once = np.float32(A[1, 1] - 3.0 * THIRD32), np.float32(A[1, 2] - 3.0 * 2 * THIRD32)
+    assert float(rr) == 2.0 ** -22 and abs(r_once[1]) > abs(r_once[0])
+
+
+def test_aca_fp32_equals_fp64_on_dyadic_block():
+    """Two rank-one blocks on disjoint rows/columns with power-of-two pivots: every
+    FP32 operation is exact, so both modes take the same steps and values."""
+    A = np.zeros((6, 5))
+    A[np.ix_([0, 3], [1, 4])] = [[8.0, 4.0], [4.0, 2.0]]
+    A[np.ix_([1, 5], [0, 2])] = [[16.0, 2.0], [4.0, 0.5]]
+    A[2, 3] = 0.25
+    r32, r64 = _aca_dense(A, 1e-12, np.float32), _aca_dense(A, 1e-12, np.float64)
+    assert r32.rows == r64.rows and r32.cols == r64.cols and len(r32.rows) == 3
+    assert np.array_equal(r32.U, r64.U) and np.array_equal(r32.V, r64.V)
+    assert np.array_equal(r32.U @ r32.V.T, A)
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_aca_fp32_recovers_rank_k_to_single_precision(k):
+    rng = np.random.default_rng(k)
+    X = rng.standard_normal((48, k)).astype(np.float32).astype(np.float64)
+    Y = rng.standard_normal((40, k)).astype(np.float32).astype(np.float64)
+    A = X @ Y.T
+    r = _aca_dense(A, 1e-5, np.float32)
+    assert len(r.rows) in (k, k + 1)
+    assert np.linalg.norm(A - r.U @ r.V.T) <= 2e-5 * np.linalg.norm(A)
+
+
+def test_full_pivot_lu_fp32_hand_example():
+    # [[3,1],[1,1]]: pivot 3, multiplier fl32(1/3), second pivot fl32(1 - fl32(1/3))
+    LU, prow, pcol, r = O.full_pivot_lu(np.array([[3.0, 1.0], [1.0, 1.0]]), 1e-12, dtype=np.float32)
+    assert r == 2 and LU.dtype == np.float32
+    assert float(LU[0, 0]) == 3.0 and float(LU[1, 0]) == THIRD32
+    assert float(LU[1, 1]) == 11184810 * 2.0 ** -24
+    LU64, _, _, _ = O.full_pivot_lu(np.array([[3.0, 1.0], [1.0, 1.0]]), 1e-12)
+    assert float(LU64[1, 1]) != float(LU[1, 1])
+
+
+def test_bdlr_fp32_skeleton_hand_example():
+    # path graph 0-1-2-3, rows {0,1}, columns {2,3}: boundary rows I = [1, 0],
+    # columns J = [2, 3] (distance 0, then 1); A(I,J) = [[3,1],[1,1]]
+    A = np.array([[5.0, 2.0, 1.0, 1.0], [2.0, 5.0, 3.0, 1.0], [1.0, 3.0, 5.0, 2.0], [1.0, 1.0, 2.0, 5.0]])
+    rowptr = np.array([0, 1, 3, 5, 6], dtype=np.int32)
+    colind = np.array([1, 0, 2, 1, 3, 2], dtype=np.int32)
+    r = O.bdlr(A, rowptr, colind, range(0, 2), range(2, 4), 1e-12, depth=1, dtype=np.float32)
+    assert r.I == [1, 0] and r.J == [2, 3] and r.Ir == [1, 0] and r.Jr == [2, 3]
+    assert r.pivots.tolist() == [3.0, 11184810 * 2.0 ** -24]
+    # rank 2 of a 2 x 2 block: the skeleton reproduces it to FP32 rounding
+    assert np.allclose(r.U @ r.V.T, A[:2, 2:], rtol=0, atol=1e-6)
 
 
 # --------------------------------------------------------------------------- BDLR
