@@ -109,7 +109,16 @@ typedef struct {
     int rank_cap;               /* maximum rank of an off-diagonal block (<= 1024);
                                    0 = 1024                                          */
     int bdlr_depth;             /* BDLR distance depth d; -1 = round(-log10 tol)     */
-    double core_cond_threshold; /* reserved (Woodbury core condition guard); 0      */
+    double core_cond_threshold; /* Woodbury core condition guard (Sec. 4.3 Factorize,
+                                   the cores S_i^(p)): kappa_1(S) = ||S||_1 ||S^-1||_1
+                                   of every core is computed exactly from the formed S
+                                   and S^-1; with FP32 factor arithmetic (precision
+                                   FP32, BF16, FP16) every core above the threshold is
+                                   formed again with FP64 products of the stored FP32
+                                   factors and inverted in FP64.  0 = tol / 2^-24
+                                   (the kappa at which the FP32 inversion error bound
+                                   kappa u_32 reaches tol); > 0: that threshold;
+                                   < 0: no estimate, no fallback                      */
     const int64_t *leaf_bounds; /* host, optional: 2^L + 1 leaf boundary offsets     */
     int n_leaf_bounds;          /* length of leaf_bounds, or 0                       */
     uint64_t seed;              /* probe seed of hodlr_precond_error                 */
@@ -132,6 +141,12 @@ typedef struct {
     int64_t bytes_factors;               /* device bytes of U, V, d, E, leaf and core factors */
     int factored;
     double ms_compress, ms_factor;       /* device time of the last build / factor */
+    /* condition guard, per core level 0..L-1 (the 2^l cores of the parents of
+     * level l + 1), zero unless factored with the guard on */
+    double core_cond_max[HODLR_MAX_LEVELS];  /* largest kappa_1(S) of the level        */
+    int cores_promoted[HODLR_MAX_LEVELS];    /* cores re-inverted in FP64               */
+    double core_cond_threshold;              /* the threshold in effect (inf: FP64
+                                                arithmetic, never promoted; -1: off)   */
 } hodlr_stats;
 
 /* Per-right-hand-side GMRES results (arrays of length s supplied by the caller,
@@ -232,7 +247,9 @@ hodlr_status gmres_solve_batched(hodlr_ctx *ctx, int nf, const hodlr_matrix *A, 
  * two of its own, the slice products run on the BF16 tensor cores, and the
  * error per term is a few units of 2^-56 max|A(i,:)| max|Z(:,j)| (that path
  * allocates about 14 n^2 bytes for A's slices per call, and falls back to the
- * double-float product when they cannot be allocated). */
+ * double-float product when they cannot be allocated).  Synchronises `stream`:
+ * a NaN, an infinity or an entry outside the representable range in A or Z
+ * returns HODLR_NONFINITE_INPUT (W is then not meaningful). */
 hodlr_status hodlr_matvec(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *Z,
                           int64_t ldz, double *W, int64_t ldw, hodlr_stream stream);
 
@@ -286,6 +303,14 @@ hodlr_status hodlr_export_level(const hodlr_t *h, int level, double *U, double *
  * Synchronises `stream`. */
 hodlr_status hodlr_export_core(const hodlr_t *h, int level, double *Sinv, hodlr_stream stream);
 
+/* The condition guard's record of the cores of level `level` (0..L-1): kappa_1
+ * of each of the 2^level cores (host, may be NULL) and whether it was
+ * re-inverted in FP64 (host, may be NULL; 1 = yes).  hodlr_export_core returns
+ * the FP64 inverse of such a core.  HODLR_INVALID_ARG when the guard is off.
+ * Synchronises `stream`. */
+hodlr_status hodlr_export_core_cond(const hodlr_t *h, int level, double *cond, int32_t *promoted,
+                                    hodlr_stream stream);
+
 hodlr_status hodlr_destroy(hodlr_t *h);
 
 const char *hodlr_status_string(hodlr_status s);
@@ -296,6 +321,19 @@ const char *hodlr_last_error(void);
  * device-side loop of a recorded GMRES iteration included (counted once the
  * solve returns).  `out` is host memory; never fails unless `out` is NULL. */
 hodlr_status hodlr_launch_count(long long *out);
+
+/* Test hook of the bounded device waits (no counterpart in the paper).  The
+ * apply of hodlr_solve and of gmres_solve waits, per tree node, for the arrival
+ * of the node's row tiles; every such wait gives up after `spin_limit` polls
+ * (0 = the library default, about 2^26 polls of ~32 ns) and then sets the
+ * context's status word, which the next synchronising call returns as
+ * HODLR_TIMEOUT; the kernel carries on and returns (the results of that call
+ * are not meaningful).  With `unreachable` non-zero each wait also expects one
+ * tile more than exists, so that every wait runs out: a test of the timeout
+ * path that never leaves a kernel waiting without bound.  Reset with (0, 0).
+ * Affects later calls on the context (a solve's recorded iteration keeps the
+ * values it was recorded with). */
+hodlr_status hodlr_ctx_set_wait_test(hodlr_ctx *ctx, unsigned long long spin_limit, int unreachable);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ Contents and the passage each follows
 * gmres                -- GMRES (Section 3) with the HODLR solve as a right
                           preconditioner.
 * precond_error        -- the randomised estimate ||(I - P^-1 A) Omega||_F/||Omega||_F.
+* precond_error_2norm  -- the exact ||I - P^-1 A||_2 by dense SVD (small n).
 * dense_floor          -- FP64 partial-pivoting dense LU residual floor.
 
 Readings of points the paper leaves open (each is also tested):
@@ -538,6 +539,13 @@ def precond_error(A: np.ndarray, prec, Omega: np.ndarray) -> float:
     """||(I - P^-1 A) Omega||_F / ||Omega||_F for a given probe block Omega."""
     E = Omega - prec(A @ Omega)
     return float(np.linalg.norm(E) / np.linalg.norm(Omega))
+
+
+def precond_error_2norm(A: np.ndarray, prec) -> float:
+    """The exact ||I - P^-1 A||_2: P^-1 applied to every column of A, then the
+    largest singular value (dense SVD; for n up to a few thousand)."""
+    E = np.eye(A.shape[0]) - prec(A)
+    return float(np.linalg.svd(E, compute_uv=False)[0])
 
 
 def dense_floor(A: np.ndarray, b: np.ndarray) -> float:

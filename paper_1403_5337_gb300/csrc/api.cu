@@ -289,6 +289,16 @@ const char *hodlr_status_string(hodlr_status s) {
 
 const char *hodlr_last_error(void) { return g_err; }
 
+hodlr_status hodlr_ctx_set_wait_test(hodlr_ctx *c, unsigned long long spin_limit, int unreachable) {
+    if (!c || spin_limit > (1ull << 40)) {
+        set_error("hodlr_ctx_set_wait_test: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    c->wait_limit = spin_limit;
+    c->wait_extra = unreachable ? 1u : 0u;
+    return HODLR_OK;
+}
+
 hodlr_status hodlr_launch_count(long long *out) {
     if (!out) return HODLR_INVALID_ARG;
     *out = hodlr::launch_total();
@@ -511,6 +521,14 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
     h->rank_cap = rank_cap;
     h->ldn = (n + 31) / 32 * 32;
     h->lv.resize(L + 1);
+    // the Woodbury core condition guard: kappa_1 of every core (unless the
+    // threshold is negative); with FP32 arithmetic the cores above the
+    // threshold are re-inverted in FP64.  Default threshold: tol / 2^-24, the
+    // condition at which an FP32 inversion's error bound kappa u_32 reaches the
+    // compression tolerance.
+    h->guard = o.core_cond_threshold >= 0.0;
+    h->promote = h->guard && h->prec == HODLR_FP32;
+    h->cond_thr = o.core_cond_threshold > 0.0 ? o.core_cond_threshold : tol / 5.9604644775390625e-8;
     int64_t bmax = 0;
     for (int i = 0; i < nleaf; ++i) bmax = std::max(bmax, bounds[i + 1] - bounds[i]);
     h->bmax = (int)bmax;
@@ -700,6 +718,9 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
     h->Vql.assign(L + 1, nullptr);
     h->Eql.assign(L + 1, nullptr);
     h->Sinv.assign(L, nullptr);
+    h->core_cond.assign(L, nullptr);
+    h->core_flag.assign(L, nullptr);
+    h->Sinv64.assign(L, nullptr);
     h->vscale.assign(L + 1, nullptr);
     h->escale.assign(L + 1, nullptr);
     if (factor_now && L > 0) {
@@ -773,6 +794,9 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
             oV = la.take(colb * pe);
         }
         const size_t oS = la.take((size_t)(1 << (l - 1)) * std::max<int64_t>(s2 * s2, 1) * pe);
+        const size_t oCond = h->guard ? la.take((size_t)(1 << (l - 1)) * sizeof(double)) : 0;
+        const size_t oFlag = h->guard ? la.take((size_t)(1 << (l - 1)) * sizeof(int)) : 0;
+        const size_t oS64 = h->promote ? la.take((size_t)(1 << (l - 1)) * std::max<int64_t>(s2 * s2, 1) * 8) : 0;
         if (h->store == HODLR_FP16) {
             const size_t scb = (size_t)lv.nnodes * std::max(lv.rp, 1) * sizeof(float);
             ovs = la.take(scb);
@@ -788,6 +812,18 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
         h->Ul[l] = lb + oU;
         h->Dl[l] = lb + oD;
         h->Sinv[l - 1] = lb + oS;
+        if (h->guard) {
+            h->core_cond[l - 1] = (double *)(lb + oCond);
+            h->core_flag[l - 1] = (int *)(lb + oFlag);
+            // a level without ranks has identity cores: kappa 1, nothing to redo
+            if (lv.rp == 0) {
+                std::vector<double> one((size_t)1 << (l - 1), 1.0);
+                cudaMemcpyAsync(h->core_cond[l - 1], one.data(), one.size() * 8, cudaMemcpyHostToDevice, st);
+                cudaMemsetAsync(h->core_flag[l - 1], 0, one.size() * sizeof(int), st);
+                cudaStreamSynchronize(st);
+            }
+        }
+        if (h->promote) h->Sinv64[l - 1] = (double *)(lb + oS64);
         if (q16) {
             h->El[l] = lb + oE;
             h->Vl[l] = lb + oV;
@@ -1021,12 +1057,16 @@ hodlr_status hodlr_matvec(hodlr_ctx *c, const hodlr_matrix *A, int s, const doub
             if (r == HODLR_OK) r = oz_matvec(c, abuf, A->n, s, Z, ldz, W, ldw, zbuf, st);
             dfree(c, zbuf, zb, st);
             dfree(c, abuf, ab, st);
-            return r;
+            HODLR_TRY(r);
+            // a non-finite or out-of-range entry is reported here, and the flag
+            // does not reach the context's next call
+            return take_status(c, st);
         }
         if (abuf) dfree(c, abuf, ab, st);
         cudaGetLastError();   // too large for the slices: the double-float product
     }
-    return matvec_impl(c, A->data, A->n, A->ld, s, Z, ldz, W, ldw, st);
+    HODLR_TRY(matvec_impl(c, A->data, A->n, A->ld, s, Z, ldz, W, ldw, st));
+    return take_status(c, st);
 }
 
 hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {
@@ -1053,9 +1093,26 @@ hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {
     o->factored = h->factored ? 1 : 0;
     o->ms_compress = h->ms_compress;
     o->ms_factor = 0.0;
+    o->core_cond_threshold = h->guard ? (h->promote ? h->cond_thr : INFINITY) : -1.0;
     if (h->factored && h->fev[1] && cudaEventSynchronize(h->fev[1]) == cudaSuccess) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->fev[0], h->fev[1]) == cudaSuccess) o->ms_factor = ms;
+        if (h->guard) {
+            std::vector<double> cv;
+            std::vector<int> fv;
+            for (int l = 0; l < h->L; ++l) {
+                const size_t nn = (size_t)1 << l;
+                cv.resize(nn);
+                fv.resize(nn);
+                if (cudaMemcpy(cv.data(), h->core_cond[l], nn * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                    cudaMemcpy(fv.data(), h->core_flag[l], nn * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+                    break;
+                for (size_t i = 0; i < nn; ++i) {
+                    o->core_cond_max[l] = std::max(o->core_cond_max[l], cv[i]);
+                    o->cores_promoted[l] += fv[i];
+                }
+            }
+        }
     }
     cudaGetLastError();
     return HODLR_OK;
@@ -1128,9 +1185,43 @@ hodlr_status hodlr_export_core(const hodlr_t *h, int level, double *Sinv, hodlr_
     else
         to_double_kernel<float><<<blocks, 256, 0, st>>>((const float *)h->Sinv[level], cnt, tmp, cnt, cnt, 1);
     note_launch();
+    if (h->promote && h->Sinv64[level]) {   // cores re-inverted in FP64: their FP64 inverse
+        std::vector<int> fv((size_t)1 << level);
+        HODLR_TRY_CUDA(cudaMemcpyAsync(fv.data(), h->core_flag[level], fv.size() * sizeof(int),
+                                       cudaMemcpyDeviceToHost, st));
+        HODLR_TRY_CUDA(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < fv.size(); ++i)
+            if (fv[i])
+                HODLR_TRY_CUDA(cudaMemcpyAsync(tmp + i * s2 * s2, h->Sinv64[level] + i * s2 * s2,
+                                               (size_t)s2 * s2 * 8, cudaMemcpyDeviceToDevice, st));
+    }
     HODLR_TRY_CUDA(cudaMemcpyAsync(Sinv, tmp, (size_t)cnt * 8, cudaMemcpyDeviceToHost, st));
     HODLR_TRY_CUDA(cudaStreamSynchronize(st));
     dfree(h->ctx, tmp, (size_t)cnt * 8, st);
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_export_core_cond(const hodlr_t *h, int level, double *cond, int32_t *promoted,
+                                    hodlr_stream stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!h || level < 0 || level >= h->L) {
+        set_error("hodlr_export_core_cond: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    if (!h->factored) {
+        set_error("hodlr_export_core_cond: not factored");
+        return HODLR_NOT_FACTORED;
+    }
+    if (!h->guard) {
+        set_error("hodlr_export_core_cond: the condition guard is off (negative core_cond_threshold)");
+        return HODLR_INVALID_ARG;
+    }
+    HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
+    const size_t nn = (size_t)1 << level;
+    if (cond) HODLR_TRY_CUDA(cudaMemcpyAsync(cond, h->core_cond[level], nn * 8, cudaMemcpyDeviceToHost, st));
+    if (promoted)
+        HODLR_TRY_CUDA(cudaMemcpyAsync(promoted, h->core_flag[level], nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    HODLR_TRY_CUDA(cudaStreamSynchronize(st));
     return HODLR_OK;
 }
 

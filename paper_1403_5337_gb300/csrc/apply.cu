@@ -73,6 +73,10 @@ struct FusedArgs {
     double *X;
     float2 *Xs;        // optional: X also as FP32 (hi, lo) pairs, ld ldx (the product's split input)
     int *status;
+    // bound of every wait (polls) and an addition to every wait's target (0;
+    // a test sets 1, a tile that never arrives, to make the waits run out)
+    unsigned long long spin_limit;
+    unsigned target_extra;
 };
 
 // Lane-row / warp-split reduction helper: part[warp][lane][q] -> sum over warps.
@@ -94,12 +98,13 @@ __device__ __forceinline__ void arrive(unsigned *cnt) {
 
 // Wait until all `target` tiles of the node have arrived (bounded: on timeout
 // the status word gets ST_TIMEOUT and the kernel carries on).
-__device__ __forceinline__ void wait_node(const unsigned *cnt, unsigned target, int *status) {
+__device__ __forceinline__ void wait_node(const unsigned *cnt, unsigned target, int *status,
+                                          unsigned long long limit) {
     if (threadIdx.x == 0) {
         const volatile unsigned *vc = cnt;
         unsigned long long spins = 0;
         while (*vc < target) {
-            if (++spins > FA_SPIN_LIMIT) {
+            if (++spins > limit) {
                 atomicOr(status, ST_TIMEOUT);
                 break;
             }
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
             const int child = leaf >> (L - c);
             const unsigned target =
                 (unsigned)(a.tile_first[(node + 1) << shift] - a.tile_first[node << shift]);
-            wait_node(a.cnt[c] + node, target, a.status);
+            wait_node(a.cnt[c] + node, target + a.target_extra, a.status, a.spin_limit);
             const T *wn = a.w[c] + (size_t)node * s2 * a.s;
             const S *Ec = a.Eb + a.eoff[c];
             const float *es = a.escale[c];
@@ -422,6 +427,8 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
     a.n = h->n;
     a.ldn = h->ldn;
     a.ldx = ldx;
+    a.spin_limit = h->ctx->wait_limit ? h->ctx->wait_limit : FA_SPIN_LIMIT;
+    a.target_extra = h->ctx->wait_extra;
     // workspace: x (T), then the zeroed region: w(c) for c = 1..L, the counters
     char *wp = reinterpret_cast<char *>(hm->work);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };

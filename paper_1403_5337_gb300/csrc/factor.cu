@@ -38,18 +38,20 @@ namespace {
 // K slices; 256 threads as 16 x 16, each owning (BM/16)^2 outputs.  The next K
 // slice is loaded into registers while the current one is multiplied from
 // shared memory.  splitK > 1 splits K into that many chunks (multiples of 16)
-// whose partial products are combined with atomics.
+// whose partial products are combined with atomics.  Operands of type TI are
+// widened to T as they are loaded; a descriptor whose gate reads 0 is skipped.
 constexpr int GB_K = 16, GB_THREADS = 256;
 
-template <typename T, int BM>
+template <typename T, typename TI, int BM>
 __global__ void __launch_bounds__(GB_THREADS)
-    gemm_batched_kernel(const GemmDesc<T> *__restrict__ descs, int transA, T alpha, int splitK) {
+    gemm_batched_kernel(const GemmDesc<T, TI> *__restrict__ descs, int transA, T alpha, int splitK) {
     constexpr int TPT = BM / 16;                 // outputs per thread per dimension
     constexpr int LPT = BM * GB_K / GB_THREADS;  // tile elements loaded per thread
-    const GemmDesc<T> d = descs[blockIdx.z / splitK];
+    const GemmDesc<T, TI> d = descs[blockIdx.z / splitK];
     const int kz = blockIdx.z % splitK;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BM;
     if (m0 >= d.M || n0 >= d.N || d.K <= 0) return;
+    if (d.gate && *d.gate == 0) return;
     const int kper = ((d.K + splitK - 1) / splitK + GB_K - 1) / GB_K * GB_K;
     const int kbeg = kz * kper;
     const int kend = min(d.K, kbeg + kper);
@@ -73,12 +75,12 @@ __global__ void __launch_bounds__(GB_THREADS)
             }
             T v = T(0);
             if (m0 + i < d.M && k0 + kk < kend)
-                v = transA ? d.A[(int64_t)(k0 + kk) + (int64_t)(m0 + i) * d.lda]
-                           : d.A[(int64_t)(m0 + i) + (int64_t)(k0 + kk) * d.lda];
+                v = (T)(transA ? d.A[(int64_t)(k0 + kk) + (int64_t)(m0 + i) * d.lda]
+                               : d.A[(int64_t)(m0 + i) + (int64_t)(k0 + kk) * d.lda]);
             ra[u] = v;
             const int kb = e % GB_K, j = e / GB_K;
             T w = T(0);
-            if (n0 + j < d.N && k0 + kb < kend) w = d.B[(int64_t)(k0 + kb) + (int64_t)(n0 + j) * d.ldb];
+            if (n0 + j < d.N && k0 + kb < kend) w = (T)d.B[(int64_t)(k0 + kb) + (int64_t)(n0 + j) * d.ldb];
             rb[u] = w;
         }
     };
@@ -150,6 +152,7 @@ struct GJDesc {
     T *out;               // b x b column-major
     int64_t ldo;
     int b;
+    const int *gate;      // device, optional: the matrix is skipped when *gate == 0
 };
 
 constexpr int GJ_THREADS = 512;
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_inverse_kernel(const GJDesc<T> 
                                                                 int *status) {
     const GJDesc<T> g = descs[blockIdx.x];
     const int b = g.b, tid = threadIdx.x;
-    if (b <= 0) return;
+    if (b <= 0 || (g.gate && *g.gate == 0)) return;
     if (g.work == nullptr) {   // host-side sizing error: report, never touch memory
         if (tid == 0) atomicOr(status, ST_RANGE);
         return;
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(GJS_THREADS) gj_inverse_smem_kernel(const GJDe
                                                                       int *status) {
     const GJDesc<T> g = descs[blockIdx.x];
     const int b = g.b, tid = threadIdx.x;
-    if (b <= 0) return;
+    if (b <= 0 || (g.gate && *g.gate == 0)) return;
     const int ldb = b + 1;
     extern __shared__ __align__(16) unsigned char smem[];
     T *a = reinterpret_cast<T *>(smem);            // ldb * b
@@ -402,6 +405,9 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJ
     const GJDesc<T> g = descs[blockIdx.x];
     const int b = g.b;
     if (b <= 0) return;
+    if constexpr (sizeof(T) == 8) {   // only the FP64 re-inversion of the guarded cores is gated
+        if (g.gate && *g.gate == 0) return;
+    }
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     __shared__ T colk[2][MR * GJR_TY];
     __shared__ T rowk[2][MC * GJR_TX];
@@ -809,6 +815,74 @@ __global__ void quantize_kernel(const float *__restrict__ src, S *__restrict__ d
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) y[i] = to_store<S>(x[i] * f);
 }
 
+// Condition of the Woodbury cores of one level in the 1-norm, exactly from the
+// matrices the factorisation forms: S = [[I, P], [Q, I]] (P, Q the two halves of
+// the children's V^T d, 2r x r column-major, ld 2r) and S^-1 (2r x 2r), so
+//   ||S||_1 = 1 + max_j max(sum_i |P(i,j)|, sum_i |Q(i,j)|),
+//   ||S^-1||_1 = max_j sum_i |S^-1(i,j)|,  kappa_1 = ||S||_1 ||S^-1||_1.
+// One CTA per core, a warp per column.  flag = kappa_1 > thr (or not finite).
+constexpr int CC_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(CC_THREADS)
+    core_cond_kernel(const T *__restrict__ Y, const T *__restrict__ Sinv, int r, double thr, double *cond, int *flag) {
+    const int i = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = CC_THREADS / 32;
+    const int64_t s2 = 2 * (int64_t)r;
+    const T *Yi = Y + (size_t)i * s2 * r;
+    const T *Si = Sinv + (size_t)i * s2 * s2;
+    __shared__ double red_s[NW], red_i[NW];
+    double ms = 0.0, mi = 0.0;
+    for (int j = warp; j < r; j += NW) {   // columns of P and Q
+        double p = 0.0, q = 0.0;
+        for (int k = lane; k < r; k += 32) {
+            p += fabs((double)Yi[k + j * s2]);
+            q += fabs((double)Yi[r + k + j * s2]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(0xffffffffu, p, o);
+            q += __shfl_xor_sync(0xffffffffu, q, o);
+        }
+        ms = fmax(ms, fmax(p, q));
+    }
+    for (int j = warp; j < s2; j += NW) {  // columns of S^-1
+        double a = 0.0;
+        for (int k = lane; k < s2; k += 32) a += fabs((double)Si[k + j * s2]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        mi = (a > mi || a != a) ? a : mi;   // a NaN column makes the core unusable
+    }
+    if (lane == 0) {
+        red_s[warp] = ms;
+        red_i[warp] = mi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            a = fmax(a, red_s[w]);
+            b = (red_i[w] > b || red_i[w] != red_i[w]) ? red_i[w] : b;
+        }
+        double k = (1.0 + a) * b;
+        if (!(k <= 1.7976931348623157e308)) k = __longlong_as_double(0x7ff0000000000000LL);   // NaN, inf -> inf
+        cond[i] = k;
+        flag[i] = (k > thr) ? 1 : 0;
+    }
+}
+
+// S^-1 of the cores re-inverted in FP64, rounded into the FP32 core array
+// (blockIdx.y = core; cores whose flag is 0 keep their FP32 inverse).
+__global__ void core_store_kernel(const double *__restrict__ S64, float *__restrict__ S32, int64_t per,
+                                  const int *__restrict__ flag) {
+    const int i = blockIdx.y;
+    if (!flag[i]) return;
+    const double *a = S64 + (size_t)i * per;
+    float *b = S32 + (size_t)i * per;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = __double2float_rn(a[e]);
+}
+
 // Which Gauss-Jordan variant launch_gj picks for matrices up to bmax: registers,
 // shared memory, or the global-memory kernel (the only one that needs GJDesc::work).
 template <typename T>
@@ -885,19 +959,21 @@ template <typename T>
 struct Rec {
     hodlr_ctx *c;
     LevelPlan *P;
-    void gj(const std::vector<GJDesc<T>> &hd) {
+    template <typename TG>
+    void gj(const std::vector<GJDesc<TG>> &hd) {
         if (hd.empty()) return;
         int bmax = 0;
         for (auto &g : hd) bmax = std::max(bmax, g.b);
-        const size_t off = P->put(hd.data(), hd.size() * sizeof(GJDesc<T>));
+        const size_t off = P->put(hd.data(), hd.size() * sizeof(GJDesc<TG>));
         const int cnt = (int)hd.size();
         hodlr_ctx *cc = c;
         LevelPlan *PP = P;
         P->ops.push_back([=](cudaStream_t s) {
-            return launch_gj<T>(cc, reinterpret_cast<const GJDesc<T> *>(PP->dblob + off), cnt, bmax, s);
+            return launch_gj<TG>(cc, reinterpret_cast<const GJDesc<TG> *>(PP->dblob + off), cnt, bmax, s);
         });
     }
-    void gemm(const std::vector<GemmDesc<T>> &hd, int transA, T alpha) {
+    template <typename TC, typename TI>
+    void gemm(const std::vector<GemmDesc<TC, TI>> &hd, int transA, TC alpha) {
         if (hd.empty()) return;
         int maxM = 0, maxN = 0, maxK = 0;
         for (auto &g : hd) {
@@ -906,25 +982,28 @@ struct Rec {
             maxK = std::max(maxK, g.K);
         }
         if (maxM == 0 || maxN == 0 || maxK == 0) return;
-        const size_t off = P->put(hd.data(), hd.size() * sizeof(GemmDesc<T>));
+        const size_t off = P->put(hd.data(), hd.size() * sizeof(GemmDesc<TC, TI>));
         const int cnt = (int)hd.size();
         hodlr_ctx *cc = c;
         LevelPlan *PP = P;
         P->ops.push_back([=](cudaStream_t s) {
-            return gemm_batched<T>(cc, reinterpret_cast<const GemmDesc<T> *>(PP->dblob + off), cnt, maxM, maxN,
-                                   maxK, transA, alpha, s);
+            return gemm_batched<TC, TI>(cc, reinterpret_cast<const GemmDesc<TC, TI> *>(PP->dblob + off), cnt, maxM,
+                                        maxN, maxK, transA, alpha, s);
         });
     }
-    void fill(const std::vector<FillDesc<T>> &hd) {
+    // generic: one recorded launch
+    void op(std::function<hodlr_status(cudaStream_t)> f) { P->ops.push_back(std::move(f)); }
+    template <typename TF>
+    void fill(const std::vector<FillDesc<TF>> &hd) {
         if (hd.empty()) return;
         int64_t most = 0;
         for (auto &f : hd) most = std::max(most, f.rows * f.cols * f.count);
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(512, (most + 2047) / 2048));
-        const size_t off = P->put(hd.data(), hd.size() * sizeof(FillDesc<T>));
+        const size_t off = P->put(hd.data(), hd.size() * sizeof(FillDesc<TF>));
         const int cnt = (int)hd.size();
         LevelPlan *PP = P;
         P->ops.push_back([=](cudaStream_t s) {
-            fill_kernel<T><<<dim3(gx, cnt), 256, 0, s>>>(reinterpret_cast<const FillDesc<T> *>(PP->dblob + off));
+            fill_kernel<TF><<<dim3(gx, cnt), 256, 0, s>>>(reinterpret_cast<const FillDesc<TF> *>(PP->dblob + off));
             note_launch();
             HODLR_TRY_CUDA(cudaGetLastError());
             return HODLR_OK;
@@ -964,6 +1043,12 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
     const size_t oM = ws.take((size_t)nn0 * rc * rc * sizeof(T));
     const bool gwn = gj_needs_work<T>(rc);
     const size_t oGW = gwn ? ws.take((size_t)nn0 * 2 * rc * rc * sizeof(T)) : 0;
+    // the FP64 re-inversion of the cores above the condition threshold (FP32 arithmetic)
+    const bool redo = h->promote && sizeof(T) == 4 && rc > 0;
+    const bool gwn64 = redo && gj_needs_work<double>(rc);
+    const size_t oY64 = redo ? ws.take((size_t)nn0 * s2c * rc * sizeof(double)) : 0;
+    const size_t oM64 = redo ? ws.take((size_t)nn0 * rc * rc * sizeof(double)) : 0;
+    const size_t oGW64 = gwn64 ? ws.take((size_t)nn0 * 2 * rc * rc * sizeof(double)) : 0;
     Pl->work = dalloc(cx, ws.bytes, s);
     if (!Pl->work) {
         set_error("factor plan: out of device memory (%zu bytes)", ws.bytes);
@@ -1079,6 +1164,71 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
             rec.gemm(g12, 0, T(-1));
             rec.gemm(g3, 0, T(-1));
         }
+        // ---- the condition guard: kappa_1(S) of every core; with FP32
+        // arithmetic, the cores above the threshold are formed again from the
+        // same stored factors with FP64 products (P, Q), inverted in FP64 and
+        // rounded into the core array before E is formed from it.  Every step is
+        // enqueued for all cores; the flag of a core decides on the device
+        // whether its CTAs do any work.
+        if (h->guard) {
+            double *cond = h->core_cond[c - 1];
+            int *flag = h->core_flag[c - 1];
+            const double thr = h->promote ? h->cond_thr : __builtin_inf();
+            const int cnt = nn0;
+            const int rcc = rc;
+            rec.op([=](cudaStream_t st) {
+                core_cond_kernel<T><<<cnt, CC_THREADS, 0, st>>>(Yo, Sinv, rcc, thr, cond, flag);
+                note_launch();
+                HODLR_TRY_CUDA(cudaGetLastError());
+                return HODLR_OK;
+            });
+        }
+        if (redo) {
+            const int *flag = h->core_flag[c - 1];
+            double *Y64 = reinterpret_cast<double *>(wb + oY64);
+            double *M64 = reinterpret_cast<double *>(wb + oM64);
+            double *gw64 = gwn64 ? reinterpret_cast<double *>(wb + oGW64) : nullptr;
+            double *S64 = h->Sinv64[c - 1];
+            auto Y64i = [&](int i) { return Y64 + (size_t)i * s2c * rc; };
+            rec.fill(std::vector<FillDesc<double>>{
+                FillDesc<double>{Y64, 0, (int64_t)nn0 * s2c * rc, 1, INT_MAX, 1, 0},
+                FillDesc<double>{M64, rc, rc, rc, 0, nn0, (int64_t)rc * rc},            // I
+                FillDesc<double>{S64, s2c, s2c, s2c, rc, nn0, s2c * s2c}});             // [0 0; 0 I]
+            std::vector<GemmDesc<double, T>> gy(2 * nn0);
+            for (int ch = 0; ch < 2 * nn0; ++ch) {
+                int64_t r0, m;
+                node_range(c, ch, r0, m);
+                gy[ch] = GemmDesc<double, T>{Vc + r0, Dc + r0, Y64i(ch / 2) + (ch & 1) * rc, ldn, ldn, s2c, rc, rc,
+                                             (int)m, flag + ch / 2};
+            }
+            rec.gemm(gy, 1, 1.0);
+            std::vector<GemmDesc<double>> gm(nn0), g12(2 * nn0), g3(nn0);
+            std::vector<GJDesc<double>> gj(nn0);
+            for (int i = 0; i < nn0; ++i) {
+                double *S = S64 + (size_t)i * s2c * s2c;
+                const double *P = Y64i(i), *Q = Y64i(i) + rc;
+                gm[i] = GemmDesc<double>{P, Q, M64 + (size_t)i * rc * rc, s2c, s2c, rc, rc, rc, rc, flag + i};
+                gj[i] = GJDesc<double>{nullptr, 0, M64 + (size_t)i * rc * rc, rc,
+                                       gw64 ? gw64 + (size_t)i * 2 * rc * rc : nullptr, S, s2c, rc, flag + i};
+                g12[2 * i] = GemmDesc<double>{S, P, S + rc * s2c, s2c, s2c, s2c, rc, rc, rc, flag + i};
+                g12[2 * i + 1] = GemmDesc<double>{Q, S, S + rc, s2c, s2c, s2c, rc, rc, rc, flag + i};
+                g3[i] = GemmDesc<double>{Q, S + rc * s2c, S + rc + rc * s2c, s2c, s2c, s2c, rc, rc, rc, flag + i};
+            }
+            rec.gemm(gm, 0, -1.0);
+            rec.gj(gj);
+            rec.gemm(g12, 0, -1.0);
+            rec.gemm(g3, 0, -1.0);
+            const int cnt = nn0;
+            const int64_t per = s2c * s2c;
+            float *S32 = reinterpret_cast<float *>(h->Sinv[c - 1]);
+            const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (per + 1023) / 1024));
+            rec.op([=](cudaStream_t st) {
+                core_store_kernel<<<dim3(gx, cnt), 256, 0, st>>>(S64, S32, per, flag);
+                note_launch();
+                HODLR_TRY_CUDA(cudaGetLastError());
+                return HODLR_OK;
+            });
+        }
         // ---- E = d_child S^-1(half, :) on every child's rows: the apply's
         // x_child -= d_child y_half with y = S^-1 w becomes x_child -= E w (the
         // first child takes the second half y2, the second child y1)
@@ -1141,8 +1291,8 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
 
 }  // namespace
 
-template <typename T>
-hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T> *d_desc, int nbatch, int maxM, int maxN,
+template <typename T, typename TI>
+hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T, TI> *d_desc, int nbatch, int maxM, int maxN,
                           int maxK, int transA, T alpha, cudaStream_t s) {
     if (nbatch > 65535) {
         hodlr::set_error("gemm_batched: too many batches (%d)", nbatch);
@@ -1160,18 +1310,20 @@ hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T> *d_desc, int nbatch, i
     if ((int64_t)nbatch * splitK > 65535) splitK = std::max(1, 65535 / nbatch);
     dim3 grid(tn, tm, nbatch * splitK);
     if (bm == 64)
-        gemm_batched_kernel<T, 64><<<grid, GB_THREADS, 0, s>>>(d_desc, transA, alpha, splitK);
+        gemm_batched_kernel<T, TI, 64><<<grid, GB_THREADS, 0, s>>>(d_desc, transA, alpha, splitK);
     else
-        gemm_batched_kernel<T, 32><<<grid, GB_THREADS, 0, s>>>(d_desc, transA, alpha, splitK);
+        gemm_batched_kernel<T, TI, 32><<<grid, GB_THREADS, 0, s>>>(d_desc, transA, alpha, splitK);
     note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
 }
 
-template hodlr_status gemm_batched<float>(hodlr_ctx *, const GemmDesc<float> *, int, int, int, int, int,
-                                          float, cudaStream_t);
-template hodlr_status gemm_batched<double>(hodlr_ctx *, const GemmDesc<double> *, int, int, int, int, int,
-                                           double, cudaStream_t);
+template hodlr_status gemm_batched<float, float>(hodlr_ctx *, const GemmDesc<float> *, int, int, int, int, int,
+                                                 float, cudaStream_t);
+template hodlr_status gemm_batched<double, double>(hodlr_ctx *, const GemmDesc<double> *, int, int, int, int, int,
+                                                   double, cudaStream_t);
+template hodlr_status gemm_batched<double, float>(hodlr_ctx *, const GemmDesc<double, float> *, int, int, int,
+                                                  int, int, double, cudaStream_t);
 
 namespace {
 

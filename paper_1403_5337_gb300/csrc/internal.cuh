@@ -95,6 +95,10 @@ struct hodlr_ctx {
     // executable graphs of finished solves, destroyed by the next solve once
     // it has work queued (their teardown is host time) or by hodlr_ctx_destroy
     std::vector<std::pair<cudaGraphExec_t, cudaGraph_t>> graph_trash;
+    // the apply's wait budget (polls; 0 = the library default) and an addition
+    // to its arrival targets, set by hodlr_ctx_set_wait_test only
+    unsigned long long wait_limit = 0;
+    unsigned wait_extra = 0;
 };
 #define HODLR_REPORT_BYTES 65536
 #define HODLR_CACHE_LIMIT (size_t(16) << 30)
@@ -180,6 +184,15 @@ struct hodlr_s {
     hodlr::FactorPlan *plan = nullptr;
     // events around the last factorisation, read lazily by hodlr_stats_get
     cudaEvent_t fev[2] = {nullptr, nullptr};
+    // Woodbury core condition guard (level l = 0..L-1: the 2^l cores of the
+    // parents of level l + 1): kappa_1(S) of every core, the flag of the cores
+    // re-inverted in FP64, and their FP64 inverses (FP32 arithmetic only)
+    bool guard = false;                // kappa_1 is computed
+    bool promote = false;              // cores above cond_thr are re-inverted in FP64
+    double cond_thr = 0.0;
+    std::vector<double *> core_cond;
+    std::vector<int *> core_flag;
+    std::vector<double *> Sinv64;
 };
 
 namespace hodlr {
@@ -225,16 +238,21 @@ hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t 
                       std::vector<void *> &Ust, std::vector<void *> &Vst);
 
 // Generic batched GEMM:  C_b += alpha * op(A_b) * B_b  (column-major), op = N or T.
-template <typename T>
+// The operands may be stored in a narrower type TI than the accumulation type
+// T (FP32 factors multiplied in FP64).  gate (device, optional): the product is
+// skipped when *gate == 0, so that work whose need is only known on the device
+// can be enqueued without a host round trip.
+template <typename T, typename TI = T>
 struct GemmDesc {
-    const T *A;
-    const T *B;
+    const TI *A;
+    const TI *B;
     T *C;
     int64_t lda, ldb, ldc;
     int M, N, K;
+    const int *gate;
 };
-template <typename T>
-hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T> *d_desc, int nbatch, int maxM,
+template <typename T, typename TI = T>
+hodlr_status gemm_batched(hodlr_ctx *c, const GemmDesc<T, TI> *d_desc, int nbatch, int maxM,
                           int maxN, int maxK, int transA, T alpha, cudaStream_t s);
 
 hodlr_status factor_impl(hodlr_t *h, cudaStream_t s);

@@ -61,7 +61,9 @@ class _Stats(C.Structure):
                 ("rank_max", C.c_int * MAX_LEVELS), ("rank_pad", C.c_int * MAX_LEVELS),
                 ("rank_mean", C.c_double * MAX_LEVELS), ("cap", C.c_int * MAX_LEVELS),
                 ("cap_hit", C.c_int), ("bytes_factors", C.c_int64), ("factored", C.c_int),
-                ("ms_compress", C.c_double), ("ms_factor", C.c_double)]
+                ("ms_compress", C.c_double), ("ms_factor", C.c_double),
+                ("core_cond_max", C.c_double * MAX_LEVELS), ("cores_promoted", C.c_int * MAX_LEVELS),
+                ("core_cond_threshold", C.c_double)]
 
 
 class _Info(C.Structure):
@@ -76,9 +78,9 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 SYMBOLS = ["hodlr_ctx_create", "hodlr_ctx_destroy", "hodlr_opts_default", "hodlr_build", "hodlr_factor",
            "hodlr_solve", "gmres_solve", "hodlr_matvec", "hodlr_matvec_noalloc", "hodlr_precond_error",
            "hodlr_stats_get",
-           "hodlr_export_level", "hodlr_export_core", "hodlr_destroy", "hodlr_status_string",
+           "hodlr_export_level", "hodlr_export_core", "hodlr_export_core_cond", "hodlr_destroy", "hodlr_status_string",
            "hodlr_last_error", "hodlr_launch_count", "hodlr_build_batched", "hodlr_factor_batched",
-           "gmres_solve_batched"]
+           "gmres_solve_batched", "hodlr_ctx_set_wait_test"]
 
 _lib = None
 # Library calls in progress on this process.  The torch allocator callbacks run
@@ -127,8 +129,10 @@ def load_library(path: str = _LIBPATH):
     lib.hodlr_stats_get.argtypes = [vp, C.POINTER(_Stats)]
     lib.hodlr_export_level.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp, vp]
     lib.hodlr_export_core.argtypes = [vp, ci, vp, vp]
+    lib.hodlr_export_core_cond.argtypes = [vp, ci, vp, vp, vp]
     lib.hodlr_destroy.argtypes = [vp]
     lib.hodlr_launch_count.argtypes = [C.POINTER(C.c_longlong)]
+    lib.hodlr_ctx_set_wait_test.argtypes = [vp, C.c_ulonglong, ci]
     lib.hodlr_build_batched.argtypes = [vp, ci, C.POINTER(_Matrix), C.POINTER(ci), cd, ci, C.POINTER(_Opts), vp,
                                         C.POINTER(vp)]
     lib.hodlr_factor_batched.argtypes = [ci, C.POINTER(vp), vp]
@@ -246,6 +250,10 @@ class Context:
         _check(lib.hodlr_ctx_create(device, self._alloc, self._free, None, C.byref(h)))
         self.handle = h
 
+    def set_wait_test(self, spin_limit: int = 0, unreachable: bool = False):
+        """Test hook of the bounded device waits (see include/hodlr.h)."""
+        _check(_lib.hodlr_ctx_set_wait_test(self.handle, int(spin_limit), 1 if unreachable else 0))
+
     def close(self):
         if self.handle:
             _lib.hodlr_ctx_destroy(self.handle)
@@ -284,7 +292,9 @@ class Hodlr:
         return dict(n=st.n, levels=L, leaf_max=st.leaf_max, rank_max=list(st.rank_max[:L]),
                     rank_pad=list(st.rank_pad[:L]), rank_mean=list(st.rank_mean[:L]), cap=list(st.cap[:L]),
                     cap_hit=bool(st.cap_hit), bytes_factors=st.bytes_factors, factored=bool(st.factored),
-                    ms_compress=st.ms_compress, ms_factor=st.ms_factor)
+                    ms_compress=st.ms_compress, ms_factor=st.ms_factor,
+                    core_cond_max=list(st.core_cond_max[:L]), cores_promoted=list(st.cores_promoted[:L]),
+                    core_cond_threshold=st.core_cond_threshold)
 
     def export_level(self, level: int, stream=None):
         """(U, V, ranks, piv_rows, piv_cols) of level `level` as numpy arrays."""
@@ -315,6 +325,14 @@ class Hodlr:
         _check(_lib.hodlr_export_core(self.handle, level, out.ctypes.data, _stream(stream)))
         return np.transpose(out, (0, 2, 1)).copy()   # column-major blocks -> [i][row][col]
 
+    def export_core_cond(self, level: int, stream=None):
+        """(kappa_1 of each core of level `level`, re-inverted-in-FP64 flags)."""
+        cond = np.zeros(1 << level)
+        flag = np.zeros(1 << level, dtype=np.int32)
+        _check(_lib.hodlr_export_core_cond(self.handle, level, cond.ctypes.data, flag.ctypes.data,
+                                           _stream(stream)))
+        return cond, flag.astype(bool)
+
     def close(self):
         if self.handle:
             if _depth > 0:
@@ -334,7 +352,7 @@ class Hodlr:
 def hodlr_build(ctx: Context, A: torch.Tensor, leaf: int, tol: float, method: str = "aca", graph=None,
                 precision: str = "fp32", compress_precision: str | None = None, rank_cap: int = 0,
                 bdlr_depth: int = -1, leaf_bounds=None, symmetric: bool = True, stream=None,
-                defer_factor: bool = False) -> Hodlr:
+                defer_factor: bool = False, core_cond_threshold: float = 0.0) -> Hodlr:
     """Compress A into HODLR form (Sec. 4.3 step 1, Sec. 5) and, unless
     defer_factor, factor it level by level meanwhile: see include/hodlr.h."""
     lib = load_library()
@@ -345,6 +363,7 @@ def hodlr_build(ctx: Context, A: torch.Tensor, leaf: int, tol: float, method: st
     o.rank_cap = rank_cap
     o.bdlr_depth = bdlr_depth
     o.defer_factor = 1 if defer_factor else 0
+    o.core_cond_threshold = float(core_cond_threshold)
     keep = []
     if leaf_bounds is not None:
         lb = np.ascontiguousarray(np.asarray(leaf_bounds, dtype=np.int64))

@@ -552,7 +552,8 @@ def test_cores_fp32_vs_fp64_front4096(H, ctx, front4096):
 
 
 @pytest.mark.parametrize("method,tol,prec", [("aca", 1e-4, "fp32"), ("aca", 1e-4, "fp64"),
-                                             ("bdlr", 1e-4, "fp32"), ("aca", 1e-8, "fp32")])
+                                             ("bdlr", 1e-4, "fp32"), ("aca", 1e-8, "fp32"),
+                                             ("bdlr", 1e-8, "fp64")])
 def test_front4096_gmres(H, ctx, front4096, method, tol, prec):
     F = front4096
     g = (F.rowptr, F.colind)
@@ -575,6 +576,44 @@ def test_front4096_gmres(H, ctx, front4096, method, tol, prec):
         ref = O.gmres(F.A, b[:, r], prec=P, tol=1e-12)
         assert abs(int(info.iters[r]) - ref.iters) <= 2, (r, info.iters, ref.iters)
         assert np.linalg.norm(x[r] - ref.x) / np.linalg.norm(ref.x) < 1e-9
+    h.close()
+
+
+def test_reduced_plane32768_fp16_32_rhs(H, ctx):
+    """The n = 32768 workload's construction scaled down: a 32 x 64 x 9 grid (4
+    planes per side, lognormal sigma 0.5, n = 2048), leaf 256 (3 levels), ACA
+    tol 1e-3, FP16 storage with per-(node, column) power-of-two scales, 32
+    right-hand sides (the tensor-core product).  The apply agrees element by
+    element with the oracle's solve on the FP32-compressed blocks to the FP16
+    storage's rounding (2^-11 per entry, grown through 3 levels: 5e-3 relative
+    per column); GMRES reaches 1e-12 on all 32; sampled columns agree with the
+    oracle's GMRES iterates to 1e-9 and its iteration counts within 3."""
+    F = fg.make_front(32, 64, 4, 4, "lognormal", 0.5, leaf=256, seed=0)
+    n = F.n
+    assert n == 2048 and F.levels == 3
+    tree = O.make_tree(n, 256, F.bounds)
+    blocks, Fac, P = O.hodlr_precond(F.A, tree, "aca", 1e-3, symmetric=True, dtype=np.float32)
+    A = _dev(F.A)
+    h = H.hodlr_build(ctx, A, 256, 1e-3, "aca", precision="fp16", leaf_bounds=F.bounds)
+    st = h.stats()
+    for l in range(1, tree.L + 1):
+        ro = max(blocks[(l - 1, i // 2)].Ua.shape[1] if i % 2 == 0 else blocks[(l - 1, i // 2)].Ub.shape[1]
+                 for i in range(1 << l))
+        assert st["rank_max"][l - 1] == ro
+    b = fg.rhs(n, 32, seed=1)
+    X = _dev(b.T)
+    H.hodlr_solve(h, X)
+    ref = O.solve(Fac, b)
+    got = X.cpu().numpy().T
+    err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() < 5e-3, err.max()
+    Xg, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    assert info.converged and np.all(info.true_relres <= 1e-12)
+    x = Xg.cpu().numpy()
+    for r in (0, 13, 31):
+        o = O.gmres(F.A, b[:, r], prec=P, tol=1e-12)
+        assert abs(int(info.iters[r]) - o.iters) <= 3, (r, info.iters[r], o.iters)
+        assert np.linalg.norm(x[r] - o.x) / np.linalg.norm(o.x) < 1e-9
     h.close()
 
 
@@ -629,6 +668,32 @@ def test_front16384_bf16_high_contrast(H, ctx, front16384):
           f"rank1 {k} precond-diff {perr:.3e}")
     assert np.isfinite(perr) and perr < 1.0
     h64.close()
+    # the Woodbury-core condition guard on this front: with a threshold below
+    # the root core's kappa_1 that core (and any above it) is re-inverted in FP64
+    # from the stored factors; its exported inverse is the FP64 inverse of the
+    # core formed from them, and the solve still reaches the target
+    st = h.stats()
+    thr = 0.5 * st["core_cond_max"][0]
+    hg = H.hodlr_build(ctx, A, 256, 1e-3, "aca", precision="bf16", leaf_bounds=F.bounds, core_cond_threshold=thr)
+    stg = hg.stats()
+    assert stg["cores_promoted"][0] == 1 and sum(stg["cores_promoted"]) >= 1
+    _, Vx, _, _, _ = hg.export_level(1)
+    Dx = hg.export_d(1)
+    rp = stg["rank_pad"][0]
+    S = np.eye(2 * rp)
+    S[:rp, rp:] = Vx[:half].T @ Dx[:half]
+    S[rp:, :rp] = Vx[half:].T @ Dx[half:]
+    ref = np.linalg.inv(S)
+    got = hg.export_core(0)[0]
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+    cond, flag = hg.export_core_cond(0)
+    kap = np.linalg.norm(S, 1) * np.linalg.norm(ref, 1)
+    assert flag[0] and abs(cond[0] - kap) <= 1e-3 * kap
+    X2, info2 = H.gmres_solve(ctx, A, Bd, hg, tol=target)
+    assert info2.converged and info2.true_relres[0] <= target
+    print(f"checker16384 guard: kappa_max per level {st['core_cond_max']} promoted at thr {thr:.3g}: "
+          f"{stg['cores_promoted']} iters {info2.iters.tolist()}")
+    hg.close()
     h.close()
 
 

@@ -586,6 +586,18 @@ def _golden(name):
     return rows
 
 
+def test_precond_error_2norm_closed_forms():
+    """P = A (exact inverse): 0.  P = I (no preconditioner) on an SPD A:
+    max |1 - lambda_i|, from the eigenvalues.  P = 2A: 1/2 exactly."""
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((40, 40))
+    A = M @ M.T / 40 + 0.5 * np.eye(40)
+    assert O.precond_error_2norm(A, lambda X: np.linalg.solve(A, X)) < 1e-12
+    lam = np.linalg.eigvalsh(A)
+    assert O.precond_error_2norm(A, lambda X: X) == pytest.approx(np.abs(1 - lam).max(), rel=1e-12)
+    assert O.precond_error_2norm(A, lambda X: np.linalg.solve(2 * A, X)) == pytest.approx(0.5, rel=1e-12)
+
+
 def test_default_bdlr_depth_follows_table3():
     """Without an explicit depth the oracle's BDLR build takes the depth the
     paper pairs with the tolerance (Table 3 caption, tests/golden): the blocks
