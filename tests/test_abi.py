@@ -199,7 +199,7 @@ def _ptxas_compile(src):
 
 
 @pytest.mark.parametrize("src,kernels,allowed", [
-    ("ozaki.cu", ("oz_gemm_kernel", "oz_split_rows_kernel", "oz_split_cols_kernel"), 0),
+    ("ozaki.cu", ("oz_tc_gemm_kernel", "oz_split_rows_kernel", "oz_split_cols_kernel", "oz_finalize_kernel"), 0),
     ("gmres.cu", ("arnoldi_tail_kernel", "residual_kernel", "start_cycle_kernel", "backsolve_kernel"), 0),
     # the double-float product at its 64-register cap (four CTAs of 256 threads
     # per SM): the variant for a general FP64 z spills 12 bytes
