@@ -37,7 +37,7 @@ __all__ = [
     "splitmix64", "uniform01", "normal", "coefficient_lognormal",
     "coefficient_checkerboard", "face_coefficients", "plane_front",
     "bisection_order", "plane_graph", "Front", "make_front", "rhs",
-    "WORKLOADS", "octree_boxes",
+    "WORKLOADS", "octree_boxes", "elastic_operator", "elastic_front", "make_elastic_front",
 ]
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -284,6 +284,144 @@ def plane_front(a: np.ndarray, n_below: int, device="cpu", method="auto") -> np.
         del G
     front = 0.5 * (front + front.T)
     return front.cpu().numpy() if dev.type == "cpu" else front
+
+
+# --------------------------------------------------------------------------- elasticity
+def elastic_operator(mu: np.ndarray, nu: float = 0.3):
+    """The 3-dof Navier-Cauchy operator -mu Lap u - (lambda + mu) grad div u on a
+    box of nodes (nz, ny, nx) = mu.shape, h = 1, Dirichlet outside the box, as
+    the sum of two positive semi-definite forms (so the matrix is SPD):
+      * sum over the 6 faces of every node of mu_f |u_p - u_q|^2 / 2 per
+        component (node coefficients mu, harmonic mean on interior faces, the
+        node's own on boundary faces), the vector Laplacian of the
+        finite-volume scalar operator;
+      * sum over the (nx+1)(ny+1)(nz+1) cells between nodes of (lambda +
+        mu)_c (div_c u)^2, div_c the one-point divergence of the trilinear
+        cell: du_a/dx_a = 1/4 sum over the cell's 4 edges along a of the
+        difference of u_a across the edge (outside nodes are zero);
+    lambda = 2 mu nu / (1 - 2 nu), cell values the mean of the cell's nodes.
+    Dofs are ordered 3 * (x + nx (y + ny z)) + component.  Returns a
+    scipy.sparse CSR matrix."""
+    import scipy.sparse as sp
+    nz, ny, nx = mu.shape
+    N = nx * ny * nz
+    fx, fy, fz = face_coefficients(mu)
+    rows, cols, vals = [], [], []
+
+    def node(i, j, k):
+        return i + nx * (j + ny * k)
+
+    # vector Laplacian (same scalar stencil on each component)
+    diag = np.zeros(N)
+    ii, jj, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    pidx = node(ii, jj, kk)
+    diag += (fx[kk, jj, ii] + fx[kk, jj, ii + 1] + fy[kk, jj, ii] + fy[kk, jj + 1, ii]
+             + fz[kk, jj, ii] + fz[kk + 1, jj, ii])
+    for (di, dj, dk, f) in ((1, 0, 0, fx[kk, jj, ii + 1]), (0, 1, 0, fy[kk, jj + 1, ii]), (0, 0, 1, fz[kk + 1, jj, ii])):
+        ok = (ii + di < nx) & (jj + dj < ny) & (kk + dk < nz)
+        a, b = pidx[ok], node(ii[ok] + di, jj[ok] + dj, kk[ok] + dk)
+        for c in range(3):
+            rows += [3 * a + c, 3 * b + c]
+            cols += [3 * b + c, 3 * a + c]
+            vals += [-f[ok], -f[ok]]
+    for c in range(3):
+        rows.append(3 * pidx + c)
+        cols.append(3 * pidx + c)
+        vals.append(diag)
+    lap = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(3 * N, 3 * N))
+    # grad-div: B^T W B over the cells
+    lam = 2.0 * mu * nu / (1.0 - 2.0 * nu)
+    pad = np.pad(lam + mu, 1, mode="edge")   # cell value: mean of the 8 (padded) nodes around it
+    cw = sum(pad[dk:dk + nz + 1, dj:dj + ny + 1, di:di + nx + 1]
+             for dk in (0, 1) for dj in (0, 1) for di in (0, 1)) / 8.0
+    ci, cj, ck = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    cidx = ci + (nx + 1) * (cj + (ny + 1) * ck)
+    brow, bcol, bval = [], [], []
+    for di in (0, 1):
+        for dj in (0, 1):
+            for dk in (0, 1):
+                xi, yj, zk = ci - 1 + di, cj - 1 + dj, ck - 1 + dk   # corner node of the cell
+                ok = (xi >= 0) & (xi < nx) & (yj >= 0) & (yj < ny) & (zk >= 0) & (zk < nz)
+                nd = node(xi[ok], yj[ok], zk[ok])
+                for c, d in ((0, di), (1, dj), (2, dk)):
+                    brow.append(cidx[ok])
+                    bcol.append(3 * nd + c)
+                    bval.append(np.full(ok.sum(), 0.25 if d == 1 else -0.25))
+    ncell = (nx + 1) * (ny + 1) * (nz + 1)
+    B = sp.csr_matrix((np.concatenate(bval), (np.concatenate(brow), np.concatenate(bcol))), shape=(ncell, 3 * N))
+    W = sp.diags(cw[ck, cj, ci])
+    return (lap + B.T @ W @ B).tocsr()
+
+
+def elastic_front(mu: np.ndarray, n_below: int, nu: float = 0.3, device="cpu") -> np.ndarray:
+    """Exact FP64 Schur complement of the elasticity operator onto plane
+    n_below (3 dofs per node, x-fastest node order): the planes on each side
+    are eliminated one at a time, S_0 = T_0, S_{k+1} = T_{k+1} - C_k^T S_k^-1
+    C_k, with C_k the (sparse) coupling of planes k and k+1; symmetrised
+    exactly."""
+    import torch
+    nz, ny, nx = mu.shape
+    K = elastic_operator(mu, nu)
+    m = 3 * nx * ny
+    dev = torch.device(device)
+
+    def blk(a, b):
+        return torch.as_tensor(K[a * m:(a + 1) * m, b * m:(b + 1) * m].toarray(), dtype=torch.float64, device=dev)
+
+    def side(planes):
+        s = None
+        for step, k in enumerate(planes):
+            t = blk(k, k)
+            if s is not None:
+                C = blk(planes[step - 1], k)
+                t -= C.T @ torch.cholesky_solve(C, torch.linalg.cholesky(s))
+            s = t
+        return s
+
+    front = blk(n_below, n_below)
+    if n_below > 0:
+        s = side(list(range(0, n_below)))
+        C = blk(n_below - 1, n_below)
+        front -= C.T @ torch.cholesky_solve(C, torch.linalg.cholesky(s))
+    if n_below < nz - 1:
+        s = side(list(range(nz - 1, n_below, -1)))
+        C = blk(n_below + 1, n_below)
+        front -= C.T @ torch.cholesky_solve(C, torch.linalg.cholesky(s))
+    front = 0.5 * (front + front.T)
+    return front.cpu().numpy() if dev.type == "cpu" else front
+
+
+def make_elastic_front(nx, ny, below, above, sigma=0.5, nu=0.3, leaf_nodes=64, seed=0, device="cpu"):
+    """An elasticity front on an nx x ny x (below + 1 + above) box: shear modulus
+    mu = exp(sigma z), z ~ N(0,1) per node (counter stream `seed`), Poisson
+    ratio nu, in the recursive-bisection order of the plane with the 3 dofs of
+    a node kept together (leaves of at most `leaf_nodes` nodes).  The graph is
+    the plane's 5-point adjacency between nodes, every dof of a node joined to
+    the other dofs of that node and to every dof of the neighbouring nodes."""
+    nz = below + 1 + above
+    mu = coefficient_lognormal(nx, ny, nz, sigma, seed)
+    A_nat = elastic_front(mu, below, nu, device=device)
+    perm_n, bounds_n, L, _ = bisection_order(nx, ny, leaf_nodes)
+    perm = (3 * perm_n[:, None] + np.arange(3)[None, :]).reshape(-1)
+    if isinstance(A_nat, np.ndarray):
+        A = np.ascontiguousarray(A_nat[np.ix_(perm, perm)])
+    else:
+        import torch
+        p = torch.as_tensor(perm, device=A_nat.device)
+        A = A_nat.index_select(0, p).index_select(1, p).contiguous()
+    rp_n, ci_n = plane_graph(nx, ny, perm_n)
+    rows = []
+    for v in range(len(perm_n)):
+        nb = [int(w) for w in ci_n[rp_n[v]:rp_n[v + 1]]] + [v]
+        for c in range(3):
+            rows.append(sorted(3 * w + d for w in nb for d in range(3) if (w, d) != (v, c)))
+    rowptr = np.zeros(len(rows) + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    colind = np.asarray([c for r in rows for c in r], dtype=np.int32)
+    return Front(A, 3 * nx * ny, nx, ny, perm, 3 * bounds_n, L, rowptr, colind,
+                 dict(nz=nz, below=below, above=above, field="elastic", sigma=sigma, nu=nu, seed=seed))
 
 
 # --------------------------------------------------------------------------- ordering

@@ -108,7 +108,12 @@ typedef struct {
                                    -1 = FP64 if precision == FP64, else FP32         */
     int rank_cap;               /* maximum rank of an off-diagonal block (<= 1024);
                                    0 = 1024                                          */
-    int bdlr_depth;             /* BDLR distance depth d; -1 = round(-log10 tol)     */
+    int bdlr_depth;             /* BDLR distance depth d; -1 = round(-log10 tol) (the
+                                   paper's Table 3 pairs); -2 = adaptive (Sec. 5.3):
+                                   every block from d = 1, grown while the relative
+                                   Frobenius error on the held-out rows and columns
+                                   (those at distance d + 1, relative to every row
+                                   and column examined) exceeds tol                 */
     double core_cond_threshold; /* Woodbury core condition guard (Sec. 4.3 Factorize,
                                    the cores S_i^(p)): kappa_1(S) = ||S||_1 ||S^-1||_1
                                    of every core is computed exactly from the formed S
@@ -147,6 +152,7 @@ typedef struct {
     int cores_promoted[HODLR_MAX_LEVELS];    /* cores re-inverted in FP64               */
     double core_cond_threshold;              /* the threshold in effect (inf: FP64
                                                 arithmetic, never promoted; -1: off)   */
+    int bdlr_depth_max;                      /* BDLR: largest depth a block used (0: ACA) */
 } hodlr_stats;
 
 /* Per-right-hand-side GMRES results (arrays of length s supplied by the caller,
@@ -210,6 +216,25 @@ hodlr_status gmres_solve(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const dou
                          int64_t ldb, double *X, int64_t ldx, const hodlr_t *P, double tol,
                          int max_iter, int restart, hodlr_gmres_info *info,
                          hodlr_stream stream);
+
+/* The diagonal (Jacobi) preconditioner P = diag(A), the "Diag" comparison of
+ * the paper's Fig. 8 (Sec. 7): a handle without levels, factored on return,
+ * that gmres_solve, hodlr_solve (X <- diag(A)^-1 X) and hodlr_precond_error
+ * accept in place of a HODLR matrix.  A zero diagonal entry returns
+ * HODLR_SINGULAR, a non-finite one HODLR_NONFINITE_INPUT.  The handle keeps a
+ * pointer to A.  Synchronises `stream`; release with hodlr_destroy. */
+hodlr_status hodlr_build_diag(hodlr_ctx *ctx, const hodlr_matrix *A, hodlr_stream stream, hodlr_t **out);
+
+/* The conventional dense solve of the front, the "LU" comparison of the
+ * paper's Table 3 (Sec. 7): LU with row partial pivoting of a copy of A (pivot
+ * = the largest |entry| of the column on and below the diagonal, lowest row on
+ * ties), right-looking in panels of 64 columns, FP64; then X = U^-1 L^-1 P B
+ * for s right-hand sides.  A: device, row-major; B, X: device, n x s
+ * column-major (ld >= n; B is not modified).  Allocates 8 n^2 bytes through
+ * the context's allocator for the call.  A zero pivot returns HODLR_SINGULAR.
+ * Synchronises `stream`. */
+hodlr_status hodlr_dense_lu_solve(hodlr_ctx *ctx, const hodlr_matrix *A, int s, const double *B, int64_t ldb,
+                                  double *X, int64_t ldx, hodlr_stream stream);
 
 /* ---------------------------------------------------------------- batches */
 /* The fronts of one nested-dissection tree solved together (independent
@@ -311,6 +336,23 @@ hodlr_status hodlr_export_core(const hodlr_t *h, int level, double *Sinv, hodlr_
 hodlr_status hodlr_export_core_cond(const hodlr_t *h, int level, double *cond, int32_t *promoted,
                                     hodlr_stream stream);
 
+/* Checkpoint of a factored HODLR matrix (or diagonal preconditioner) in host
+ * memory: the paper defines no format; the image holds the object's
+ * metadata and the contents of its device buffers.  hodlr_save writes the
+ * image into buf (host, `bytes` long) and *needed (host) receives its size;
+ * with buf NULL only the size is returned.  HODLR_NOT_FACTORED before the
+ * factorisation, HODLR_RANGE when bytes < *needed.  Synchronises the device.
+ * hodlr_load rebuilds the object on ctx's device from an image of this
+ * library version (HODLR_INVALID_ARG for anything else): it holds the same
+ * factors bit for bit (saving it again gives the same image), so it applies
+ * the same preconditioner up to the apply's own run-to-run rounding (its node
+ * sums are atomic); it is factored and keeps a pointer to A (which may be
+ * NULL; hodlr_precond_error then refuses).  A restored object is not factored again (hodlr_factor
+ * returns at once).  Synchronises `stream`. */
+hodlr_status hodlr_save(const hodlr_t *h, void *buf, size_t bytes, size_t *needed, hodlr_stream stream);
+hodlr_status hodlr_load(hodlr_ctx *ctx, const hodlr_matrix *A, const void *buf, size_t bytes, hodlr_stream stream,
+                        hodlr_t **out);
+
 hodlr_status hodlr_destroy(hodlr_t *h);
 
 const char *hodlr_status_string(hodlr_status s);
@@ -321,6 +363,18 @@ const char *hodlr_last_error(void);
  * device-side loop of a recorded GMRES iteration included (counted once the
  * solve returns).  `out` is host memory; never fails unless `out` is NULL. */
 hodlr_status hodlr_launch_count(long long *out);
+
+/* Per-kernel device time (diagnostics, no counterpart in the paper).  While
+ * profiling is on, the library records a CUDA event pair on the launching
+ * stream around each launch of its main kernels ("aca_cluster_kernel",
+ * "gj_cluster_kernel", "apply_fused_kernel", "df_matvec_kernel",
+ * "oz_split_rows_kernel", "oz_split_cols_kernel", "oz_tc_gemm_kernel"),
+ * except launches recorded into a graph (the GMRES iterations).
+ * hodlr_profile_enable(on) clears the records and switches recording on or
+ * off; hodlr_profile_read waits for the recorded launches of `kernel` and
+ * returns their total time (ms) and count (host pointers). */
+hodlr_status hodlr_profile_enable(int on);
+hodlr_status hodlr_profile_read(const char *kernel, double *ms_total, long long *launches);
 
 /* Test hook of the bounded device waits (no counterpart in the paper).  The
  * apply of hodlr_solve and of gmres_solve waits, per tree node, for the arrival

@@ -17,6 +17,11 @@ Contents and the passage each follows
 * aca                  -- partial-pivoting ACA (Section 5.1, Rjasanow's scheme).
 * bdlr                 -- boundary-distance row/column selection plus the
                           full-pivoting-LU pseudo-skeleton of Section 5.3.
+* bdlr_adaptive        -- the same with the depth grown until the relative
+                          Frobenius error on held-out rows and columns meets
+                          the tolerance (Section 5.3).
+* bdlr_diagnostics     -- pivot size vs boundary distance, singular values,
+                          BDLR vs SVD error per rank (Figs. 4-6).
 * build / assemble     -- the HODLR approximation K~ of the front.
 * factor / solve       -- the recursive Woodbury factorisation and solve of
                           Section 4.3 (Factorize steps 1-5, Solve steps 1-3).
@@ -311,7 +316,82 @@ def bdlr(A: np.ndarray, rowptr, colind, rows: range, cols: range, eps: float,
     return BDLRResult(X, Y.T.copy(), I, J, Ir, Jr, np.diag(LU)[:r].copy())
 
 
-# --------------------------------------------------------------------------- HODLR
+def heldout_error(A, rows: range, cols: range, U, V, Hr, Hc, I=(), J=()) -> float:
+    """Relative Frobenius error of the approximation A(rows, cols) ~ U V^T
+    measured on held-out rows Hr (global indices in rows) and columns Hc (in
+    cols): the squared residuals of those rows and columns over the squared
+    entries of every row and column examined, the selected I, J and the held
+    out ones (the block's magnitude as seen by the sample); 0 when nothing is
+    held out."""
+    num = den = 0.0
+    for h in Hr:
+        a = A[h, cols.start:cols.stop]
+        r = a - U[h - rows.start] @ V.T
+        num += float(r @ r)
+    for h in Hc:
+        a = A[rows.start:rows.stop, h]
+        r = a - U @ V[h - cols.start]
+        num += float(r @ r)
+    for h in list(Hr) + list(I):
+        a = A[h, cols.start:cols.stop]
+        den += float(a @ a)
+    for h in list(Hc) + list(J):
+        a = A[rows.start:rows.stop, h]
+        den += float(a @ a)
+    return math.sqrt(num / den) if den > 0 and (Hr or Hc) else 0.0
+
+
+def bdlr_adaptive(A, rowptr, colind, rows: range, cols: range, eps: float, depth0: int = 1,
+                  rank_cap: int = 1 << 30, dtype=np.float64):
+    """The adaptive pseudo-skeleton of Section 5.3: BDLR at depth d, then the
+    relative Frobenius error on the rows and columns held out of it -- those at
+    distance exactly d + 1 from the boundary -- relative to every row and
+    column examined (heldout_error), and, while that error exceeds eps and
+    such rows or columns exist, the same with depth d + 1.  Returns
+    (the BDLRResult of the final depth, that depth, its held-out error)."""
+    d = depth0
+    while True:
+        res = bdlr(A, rowptr, colind, rows, cols, eps, d, rank_cap, dtype)
+        _, dr = boundary_distance(rowptr, colind, rows, cols, d + 1)
+        _, dc = boundary_distance(rowptr, colind, cols, rows, d + 1)
+        Hr = [rows.start + i for i in np.flatnonzero(dr == d + 1)]
+        Hc = [cols.start + j for j in np.flatnonzero(dc == d + 1)]
+        err = heldout_error(A, rows, cols, res.U, res.V, Hr, Hc, res.I, res.J)
+        if err <= eps or (not Hr and not Hc):
+            return res, d, err
+        d += 1
+
+
+def bdlr_diagnostics(A, rowptr, colind, rows: range, cols: range, eps: float, depth: int):
+    """The data of the paper's Figs. 4-6 for one off-diagonal block: the
+    magnitude of every pivot of the full-pivoting LU of A^ with the boundary
+    distances of its row and column (Fig. 4), the singular values of the block
+    (Fig. 5), and for every rank r the relative Frobenius error of the
+    BDLR approximation truncated to r pivots next to that of the rank-r SVD
+    (Fig. 6)."""
+    B = A[rows.start:rows.stop, cols.start:cols.stop]
+    I, dI = boundary_distance(rowptr, colind, rows, cols, depth)
+    J, dJ = boundary_distance(rowptr, colind, cols, rows, depth)
+    LU, prow, pcol, r = full_pivot_lu(A[np.ix_(I, J)], eps)
+    piv = np.abs(np.diag(LU)[:r])
+    row_d = [int(dI[I[p] - rows.start]) for p in prow[:r]]
+    col_d = [int(dJ[J[p] - cols.start]) for p in pcol[:r]]
+    sv = np.linalg.svd(B, compute_uv=False)
+    nB = np.linalg.norm(B)
+    bdlr_err, svd_err = [], []
+    for k in range(1, r + 1):
+        Ir = [I[p] for p in prow[:k]]
+        Jr = [J[p] for p in pcol[:k]]
+        C = A[rows.start:rows.stop][:, Jr]
+        R = A[Ir][:, cols.start:cols.stop]
+        approx = C @ np.linalg.solve(A[np.ix_(Ir, Jr)], R)
+        bdlr_err.append(float(np.linalg.norm(B - approx) / nB))
+        svd_err.append(float(math.sqrt(max(float(np.sum(sv[k:] ** 2)), 0.0)) / nB))
+    return dict(pivots=piv, row_dist=row_d, col_dist=col_d, singular_values=sv,
+                bdlr_err=np.array(bdlr_err), svd_err=np.array(svd_err))
+
+
+# --------------------------------------------------------------------------- HODLR# --------------------------------------------------------------------------- HODLR
 @dataclass
 class Blocks:
     """Off-diagonal factors per internal node (l, i), children a=(l+1,2i), b=(l+1,2i+1):
@@ -329,7 +409,8 @@ def build(A: np.ndarray, tree: Tree, method: str = "aca", tol: float = 1e-6,
           dtype=np.float64):
     """Compress every off-diagonal block of every level with ACA or BDLR (Section 4.3,
     Factorize step 1).  `symmetric` only changes how a column is fetched (as the
-    equal row), never a value."""
+    equal row), never a value.  BDLR depth: >= 0 fixed, -1 round(-log10 tol),
+    -2 adaptive per block (bdlr_adaptive)."""
     blocks = {}
     for l in range(tree.L):
         for i in range(1 << l):
@@ -342,6 +423,10 @@ def build(A: np.ndarray, tree: Tree, method: str = "aca", tol: float = 1e-6,
                               (lambda k: A[c0 + k, r0:r1]) if symmetric else
                               (lambda k: A[r0:r1, c0 + k]),
                               r1 - r0, c1 - c0, tol, rank_cap, dtype)
+                elif method == "bdlr" and depth == -2:
+                    # the adaptive depth of Section 5.3
+                    res, _, _ = bdlr_adaptive(A, graph[0], graph[1], range(r0, r1), range(c0, c1), tol,
+                                              1, rank_cap, dtype)
                 elif method == "bdlr":
                     d = depth if depth >= 0 else int(round(-math.log10(tol)))
                     res = bdlr(A, graph[0], graph[1], range(r0, r1), range(c0, c1), tol, d,

@@ -8,4 +8,6 @@ reached through the ctypes binding in `hodlr`.
 from .hodlr import (ACA, BDLR, BF16, FP16, FP32, FP64, Context, GmresInfo, Hodlr, HodlrError,  # noqa: F401
                     NotConverged, gmres_solve, hodlr_build, hodlr_factor, hodlr_matvec,
                     hodlr_launch_count, hodlr_matvec_noalloc, hodlr_precond_error, hodlr_solve,
-                    hodlr_build_batched, hodlr_factor_batched, gmres_solve_batched, load_library)
+                    hodlr_build_batched, hodlr_factor_batched, gmres_solve_batched, load_library,
+                    hodlr_profile_enable, hodlr_profile_read, hodlr_build_diag, hodlr_dense_lu_solve,
+                    hodlr_save, hodlr_load)

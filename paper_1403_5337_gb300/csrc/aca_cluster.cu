@@ -607,7 +607,11 @@ hodlr_status launch_level_npt(hodlr_ctx *c, const double *A, int64_t lda, int sy
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, aca_cluster_kernel<T, NPT>, A, lda, sym, d_blocks, tol * tol, kcs, c->d_status));
+    {
+        ProfScope ps("aca_cluster_kernel", cfg.stream);
+        HODLR_TRY_CUDA(
+            cudaLaunchKernelEx(&cfg, aca_cluster_kernel<T, NPT>, A, lda, sym, d_blocks, tol * tol, kcs, c->d_status));
+    }
     note_launch();
     return HODLR_OK;
 }

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -33,6 +34,56 @@ void note_launch(long long k) {
 long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
 LaunchCapture::LaunchCapture() : prev(t_capture) { t_capture = this; }
 LaunchCapture::~LaunchCapture() { t_capture = prev; }
+
+// ------------------------------------------------------------------ profiling
+namespace {
+struct ProfRec {
+    const char *name;
+    cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof;
+std::atomic<int> g_prof_on{0};
+}  // namespace
+
+ProfScope::ProfScope(const char *kernel, cudaStream_t stream) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess) {
+        cudaGetLastError();
+        e0 = nullptr;
+        return;
+    }
+    name = kernel;
+    s = stream;
+    cudaEventRecord(e0, s);
+}
+
+ProfScope::~ProfScope() {
+    if (!e0) return;
+    cudaEvent_t e1 = nullptr;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(e0);
+        return;
+    }
+    cudaEventRecord(e1, s);
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof.push_back(ProfRec{name, e0, e1});
+}
+
+static void prof_clear() {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    for (auto &r : g_prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    g_prof.clear();
+}
 
 hodlr_status status_from_word(int w) {
     if (w & ST_NONFINITE) return HODLR_NONFINITE_INPUT;
@@ -296,6 +347,33 @@ hodlr_status hodlr_ctx_set_wait_test(hodlr_ctx *c, unsigned long long spin_limit
     }
     c->wait_limit = spin_limit;
     c->wait_extra = unreachable ? 1u : 0u;
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_profile_enable(int on) {
+    hodlr::prof_clear();
+    hodlr::g_prof_on.store(on ? 1 : 0);
+    return HODLR_OK;
+}
+
+hodlr_status hodlr_profile_read(const char *kernel, double *ms_total, long long *launches) {
+    if (!kernel || !ms_total || !launches) {
+        set_error("hodlr_profile_read: NULL argument");
+        return HODLR_INVALID_ARG;
+    }
+    double ms = 0.0;
+    long long cnt = 0;
+    std::lock_guard<std::mutex> lock(hodlr::g_prof_mu);
+    for (auto &r : hodlr::g_prof) {
+        if (std::strcmp(r.name, kernel) != 0) continue;
+        float t = 0.f;
+        HODLR_TRY_CUDA(cudaEventSynchronize(r.e1));
+        HODLR_TRY_CUDA(cudaEventElapsedTime(&t, r.e0, r.e1));
+        ms += t;
+        ++cnt;
+    }
+    *ms_total = ms;
+    *launches = cnt;
     return HODLR_OK;
 }
 
@@ -650,7 +728,9 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
         rs = launch_aca_levels(c, A->data, A->ld, h->sym, cprec, db, first, maxdim, tol, st, done);
         for (int l = 1; l <= L; ++l) rstream[l] = c->side[(l - 1) % HODLR_SIDE_STREAMS];
     } else {
-        const int depth = o.bdlr_depth >= 0 ? o.bdlr_depth : (int)std::lround(-std::log10(tol));
+        // -2: the adaptive depth of Sec. 5.3 (run_bdlr grows it per block)
+        const int depth = o.bdlr_depth >= 0 ? o.bdlr_depth
+                                            : (o.bdlr_depth == -2 ? -1 : (int)std::lround(-std::log10(tol)));
         rs = run_bdlr(h, g, depth, st, Ust, Vst);
         done.assign(L, nullptr);
         for (int l = 0; l < L; ++l) {
@@ -720,6 +800,7 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
     h->Sinv.assign(L, nullptr);
     h->core_cond.assign(L, nullptr);
     h->core_flag.assign(L, nullptr);
+    h->core_count.assign(L, nullptr);
     h->Sinv64.assign(L, nullptr);
     h->vscale.assign(L + 1, nullptr);
     h->escale.assign(L + 1, nullptr);
@@ -796,6 +877,7 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
         const size_t oS = la.take((size_t)(1 << (l - 1)) * std::max<int64_t>(s2 * s2, 1) * pe);
         const size_t oCond = h->guard ? la.take((size_t)(1 << (l - 1)) * sizeof(double)) : 0;
         const size_t oFlag = h->guard ? la.take((size_t)(1 << (l - 1)) * sizeof(int)) : 0;
+        const size_t oCount = h->guard ? la.take(sizeof(unsigned)) : 0;
         const size_t oS64 = h->promote ? la.take((size_t)(1 << (l - 1)) * std::max<int64_t>(s2 * s2, 1) * 8) : 0;
         if (h->store == HODLR_FP16) {
             const size_t scb = (size_t)lv.nnodes * std::max(lv.rp, 1) * sizeof(float);
@@ -815,6 +897,7 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
         if (h->guard) {
             h->core_cond[l - 1] = (double *)(lb + oCond);
             h->core_flag[l - 1] = (int *)(lb + oFlag);
+            h->core_count[l - 1] = (unsigned *)(lb + oCount);
             // a level without ranks has identity cores: kappa 1, nothing to redo
             if (lv.rp == 0) {
                 std::vector<double> one((size_t)1 << (l - 1), 1.0);
@@ -841,6 +924,7 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
         cudaStreamWaitEvent(sl, st_mark, 0);
         cudaStreamWaitEvent(sl, ljoin, 0);        // the leaf inverses (read by the share)
         cudaStreamWaitEvent(sl, done[l - 1], 0);  // level l compressed into the staging
+        if (h->guard) cudaMemsetAsync(h->core_count[l - 1], 0, sizeof(unsigned), sl);
         if (lv.rp > 0) {
             // compaction writes the ranks' columns only: zero U and V
             cudaMemsetAsync(h->Ul[l], 0, colb * pe, sl);
@@ -1085,6 +1169,7 @@ hodlr_status hodlr_stats_get(const hodlr_t *h, hodlr_stats *o) {
         o->cap[l - 1] = h->lv[l].cap;
     }
     o->cap_hit = h->cap_hit;
+    o->bdlr_depth_max = h->bdlr_depth_max;
     const size_t pe = elem_size(h->prec);
     // U, d, V (ldn x rp each) and E (ldn x 2 rp) per level, the leaf inverses, the cores
     int64_t b = (int64_t)5 * h->ldn * h->Wtot * pe + ((int64_t)1 << h->L) * h->bmax * h->bmax * pe;
@@ -1234,6 +1319,10 @@ hodlr_status hodlr_precond_error(hodlr_t *h, int k, const double *Omega, int64_t
     if (!h->factored) {
         set_error("hodlr_precond_error: not factored");
         return HODLR_NOT_FACTORED;
+    }
+    if (!h->A) {
+        set_error("hodlr_precond_error: the object holds no matrix A (restored without one)");
+        return HODLR_INVALID_ARG;
     }
     HODLR_TRY_CUDA(cudaSetDevice(h->ctx->device));
     const int64_t n = h->n;

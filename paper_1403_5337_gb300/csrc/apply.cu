@@ -474,7 +474,12 @@ hodlr_status solve_fused(const hodlr_t *h, int s, double *X, int64_t ldx, cudaSt
     if (s <= 1) return launch_fused<T, S, 1>(h, a, st);
     if (s <= 2) return launch_fused<T, S, 2>(h, a, st);
     if (s <= 4) return launch_fused<T, S, 4>(h, a, st);
-    return launch_fused<T, S, 8>(h, a, st);
+    if (s <= 8) return launch_fused<T, S, 8>(h, a, st);
+    // many right-hand sides: one pass over the factors' rows for 16 or 32 of them
+    if constexpr (sizeof(T) == 4) {
+        if (s > 16) return launch_fused<T, S, 32>(h, a, st);
+    }
+    return launch_fused<T, S, 16>(h, a, st);
 }
 
 template <typename T, typename S, int RC>
@@ -531,7 +536,10 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a0, cudaStrea
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, apply_fused_kernel<T, S, RC>, a));
+    {
+        ProfScope ps("apply_fused_kernel", st);
+        HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, apply_fused_kernel<T, S, RC>, a));
+    }
     note_launch();
     return HODLR_OK;
 }
@@ -539,6 +547,7 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a0, cudaStrea
 }  // namespace
 
 hodlr_status solve_impl(const hodlr_t *h, int s, double *X, int64_t ldx, cudaStream_t st, float2 *Xs) {
+    if (h->diag) return diag_solve(h, s, X, ldx, st, Xs);
     if (h->prec == HODLR_FP64) return solve_fused<double, double>(h, s, X, ldx, st, h->Vl, h->El, nullptr, nullptr, Xs);
     if (h->store == HODLR_BF16)
         return solve_fused<float, __nv_bfloat16>(h, s, X, ldx, st, h->Vql, h->Eql, nullptr, nullptr, Xs);

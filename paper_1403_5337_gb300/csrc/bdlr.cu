@@ -14,6 +14,7 @@
 // reproducible.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <vector>
 
 #include "internal.cuh"
@@ -191,9 +192,10 @@ __global__ void bdlr_v_kernel(const double *__restrict__ A, int64_t lda, const B
 }
 
 // Boundary-distance selection of one side: vertices of [o0,o1) with d <= depth,
-// sorted by (d, index); boundary = vertices with an edge into [t0,t1).
+// sorted by (d, index); boundary = vertices with an edge into [t0,t1).  ring
+// (optional): the vertices at distance exactly depth + 1, by index.
 void select_side(const hodlr_graph *g, int64_t o0, int64_t o1, int64_t t0, int64_t t1, int depth,
-                 std::vector<int32_t> &out) {
+                 std::vector<int32_t> &out, std::vector<int32_t> *ring = nullptr) {
     const int64_t m = o1 - o0;
     std::vector<int> dist(m, -1);
     std::vector<int32_t> frontier, next;
@@ -208,7 +210,8 @@ void select_side(const hodlr_graph *g, int64_t o0, int64_t o1, int64_t t0, int64
         }
     }
     int dd = 0;
-    while (!frontier.empty() && dd < depth) {
+    const int reach = ring ? depth + 1 : depth;
+    while (!frontier.empty() && dd < reach) {
         next.clear();
         for (int32_t v : frontier)
             for (int32_t e = g->rowptr[v]; e < g->rowptr[v + 1]; ++e) {
@@ -225,64 +228,159 @@ void select_side(const hodlr_graph *g, int64_t o0, int64_t o1, int64_t t0, int64
     for (int q = 0; q <= depth; ++q)
         for (int64_t v = o0; v < o1; ++v)
             if (dist[v - o0] == q) out.push_back((int32_t)v);
+    if (ring) {
+        ring->clear();
+        for (int64_t v = o0; v < o1; ++v)
+            if (dist[v - o0] == depth + 1) ring->push_back((int32_t)v);
+    }
+}
+
+// The held-out error of the adaptive scheme (Sec. 5.3), for one block per
+// blockIdx.y: vector q of the sample list (rows: the held-out ring Hr, then the
+// selected I; columns: the ring Hc, then J) -- a row h contributes its squared
+// residual A(h, C) - U(h, :) V(C, :)^T to num when held out, and its squared
+// entries to den always; likewise a column.  FP64 sums, one CTA per vector.
+struct HeldDesc {
+    const int32_t *vec;    // nHr + nI rows, then nHc + nJ columns (global indices)
+    int nHr, nI, nHc, nJ;
+    int64_t r0, m, c0, nc, ld;
+    const void *U, *V;
+    const int32_t *rank;
+    double *num, *den;
+};
+
+template <typename T>
+__global__ void bdlr_heldout_kernel(const double *__restrict__ A, int64_t lda, const HeldDesc *__restrict__ descs) {
+    const HeldDesc d = descs[blockIdx.y];
+    const int q = blockIdx.x;
+    const int nrow = d.nHr + d.nI, ntot = nrow + d.nHc + d.nJ;
+    if (q >= ntot) return;
+    const bool is_row = q < nrow;
+    const bool held = is_row ? q < d.nHr : (q - nrow) < d.nHc;
+    const int64_t h = d.vec[q];
+    const int r = *d.rank;
+    const T *U = reinterpret_cast<const T *>(d.U);
+    const T *V = reinterpret_cast<const T *>(d.V);
+    double sr = 0.0, sa = 0.0;
+    const int64_t len = is_row ? d.nc : d.m;
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+        const int64_t row = is_row ? h : d.r0 + t, col = is_row ? d.c0 + t : h;
+        const double a = A[row * lda + col];
+        sa += a * a;
+        if (held) {
+            double uv = 0.0;
+            for (int k = 0; k < r; ++k) uv += (double)U[row + (int64_t)k * d.ld] * (double)V[col + (int64_t)k * d.ld];
+            sr += (a - uv) * (a - uv);
+        }
+    }
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = sr;
+        red[1][threadIdx.x >> 5] = sa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a0 += red[0][w];
+            a1 += red[1][w];
+        }
+        if (held) atomicAdd(d.num, a0);
+        atomicAdd(d.den, a1);
+    }
 }
 
 }  // namespace
 
-hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t s, std::vector<void *> &Ust,
-                      std::vector<void *> &Vst) {
+namespace {
+
+struct BdlrBlock {
+    int l, i, depth;
+};
+
+// One pass of BDLR over `todo` (each block at its own depth): the index lists
+// on the host, the gather, LU and triangular solves on the device; with
+// `held` also the held-out error of every block (err[k], and whether it had
+// any held-out row or column, ring[k]).
+hodlr_status bdlr_pass(hodlr_t *h, const hodlr_graph *g, const std::vector<BdlrBlock> &todo, cudaStream_t s,
+                       std::vector<void *> &Ust, std::vector<void *> &Vst, bool held, std::vector<double> &err,
+                       std::vector<char> &ring) {
     hodlr_ctx *c = h->ctx;
     const int L = h->L;
-    if (h->n > INT32_MAX) {
-        set_error("BDLR: n beyond 2^31");
-        return HODLR_RANGE;
-    }
-    for (int64_t v = 0; v < h->n; ++v)
-        if (g->rowptr[v + 1] < g->rowptr[v]) {
-            set_error("BDLR: graph rowptr not monotone at %lld", (long long)v);
-            return HODLR_INVALID_ARG;
-        }
     std::vector<BdlrDesc> descs;
-    std::vector<int32_t> idx;            // all I and J lists, concatenated
+    std::vector<int32_t> idx;                        // all I and J lists, concatenated
     std::vector<std::pair<size_t, size_t>> ij_off;   // offset of I, J per block
+    std::vector<int32_t> hv;                         // held-out samples per block: Hr, I, Hc, J
+    std::vector<HeldDesc> hd;
+    std::vector<size_t> hv_off;
     size_t ah_elems = 0, perm_elems = 0;
-    std::vector<int32_t> side;
-    for (int l = 1; l <= L; ++l) {
-        const int nn = 1 << l;
-        for (int i = 0; i < nn; ++i) {
-            const int64_t r0 = h->bounds[(size_t)i << (L - l)], r1 = h->bounds[(size_t)(i + 1) << (L - l)];
-            const int sib = i ^ 1;
-            const int64_t c0 = h->bounds[(size_t)sib << (L - l)], c1 = h->bounds[(size_t)(sib + 1) << (L - l)];
-            BdlrDesc d{};
-            const size_t oi = idx.size();
-            select_side(g, r0, r1, c0, c1, depth, side);
-            idx.insert(idx.end(), side.begin(), side.end());
-            d.nI = (int)side.size();
-            const size_t oj = idx.size();
-            select_side(g, c0, c1, r0, r1, depth, side);
-            idx.insert(idx.end(), side.begin(), side.end());
-            d.nJ = (int)side.size();
-            ij_off.push_back({oi, oj});
-            d.r0 = r0;
-            d.m = r1 - r0;
-            d.c0 = c0;
-            d.nc = c1 - c0;
-            d.ld = h->ldn;
-            d.U = Ust[l];
-            d.V = Vst[l];
-            d.cap = h->lv[l].cap;
-            d.rank = h->d_ranks[l] + i;
-            d.prow = h->piv_rows[l] + (size_t)i * h->lv[l].cap;
-            d.pcol = h->piv_cols[l] + (size_t)i * h->lv[l].cap;
-            ah_elems += (size_t)d.nI * d.nJ;
-            perm_elems += (size_t)d.nI + d.nJ;
-            descs.push_back(d);
+    int max_vec = 0;
+    std::vector<int32_t> side, sideJ, rr, rc;
+    ring.assign(todo.size(), 0);
+    for (const BdlrBlock &bk : todo) {
+        const int l = bk.l, i = bk.i;
+        const int64_t r0 = h->bounds[(size_t)i << (L - l)], r1 = h->bounds[(size_t)(i + 1) << (L - l)];
+        const int sib = i ^ 1;
+        const int64_t c0 = h->bounds[(size_t)sib << (L - l)], c1 = h->bounds[(size_t)(sib + 1) << (L - l)];
+        BdlrDesc d{};
+        const size_t oi = idx.size();
+        select_side(g, r0, r1, c0, c1, bk.depth, side, held ? &rr : nullptr);
+        idx.insert(idx.end(), side.begin(), side.end());
+        d.nI = (int)side.size();
+        const size_t oj = idx.size();
+        select_side(g, c0, c1, r0, r1, bk.depth, sideJ, held ? &rc : nullptr);
+        idx.insert(idx.end(), sideJ.begin(), sideJ.end());
+        d.nJ = (int)sideJ.size();
+        ij_off.push_back({oi, oj});
+        d.r0 = r0;
+        d.m = r1 - r0;
+        d.c0 = c0;
+        d.nc = c1 - c0;
+        d.ld = h->ldn;
+        d.U = Ust[l];
+        d.V = Vst[l];
+        d.cap = h->lv[l].cap;
+        d.rank = h->d_ranks[l] + i;
+        d.prow = h->piv_rows[l] + (size_t)i * h->lv[l].cap;
+        d.pcol = h->piv_cols[l] + (size_t)i * h->lv[l].cap;
+        ah_elems += (size_t)d.nI * d.nJ;
+        perm_elems += (size_t)d.nI + d.nJ;
+        descs.push_back(d);
+        if (held) {
+            ring[descs.size() - 1] = (!rr.empty() || !rc.empty()) ? 1 : 0;
+            hv_off.push_back(hv.size());
+            hv.insert(hv.end(), rr.begin(), rr.end());
+            hv.insert(hv.end(), side.begin(), side.end());
+            hv.insert(hv.end(), rc.begin(), rc.end());
+            hv.insert(hv.end(), sideJ.begin(), sideJ.end());
+            HeldDesc q{};
+            q.nHr = (int)rr.size();
+            q.nI = d.nI;
+            q.nHc = (int)rc.size();
+            q.nJ = d.nJ;
+            q.r0 = r0;
+            q.m = d.m;
+            q.c0 = c0;
+            q.nc = d.nc;
+            q.ld = h->ldn;
+            q.U = Ust[l];
+            q.V = Vst[l];
+            q.rank = d.rank;
+            hd.push_back(q);
+            max_vec = std::max(max_vec, q.nHr + q.nI + q.nHc + q.nJ);
         }
     }
     const size_t es = elem_size(h->cprec);
     const int nb = (int)descs.size();
     const size_t bytes = idx.size() * 4 + 256 + ah_elems * es + 256 + perm_elems * 4 + 256 + nb * sizeof(BdlrDesc) +
-                         256 + nb * 4 + 256;
+                         256 + nb * 4 + 256 + (held ? hv.size() * 4 + 256 + nb * sizeof(HeldDesc) + 256 +
+                                                          2 * nb * sizeof(double) + 256
+                                                    : 0);
     char *base = (char *)dalloc(c, bytes, s);
     if (!base) return HODLR_OUT_OF_MEMORY;
     char *p = base;
@@ -296,6 +394,9 @@ hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t 
     int32_t *d_perm = (int32_t *)carve(perm_elems * 4);
     BdlrDesc *d_desc = (BdlrDesc *)carve(nb * sizeof(BdlrDesc));
     int32_t *d_caphit = (int32_t *)carve(nb * 4);
+    int32_t *d_hv = held ? (int32_t *)carve(hv.size() * 4) : nullptr;
+    HeldDesc *d_hd = held ? (HeldDesc *)carve(nb * sizeof(HeldDesc)) : nullptr;
+    double *d_nd = held ? (double *)carve(2 * nb * sizeof(double)) : nullptr;
     size_t ao = 0, po = 0;
     int64_t max_rows = 0;
     for (int b = 0; b < nb; ++b) {
@@ -310,37 +411,87 @@ hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t 
         po += d.nJ;
         d.cap_hit = d_caphit + b;
         max_rows = std::max(max_rows, std::max(d.m, d.nc));
+        if (held) {
+            hd[b].vec = d_hv + hv_off[b];
+            hd[b].num = d_nd + 2 * b;
+            hd[b].den = d_nd + 2 * b + 1;
+        }
     }
     hodlr_status rs = HODLR_OK;
     if (cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_desc, descs.data(), nb * sizeof(BdlrDesc), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaMemcpyAsync(d_desc, descs.data(), nb * sizeof(BdlrDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (held && (cudaMemcpyAsync(d_hv, hv.data(), hv.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                  cudaMemcpyAsync(d_hd, hd.data(), nb * sizeof(HeldDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                  cudaMemsetAsync(d_nd, 0, 2 * nb * sizeof(double), s) != cudaSuccess))) {
         rs = HODLR_CUDA_ERROR;
     } else {
         const dim3 tgrid((unsigned)((max_rows + 127) / 128), nb);
         if (h->cprec == HODLR_FP64) {
             bdlr_lu_kernel<double><<<nb, LU_THREADS, 0, s>>>(h->A, h->lda, d_desc, h->tol, c->d_status);
-            note_launch();
             bdlr_u_kernel<double><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
-            note_launch();
             bdlr_v_kernel<double><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
-            note_launch();
+            if (held) bdlr_heldout_kernel<double><<<dim3(max_vec, nb), 128, 0, s>>>(h->A, h->lda, d_hd);
         } else {
             bdlr_lu_kernel<float><<<nb, LU_THREADS, 0, s>>>(h->A, h->lda, d_desc, h->tol, c->d_status);
-            note_launch();
             bdlr_u_kernel<float><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
-            note_launch();
             bdlr_v_kernel<float><<<tgrid, 128, 0, s>>>(h->A, h->lda, d_desc);
-            note_launch();
+            if (held) bdlr_heldout_kernel<float><<<dim3(max_vec, nb), 128, 0, s>>>(h->A, h->lda, d_hd);
         }
+        note_launch(held ? 4 : 3);
         if (cudaGetLastError() != cudaSuccess) rs = HODLR_CUDA_ERROR;
     }
     std::vector<int32_t> hc(nb);
+    std::vector<double> nd(held ? 2 * nb : 0);
     cudaMemcpyAsync(hc.data(), d_caphit, nb * 4, cudaMemcpyDeviceToHost, s);
+    if (held) cudaMemcpyAsync(nd.data(), d_nd, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     for (int v : hc) h->cap_hit |= v;
+    if (held) {
+        err.assign(nb, 0.0);
+        for (int b = 0; b < nb; ++b)
+            err[b] = (ring[b] && nd[2 * b + 1] > 0.0) ? std::sqrt(nd[2 * b] / nd[2 * b + 1]) : 0.0;
+    }
     dfree(c, base, bytes, s);
     if (rs != HODLR_OK) set_error("BDLR kernel launch failed");
     return rs;
+}
+
+}  // namespace
+
+// depth >= 0: every block at that depth.  depth < 0: the adaptive scheme of
+// Sec. 5.3 -- every block from depth 1; a block whose relative Frobenius error
+// on the held-out rows and columns (those at distance depth + 1, relative to
+// every row and column examined) exceeds tol, while such rows or columns
+// exist, is computed again at depth + 1.
+hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t s, std::vector<void *> &Ust,
+                      std::vector<void *> &Vst) {
+    const int L = h->L;
+    if (h->n > INT32_MAX) {
+        set_error("BDLR: n beyond 2^31");
+        return HODLR_RANGE;
+    }
+    for (int64_t v = 0; v < h->n; ++v)
+        if (g->rowptr[v + 1] < g->rowptr[v]) {
+            set_error("BDLR: graph rowptr not monotone at %lld", (long long)v);
+            return HODLR_INVALID_ARG;
+        }
+    const bool adaptive = depth < 0;
+    std::vector<BdlrBlock> todo;
+    for (int l = 1; l <= L; ++l)
+        for (int i = 0; i < (1 << l); ++i) todo.push_back(BdlrBlock{l, i, adaptive ? 1 : depth});
+    std::vector<double> err;
+    std::vector<char> ring;
+    h->bdlr_depth_max = 0;
+    while (!todo.empty()) {
+        HODLR_TRY(bdlr_pass(h, g, todo, s, Ust, Vst, adaptive, err, ring));
+        for (auto &b : todo) h->bdlr_depth_max = std::max(h->bdlr_depth_max, b.depth);
+        if (!adaptive) break;
+        std::vector<BdlrBlock> next;
+        for (size_t k = 0; k < todo.size(); ++k)
+            if (err[k] > h->tol && ring[k]) next.push_back(BdlrBlock{todo[k].l, todo[k].i, todo[k].depth + 1});
+        todo.swap(next);
+    }
+    return HODLR_OK;
 }
 
 }  // namespace hodlr

@@ -483,33 +483,25 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJ
                 break;
             }
             const int py = pr % GJR_TY, pp = pr / GJR_TY;
-            // The four cases of the sweep as one update a(i, j) -= (c_i / p) r_j, with
-            // the pivot row r = a(pr, :) except r_k = p + 1 and the pivot column
-            // c = a(:, k) except c_pr = p - 1 (p = a(pr, k)):
-            //   i != pr, j != k:  a - a(i,k) a(pr,j) / p
-            //   i != pr, j == k:  a(i,k) - a(i,k)(p + 1)/p      = -a(i,k) / p
-            //   i == pr, j != k:  a(pr,j) - (p - 1) a(pr,j) / p =  a(pr,j) / p
-            //   i == pr, j == k:  p - (p - 1)(p + 1) / p        =  1 / p
-            // (each exact up to the rounding of 1/p, p +- 1 and the update).
+            // the pivot row as it is before the sweep (p = a(pr, k))
             if (ty == py) {
 #pragma unroll
                 for (int p = 0; p < MR; ++p)
                     if (p == pp) {
                         used |= 1ull << p;
 #pragma unroll
-                        for (int q = 0; q < MC; ++q) {
-                            const int j = tx + GJR_TX * q;
-                            rowk[par][j] = (j == k) ? piv + T(1) : a[p][q];
-                        }
+                        for (int q = 0; q < MC; ++q) rowk[par][tx + GJR_TX * q] = a[p][q];
                     }
             }
             if (tid == 0) {
                 prow[k] = pr;
                 krow[pr] = k;
-                colk[par][pr] = piv - T(1);
             }
             __syncthreads();
-            // C. sweep the pivot (pr, k)
+            // C. sweep the pivot (pr, k): a(i, j) -= a(i, k) a(pr, j) / p on
+            // every element, then the pivot row becomes a(pr, j) / p, the pivot
+            // column -a(i, k) / p and the pivot 1 / p (scale-invariant: no step
+            // loses digits to the size of p)
             const T d = T(1) / piv;
             T rk[MC];
 #pragma unroll
@@ -519,6 +511,16 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_inverse_reg_kernel(const GJ
                 const T f = colk[par][ty + GJR_TY * p] * d;
 #pragma unroll
                 for (int q = 0; q < MC; ++q) a[p][q] = fma(-f, rk[q], a[p][q]);
+                if (tx == kx) a[p][kq] = -f;   // the pivot column
+            }
+            if (ty == py) {
+#pragma unroll
+                for (int p = 0; p < MR; ++p)
+                    if (p == pp) {
+#pragma unroll
+                        for (int q = 0; q < MC; ++q) a[p][q] = rk[q] * d;
+                        if (tx == kx) a[p][kq] = d;
+                    }
             }
         }
     }
@@ -666,14 +668,21 @@ __global__ void __launch_bounds__(GJR_THREADS, 1) gj_blocked_kernel(const GJDesc
                     }
                 const T pv = rr[t];
                 const T d = T(1) / pv;
-                rr[t] = pv + T(1);
+                // elimination on every entry, then the pivot column -v(i, t) / p,
+                // the pivot row v(pr, :) / p and the pivot 1 / p (scale-invariant)
 #pragma unroll
                 for (int m = 0; m < MW; ++m) {
                     const bool isp = (tx + 32 * m) == pr;
-                    const T f = (isp ? pv - T(1) : v[m][t]) * d;
+                    const T f = v[m][t] * d;
 #pragma unroll
                     for (int t2 = 0; t2 < NB; ++t2) v[m][t2] = fmaf(-f, rr[t2], v[m][t2]);
-                    if (isp) ub |= 1u << m;
+                    v[m][t] = -f;
+                    if (isp) {
+#pragma unroll
+                        for (int t2 = 0; t2 < NB; ++t2) v[m][t2] = rr[t2] * d;
+                        v[m][t] = d;
+                        ub |= 1u << m;
+                    }
                 }
                 if (tx == 0) {
                     piv[t] = pr;
@@ -766,6 +775,230 @@ hodlr_status launch_gj_blocked(hodlr_ctx *c, const GJDesc<T> *dd, int count, cud
     return HODLR_OK;
 }
 
+// Gauss-Jordan inversion of matrices up to 256 x 256 held in the registers of
+// a cluster of CL CTAs: CTA r of the cluster owns the columns r MC 32 ..
+// (r + 1) MC 32 - 1 of every row (256 threads as 8 x 32, thread (ty, tx) the
+// rows ty + 8 p, p < MR, and the columns tx + 32 q of its slice, q < MC).  The
+// sweep is the implicit-pivoting one of gj_inverse_reg_kernel (pivot p_k =
+// argmax |a(i, k)| over the rows not yet pivots, lowest row on ties; one FMA
+// per element and step).  Per step only the pivot column crosses the cluster:
+// the CTA owning column k picks the pivot, writes the column (with its pivot
+// entry adjusted) and the pivot's row and value into every CTA's shared memory
+// (DSMEM stores), and one cluster barrier publishes them; each CTA then posts
+// its part of the pivot row locally and updates its own columns.  Buffers are
+// double-buffered by step parity: a CTA writes step k's buffers only after the
+// cluster barrier of step k - 1, which its peers pass only once they finished
+// reading step k - 2's.  One cluster per matrix (blockIdx.x / CL).
+template <typename T, int CL, int MR, int MC>
+__global__ void __launch_bounds__(GJR_THREADS, 1) gj_cluster_kernel(const GJDesc<T> *__restrict__ descs,
+                                                                   int *status) {
+    constexpr int BR = MR * GJR_TY;          // rows held (256)
+    constexpr int CW = MC * GJR_TX;          // columns per CTA
+    const GJDesc<T> g = descs[blockIdx.x / CL];
+    const int b = g.b;
+    // every CTA of the cluster reads the same descriptor: all leave here together
+    if (b <= 0 || (g.gate && *g.gate == 0)) return;
+    unsigned rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int c0 = (int)rank * CW;           // first column of this CTA
+    __shared__ T colk[2][BR];
+    __shared__ T rowk[2][CW];
+    __shared__ T cand_v[2][GJR_TY];
+    __shared__ int cand_i[2][GJR_TY];
+    __shared__ int s_pr[2];
+    __shared__ T s_piv[2];
+    __shared__ int s_fail[2];
+    __shared__ int prow[BR];   // pivot row of step k
+    __shared__ int krow[BR];   // step at which row i was the pivot
+    T a[MR][MC];
+    unsigned long long used = 0;
+#pragma unroll
+    for (int p = 0; p < MR; ++p) {
+        const int i = ty + GJR_TY * p;
+        if (i >= b) used |= 1ull << p;
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int j = c0 + tx + GJR_TX * q;
+            T v = T(0);
+            if (b > 0 && i < b && j < b)
+                v = g.srcA ? dev::from_double<T>(g.srcA[(int64_t)i * g.lda + j]) : g.srcM[i + (int64_t)j * g.ldm];
+            a[p][q] = v;
+        }
+    }
+    if (tid < 2) s_fail[tid] = 0;
+    // the DSMEM addresses of the shared buffers in every CTA of the cluster
+    auto remote = [](const void *p, unsigned r) {
+        unsigned out;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(r));
+        return out;
+    };
+    auto st_remote = [](unsigned addr, T v) {
+        if constexpr (sizeof(T) == 4)
+            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+        else
+            asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+    };
+    auto st_remote_i = [](unsigned addr, int v) {
+        asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    };
+    auto cluster_sync = []() {
+        asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    };
+    cluster_sync();   // every CTA of the cluster is running and initialised
+    bool fail = false;
+    for (int owner = 0; owner < CL && !fail; ++owner) {
+#pragma unroll
+        for (int kq = 0; kq < MC; ++kq) {
+            const int kbase = owner * CW + kq * GJR_TX;
+            const int kxe = min(GJR_TX, b - kbase);
+            for (int kx = 0; kx < kxe && !fail; ++kx) {
+                const int k = kbase + kx;
+                const int par = k & 1;
+                const bool mine = (int)rank == owner;
+                // A. the owner's column-k threads post it and their best unused row
+                if (mine && tx == kx) {
+                    T bv = T(-1), sv = T(0);
+                    int bi = INT_MAX;
+#pragma unroll
+                    for (int p = 0; p < MR; ++p) {
+                        const T v = a[p][kq];
+                        colk[par][ty + GJR_TY * p] = v;
+                        const T av = fabs(v);
+                        if (!((used >> p) & 1ull) && av > bv) {
+                            bv = av;
+                            sv = v;
+                            bi = ty + GJR_TY * p;
+                        }
+                    }
+                    cand_v[par][ty] = sv;
+                    cand_i[par][ty] = bi;
+                }
+                __syncthreads();
+                // B. the owner merges the candidates and publishes the column
+                if (mine) {
+                    T pa = T(-1), piv = T(0);
+                    int pr = INT_MAX;
+                    if (tx < GJR_TY) {
+                        pr = cand_i[par][tx];
+                        piv = cand_v[par][tx];
+                        pa = pr == INT_MAX ? T(-1) : fabs(piv);
+                    }
+#pragma unroll
+                    for (int o = GJR_TY / 2; o > 0; o >>= 1) {
+                        const T oa = __shfl_xor_sync(0xffffffffu, pa, o);
+                        const T ov = __shfl_xor_sync(0xffffffffu, piv, o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, pr, o);
+                        if (oa > pa || (oa == pa && oi < pr)) {
+                            pa = oa;
+                            piv = ov;
+                            pr = oi;
+                        }
+                    }
+                    pa = __shfl_sync(0xffffffffu, pa, 0);
+                    piv = __shfl_sync(0xffffffffu, piv, 0);
+                    pr = __shfl_sync(0xffffffffu, pr, 0);
+                    const bool bad = !(pa > T(0));
+                    // every other CTA receives the column; every CTA the pivot row and value
+                    for (int r = 0; r < CL; ++r) {
+                        if (r != (int)rank)
+                            for (int i = tid; i < BR; i += GJR_THREADS)
+                                st_remote(remote(&colk[par][i], r), colk[par][i]);
+                        if (tid == 0) {
+                            st_remote_i(remote(&s_pr[par], r), bad ? 0 : pr);
+                            st_remote(remote(&s_piv[par], r), piv);
+                            st_remote_i(remote(&s_fail[par], r), bad ? 1 : 0);
+                        }
+                    }
+                }
+                cluster_sync();
+                if (s_fail[par]) {   // uniform across the cluster
+                    fail = true;
+                    break;
+                }
+                const int pr = s_pr[par];
+                const T piv = s_piv[par];
+                const int py = pr % GJR_TY, pp = pr / GJR_TY;
+                // C. the pivot row's owners post this CTA's part of it (before the sweep)
+                if (ty == py) {
+#pragma unroll
+                    for (int p = 0; p < MR; ++p)
+                        if (p == pp) {
+                            used |= 1ull << p;
+#pragma unroll
+                            for (int q = 0; q < MC; ++q) rowk[par][tx + GJR_TX * q] = a[p][q];
+                        }
+                }
+                if (tid == 0) {
+                    prow[k] = pr;
+                    krow[pr] = k;
+                }
+                __syncthreads();
+                // D. sweep the pivot (pr, k) on this CTA's columns: the elimination
+                // on every element, then the pivot column -a(i, k) / p, the pivot
+                // row a(pr, j) / p and the pivot 1 / p (scale-invariant)
+                const T d = T(1) / piv;
+                T rk[MC];
+#pragma unroll
+                for (int q = 0; q < MC; ++q) rk[q] = rowk[par][tx + GJR_TX * q];
+                const bool kcol = mine && tx == kx;
+#pragma unroll
+                for (int p = 0; p < MR; ++p) {
+                    const T f = colk[par][ty + GJR_TY * p] * d;
+#pragma unroll
+                    for (int q = 0; q < MC; ++q) a[p][q] = fma(-f, rk[q], a[p][q]);
+                    if (kcol) a[p][kq] = -f;
+                }
+                if (ty == py) {
+#pragma unroll
+                    for (int p = 0; p < MR; ++p)
+                        if (p == pp) {
+#pragma unroll
+                            for (int q = 0; q < MC; ++q) a[p][q] = rk[q] * d;
+                            if (kcol) a[p][kq] = d;
+                        }
+                }
+            }
+        }
+    }
+    if (fail) {
+        if (tid == 0 && rank == 0) atomicOr(status, ST_SINGULAR);
+        cluster_sync();
+        return;
+    }
+    __syncthreads();
+    // M^-1(krow[i], prow[j]) = a(i, j) on this CTA's columns
+#pragma unroll
+    for (int p = 0; p < MR; ++p)
+#pragma unroll
+        for (int q = 0; q < MC; ++q) {
+            const int i = ty + GJR_TY * p, j = c0 + tx + GJR_TX * q;
+            if (i < b && j < b) g.out[krow[i] + (int64_t)prow[j] * g.ldo] = a[p][q];
+        }
+    cluster_sync();   // no CTA leaves while a peer may still address its shared memory
+}
+
+template <typename T, int CL, int MR, int MC>
+hodlr_status launch_gj_cluster(hodlr_ctx *c, const GJDesc<T> *dd, int count, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(count * CL));
+    cfg.blockDim = dim3(GJR_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    {
+        ProfScope ps("gj_cluster_kernel", s);
+        HODLR_TRY_CUDA(cudaLaunchKernelEx(&cfg, gj_cluster_kernel<T, CL, MR, MC>, dd, c->d_status));
+    }
+    note_launch();
+    return HODLR_OK;
+}
+
 template <typename T>
 size_t gjs_smem(int b) {
     return ((size_t)(b + 1) * b + 2 * (size_t)b) * sizeof(T) + (size_t)b * sizeof(int) + 16;
@@ -821,11 +1054,15 @@ __global__ void quantize_kernel(const float *__restrict__ src, S *__restrict__ d
 //   ||S||_1 = 1 + max_j max(sum_i |P(i,j)|, sum_i |Q(i,j)|),
 //   ||S^-1||_1 = max_j sum_i |S^-1(i,j)|,  kappa_1 = ||S||_1 ||S^-1||_1.
 // One CTA per core, a warp per column.  flag = kappa_1 > thr (or not finite).
+// The last CTA to finish (counter, reset by it) sets the graph's conditional
+// to whether any core of the level is flagged, when the kernel runs inside the
+// guard's graph (has_handle).
 constexpr int CC_THREADS = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(CC_THREADS)
-    core_cond_kernel(const T *__restrict__ Y, const T *__restrict__ Sinv, int r, double thr, double *cond, int *flag) {
+    core_cond_kernel(const T *__restrict__ Y, const T *__restrict__ Sinv, int r, double thr, double *cond, int *flag,
+                     unsigned *counter, int has_handle, cudaGraphConditionalHandle handle) {
     const int i = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = CC_THREADS / 32;
     const int64_t s2 = 2 * (int64_t)r;
@@ -868,6 +1105,14 @@ __global__ void __launch_bounds__(CC_THREADS)
         if (!(k <= 1.7976931348623157e308)) k = __longlong_as_double(0x7ff0000000000000LL);   // NaN, inf -> inf
         cond[i] = k;
         flag[i] = (k > thr) ? 1 : 0;
+        __threadfence();
+        if (atomicAdd(counter, 1u) == gridDim.x - 1) {   // the last core of the level
+            __threadfence();
+            int any = 0;
+            for (unsigned c = 0; c < gridDim.x; ++c) any |= reinterpret_cast<volatile int *>(flag)[c];
+            *counter = 0u;
+            if (has_handle) cudaGraphSetConditional(handle, any ? 1u : 0u);
+        }
     }
 }
 
@@ -887,8 +1132,7 @@ __global__ void core_store_kernel(const double *__restrict__ S64, float *__restr
 // shared memory, or the global-memory kernel (the only one that needs GJDesc::work).
 template <typename T>
 bool gj_needs_work(int bmax) {
-    if (bmax <= 128) return false;
-    if (sizeof(T) == 4 && bmax <= 192) return false;
+    if (bmax <= 256) return false;   // registers (of one CTA, or of a cluster from 161 (FP32) / 129 (FP64))
     return gjs_smem<T>(bmax) > GJS_SMEM_MAX;
 }
 
@@ -901,10 +1145,11 @@ hodlr_status launch_gj(hodlr_ctx *c, const GJDesc<T> *dd, int count, int bmax, c
         if (bmax <= 128) return launch_gj_blocked<T, 16, 4>(c, dd, count, s);
         if (bmax <= 144) return launch_gj_blocked<T, 18, 5>(c, dd, count, s);
         if (bmax <= 160) return launch_gj_blocked<T, 20, 5>(c, dd, count, s);
-        if (bmax <= 192) return launch_gj_reg<T, 24, 6>(c, dd, count, s);   // the blocked tile would spill
+        if (bmax <= 256) return launch_gj_cluster<T, 2, 32, 4>(c, dd, count, s);   // 161 .. 256: two CTAs
     } else {
         if (bmax <= 96) return launch_gj_reg<T, 12, 3>(c, dd, count, s);
         if (bmax <= 128) return launch_gj_reg<T, 16, 4>(c, dd, count, s);
+        if (bmax <= 256) return launch_gj_cluster<T, 8, 32, 1>(c, dd, count, s);   // 129 .. 256: eight CTAs
     }
     if (gjs_smem<T>(bmax) <= GJS_SMEM_MAX) {
         const size_t sm = gjs_smem<T>(bmax);
@@ -940,6 +1185,22 @@ struct LevelPlan {
     size_t dbytes = 0;
     void *work = nullptr;
     size_t work_bytes = 0;
+    // the condition guard's FP64 re-inversion of the cores of this share's
+    // parents: recorded apart, then built into one graph (the condition kernel,
+    // then a conditional node whose body runs when some core is flagged)
+    std::vector<std::function<hodlr_status(cudaStream_t)>> redo;
+    cudaGraph_t ggraph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    struct {
+        const void *Y = nullptr, *Sinv = nullptr;
+        int r = 0;
+        double thr = 0.0;
+        double *cond = nullptr;
+        int *flag = nullptr;
+        unsigned *counter = nullptr;
+        int count = 0;
+        size_t esize = 0;
+    } cond_args;
 
     size_t put(const void *p, size_t bytes) {
         const size_t off = (blob.size() + 255) & ~size_t(255);
@@ -959,6 +1220,8 @@ template <typename T>
 struct Rec {
     hodlr_ctx *c;
     LevelPlan *P;
+    std::vector<std::function<hodlr_status(cudaStream_t)>> *to = nullptr;   // default: P->ops
+    std::vector<std::function<hodlr_status(cudaStream_t)>> &dst() { return to ? *to : P->ops; }
     template <typename TG>
     void gj(const std::vector<GJDesc<TG>> &hd) {
         if (hd.empty()) return;
@@ -968,7 +1231,7 @@ struct Rec {
         const int cnt = (int)hd.size();
         hodlr_ctx *cc = c;
         LevelPlan *PP = P;
-        P->ops.push_back([=](cudaStream_t s) {
+        dst().push_back([=](cudaStream_t s) {
             return launch_gj<TG>(cc, reinterpret_cast<const GJDesc<TG> *>(PP->dblob + off), cnt, bmax, s);
         });
     }
@@ -986,13 +1249,13 @@ struct Rec {
         const int cnt = (int)hd.size();
         hodlr_ctx *cc = c;
         LevelPlan *PP = P;
-        P->ops.push_back([=](cudaStream_t s) {
+        dst().push_back([=](cudaStream_t s) {
             return gemm_batched<TC, TI>(cc, reinterpret_cast<const GemmDesc<TC, TI> *>(PP->dblob + off), cnt, maxM,
                                         maxN, maxK, transA, alpha, s);
         });
     }
     // generic: one recorded launch
-    void op(std::function<hodlr_status(cudaStream_t)> f) { P->ops.push_back(std::move(f)); }
+    void op(std::function<hodlr_status(cudaStream_t)> f) { dst().push_back(std::move(f)); }
     template <typename TF>
     void fill(const std::vector<FillDesc<TF>> &hd) {
         if (hd.empty()) return;
@@ -1002,7 +1265,7 @@ struct Rec {
         const size_t off = P->put(hd.data(), hd.size() * sizeof(FillDesc<TF>));
         const int cnt = (int)hd.size();
         LevelPlan *PP = P;
-        P->ops.push_back([=](cudaStream_t s) {
+        dst().push_back([=](cudaStream_t s) {
             fill_kernel<TF><<<dim3(gx, cnt), 256, 0, s>>>(reinterpret_cast<const FillDesc<TF> *>(PP->dblob + off));
             note_launch();
             HODLR_TRY_CUDA(cudaGetLastError());
@@ -1010,6 +1273,56 @@ struct Rec {
         });
     }
 };
+
+// The guard's graph of one share: the condition kernel (which sets the
+// conditional to whether any core was flagged), then a conditional node whose
+// body is the recorded FP64 re-inversion, captured on a side stream.  Kernels
+// of the body are not counted by hodlr_launch_count (they run only when a core
+// is flagged).
+hodlr_status build_guard_graph(hodlr_ctx *cx, LevelPlan *Pl) {
+    auto &ca = Pl->cond_args;
+    HODLR_TRY_CUDA(cudaGraphCreate(&Pl->ggraph, 0));
+    cudaGraphConditionalHandle handle;
+    HODLR_TRY_CUDA(cudaGraphConditionalHandleCreate(&handle, Pl->ggraph, 0, cudaGraphCondAssignDefault));
+    const float *Y = reinterpret_cast<const float *>(ca.Y);
+    const float *Sv = reinterpret_cast<const float *>(ca.Sinv);
+    int has = 1;
+    void *kargs[] = {(void *)&Y, (void *)&Sv, (void *)&ca.r, (void *)&ca.thr, (void *)&ca.cond, (void *)&ca.flag,
+                     (void *)&ca.counter, (void *)&has, (void *)&handle};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)core_cond_kernel<float>;
+    kp.gridDim = dim3((unsigned)ca.count);
+    kp.blockDim = dim3(CC_THREADS);
+    kp.kernelParams = kargs;
+    cudaGraphNode_t knode, cnode;
+    HODLR_TRY_CUDA(cudaGraphAddKernelNode(&knode, Pl->ggraph, nullptr, 0, &kp));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    HODLR_TRY_CUDA(cudaGraphAddNode(&cnode, Pl->ggraph, &knode, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = cx->side[HODLR_SIDE_STREAMS - 1];
+    HODLR_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    hodlr_status rs = HODLR_OK;
+    {
+        LaunchCapture cap;   // not executed now
+        for (auto &f : Pl->redo) {
+            rs = f(cs);
+            if (rs != HODLR_OK) break;
+        }
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    HODLR_TRY(rs);
+    if (ce != cudaSuccess) {
+        set_error("factor: capture of the condition guard failed: %s", cudaGetErrorString(ce));
+        return HODLR_CUDA_ERROR;
+    }
+    HODLR_TRY_CUDA(cudaGraphInstantiate(&Pl->gexec, Pl->ggraph, 0));
+    return HODLR_OK;
+}
 
 template <typename T>
 hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) {
@@ -1171,26 +1484,38 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
         // enqueued for all cores; the flag of a core decides on the device
         // whether its CTAs do any work.
         if (h->guard) {
+            // the condition kernel: launched alone, or (FP32 arithmetic) as the
+            // first node of the guard's graph built when the share is uploaded
+            LevelPlan *PP = Pl;
             double *cond = h->core_cond[c - 1];
             int *flag = h->core_flag[c - 1];
+            unsigned *counter = h->core_count[c - 1];
             const double thr = h->promote ? h->cond_thr : __builtin_inf();
             const int cnt = nn0;
             const int rcc = rc;
             rec.op([=](cudaStream_t st) {
-                core_cond_kernel<T><<<cnt, CC_THREADS, 0, st>>>(Yo, Sinv, rcc, thr, cond, flag);
+                if (PP->gexec) {
+                    HODLR_TRY_CUDA(cudaGraphLaunch(PP->gexec, st));
+                } else {
+                    core_cond_kernel<T><<<cnt, CC_THREADS, 0, st>>>(Yo, Sinv, rcc, thr, cond, flag, counter, 0,
+                                                                    cudaGraphConditionalHandle{});
+                    HODLR_TRY_CUDA(cudaGetLastError());
+                }
                 note_launch();
-                HODLR_TRY_CUDA(cudaGetLastError());
                 return HODLR_OK;
             });
+            Pl->cond_args = {reinterpret_cast<const void *>(Yo), reinterpret_cast<const void *>(Sinv), rcc, thr, cond,
+                             flag, counter, cnt, sizeof(T)};
         }
         if (redo) {
+            Rec<T> rr{cx, Pl, &Pl->redo};
             const int *flag = h->core_flag[c - 1];
             double *Y64 = reinterpret_cast<double *>(wb + oY64);
             double *M64 = reinterpret_cast<double *>(wb + oM64);
             double *gw64 = gwn64 ? reinterpret_cast<double *>(wb + oGW64) : nullptr;
             double *S64 = h->Sinv64[c - 1];
             auto Y64i = [&](int i) { return Y64 + (size_t)i * s2c * rc; };
-            rec.fill(std::vector<FillDesc<double>>{
+            rr.fill(std::vector<FillDesc<double>>{
                 FillDesc<double>{Y64, 0, (int64_t)nn0 * s2c * rc, 1, INT_MAX, 1, 0},
                 FillDesc<double>{M64, rc, rc, rc, 0, nn0, (int64_t)rc * rc},            // I
                 FillDesc<double>{S64, s2c, s2c, s2c, rc, nn0, s2c * s2c}});             // [0 0; 0 I]
@@ -1201,7 +1526,7 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
                 gy[ch] = GemmDesc<double, T>{Vc + r0, Dc + r0, Y64i(ch / 2) + (ch & 1) * rc, ldn, ldn, s2c, rc, rc,
                                              (int)m, flag + ch / 2};
             }
-            rec.gemm(gy, 1, 1.0);
+            rr.gemm(gy, 1, 1.0);
             std::vector<GemmDesc<double>> gm(nn0), g12(2 * nn0), g3(nn0);
             std::vector<GJDesc<double>> gj(nn0);
             for (int i = 0; i < nn0; ++i) {
@@ -1214,15 +1539,15 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
                 g12[2 * i + 1] = GemmDesc<double>{Q, S, S + rc, s2c, s2c, s2c, rc, rc, rc, flag + i};
                 g3[i] = GemmDesc<double>{Q, S + rc * s2c, S + rc + rc * s2c, s2c, s2c, s2c, rc, rc, rc, flag + i};
             }
-            rec.gemm(gm, 0, -1.0);
-            rec.gj(gj);
-            rec.gemm(g12, 0, -1.0);
-            rec.gemm(g3, 0, -1.0);
+            rr.gemm(gm, 0, -1.0);
+            rr.gj(gj);
+            rr.gemm(g12, 0, -1.0);
+            rr.gemm(g3, 0, -1.0);
             const int cnt = nn0;
             const int64_t per = s2c * s2c;
             float *S32 = reinterpret_cast<float *>(h->Sinv[c - 1]);
             const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (per + 1023) / 1024));
-            rec.op([=](cudaStream_t st) {
+            rr.op([=](cudaStream_t st) {
                 core_store_kernel<<<dim3(gx, cnt), 256, 0, st>>>(S64, S32, per, flag);
                 note_launch();
                 HODLR_TRY_CUDA(cudaGetLastError());
@@ -1286,6 +1611,7 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
     }
     if (!Pl->blob.empty())
         HODLR_TRY_CUDA(cudaMemcpyAsync(Pl->dblob, Pl->blob.data(), Pl->blob.size(), cudaMemcpyHostToDevice, s));
+    if (!Pl->redo.empty()) HODLR_TRY(build_guard_graph(cx, Pl));
     return HODLR_OK;
 }
 
@@ -1386,6 +1712,8 @@ hodlr_status run_level(hodlr_t *h, int c, cudaStream_t s, const cudaEvent_t *sha
 void free_plan(hodlr_t *h, cudaStream_t s) {
     if (!h->plan) return;
     for (auto &P : h->plan->lv) {
+        if (P.gexec) cudaGraphExecDestroy(P.gexec);
+        if (P.ggraph) cudaGraphDestroy(P.ggraph);
         if (P.work) dfree(h->ctx, P.work, P.work_bytes, s);
         if (P.dblob) dfree(h->ctx, P.dblob, P.dbytes, s);
     }

@@ -712,6 +712,7 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
     const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     if (!vec || n % 2 != 0) Asp = nullptr;   // the split buffer is read as 16-byte pairs of columns
     for (int r0 = 0; r0 < s && e == cudaSuccess; r0 += MV_S) {
+        ProfScope ps("df_matvec_kernel", st);
         if (vec)
             if (z_fp32)
                 df_matvec_kernel<true, true><<<grid, MV_THREADS, 0, st>>>(A, n, lda, zs, s, r0, W, ldw, c->d_status,

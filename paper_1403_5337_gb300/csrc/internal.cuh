@@ -49,6 +49,18 @@ hodlr_status status_from_word(int w);
 // per replay.
 void note_launch(long long k = 1);
 long long launch_total();
+// Per-kernel device time (hodlr_profile_enable): a ProfScope around a launch
+// records CUDA events on the launching stream before and after it, unless
+// profiling is off or the stream is being captured into a graph.
+struct ProfScope {
+    const char *name = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(const char *kernel, cudaStream_t stream);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+};
 struct LaunchCapture {
     long long captured = 0;
     LaunchCapture *prev = nullptr;
@@ -155,6 +167,7 @@ struct hodlr_s {
     double tol = 0.0;
     int rank_cap = 1024;
     int cap_hit = 0;
+    int bdlr_depth_max = 0;           // BDLR: the largest distance depth a block used
     std::vector<hodlr::Level> lv;     // index 1..L used
     int64_t ldn = 0;                  // leading dimension of U, D, V (n rounded up to 32)
     int64_t Wtot = 0;                 // sum of rp over the levels
@@ -187,11 +200,16 @@ struct hodlr_s {
     // Woodbury core condition guard (level l = 0..L-1: the 2^l cores of the
     // parents of level l + 1): kappa_1(S) of every core, the flag of the cores
     // re-inverted in FP64, and their FP64 inverses (FP32 arithmetic only)
+    // the diagonal (Jacobi) preconditioner of the paper's comparison: no levels,
+    // the apply is X <- diag(A)^-1 X (baselines.cu)
+    bool diag = false;
+    double *dinv = nullptr;
     bool guard = false;                // kappa_1 is computed
     bool promote = false;              // cores above cond_thr are re-inverted in FP64
     double cond_thr = 0.0;
     std::vector<double *> core_cond;
     std::vector<int *> core_flag;
+    std::vector<unsigned *> core_count;   // per level: the condition kernel's completion counter (self-resetting)
     std::vector<double *> Sinv64;
 };
 
@@ -272,6 +290,7 @@ void free_plan(hodlr_t *h, cudaStream_t s);
 // split the product reads.
 hodlr_status solve_impl(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s, float2 *Xs = nullptr);
 hodlr_status solve_prepare(const hodlr_t *h, int s_rhs, cudaStream_t s);
+hodlr_status diag_solve(const hodlr_t *h, int s_rhs, double *X, int64_t ldx, cudaStream_t s, float2 *Xs);
 // Asp / split_state: optional n x n buffer of A's FP32 (hi, lo) pairs, written by
 // the first product while *split_state is 0 and read by later ones.
 // z_split: work already holds the FP32 split of Z (ld n), written by the apply;

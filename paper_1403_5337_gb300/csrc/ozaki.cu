@@ -550,7 +550,10 @@ hodlr_status oz_split_a(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, v
     auto *sl = reinterpret_cast<__nv_bfloat16 *>(abuf);
     int *ea = reinterpret_cast<int *>(reinterpret_cast<char *>(abuf) +
                                       align256((size_t)S * np * kp * sizeof(__nv_bfloat16)));
-    oz_split_rows_kernel<<<(unsigned)(np / 8), 256, 0, st>>>(A, n, lda, np, kp, sl, ea, c->d_status);
+    {
+        ProfScope ps("oz_split_rows_kernel", st);
+        oz_split_rows_kernel<<<(unsigned)(np / 8), 256, 0, st>>>(A, n, lda, np, kp, sl, ea, c->d_status);
+    }
     note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     return HODLR_OK;
@@ -576,7 +579,10 @@ hodlr_status oz_matvec(hodlr_ctx *c, const void *abuf, int64_t n, int s, const d
     auto *Phi = reinterpret_cast<unsigned long long *>(zp);
     zp += align256((size_t)sp * np * sizeof(unsigned long long));
     auto *Plo = reinterpret_cast<unsigned long long *>(zp);
-    oz_split_cols_kernel<<<(unsigned)sp, 256, 0, st>>>(Z, ldz, n, s, kp, sp, zs, ez, c->d_status);
+    {
+        ProfScope ps("oz_split_cols_kernel", st);
+        oz_split_cols_kernel<<<(unsigned)sp, 256, 0, st>>>(Z, ldz, n, s, kp, sp, zs, ez, c->d_status);
+    }
     note_launch();
     HODLR_TRY_CUDA(cudaMemsetAsync(Phi, 0, 2 * align256((size_t)sp * np * sizeof(unsigned long long)), st));
     CUtensorMap mA, mZ;
@@ -593,7 +599,10 @@ hodlr_status oz_matvec(hodlr_ctx *c, const void *abuf, int64_t n, int s, const d
     TcArgs ta{ea, ez, n, s, nchunks, per, Phi, Plo, np, c->d_status};
     HODLR_TRY_CUDA(cudaFuncSetAttribute(oz_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     const dim3 grid((unsigned)(np / TC_BM), (unsigned)(sp / TC_BN), (unsigned)ksplit);
-    oz_tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mZ, ta);
+    {
+        ProfScope ps("oz_tc_gemm_kernel", st);
+        oz_tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mZ, ta);
+    }
     note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
     const unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);

@@ -63,7 +63,7 @@ class _Stats(C.Structure):
                 ("cap_hit", C.c_int), ("bytes_factors", C.c_int64), ("factored", C.c_int),
                 ("ms_compress", C.c_double), ("ms_factor", C.c_double),
                 ("core_cond_max", C.c_double * MAX_LEVELS), ("cores_promoted", C.c_int * MAX_LEVELS),
-                ("core_cond_threshold", C.c_double)]
+                ("core_cond_threshold", C.c_double), ("bdlr_depth_max", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -80,7 +80,8 @@ SYMBOLS = ["hodlr_ctx_create", "hodlr_ctx_destroy", "hodlr_opts_default", "hodlr
            "hodlr_stats_get",
            "hodlr_export_level", "hodlr_export_core", "hodlr_export_core_cond", "hodlr_destroy", "hodlr_status_string",
            "hodlr_last_error", "hodlr_launch_count", "hodlr_build_batched", "hodlr_factor_batched",
-           "gmres_solve_batched", "hodlr_ctx_set_wait_test"]
+           "gmres_solve_batched", "hodlr_ctx_set_wait_test", "hodlr_profile_enable", "hodlr_profile_read",
+           "hodlr_build_diag", "hodlr_dense_lu_solve", "hodlr_save", "hodlr_load"]
 
 _lib = None
 # Library calls in progress on this process.  The torch allocator callbacks run
@@ -121,6 +122,10 @@ def load_library(path: str = _LIBPATH):
     lib.hodlr_build.argtypes = [vp, C.POINTER(_Matrix), ci, cd, ci, C.POINTER(_Graph), C.POINTER(_Opts), vp,
                                 C.POINTER(vp)]
     lib.hodlr_factor.argtypes = [vp, vp]
+    lib.hodlr_build_diag.argtypes = [vp, C.POINTER(_Matrix), vp, C.POINTER(vp)]
+    lib.hodlr_save.argtypes = [vp, vp, C.c_size_t, C.POINTER(C.c_size_t), vp]
+    lib.hodlr_load.argtypes = [vp, C.POINTER(_Matrix), vp, C.c_size_t, vp, C.POINTER(vp)]
+    lib.hodlr_dense_lu_solve.argtypes = [vp, C.POINTER(_Matrix), ci, vp, i64, vp, i64, vp]
     lib.hodlr_solve.argtypes = [vp, ci, vp, i64, vp]
     lib.gmres_solve.argtypes = [vp, C.POINTER(_Matrix), ci, vp, i64, vp, i64, vp, cd, ci, ci, C.POINTER(_Info), vp]
     lib.hodlr_matvec.argtypes = [vp, C.POINTER(_Matrix), ci, vp, i64, vp, i64, vp]
@@ -133,6 +138,8 @@ def load_library(path: str = _LIBPATH):
     lib.hodlr_destroy.argtypes = [vp]
     lib.hodlr_launch_count.argtypes = [C.POINTER(C.c_longlong)]
     lib.hodlr_ctx_set_wait_test.argtypes = [vp, C.c_ulonglong, ci]
+    lib.hodlr_profile_enable.argtypes = [ci]
+    lib.hodlr_profile_read.argtypes = [C.c_char_p, C.POINTER(cd), C.POINTER(C.c_longlong)]
     lib.hodlr_build_batched.argtypes = [vp, ci, C.POINTER(_Matrix), C.POINTER(ci), cd, ci, C.POINTER(_Opts), vp,
                                         C.POINTER(vp)]
     lib.hodlr_factor_batched.argtypes = [ci, C.POINTER(vp), vp]
@@ -294,7 +301,7 @@ class Hodlr:
                     cap_hit=bool(st.cap_hit), bytes_factors=st.bytes_factors, factored=bool(st.factored),
                     ms_compress=st.ms_compress, ms_factor=st.ms_factor,
                     core_cond_max=list(st.core_cond_max[:L]), cores_promoted=list(st.cores_promoted[:L]),
-                    core_cond_threshold=st.core_cond_threshold)
+                    core_cond_threshold=st.core_cond_threshold, bdlr_depth_max=st.bdlr_depth_max)
 
     def export_level(self, level: int, stream=None):
         """(U, V, ranks, piv_rows, piv_cols) of level `level` as numpy arrays."""
@@ -334,6 +341,10 @@ class Hodlr:
         return cond, flag.astype(bool)
 
     def close(self):
+        if self.handle and self.ctx is not None and not self.ctx.handle:
+            # the context is gone, and the device memory with it: nothing to release
+            self.handle = None
+            return
         if self.handle:
             if _depth > 0:
                 _deferred.append(self.handle)
@@ -380,6 +391,49 @@ def hodlr_build(ctx: Context, A: torch.Tensor, leaf: int, tol: float, method: st
     _check(lib.hodlr_build(ctx.handle, C.byref(mat), int(leaf), float(tol), _METHOD[method], gp, C.byref(o),
                            _stream(stream), C.byref(h)))
     return Hodlr(ctx, h, A, keep)
+
+
+def hodlr_build_diag(ctx: Context, A: torch.Tensor, symmetric: bool = True, stream=None) -> Hodlr:
+    """The diagonal (Jacobi) preconditioner of the paper's comparison (Fig. 8):
+    a handle that gmres_solve and hodlr_solve take like a HODLR matrix."""
+    lib = load_library()
+    mat = _mat(A, symmetric)
+    h = C.c_void_p()
+    _check(lib.hodlr_build_diag(ctx.handle, C.byref(mat), _stream(stream), C.byref(h)))
+    return Hodlr(ctx, h, A, [])
+
+
+def hodlr_dense_lu_solve(ctx: Context, A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+    """The paper's dense LU comparator (Table 3): X = A^-1 B by partial-pivoting
+    LU on the GPU; B is (s, n) or (n,)."""
+    lib = load_library()
+    mat = _mat(A, False)
+    bptr, s, ldb = _rhs(B, A.shape[0])
+    X = torch.empty_like(B, memory_format=torch.contiguous_format)
+    xptr, _, ldx = _rhs(X, A.shape[0])
+    _check(lib.hodlr_dense_lu_solve(ctx.handle, C.byref(mat), s, C.c_void_p(bptr), ldb, C.c_void_p(xptr), ldx,
+                                    _stream(stream)))
+    return X
+
+
+def hodlr_save(h: Hodlr, stream=None) -> bytes:
+    """The checkpoint image of a factored HODLR matrix (host bytes)."""
+    need = C.c_size_t(0)
+    _check(_lib.hodlr_save(h.handle, None, 0, C.byref(need), _stream(stream)))
+    buf = (C.c_char * need.value)()
+    _check(_lib.hodlr_save(h.handle, buf, need.value, C.byref(need), _stream(stream)))
+    return bytes(buf)
+
+
+def hodlr_load(ctx: Context, image: bytes, A: torch.Tensor | None = None, symmetric: bool = True,
+               stream=None) -> Hodlr:
+    """Restore a HODLR matrix from hodlr_save's image (A optional: only
+    hodlr_precond_error needs it)."""
+    lib = load_library()
+    mat = C.byref(_mat(A, symmetric)) if A is not None else None
+    h = C.c_void_p()
+    _check(lib.hodlr_load(ctx.handle, mat, image, len(image), _stream(stream), C.byref(h)))
+    return Hodlr(ctx, h, A, [])
 
 
 def hodlr_factor(h: Hodlr, stream=None) -> None:
@@ -521,3 +575,16 @@ def hodlr_precond_error(h: Hodlr, Omega: torch.Tensor, stream=None) -> float:
     out = C.c_double()
     _check(_lib.hodlr_precond_error(h.handle, k, C.c_void_p(ptr), ld, C.byref(out), _stream(stream)))
     return out.value
+
+
+def hodlr_profile_enable(on: bool = True) -> None:
+    """Switch the library's per-kernel event timing on or off (clears it)."""
+    _check(load_library().hodlr_profile_enable(1 if on else 0))
+
+
+def hodlr_profile_read(kernel: str):
+    """(total ms, launches) recorded for `kernel` since profiling was enabled."""
+    ms = C.c_double()
+    cnt = C.c_longlong()
+    _check(load_library().hodlr_profile_read(kernel.encode(), C.byref(ms), C.byref(cnt)))
+    return ms.value, int(cnt.value)

@@ -109,6 +109,29 @@ def test_bdlr_matches_oracle(H, ctx, front576, cprec, dtype, rtol):
     h.close()
 
 
+@pytest.mark.parametrize("cprec,dtype,rtol", [("fp64", np.float64, 1e-10), ("fp32", np.float32, 1e-3)])
+@pytest.mark.parametrize("tol", [1e-3, 1e-6])
+def test_adaptive_bdlr_matches_oracle(H, ctx, front576, cprec, dtype, rtol, tol):
+    """The adaptive pseudo-skeleton (Sec. 5.3, bdlr_depth = -2): every block
+    grows its depth until the held-out error meets tol; the selected pivots and
+    ranks of every block equal the oracle's, and so does the largest depth."""
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    g = (F.rowptr, F.colind)
+    blocks = O.build(F.A, tree, "bdlr", tol, graph=g, depth=-2, dtype=dtype)
+    dmax = 0
+    for (l, i) in blocks:
+        a, b = range(*tree.range(l + 1, 2 * i)), range(*tree.range(l + 1, 2 * i + 1))
+        for rows, cols in ((a, b), (b, a)):
+            _, d, _ = O.bdlr_adaptive(F.A, g[0], g[1], rows, cols, tol, 1, 1 << 30, dtype)
+            dmax = max(dmax, d)
+    h = H.hodlr_build(ctx, _dev(F.A), 64, tol, "bdlr", graph=g, precision="fp64", compress_precision=cprec,
+                      bdlr_depth=-2)
+    _compare_compression(h, F, blocks, tree, rtol)
+    assert h.stats()["bdlr_depth_max"] == dmax
+    h.close()
+
+
 def test_aca_nonsymmetric_column_reads(H, ctx, front576):
     F = front576
     tree = O.make_tree(F.n, 64, F.bounds)
@@ -495,6 +518,73 @@ def test_rank_zero_blocks(H, ctx):
     h.close()
 
 
+@pytest.mark.parametrize("prec,tol,rtol", [("fp64", 1e-8, 1e-10), ("fp32", 1e-5, 2e-4)])
+def test_large_leaves_cluster_inverse(H, ctx, prec, tol, rtol):
+    """Leaves of 193 to 256 rows (ragged: 230, 250, 220, 256) are inverted by a
+    cluster of CTAs sharing the columns; d = K_leaf^-1 U of the deepest level
+    and the solve agree with the oracle's LU-based recursion."""
+    rng = np.random.default_rng(8)
+    n = 956
+    bounds = np.array([0, 230, 480, 700, 956])
+    # a Gaussian kernel (numerically low-rank off the diagonal) plus a random
+    # SPD block on every leaf
+    x = np.linspace(0, 1, n)
+    A = np.exp(-((x[:, None] - x[None, :]) / 0.3) ** 2) + 0.5 * np.eye(n)
+    for i in range(4):
+        r0, r1 = bounds[i], bounds[i + 1]
+        M = rng.standard_normal((r1 - r0, r1 - r0))
+        A[r0:r1, r0:r1] += M @ M.T / (r1 - r0)
+    tree = O.make_tree(n, 256, bounds)
+    dtype = np.float64 if prec == "fp64" else np.float32
+    blocks = O.build(A, tree, "aca", tol, dtype=dtype)
+    Fac = O.factor(A, tree, blocks)
+    h = H.hodlr_build(ctx, _dev(A), 256, tol, "aca", precision=prec, leaf_bounds=bounds)
+    D = h.export_d(2)
+    for i in range(4):
+        r0, r1 = tree.range(2, i)
+        ref = Fac.d[(2, i)]
+        got = D[r0:r1, :ref.shape[1]]
+        assert np.abs(got - ref).max() <= rtol * np.abs(ref).max(), (i, np.abs(got - ref).max())
+    b = rng.standard_normal((3, n))
+    X = _dev(b)
+    H.hodlr_solve(h, X)
+    ref = O.solve(Fac, b.T).T
+    assert np.linalg.norm(X.cpu().numpy() - ref) / np.linalg.norm(ref) < rtol
+    h.close()
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-10), ("fp32", 2e-4)])
+@pytest.mark.parametrize("leaf", [32, 64, 96, 128, 160, 192, 256])
+@pytest.mark.parametrize("scale", [1e6, 1e-6])
+def test_leaf_inverse_is_scale_invariant(H, ctx, prec, rtol, leaf, scale):
+    """Every Gauss-Jordan size class (registers, blocked panels, clusters of
+    CTAs) on a matrix scaled by 1e6 or 1e-6: a uniform scale leaves the
+    condition unchanged, so d = K_leaf^-1 U of the deepest level must agree
+    with the FP64 solve of the leaf to the arithmetic's unit roundoff times
+    the leaf's condition (below 10 here), whatever the size of the pivots."""
+    rng = np.random.default_rng(leaf)
+    n = 4 * leaf
+    x = np.linspace(0, 1, n)
+    K = np.exp(-((x[:, None] - x[None, :]) / 0.3) ** 2) + 0.5 * np.eye(n)
+    for i in range(4):
+        M = rng.standard_normal((leaf, leaf))
+        K[i * leaf:(i + 1) * leaf, i * leaf:(i + 1) * leaf] += M @ M.T / leaf
+    A = scale * K
+    tol = 1e-8 if prec == "fp64" else 1e-5
+    h = H.hodlr_build(ctx, _dev(A), leaf, tol, "aca", precision=prec)
+    st = h.stats()
+    L = st["levels"]
+    assert L == 2 and st["leaf_max"] == leaf
+    U, _, _, _, _ = h.export_level(L)
+    D = h.export_d(L)
+    for i in range(4):
+        r0, r1 = i * leaf, (i + 1) * leaf
+        ref = np.linalg.solve(A[r0:r1, r0:r1], U[r0:r1])
+        err = np.abs(D[r0:r1] - ref).max() / np.abs(ref).max()
+        assert err <= rtol, (leaf, scale, i, err)
+    h.close()
+
+
 def test_nonfinite_input_is_reported(H, ctx, front576):
     A = front576.A.copy()
     A[0, 300] = np.nan                   # row 0 of the top block is always read
@@ -614,6 +704,36 @@ def test_reduced_plane32768_fp16_32_rhs(H, ctx):
         o = O.gmres(F.A, b[:, r], prec=P, tol=1e-12)
         assert abs(int(info.iters[r]) - o.iters) <= 3, (r, info.iters[r], o.iters)
         assert np.linalg.norm(x[r] - o.x) / np.linalg.norm(o.x) < 1e-9
+    h.close()
+
+
+@pytest.mark.parametrize("method,prec", [("aca", "fp64"), ("aca", "fp32"), ("bdlr", "fp64")])
+def test_elastic_front_gmres(H, ctx, method, prec):
+    """The 3-dof elasticity front (Navier-Cauchy, lognormal shear modulus,
+    Poisson ratio 0.3) of a 24 x 24 x 9 box, n = 1728, leaves of 36 nodes:
+    ranks per level equal the oracle's, GMRES reaches 1e-12, iterates agree with
+    the oracle's to 1e-9 and iteration counts within 2."""
+    E = fg.make_elastic_front(24, 24, 4, 4, leaf_nodes=64)
+    tree = O.make_tree(E.n, 108, E.bounds)
+    g = (E.rowptr, E.colind)
+    tol = 1e-6 if method == "aca" else 1e-4
+    dtype = np.float64 if prec == "fp64" else np.float32
+    blocks, Fac, P = O.hodlr_precond(E.A, tree, method, tol, graph=g, symmetric=True, dtype=dtype)
+    A = _dev(E.A)
+    h = H.hodlr_build(ctx, A, 108, tol, method, graph=g, precision=prec, leaf_bounds=E.bounds)
+    st = h.stats()
+    for l in range(1, tree.L + 1):
+        ro = max(blocks[(l - 1, i // 2)].Ua.shape[1] if i % 2 == 0 else blocks[(l - 1, i // 2)].Ub.shape[1]
+                 for i in range(1 << l))
+        assert st["rank_max"][l - 1] == ro
+    b = fg.rhs(E.n, 2, seed=1)
+    X, info = H.gmres_solve(ctx, A, _dev(b.T), h, tol=1e-12)
+    assert info.converged and np.all(info.true_relres <= 1e-12)
+    x = X.cpu().numpy()
+    for r in range(2):
+        ref = O.gmres(E.A, b[:, r], prec=P, tol=1e-12)
+        assert abs(int(info.iters[r]) - ref.iters) <= 2, (info.iters[r], ref.iters)
+        assert np.linalg.norm(x[r] - ref.x) / np.linalg.norm(ref.x) < 1e-9
     h.close()
 
 

@@ -71,6 +71,43 @@ def test_line_and_plane_eliminations_agree():
     assert np.abs(F1 - F2).max() <= 1e-13 * np.abs(F1).max()
 
 
+def test_elastic_operator_spd_and_consistent():
+    """The 3-dof elasticity operator: symmetric positive definite, and with a
+    constant shear modulus it annihilates every linear displacement field
+    u(x) = M x + c on the nodes whose stencil stays inside the box (the
+    discrete Laplacian of a linear field and the gradient of a constant
+    divergence both vanish)."""
+    nz, ny, nx = 6, 6, 6
+    K = fg.elastic_operator(np.ones((nz, ny, nx)), nu=0.3).toarray()
+    assert np.array_equal(K, K.T)
+    assert np.linalg.eigvalsh(K).min() > 0
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((3, 3))
+    c = rng.standard_normal(3)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    X = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(float)    # x-fastest node order
+    u = (X @ M.T + c).reshape(-1)                                            # 3 dofs per node
+    r = (K @ u).reshape(-1, 3)
+    inner = ((X > 1) & (X < np.array([nx, ny, nz]) - 2)).all(axis=1)
+    assert inner.sum() > 0
+    assert np.abs(r[inner]).max() <= 1e-12 * np.abs(K).max() * np.abs(u).max()
+    assert np.abs(r[~inner]).max() > 1e-3   # the Dirichlet boundary does act
+
+
+def test_elastic_front_is_brute_force_schur_complement():
+    mu = fg.coefficient_lognormal(4, 3, 5, 0.7, seed=2)
+    K = fg.elastic_operator(mu).toarray()
+    m = 3 * 4 * 3
+    s = np.arange(m) + 2 * m
+    i = np.setdiff1d(np.arange(K.shape[0]), s)
+    S = K[np.ix_(s, s)] - K[np.ix_(s, i)] @ np.linalg.solve(K[np.ix_(i, i)], K[np.ix_(i, s)])
+    F = fg.elastic_front(mu, 2)
+    assert np.allclose(F, S, rtol=1e-12, atol=1e-12 * np.abs(S).max())
+    E = fg.make_elastic_front(8, 8, 2, 2, leaf_nodes=16)
+    np.linalg.cholesky(E.A)
+    assert E.n == 192 and E.bounds[-1] == 192 and np.all(np.diff(E.bounds) % 3 == 0)
+
+
 def test_front_invariants():
     F = fg.make_front(8, 6, 3, 2, "lognormal", 0.5, leaf=8, seed=0)
     A = F.A
@@ -377,6 +414,63 @@ def test_bdlr_exact_when_skeleton_has_full_rank():
     assert len(res.Ir) == k
     blk = A[:16, 16:]
     assert np.linalg.norm(res.U @ res.V.T - blk) / np.linalg.norm(blk) < 1e-12
+
+
+def _top_block(F, leaf=64):
+    tree = O.make_tree(F.n, leaf, F.bounds)
+    a0, a1 = tree.range(1, 0)
+    b0, b1 = tree.range(1, 1)
+    return range(a0, a1), range(b0, b1)
+
+
+def test_bdlr_error_never_beats_svd():
+    """Figs. 4-6 diagnostics: by Eckart-Young, no rank-r approximation beats the
+    truncated SVD in the Frobenius norm, so the BDLR error at every rank is at
+    least the SVD's; and the largest pivots sit on the boundary (distance 0)."""
+    F = fg.make_front(24, 24, 8, 8, "lognormal", 0.5, leaf=64, seed=0)
+    R, C = _top_block(F)
+    D = O.bdlr_diagnostics(F.A, F.rowptr, F.colind, R, C, 1e-8, 6)
+    assert len(D["bdlr_err"]) >= 20
+    assert np.all(D["bdlr_err"] >= D["svd_err"] * (1 - 1e-9))
+    assert np.all(np.diff(D["singular_values"]) <= 0)
+    assert D["row_dist"][0] == 0 and D["col_dist"][0] == 0
+    assert np.mean(D["row_dist"][:8]) <= np.mean(D["row_dist"])
+
+
+def test_heldout_error_closed_forms():
+    rng = np.random.default_rng(1)
+    X, Y = rng.standard_normal((30, 3)), rng.standard_normal((20, 3))
+    A = np.zeros((50, 50))
+    A[:30, 30:] = X @ Y.T
+    R, C = range(0, 30), range(30, 50)
+    # exact factors: no residual
+    assert O.heldout_error(A, R, C, X, Y, [1, 5], [33], [0], [30]) <= 1e-15
+    # no factors: the held-out rows' and columns' share of the examined mass
+    Z, W = np.zeros((30, 3)), np.zeros((20, 3))
+    Hr, Hc, I, J = [2, 7], [35], [0, 1], [30, 31]
+    num = sum(np.sum(A[h, 30:] ** 2) for h in Hr) + np.sum(A[:30, 35] ** 2)
+    den = sum(np.sum(A[h, 30:] ** 2) for h in Hr + I) + sum(np.sum(A[:30, h] ** 2) for h in Hc + J)
+    assert O.heldout_error(A, R, C, Z, W, Hr, Hc, I, J) == pytest.approx(np.sqrt(num / den), rel=1e-14)
+    assert O.heldout_error(A, R, C, Z, W, [], [], I, J) == 0.0
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_adaptive_bdlr_takes_the_least_sufficient_depth(eps):
+    """Section 5.3's adaptive pseudo-skeleton: the returned depth meets eps on
+    its held-out rows and columns and the depth below it does not."""
+    F = fg.make_front(24, 24, 8, 8, "lognormal", 0.5, leaf=64, seed=0)
+    R, C = _top_block(F)
+    res, d, err = O.bdlr_adaptive(F.A, F.rowptr, F.colind, R, C, eps)
+    assert err <= eps
+    if d > 1:
+        prev = O.bdlr(F.A, F.rowptr, F.colind, R, C, eps, d - 1)
+        _, dr = O.boundary_distance(F.rowptr, F.colind, R, C, d)
+        _, dc = O.boundary_distance(F.rowptr, F.colind, C, R, d)
+        Hr = [R.start + i for i in np.flatnonzero(dr == d)]
+        Hc = [C.start + j for j in np.flatnonzero(dc == d)]
+        assert O.heldout_error(F.A, R, C, prev.U, prev.V, Hr, Hc, prev.I, prev.J) > eps
+    blk = F.A[R.start:R.stop, C.start:C.stop]
+    assert np.linalg.norm(blk - res.U @ res.V.T) / np.linalg.norm(blk) < 20 * eps
 
 
 # --------------------------------------------------------------------------- HODLR
