@@ -471,6 +471,42 @@ def run_matvec_probe(args):
     print(json.dumps(out))
 
 
+def run_apply_probe(args):
+    """The HODLR apply alone on a workload's front: build and factor, release A,
+    then time hodlr_solve on the workload's right-hand sides, for a profiler
+    capture that holds only the factors on the device (--probe-apply)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_1403_5337_gb300 as H
+    F, Bh = make_inputs(args.workload, "cuda")
+    leaf = WORKLOADS[args.workload]["front"]["leaf"]
+    ctx = H.Context(0)
+    h0 = H.hodlr_build(ctx, F.A, leaf, args.tol, args.method, graph=(F.rowptr, F.colind), precision=args.precision)
+    image = H.hodlr_save(h0)
+    h0.close()
+    del F, h0
+    torch.cuda.empty_cache()
+    h = H.hodlr_load(ctx, image)        # the same factors, without A
+    torch.cuda.reset_peak_memory_stats()
+    X = torch.as_tensor(np.ascontiguousarray(Bh.T), device="cuda")
+    for _ in range(args.warmup):
+        H.hodlr_solve(h, X)
+    torch.cuda.synchronize()
+    H.hodlr_profile_enable(True)
+    for _ in range(args.steps):
+        H.hodlr_solve(h, X)
+    torch.cuda.synchronize()
+    ms, cnt = H.hodlr_profile_read("apply_fused_kernel")
+    H.hodlr_profile_enable(False)
+    st = h.stats()
+    h.close()
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "nrhs": int(X.shape[0]),
+                      "apply_fused_kernel_ms": ms / max(cnt, 1), "launches": cnt,
+                      "rank_pad": st["rank_pad"], "image_bytes": len(image),
+                      "device_bytes_after_load": torch.cuda.max_memory_allocated()}))
+
+
 
 def run_peaks(args):
     """Measured GEMM rates of the pipes the path uses beside the tensor cores:
@@ -522,6 +558,8 @@ def main():
     ap.add_argument("--probe", type=int, nargs=2, metavar=("N", "S"),
                     help="time hodlr_matvec of a random N x N matrix with S right-hand sides")
     ap.add_argument("--peaks", action="store_true", help="measure the FP64 and FP32 (SIMT) GEMM rates")
+    ap.add_argument("--probe-apply", action="store_true",
+                    help="time hodlr_solve alone on the workload's factors, with A released")
     args = ap.parse_args()
     if args.peaks:
         return run_peaks(args)
@@ -535,6 +573,8 @@ def main():
         return run_reference(args)
     if args.probe:
         return run_matvec_probe(args)
+    if args.probe_apply:
+        return run_apply_probe(args)
     if args.kernels:
         return run_kernels(args)
     if args.workload == "octree585":

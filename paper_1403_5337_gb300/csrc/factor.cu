@@ -1493,7 +1493,11 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
             const double thr = h->promote ? h->cond_thr : __builtin_inf();
             const int cnt = nn0;
             const int rcc = rc;
+            hodlr_ctx *gcx = cx;
             rec.op([=](cudaStream_t st) {
+                // the guard's graph is built here, on first use: its host cost
+                // then overlaps the GPU work already enqueued for this share
+                if (!PP->redo.empty() && !PP->gexec) HODLR_TRY(build_guard_graph(gcx, PP));
                 if (PP->gexec) {
                     HODLR_TRY_CUDA(cudaGraphLaunch(PP->gexec, st));
                 } else {
@@ -1611,7 +1615,6 @@ hodlr_status plan_level_typed(hodlr_t *h, LevelPlan *Pl, int c, cudaStream_t s) 
     }
     if (!Pl->blob.empty())
         HODLR_TRY_CUDA(cudaMemcpyAsync(Pl->dblob, Pl->blob.data(), Pl->blob.size(), cudaMemcpyHostToDevice, s));
-    if (!Pl->redo.empty()) HODLR_TRY(build_guard_graph(cx, Pl));
     return HODLR_OK;
 }
 
