@@ -312,10 +312,21 @@ def run_batch(args):
         samples.setdefault(A.shape[0], (A, Bs[f]))
     choice = autotune.tune(ctx, samples, tol=args.tol, precision=args.precision)
     autotune.save(choice, os.path.join(_scratch_dir(), "autotune_octree585.json"))
-    setting = [autotune.lookup(choice, A.shape[0]) for A in As]
-    groups = {}   # one batched build per rank cap
-    for f, (leaf, cap) in enumerate(setting):
-        groups.setdefault(cap, []).append(f)
+    # the per-size choices are timed on one front alone; the batch runs the
+    # fronts concurrently, one batched build per rank cap, so the batch step
+    # itself decides between them, the tuned leaves without caps (one group)
+    # and the fixed rule (leaf 128 from n = 1024 on, else 64; no cap)
+    candidates = {
+        "tuned": [autotune.lookup(choice, A.shape[0]) for A in As],
+        "tuned_leaves_uncapped": [(autotune.lookup(choice, A.shape[0])[0], 0) for A in As],
+        "fixed": [(128 if A.shape[0] >= 1024 else 64, 0) for A in As],
+    }
+
+    def grouped(setting):
+        groups = {}   # one batched build per rank cap
+        for f, (leaf, cap) in enumerate(setting):
+            groups.setdefault(cap, []).append(f)
+        return groups
 
     def step(marks=None):
         hs = [None] * len(As)
@@ -336,6 +347,25 @@ def run_batch(args):
             h.close()
         return res
 
+    batch_ms = {}
+    for name, cand in candidates.items():
+        setting, groups = cand, grouped(cand)
+        step()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        batch_ms[name] = min(ts)
+    chosen = min(batch_ms, key=batch_ms.get)
+    setting = candidates[chosen]
+    groups = grouped(setting)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -367,6 +397,7 @@ def run_batch(args):
                        "fronts": len(As), "tol": args.tol, "precision": args.precision, "gmres_tol": 1e-12,
                        "autotuned": {str(k): {"leaf": v["leaf"], "rank_cap": v["rank_cap"], "ms": v["ms"]}
                                      for k, v in choice.items()},
+                       "setting": chosen, "batch_ms_by_setting": batch_ms,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas x1"},
             "converged": bool(np.all(tr <= 1e-12)), "iters_max": int(its.max()), "iters_mean": float(its.mean()),
             "true_relres_max": float(tr.max()), "gpu_launches": l1 - l0,

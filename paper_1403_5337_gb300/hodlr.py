@@ -291,6 +291,7 @@ class Hodlr:
         self.handle = handle
         self.A = A          # the library keeps a pointer to A: keep it alive
         self._keep = keep
+        self.n = int(A.shape[0]) if A is not None else self.stats()["n"]
 
     def stats(self) -> dict:
         st = _Stats()
@@ -443,7 +444,7 @@ def hodlr_factor(h: Hodlr, stream=None) -> None:
 
 def hodlr_solve(h: Hodlr, X: torch.Tensor, stream=None) -> torch.Tensor:
     """X <- K~^-1 X in place (Sec. 4.3 Solve); X is (s, n) or (n,)."""
-    ptr, s, ld = _rhs(X, h.A.shape[0])
+    ptr, s, ld = _rhs(X, h.n)
     _check(_lib.hodlr_solve(h.handle, s, C.c_void_p(ptr), ld, _stream(stream)))
     return X
 
@@ -500,7 +501,7 @@ def gmres_solve(ctx: Context, A: torch.Tensor, B: torch.Tensor, P: Hodlr | None 
 
 
 def hodlr_build_batched(ctx: Context, As, leaves, tol: float, method: str = "aca", precision: str = "fp32",
-                        rank_cap: int = 0, symmetric: bool = True, stream=None):
+                        rank_cap: int = 0, symmetric: bool = True, stream=None, core_cond_threshold: float = 0.0):
     """Compress every front of a batch (list of (n_f, n_f) FP64 device tensors):
     one HODLR matrix per front, same tol and options (include/hodlr.h)."""
     lib = load_library()
@@ -510,6 +511,7 @@ def hodlr_build_batched(ctx: Context, As, leaves, tol: float, method: str = "aca
     o = _opts()
     o.precision = _PREC[precision]
     o.rank_cap = rank_cap
+    o.core_cond_threshold = float(core_cond_threshold)
     out = (C.c_void_p * max(nf, 1))()
     _check(lib.hodlr_build_batched(ctx.handle, nf, mats, lv, float(tol), _METHOD[method], C.byref(o),
                                    _stream(stream), out))
@@ -571,7 +573,7 @@ def hodlr_launch_count() -> int:
 
 def hodlr_precond_error(h: Hodlr, Omega: torch.Tensor, stream=None) -> float:
     """||(I - P^-1 A) Omega||_F / ||Omega||_F for a (k, n) probe block Omega."""
-    ptr, k, ld = _rhs(Omega, h.A.shape[0])
+    ptr, k, ld = _rhs(Omega, h.n)
     out = C.c_double()
     _check(_lib.hodlr_precond_error(h.handle, k, C.c_void_p(ptr), ld, C.byref(out), _stream(stream)))
     return out.value

@@ -321,6 +321,39 @@ def test_tensor_core_product_fp64_accurate(H, ctx, front576, n, s):
     assert np.median(err[nz] / absz[nz]) < 2.0 ** -48
 
 
+def test_tensor_core_product_digit_edges(H, ctx):
+    """Rows whose largest entry lies just below a power of two (the top digit
+    at its largest), rows of +-(2 - 2^-52), a row of one value, rows with
+    subnormal and zero entries, a row of tiny entries at the padded edge and a
+    row at 2^41: each entry of A Z within the digit-rounding bound of the
+    other test, and a zero row of A gives exact zeros."""
+    rng = np.random.default_rng(5)
+    n, s = 300, 17
+    A = rng.standard_normal((n, n))
+    A[0, :] = (2.0 - 2.0 ** -52) * np.sign(rng.standard_normal(n))
+    A[1, :] = rng.uniform(-1.0, 1.0, n)
+    A[1, 7] = 1.9990234375
+    A[1, 8] = -1.9990234375
+    A[2, :] = 1.9921875 * rng.uniform(-1.0, 1.0, n)
+    A[2, 3] = -1.9921875
+    A[3, :] = 0.75
+    A[4, :] = 5e-324 * rng.integers(-3, 4, n)    # subnormal: below the digits' reach
+    A[4, 0] = 1.0
+    A[5, :] = 0.0
+    A[6, :] = np.ldexp(rng.uniform(1.99, 2.0, n), 40) * np.sign(rng.standard_normal(n))
+    A[n - 1, :] = rng.standard_normal(n) * 1e-300
+    Z = rng.standard_normal((s, n))
+    W = H.hodlr_matvec(ctx, _dev(A), _dev(Z)).cpu().numpy()
+    ref = (A @ Z.T).T
+    scale = np.ldexp(1.0, (_row_exponents(Z)[:, None] + _row_exponents(A)[None, :]).astype(int))
+    absz = (np.abs(A) @ np.abs(Z.T)).T
+    err = np.abs(W - ref)
+    assert np.all(err <= 8 * n * 2.0 ** -56 * scale + n * 2.0 ** -50 * absz)
+    assert np.all(W[:, 5] == 0.0)
+    # the constant row: 0.75 sum_k Z(j, k) to FP64 accuracy
+    np.testing.assert_allclose(W[:, 3], 0.75 * Z.sum(axis=1), rtol=0, atol=1e-13 * np.abs(Z).sum(axis=1).max())
+
+
 def test_gmres_many_rhs_tensor_core_product(H, ctx, front576):
     """GMRES with 20 right-hand sides (products on the tensor cores) gives the
     same solutions as two solves of 10 (double-float products), each to a true
