@@ -727,11 +727,11 @@ def main():
     if "oz_tc_gemm_kernel" in prof:
         # the FP64-accurate product: 8 n^2 bytes of A per product (the
         # algorithm's), plus Z read and W written; the kernel itself streams
-        # 14 n_p k_p bytes of BF16 digit slices
+        # 7 n_p k_p bytes, A's exact digit bytes made once per solve
         t = prof["oz_tc_gemm_kernel"]["launch_ms"]
         kernels["oz_tc_gemm_kernel"] = {"launch_ms": t, "ms_per_step": t * n_mv,
                                         "bytes": 8.0 * n * n + 16.0 * n * nrhs,
-                                        "kernel_bytes": 14.0 * (-(-n // 128) * 128) * (-(-n // 32) * 32)}
+                                        "kernel_bytes": 7.0 * (-(-n // 128) * 128) * (-(-n // 32) * 32)}
     elif "df_matvec_kernel" in prof:
         t = prof["df_matvec_kernel"]["launch_ms"] * -(-nrhs // 4)   # one launch per 4 rhs
         kernels["df_matvec_kernel"] = {"launch_ms": t, "ms_per_step": t * n_mv, "bytes": 8.0 * n * n + 16.0 * n * nrhs}

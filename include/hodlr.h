@@ -269,9 +269,9 @@ hodlr_status gmres_solve_batched(hodlr_ctx *ctx, int nf, const hodlr_matrix *A, 
  * inside gmres_solve: for s < 16 or n < 256 the double-float product on the FP32
  * pipes (each entry split into FP32 pairs); otherwise every row of A and column
  * of Z is split exactly into seven base-256 digit slices relative to a power of
- * two of its own, the slice products run on the BF16 tensor cores, and the
+ * two of its own, the slice products run on the FP16 tensor cores, and the
  * error per term is a few units of 2^-56 max|A(i,:)| max|Z(:,j)| (that path
- * allocates about 14 n^2 bytes for A's slices per call, and falls back to the
+ * allocates about 7 n^2 bytes for A's digits (one byte each) per call, and falls back to the
  * double-float product when they cannot be allocated).  Synchronises `stream`:
  * a NaN, an infinity or an entry outside the representable range in A or Z
  * returns HODLR_NONFINITE_INPUT (W is then not meaningful). */

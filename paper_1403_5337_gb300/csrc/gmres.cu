@@ -15,7 +15,7 @@
 // as an unevaluated float pair with TwoSum.  The relative error per term is
 // about 2^-48, comparable to an FP64 dot product's accumulated rounding.
 // With 16 or more right-hand sides the product is a GEMM and takes the exact
-// digit-slice product on the BF16 tensor cores instead (ozaki.cu).
+// digit-slice product on the FP16 tensor cores instead (ozaki.cu).
 #include <algorithm>
 #include <cmath>
 #include <memory>

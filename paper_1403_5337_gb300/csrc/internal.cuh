@@ -300,7 +300,7 @@ hodlr_status matvec_impl(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, 
                          void *work = nullptr, bool w_zeroed = false, float2 *Asp = nullptr,
                          const int *split_state = nullptr, bool z_split = false, bool z_fp32 = false);
 
-// FP64-accurate product on the BF16 tensor cores for many right-hand sides
+// FP64-accurate product on the FP16 tensor cores for many right-hand sides
 // (ozaki.cu): A's rows and Z's columns split exactly into OZ_SLICES base-256
 // digit slices.  oz_split_a writes A's slices into abuf (oz_a_bytes(n) bytes,
 // once per A); oz_matvec splits Z into zbuf (oz_z_bytes(n, s) bytes) and

@@ -1,4 +1,4 @@
-// FP64-accurate W = A Z on the BF16 tensor cores (tcgen05), for many
+// FP64-accurate W = A Z on the FP16 tensor cores (tcgen05), for many
 // right-hand sides.
 //
 // GMRES (Sec. 3) needs the product with the FP64 front A to FP64 accuracy.
@@ -7,41 +7,55 @@
 // every FP64 entry is split exactly into balanced base-256 digits relative to a
 // power of two shared by its row of A (column of Z):
 //   a = 2^(e_i - 8) sum_p d_p 2^(-8p),  p = 0..6,  d_p integer, |d_p| <= 128,
-// e_i the least exponent with max_k |A(i,k)| < 2^(e_i - 1), the last digit
-// rounded to nearest (every digit is an exact BF16 number), so that
+// the last digit rounded to nearest, so that
 //   (A Z)(i,j) = 2^(e_i + f_j - 16) sum_t 2^(-8t) sum_{p+q=t} (A_p Z_q)(i,j).
 // The 28 slice products of the levels t = 0..6 (the pairs with t >= 7 lie
 // below 2^-56 of the leading level and are dropped) run on the tensor cores:
 // for slice p of A one MMA multiplies it with the Z slices 0..6-p stacked along
 // N, into the TMEM accumulators of the levels p..6 (level t at columns 32 t).
-// Over one chunk of 32 values of k a level's sum is an integer of magnitude at
-// most 32 (t + 1) 2^14 <= 7 * 2^19 < 2^22, so the FP32 accumulation is exact
-// whatever rounding the tensor core applies.  After every chunk the epilogue
-// warps read the 7 levels out of TMEM and add them, as integers, into two
-// 64-bit sums per (row, rhs): hi = sum over t <= 2 of A_t 2^(8(2-t)) and lo =
-// sum over t = 3..6 of A_t 2^(8(6-t)).  Integer sums are exact and
-// order-independent, so split-K partial sums combine with integer atomics and
-// the product is bitwise reproducible.  Finally
+// Every digit is an exact FP16 number, and over one chunk of 32 values of k a
+// level's sum is an integer of magnitude at most 32 (t + 1) 2^14 <= 7 * 2^19 <
+// 2^22, so the FP32 accumulation is exact whatever rounding the tensor core
+// applies.
+//
+// A's digits live in HBM as bytes (7 n^2 bytes, made once per A): byte p of
+// entry (i, k) is d_p + 128.  They are the two's-complement balanced digits of
+// the signed integer round(a 2^(56 - e_i)), which lies strictly inside
+// (-2^55 + B, 2^55 - B) for B = sum_{p<6} 128 * 256^p, so that the top digit
+// stays in [-128, 127] as well: e_i is the least exponent with that property
+// for the row's largest entry.  The GEMM kernel turns the bytes of a tile into
+// FP16 digits in shared memory (two byte permutes and two FP16x2 adds per four
+// digits) for the MMAs.  Z's digits (sign and magnitude, the top digit in
+// [0, 128]) are written as FP16 slices per product.
+//
+// The GEMM kernel is persistent: one CTA per SM walks a contiguous range of
+// (row tile, rhs tile, chunk of 32 k) units, the split of the work over SMs
+// balanced to one unit.  Both operands are stored unit by unit (one unit of A
+// is 28 KB of bytes, one of Z 14 KB of FP16 already in the shared-memory
+// operand's 64-byte-swizzled order), so each arrives by one bulk copy.  Warp 0
+// streams A's units (3 stages); warps 2-3 convert them into the FP16 slices of
+// one of 2 MMA stages and fetch Z's unit into it; warp 1 allocates TMEM
+// (two accumulator sets of 224 columns) and issues the MMAs (M = 128, N =
+// 32 (7 - p), K = 16, two k-steps per chunk); warps 4-11 drain the accumulators
+// after every chunk (warp w reads the TMEM lanes of quarter w mod 4, i.e. 32
+// rows, and 16 of the 32 right-hand sides), adding each level's integer into a
+// 32-bit sum (exact for 512 chunks), and at the end of a tile's run of units
+// (or after 512 chunks) add, as 64-bit integers,
+//   hi = sum_{t <= 2} x_t 2^(8(2-t)),  lo = sum_{t = 3..6} x_t 2^(8(6-t))
+// into the tile's partial sums with atomics.  Integer sums are exact and
+// order-independent, so the product is bitwise reproducible.  Finally
 //   W(i,j) = 2^(e_i + f_j - 32) hi + 2^(e_i + f_j - 64) lo   (FP64).
-// The error per term is at most about 2^-56 max|A(i,:)| max|Z(:,j)| (digit
+// The error per term is at most about 2^-55 max|A(i,:)| max|Z(:,j)| (digit
 // rounding) plus the final FP64 rounding.
 //
-// The GEMM kernel is warp-specialised: warp 0 streams 3 shared-memory stages
-// of (7 slices of 128 rows of A, 7 slices of 32 columns of Z) x 32 values of k
-// with TMA (64-byte swizzle); warp 1 allocates TMEM (two accumulator sets of
-// 224 columns) and issues the MMAs (M = 128, N = 32 (7 - p), K = 16, two
-// k-steps per chunk); warps 2..9 drain the accumulators (warp w reads the TMEM
-// lanes of quarter w mod 4, i.e. 32 rows, and 16 of the 32 right-hand sides).
 // Every wait on an mbarrier is bounded (about 2 s of global time): on timeout
 // the status word gets ST_TIMEOUT, every role leaves its loop, the copies and
 // MMAs already issued are waited for (bounded too), TMEM is freed and the
 // kernel returns.
-#include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdint>
-#include <mutex>
 
 #include "internal.cuh"
 
@@ -49,26 +63,37 @@ namespace hodlr {
 namespace {
 
 constexpr int S = OZ_SLICES;        // 7 digit slices
-constexpr int TC_BM = 128;          // rows of A per CTA (the MMA's M)
-constexpr int TC_BN = 32;           // right-hand sides per CTA
-constexpr int TC_BK = 32;           // k per chunk: one shared-memory stage, one exact flush
-constexpr int TC_STAGES = 3;
-constexpr int TC_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int TC_BM = 128;          // rows of A per unit (the MMA's M)
+constexpr int TC_BN = 32;           // right-hand sides per unit
+constexpr int TC_BK = 32;           // k per unit: one exact flush of TMEM
+constexpr int TC_TSTAGES = 3;       // stages of A's bytes
+constexpr int TC_MSTAGES = 2;       // MMA stages (FP16 slices of A and Z)
+constexpr int TC_THREADS = 384;     // warp 0 loads, 1 MMA, 2-3 convert, 4-11 drain
+constexpr int TC_CONV_WARPS = 2;
+constexpr int TC_EPI_WARP0 = 4;
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_ACC_COLS = S * TC_BN;          // 224 TMEM columns per accumulator set
 constexpr int TC_TMEM_COLS = 512;
-constexpr uint32_t TC_A_BYTES = S * TC_BM * TC_BK * 2;   // 57344
-constexpr uint32_t TC_Z_BYTES = S * TC_BN * TC_BK * 2;   // 14336
-constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_Z_BYTES;
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
-static_assert(TC_SMEM <= 227 * 1024, "three stages must fit in shared memory");
-static_assert(TC_A_BYTES % 1024 == 0 && TC_Z_BYTES % 1024 == 0, "stages keep the swizzle alignment");
+constexpr uint32_t TC_AB_BYTES = S * TC_BM * TC_BK;           // 28672: A's bytes of a unit
+constexpr uint32_t TC_AH_BYTES = S * TC_BM * TC_BK * 2;       // 57344: A's FP16 slices
+constexpr uint32_t TC_Z_BYTES = S * TC_BN * TC_BK * 2;        // 14336: Z's FP16 slices
+constexpr uint32_t TC_MSTAGE_BYTES = TC_AH_BYTES + TC_Z_BYTES;
+constexpr size_t TC_SMEM = (size_t)TC_MSTAGES * TC_MSTAGE_BYTES + (size_t)TC_TSTAGES * TC_AB_BYTES +
+                           1024 /* alignment */ + 256 /* barriers */;
+static_assert(TC_SMEM <= 227 * 1024, "the stages must fit in shared memory");
+static_assert(TC_AB_BYTES % 1024 == 0 && TC_AH_BYTES % 1024 == 0 && TC_Z_BYTES % 1024 == 0,
+              "stages keep the swizzle alignment");
 // the exact-flush bound: 32 values of k, 7 pairs, |digit products| <= 2^14
 static_assert((long long)TC_BK * S * (1 << 14) < (1 << 22), "level sums of a chunk must stay below 2^22");
+// 32-bit level sums over TC_FLUSH chunks stay below 2^31 in magnitude
+constexpr int TC_FLUSH = 512;
+static_assert((long long)TC_FLUSH * TC_BK * S * (1 << 14) < (1ll << 31), "32-bit level sums must not overflow");
 
 constexpr float MAGIC = 12582912.0f;            // 1.5 * 2^23: x + MAGIC has the bits 0x4B400000 + x
 constexpr uint32_t MAGIC_BITS = 0x4B400000u;
 constexpr unsigned long long GT_LIMIT_NS = 2000000000ull;   // bound of every wait
+// the six lower digits' bias: sum_{p<6} 128 * 256^p
+constexpr unsigned long long DIGIT_BIAS = 0x808080808080ull;
 
 inline int64_t oz_np(int64_t n) { return (n + TC_BM - 1) / TC_BM * TC_BM; }
 inline int64_t oz_kp(int64_t n) { return (n + TC_BK - 1) / TC_BK * TC_BK; }
@@ -80,23 +105,27 @@ __device__ __forceinline__ int exp_field(double a) {
     return (int)((unsigned long long)__double_as_longlong(a) >> 52) & 0x7FF;
 }
 
-// The balanced digits of a relative to 2^e (|a| < 2^(e-1); a not finite or
+// round(|a| 2^(56 - e)) (ties away from zero) for an entry a of the row or
+// column whose exponent is e, so that sh = 1019 + e - ex >= -2; zero for a
+// zero, subnormal or non-finite a.
+__device__ __forceinline__ unsigned long long scaled_magnitude(unsigned long long u, int e) {
+    const int ex = (int)(u >> 52) & 0x7FF;
+    if (ex == 0 || ex == 0x7FF) return 0ull;
+    const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 1019 + e - ex;
+    if (sh <= 0) return mant << (-sh);
+    if (sh < 56) return (mant + (1ull << (sh - 1))) >> sh;
+    return 0ull;
+}
+
+// Z's balanced digits relative to 2^e (|a| < 2^(e-1); a not finite or
 // subnormal: all zero): F = round(|a| 2^(56 - e)) <= 2^55 written in base 256
 // with the six lower digits in [-128, 128) (a digit of 128 or more becomes
 // d - 256 with a carry into the next one) and the top digit, F's bits from 48
 // on plus that carry, in [0, 128]; the sign of a on every digit.
-__device__ __forceinline__ void balanced_digits(double a, int e, __nv_bfloat16 (&out)[S]) {
+__device__ __forceinline__ void balanced_digits(double a, int e, __half (&out)[S]) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(a);
-    const int ex = (int)(u >> 52) & 0x7FF;
-    unsigned long long F = 0;
-    if (ex != 0 && ex != 0x7FF) {
-        const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = 1019 + e - ex;   // F = mant 2^(-sh); sh >= -2 as |a| < 2^(e-1)
-        if (sh <= 0)
-            F = mant << (-sh);
-        else if (sh < 56)
-            F = (mant + (1ull << (sh - 1))) >> sh;
-    }
+    unsigned long long F = scaled_magnitude(u, e);
     const bool neg = (u >> 63) != 0;
 #pragma unroll
     for (int p = S - 1; p >= 0; --p) {
@@ -106,47 +135,98 @@ __device__ __forceinline__ void balanced_digits(double a, int e, __nv_bfloat16 (
             d -= 256;
             F += 1;
         }
-        out[p] = __float2bfloat16_rn((float)(neg ? -d : d));
+        out[p] = __int2half_rn(neg ? -d : d);
     }
 }
 
-// One warp per row of the padded np x kp slices: the row's exponent, then its
-// digits (zero outside the n x n matrix).  Slices: [S][np][kp] BF16.
+// A's digit bytes of one entry relative to 2^e, packed: byte 6 - p of the
+// result is d_p + 128.  G = round(a 2^(56-e)) + DIGIT_BIAS (two's complement)
+// holds d_p + 128 in its bytes 0..5 (p = 6..1) and the top digit d_0 in its
+// bits 48..63, which e keeps in [-128, 127].
+__device__ __forceinline__ unsigned long long digit_bytes(double a, int e) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+    unsigned long long F = scaled_magnitude(u, e);
+    if (u >> 63) F = 0ull - F;
+    const unsigned long long G = F + DIGIT_BIAS;
+    return (G & 0xFFFFFFFFFFFFull) | ((((G >> 48) & 0xFFull) ^ 0x80ull) << 48);
+}
+
+// The row exponent of A: the least e with |a| < 2^(e-1) for the row's largest
+// entry M whose scaled value also leaves the top digit below 128:
+// round(M 2^(56-e)) + DIGIT_BIAS < 2^55.  M = 0 gives e = -1021 (all digits 0).
+__device__ __forceinline__ int row_exponent(unsigned long long mbits) {
+    const int ex = (int)(mbits >> 52) & 0x7FF;
+    if (ex == 0) return -1021;
+    int e = ex - 1021;
+    const unsigned long long top = (((mbits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2);   // round(M 2^(56-e))
+    if (top + DIGIT_BIAS >= (1ull << 55)) e += 1;
+    return e;
+}
+
+// One warp per 4 rows of the padded np x kp matrix (8 lanes per row): each
+// row's exponent from its largest magnitude, then its digit bytes (zero outside
+// the n x n matrix), in units of 128 rows x 32 k: unit (row tile, chunk) is one
+// block of 7 x 128 x 32 bytes ([slice][row][k]) at (row tile * chunks + chunk)
+// * 28672, so that the GEMM fetches a unit with one bulk copy.  A lane takes 4
+// consecutive k of its row, so the warp writes 128 contiguous bytes of every
+// slice of a unit per chunk.
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(const double *__restrict__ A, int64_t n, int64_t lda,
-                                                            int64_t np, int64_t kp, __nv_bfloat16 *__restrict__ sl,
+                                                            int64_t np, int64_t kp, uint8_t *__restrict__ sl,
                                                             int *__restrict__ ea, int *status) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-    if (i >= np) return;
+    const int64_t i = ((int64_t)blockIdx.x * 8 + warp) * 4 + (lane >> 3);
+    const int sub = lane & 7;
+    if (i >= np) return;   // the grid covers np rows exactly: whole warps only
     const double *row = A + i * lda;
-    int mx = 0, bad = 0;
+    unsigned long long mx = 0ull;
+    int bad = 0;
     if (i < n)
-        for (int64_t k = lane; k < n; k += 32) {
-            const int ex = exp_field(row[k]);
-            if (ex == 0x7FF)
+        for (int64_t k = sub; k < n; k += 8) {
+            const unsigned long long u = (unsigned long long)__double_as_longlong(row[k]) & 0x7FFFFFFFFFFFFFFFull;
+            if ((u >> 52) == 0x7FF)
                 bad = 1;
             else
-                mx = max(mx, ex);
+                mx = u > mx ? u : mx;
         }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    bad = __any_sync(0xffffffffu, bad);
-    const int e = mx - 1021;
-    if (lane == 0) {
+    for (int o = 4; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    const int e = row_exponent(mx);
+    if (sub == 0) {
         ea[i] = e;
         if (bad) atomicOr(status, ST_NONFINITE);
     }
-    for (int64_t k = lane; k < kp; k += 32) {
-        __nv_bfloat16 d[S];
-        balanced_digits((i < n && k < n) ? row[k] : 0.0, e, d);
+    const int64_t nchunks = kp / TC_BK;
+    uint8_t *u0 = sl + (i >> 7) * nchunks * (int64_t)TC_AB_BYTES + (i & 127) * TC_BK + sub * 4;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int64_t k0 = c * TC_BK + sub * 4;
+        uint32_t w[S];
 #pragma unroll
-        for (int p = 0; p < S; ++p) sl[((int64_t)p * np + i) * kp + k] = d[p];
+        for (int p = 0; p < S; ++p) w[p] = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t k = k0 + q;
+            const unsigned long long g = digit_bytes((i < n && k < n) ? row[k] : 0.0, e);
+#pragma unroll
+            for (int p = 0; p < S; ++p) w[p] |= (uint32_t)((g >> (8 * (S - 1 - p))) & 0xFFu) << (8 * q);
+        }
+        uint8_t *u = u0 + c * TC_AB_BYTES;
+#pragma unroll
+        for (int p = 0; p < S; ++p) *reinterpret_cast<uint32_t *>(u + p * (TC_BM * TC_BK)) = w[p];
     }
 }
 
-// One CTA per column of the padded Z slices: [S][sp][kp] BF16.
+// One CTA per column of the padded Z: FP16 digit slices in units of 32
+// columns x 32 k, unit (rhs tile, chunk) one block of 7 x 32 x 32 halves
+// ([slice][column][k]) at (rhs tile * chunks + chunk) * 14336 bytes, each
+// 64-byte row already in the 64-byte-swizzled order of the shared-memory
+// operand (16-byte piece c of row r at piece c ^ ((r / 2) mod 4)), so that a
+// bulk copy of the unit is the MMA's B operand.
 __global__ void __launch_bounds__(256) oz_split_cols_kernel(const double *__restrict__ Z, int64_t ldz, int64_t n,
-                                                            int s, int64_t kp, int sp, __nv_bfloat16 *__restrict__ zs,
+                                                            int s, int64_t kp, int sp, __half *__restrict__ zs,
                                                             int *__restrict__ ez, int *status) {
     __shared__ int s_max, s_bad;
     const int j = blockIdx.x;
@@ -179,10 +259,13 @@ __global__ void __launch_bounds__(256) oz_split_cols_kernel(const double *__rest
         if (s_bad) atomicOr(status, ST_NONFINITE);
     }
     for (int64_t k = threadIdx.x; k < kp; k += blockDim.x) {
-        __nv_bfloat16 d[S];
+        __half d[S];
         balanced_digits((j < s && k < n) ? col[k] : 0.0, e, d);
+        const int jr = j & 31, kk = (int)(k & 31);
+        __half *u = zs + ((int64_t)(j >> 5) * (kp / TC_BK) + (k >> 5)) * (TC_Z_BYTES / 2) + jr * TC_BK +
+                    (((kk >> 3) ^ ((jr >> 1) & 3)) << 3) + (kk & 7);
 #pragma unroll
-        for (int p = 0; p < S; ++p) zs[((int64_t)p * sp + j) * kp + k] = d[p];
+        for (int p = 0; p < S; ++p) u[p * (TC_BN * TC_BK)] = d[p];
     }
 }
 
@@ -244,13 +327,12 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, int *s
     }
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-        : "memory");
+// One contiguous block of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 // Shared-memory matrix descriptor of a K-major tile with 64-byte swizzle: rows
@@ -264,12 +346,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor of kind::f16: BF16 A and B (both K-major), FP32 D, M x N.
+// Instruction descriptor of kind::f16: FP16 A and B (both K-major; format
+// code 0 in bits 7-9 and 10-12), FP32 D (bit 4), M x N.
 __device__ __forceinline__ uint32_t mma_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+// Shared-memory writes of this thread made visible to the async proxy (the
+// tensor core's operand reads).
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             dtmem),
@@ -285,63 +372,124 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// Issue a load of 16 columns without waiting for it (tmem_wait() completes it).
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+
+// Wait for this thread's TMEM loads; the registers they wrote pass through an
+// empty asm so that no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&a)[16], uint32_t (&b)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+    for (int c = 0; c < 16; ++c) asm volatile("" : "+r"(a[c]), "+r"(b[c]));
+}
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(x), "r"(y), "r"(z), "r"(w));
+}
+
+// Four digit bytes u (one word) as two FP16x2 words of d = u - 128: a byte
+// permute puts each u under the FP16 exponent of 1024 (0x64uu = 1024 + u,
+// exact), and one FP16x2 add of -1152 (0xE480) leaves u - 128, exact.
+__device__ __forceinline__ void bytes_to_half2(uint32_t w, uint32_t &lo, uint32_t &hi) {
+    constexpr uint32_t E1024 = 0x64646464u, BIAS = 0xE480E480u;
+    lo = hadd2(prmt(w, E1024, 0x4140u), BIAS);
+    hi = hadd2(prmt(w, E1024, 0x4342u), BIAS);
 }
 
 // ------------------------------------------------------------------ the GEMM
 struct TcArgs {
-    const int *ea, *ez;
     int64_t n;
     int s;
-    int nchunks;          // kp / 32
-    int chunks_per_cta;   // along the split of k (blockIdx.z)
+    int nchunks;                     // kp / 32
+    int ntn;                         // tiles of 32 right-hand sides
+    long long units;                 // row tiles x rhs tiles x chunks
     unsigned long long *Phi, *Plo;   // [sp][np] integer partial sums
     int64_t np;
     int *status;
 };
 
+// A position in the unit sequence, advanced one unit at a time (no divisions
+// in the roles' loops): units run over the chunks of a tile, then the next
+// tile; tile = row tile * ntn + rhs tile.
+struct Cursor {
+    int tile, chunk;
+    __device__ __forceinline__ void next(int nchunks) {
+        if (++chunk == nchunks) {
+            chunk = 0;
+            ++tile;
+        }
+    }
+};
+
+__device__ __forceinline__ Cursor cursor_at(const TcArgs &a, long long u) {
+    const long long tile = u / a.nchunks;
+    return Cursor{(int)tile, (int)(u - tile * a.nchunks)};
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    oz_tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapZ,
-                      const TcArgs a) {
+    oz_tc_gemm_kernel(const uint8_t *__restrict__ Ab, const __half *__restrict__ Zb, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    // 1024-byte aligned stage area (the swizzled tiles' phase depends on the address)
+    // 1024-byte aligned stage area (the swizzled tiles' phase depends on the address):
+    // [MMA stage 0][MMA stage 1][byte stage 0..2][barriers]
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + TC_STAGES * TC_STAGE_BYTES);
-    // bars: full[3], empty[3], acc_full[2], acc_empty[2], drain
+    unsigned char *tsm = smem + TC_MSTAGES * TC_MSTAGE_BYTES;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(tsm + TC_TSTAGES * TC_AB_BYTES);
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TC_BM, j0 = blockIdx.y * TC_BN;
-    const int c_begin = blockIdx.z * a.chunks_per_cta;
-    const int c_end = min(a.nchunks, c_begin + a.chunks_per_cta);
-    const int nch = max(0, c_end - c_begin);
-    const uint32_t sbase = smem_u32(smem);
+    // this CTA's units: [u0, u0 + nu), the split balanced to one unit
+    const long long u0 = a.units * blockIdx.x / gridDim.x;
+    const int nu = (int)(a.units * (blockIdx.x + 1) / gridDim.x - u0);
+    const uint32_t mbase = smem_u32(smem);
+    const uint32_t tbase = smem_u32(tsm);
     const uint32_t bar0 = smem_u32(bars);
-    auto full = [&](int st) { return bar0 + 8u * st; };
-    auto empty = [&](int st) { return bar0 + 8u * (TC_STAGES + st); };
-    auto accf = [&](int b) { return bar0 + 8u * (2 * TC_STAGES + b); };
-    auto acce = [&](int b) { return bar0 + 8u * (2 * TC_STAGES + 2 + b); };
-    const uint32_t drain = bar0 + 8u * (2 * TC_STAGES + 4);
+    auto tfull = [&](int st) { return bar0 + 8u * st; };
+    auto tempty = [&](int st) { return bar0 + 8u * (3 + st); };
+    auto cfull = [&](int ms) { return bar0 + 8u * (6 + ms); };
+    auto zfull = [&](int ms) { return bar0 + 8u * (8 + ms); };
+    auto mempty = [&](int ms) { return bar0 + 8u * (10 + ms); };
+    auto accf = [&](int b) { return bar0 + 8u * (12 + b); };
+    auto acce = [&](int b) { return bar0 + 8u * (14 + b); };
+    const uint32_t drain = bar0 + 8u * 16;
+    static_assert(TC_TSTAGES == 3 && TC_MSTAGES == 2, "barrier layout");
 
     if (threadIdx.x == 0) {
-        for (int st = 0; st < TC_STAGES; ++st) {
-            mbar_init(full(st), 1);
-            mbar_init(empty(st), 1);
+        for (int st = 0; st < TC_TSTAGES; ++st) {
+            mbar_init(tfull(st), 1);
+            mbar_init(tempty(st), TC_CONV_WARPS);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(accf(b), 1);
-            mbar_init(acce(b), TC_EPI_WARPS);
+        for (int ms = 0; ms < TC_MSTAGES; ++ms) {
+            mbar_init(cfull(ms), TC_CONV_WARPS);
+            mbar_init(zfull(ms), 1);
+            mbar_init(mempty(ms), 1);
+            mbar_init(accf(ms), 1);
+            mbar_init(acce(ms), TC_EPI_WARPS);
         }
         mbar_init(drain, 1);
         s_abort = 0;
@@ -360,108 +508,206 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     volatile int *abort = &s_abort;
 
     if (warp == 0) {
-        // ---------------- TMA producer
-        if (lane == 0 && nch > 0) {
+        // ---------------- producer of A's digit bytes (bulk copies)
+        if (lane == 0 && nu > 0) {
             int issued = 0;
-            for (int c = 0; c < nch; ++c) {
-                const int st = c % TC_STAGES;
-                const uint32_t ph = (uint32_t)((c / TC_STAGES) & 1);
-                if (!mbar_wait(empty(st), ph ^ 1u, abort, a.status)) break;
-                const uint32_t sa = sbase + st * TC_STAGE_BYTES;
-                mbar_expect_tx(full(st), TC_STAGE_BYTES);
-                const int k0 = (c_begin + c) * TC_BK;
-                tma_load_3d(sa, &mapA, k0, m0, 0, full(st));
-                tma_load_3d(sa + TC_A_BYTES, &mapZ, k0, j0, 0, full(st));
+            Cursor cu = cursor_at(a, u0);
+            for (int i = 0; i < nu; ++i, cu.next(a.nchunks)) {
+                const int st = i % TC_TSTAGES;
+                const uint32_t ph = (uint32_t)((i / TC_TSTAGES) & 1);
+                if (!mbar_wait(tempty(st), ph ^ 1u, abort, a.status)) break;
+                const long long ua = (long long)(cu.tile / a.ntn) * a.nchunks + cu.chunk;
+                mbar_expect_tx(tfull(st), TC_AB_BYTES);
+                bulk_load(tbase + st * TC_AB_BYTES, Ab + ua * TC_AB_BYTES, TC_AB_BYTES, tfull(st));
                 ++issued;
             }
             // copies still in flight when the pipeline stopped early: wait for
             // them (bounded) before the CTA may leave
             if (*abort)
-                for (int c = max(0, issued - TC_STAGES); c < issued; ++c)
-                    mbar_drain(full(c % TC_STAGES), (uint32_t)((c / TC_STAGES) & 1), a.status);
+                for (int i = max(0, issued - TC_TSTAGES); i < issued; ++i)
+                    mbar_drain(tfull(i % TC_TSTAGES), (uint32_t)((i / TC_TSTAGES) & 1), a.status);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
-        if (lane == 0 && nch > 0) {
-            for (int c = 0; c < nch; ++c) {
-                const int st = c % TC_STAGES;
-                const uint32_t ph = (uint32_t)((c / TC_STAGES) & 1);
-                const int b = c & 1;
-                const uint32_t aph = (uint32_t)((c >> 1) & 1);
-                if (!mbar_wait(full(st), ph, abort, a.status)) break;
-                if (!mbar_wait(acce(b), aph ^ 1u, abort, a.status)) break;
+        if (lane == 0 && nu > 0) {
+            for (int i = 0; i < nu; ++i) {
+                const int ms = i & 1;
+                const uint32_t ph = (uint32_t)((i >> 1) & 1);
+                if (!mbar_wait(cfull(ms), ph, abort, a.status)) break;
+                if (!mbar_wait(zfull(ms), ph, abort, a.status)) break;
+                if (!mbar_wait(acce(ms), ph ^ 1u, abort, a.status)) break;
                 tc_fence_after();
-                const uint32_t sa = sbase + st * TC_STAGE_BYTES;
-                const uint32_t sz = sa + TC_A_BYTES;
-                const uint32_t dcol = tmem + (uint32_t)(b * TC_ACC_COLS);
+                const uint32_t sa = mbase + ms * TC_MSTAGE_BYTES;
+                const uint32_t sz = sa + TC_AH_BYTES;
+                const uint32_t dcol = tmem + (uint32_t)(ms * TC_ACC_COLS);
 #pragma unroll
                 for (int ks = 0; ks < TC_BK / 16; ++ks) {
 #pragma unroll
                     for (int p = 0; p < S; ++p) {
                         const uint64_t ad = smem_desc(sa + p * (TC_BM * TC_BK * 2) + ks * 32);
                         const uint64_t bd = smem_desc(sz + ks * 32);
-                        mma_bf16(dcol + 32u * p, ad, bd, mma_idesc(TC_BM, TC_BN * (S - p)),
-                                 (ks == 0 && p == 0) ? 0u : 1u);
+                        mma_f16(dcol + 32u * p, ad, bd, mma_idesc(TC_BM, TC_BN * (S - p)),
+                                (ks == 0 && p == 0) ? 0u : 1u);
                     }
                 }
-                mma_commit(empty(st));   // the stage is free once these MMAs have read it
-                mma_commit(accf(b));     // the accumulators are complete
+                mma_commit(mempty(ms));   // the stage is free once these MMAs have read it
+                mma_commit(accf(ms));     // the accumulators are complete
             }
             // every MMA issued is complete before TMEM is released
             mma_commit(drain);
             mbar_drain(drain, 0, a.status);
         }
-    } else {
-        // ---------------- epilogue: warp w drains TMEM lanes 32 (w mod 4).., rhs 16 h..
-        const int q = warp & 3, h = (warp - 2) >> 2;
-        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        unsigned long long hi[16], lo[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0ull;
-        int done = 0;
-        for (int c = 0; c < nch; ++c) {
-            const int b = c & 1;
-            const uint32_t aph = (uint32_t)((c >> 1) & 1);
-            // one lane waits, the warp follows it (tcgen05.ld needs the whole warp)
-            int ok = 0;
-            if (lane == 0) ok = mbar_wait(accf(b), aph, abort, a.status) ? 1 : 0;
+    } else if (warp < TC_EPI_WARP0) {
+        // ---------------- converters: warp wc turns rows 64 wc.. of every slice
+        // of A's byte unit into FP16 digits in the MMA stage; warp 2 also fetches
+        // Z's unit into that stage
+        const int wc = warp - 2;
+        int zissued = 0;
+        Cursor cu = cursor_at(a, u0);
+        // 7 slices x 64 rows x 2 halves of 16 values of k: 28 pieces per lane;
+        // lane l takes row 64 wc + 16 jj + l / 2, half l mod 2, of every slice p
+        // and jj = 0..3, so that its offsets are constants plus a lane term, and
+        // row r's 64-byte swizzle (r / 2) mod 4 = (l / 4) mod 4 is the lane's own
+        const uint32_t src_lane = (uint32_t)((wc * 64 + (lane >> 1)) * TC_BK + (lane & 1) * 16);
+        const uint32_t dst_lane = (uint32_t)((wc * 64 + (lane >> 1)) * (TC_BK * 2));
+        const int sw = (lane >> 2) & 3, hh = lane & 1;
+        const uint32_t c0 = (uint32_t)(((2 * hh) ^ sw) << 4), c1 = (uint32_t)(((2 * hh + 1) ^ sw) << 4);
+        constexpr int NP = S * 4, G = NP / 2;   // pieces, and pieces loaded before any is converted
+        for (int i = 0; i < nu; ++i, cu.next(a.nchunks)) {
+            const int st = i % TC_TSTAGES;
+            const uint32_t ph = (uint32_t)((i / TC_TSTAGES) & 1);
+            const int ms = i & 1;
+            const uint32_t mph = (uint32_t)((i >> 1) & 1);
+            int ok = 1;
+            if (lane == 0)
+                ok = (mbar_wait(tfull(st), ph, abort, a.status) && mbar_wait(mempty(ms), mph ^ 1u, abort, a.status))
+                         ? 1
+                         : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
-            tc_fence_after();
-            const uint32_t t0 = tmem + lane_base + (uint32_t)(b * TC_ACC_COLS + 16 * h);
-            float v[16];
-            // levels 0..2 into hi (units of level 2), 3..6 into lo (units of level 6)
+            // every lane acquires both completed phases itself (neither can move
+            // on before this warp arrives below)
+            mbar_try(tfull(st), ph);
+            mbar_try(mempty(ms), mph ^ 1u);
+            const uint32_t sa = mbase + ms * TC_MSTAGE_BYTES;
+            if (wc == 0 && lane == 0) {
+                const long long uz = (long long)(cu.tile % a.ntn) * a.nchunks + cu.chunk;
+                mbar_expect_tx(zfull(ms), TC_Z_BYTES);
+                bulk_load(sa + TC_AH_BYTES, Zb + uz * (TC_Z_BYTES / 2), TC_Z_BYTES, zfull(ms));
+                ++zissued;
+            }
+            const uint32_t src = tbase + st * TC_AB_BYTES + src_lane;
+            const uint32_t dst = sa + dst_lane;
+            // half of the pieces' loads in flight before their conversion (one
+            // load at a time stalled each warp on shared-memory latency)
 #pragma unroll
-            for (int t = 0; t < S; ++t) {
-                tmem_ld16(t0 + 32u * t, v);
-                const unsigned long long m = (t <= 2) ? (1ull << (8 * (2 - t))) : (1ull << (8 * (6 - t)));
+            for (int g0 = 0; g0 < NP; g0 += G) {
+                uint4 b[G];
 #pragma unroll
-                for (int col = 0; col < 16; ++col) {
-                    const unsigned long long bits = __float_as_uint(v[col] + MAGIC);
-                    if (t <= 2)
-                        hi[col] += bits * m;
-                    else
-                        lo[col] += bits * m;
+                for (int t = 0; t < G; ++t)
+                    b[t] = ld_shared_v4(src + ((g0 + t) >> 2) * (TC_BM * TC_BK) + ((g0 + t) & 3) * 16 * TC_BK);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int p = (g0 + t) >> 2, jj = (g0 + t) & 3;
+                    uint32_t o[8];
+                    bytes_to_half2(b[t].x, o[0], o[1]);
+                    bytes_to_half2(b[t].y, o[2], o[3]);
+                    bytes_to_half2(b[t].z, o[4], o[5]);
+                    bytes_to_half2(b[t].w, o[6], o[7]);
+                    const uint32_t row = dst + (uint32_t)(p * (TC_BM * TC_BK * 2) + jj * 16 * (TC_BK * 2));
+                    st_shared_v4(row + c0, o[0], o[1], o[2], o[3]);
+                    st_shared_v4(row + c1, o[4], o[5], o[6], o[7]);
                 }
             }
-            tc_fence_before();
+            fence_proxy_async();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acce(b));
-            ++done;
+            if (lane == 0) {
+                mbar_arrive(cfull(ms));
+                mbar_arrive(tempty(st));
+            }
         }
-        // remove the conversion's bias (modular arithmetic: exact whenever the
-        // true sums fit in 64 bits, which they do)
-        const unsigned long long bh = (unsigned long long)done * MAGIC_BITS * (65536ull + 256ull + 1ull);
-        const unsigned long long bl =
-            (unsigned long long)done * MAGIC_BITS * ((1ull << 24) + (1ull << 16) + (1ull << 8) + 1ull);
-        const int64_t row = m0 + 32 * q + lane;
-        if (!*abort && done > 0 && row < a.n) {
+        if (*abort && wc == 0 && lane == 0)
+            for (int i = max(0, zissued - TC_MSTAGES); i < zissued; ++i)
+                mbar_drain(zfull(i & 1), (uint32_t)((i >> 1) & 1), a.status);
+    } else {
+        // ---------------- epilogue: warp w drains TMEM lanes 32 (w mod 4).., rhs 16 h..
+        const int q = warp & 3, h = (warp - TC_EPI_WARP0) >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        Cursor cu = cursor_at(a, u0);
+        int i = 0;
+        bool ok = true;
+        while (ok && i < nu) {
+            // one run of units of the same tile (at most TC_FLUSH of them)
+            const int tile = cu.tile;
+            uint32_t acc[S][16];
 #pragma unroll
-            for (int col = 0; col < 16; ++col) {
-                const int j = j0 + 16 * h + col;
-                if (j < a.s) {
-                    atomicAdd(a.Phi + (int64_t)j * a.np + row, hi[col] - bh);
-                    atomicAdd(a.Plo + (int64_t)j * a.np + row, lo[col] - bl);
+            for (int t = 0; t < S; ++t)
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[t][c] = 0u;
+            int cnt = 0;
+            do {
+                const int b = i & 1;
+                const uint32_t aph = (uint32_t)((i >> 1) & 1);
+                // one lane waits, the warp follows it (tcgen05.ld needs the whole warp)
+                int w = 0;
+                if (lane == 0) w = mbar_wait(accf(b), aph, abort, a.status) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t t0 = tmem + lane_base + (uint32_t)(b * TC_ACC_COLS + 16 * h);
+                // two levels' loads in flight per wait
+#pragma unroll
+                for (int t = 0; t < S; t += 2) {
+                    uint32_t va[16], vb[16];
+                    tmem_ld16_issue(t0 + 32u * t, va);
+                    if (t + 1 < S)
+                        tmem_ld16_issue(t0 + 32u * (t + 1), vb);
+                    else
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) vb[c] = 0u;
+                    tmem_wait(va, vb);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) acc[t][c] += __float_as_uint(__uint_as_float(va[c]) + MAGIC);
+                    if (t + 1 < S) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            acc[t + 1][c] += __float_as_uint(__uint_as_float(vb[c]) + MAGIC);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce(b));
+                ++cnt;
+                ++i;
+                cu.next(a.nchunks);
+            } while (i < nu && cu.tile == tile && cnt < TC_FLUSH);
+            if (!ok || *abort) break;
+            // remove the conversion's bias (modular: exact while the true sums
+            // stay below 2^31 in magnitude) and add the levels as 64-bit
+            // integers into the tile's partial sums
+            const uint32_t bias = (uint32_t)cnt * MAGIC_BITS;
+            const int tm = tile / a.ntn, tn = tile - tm * a.ntn;
+            const int64_t row = (int64_t)tm * TC_BM + 32 * q + lane;
+            if (row < a.n) {
+                const int j0 = tn * TC_BN + 16 * h;
+                const int ncol = a.s - j0;   // columns of this lane's 16 that exist
+                unsigned long long *ph = a.Phi + (int64_t)j0 * a.np + row;
+                unsigned long long *pl = a.Plo + (int64_t)j0 * a.np + row;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if (c < ncol) {
+                        const long long hi = (long long)(int)(acc[0][c] - bias) * 65536ll +
+                                             (long long)(int)(acc[1][c] - bias) * 256ll +
+                                             (long long)(int)(acc[2][c] - bias);
+                        const long long lo = (long long)(int)(acc[3][c] - bias) * 16777216ll +
+                                             (long long)(int)(acc[4][c] - bias) * 65536ll +
+                                             (long long)(int)(acc[5][c] - bias) * 256ll +
+                                             (long long)(int)(acc[6][c] - bias);
+                        atomicAdd(ph, (unsigned long long)hi);
+                        atomicAdd(pl, (unsigned long long)lo);
+                    }
+                    ph += a.np;
+                    pl += a.np;
                 }
             }
         }
@@ -488,71 +734,29 @@ __global__ void oz_finalize_kernel(const unsigned long long *__restrict__ Phi, c
     }
 }
 
-// ------------------------------------------------------------------ tensor maps
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encode_fn() {
-    static EncodeTiled fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-        cudaGetLastError();
-    });
-    return fn;
-}
-
-// [slices][rows][kp] BF16 slices, boxes of 32 k x `box_rows` rows x 7 slices, 64-byte swizzle
-hodlr_status make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t kp, int box_rows) {
-    EncodeTiled fn = encode_fn();
-    if (!fn) {
-        set_error("oz: cuTensorMapEncodeTiled is not available from the driver");
-        return HODLR_CUDA_ERROR;
-    }
-    const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)S};
-    const cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)rows * kp * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, (cuuint32_t)S};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("oz: cuTensorMapEncodeTiled failed (%d)", (int)r);
-        return HODLR_CUDA_ERROR;
-    }
-    return HODLR_OK;
-}
-
 }  // namespace
 
 bool oz_eligible(int64_t n, int s) { return s >= OZ_MIN_RHS && n >= OZ_MIN_N; }
 
 size_t oz_a_bytes(int64_t n) {
     const int64_t np = oz_np(n), kp = oz_kp(n);
-    return align256((size_t)S * np * kp * sizeof(__nv_bfloat16)) + align256((size_t)np * sizeof(int));
+    return align256((size_t)S * np * kp) + align256((size_t)np * sizeof(int));
 }
 
 size_t oz_z_bytes(int64_t n, int s) {
     const int64_t np = oz_np(n), kp = oz_kp(n);
     const int sp = oz_sp(s);
-    return align256((size_t)S * sp * kp * sizeof(__nv_bfloat16)) + align256((size_t)sp * sizeof(int)) +
+    return align256((size_t)S * sp * kp * sizeof(__half)) + align256((size_t)sp * sizeof(int)) +
            2 * align256((size_t)sp * np * sizeof(unsigned long long));
 }
 
 hodlr_status oz_split_a(hodlr_ctx *c, const double *A, int64_t n, int64_t lda, void *abuf, cudaStream_t st) {
     const int64_t np = oz_np(n), kp = oz_kp(n);
-    auto *sl = reinterpret_cast<__nv_bfloat16 *>(abuf);
-    int *ea = reinterpret_cast<int *>(reinterpret_cast<char *>(abuf) +
-                                      align256((size_t)S * np * kp * sizeof(__nv_bfloat16)));
+    auto *sl = reinterpret_cast<uint8_t *>(abuf);
+    int *ea = reinterpret_cast<int *>(reinterpret_cast<char *>(abuf) + align256((size_t)S * np * kp));
     {
         ProfScope ps("oz_split_rows_kernel", st);
-        oz_split_rows_kernel<<<(unsigned)(np / 8), 256, 0, st>>>(A, n, lda, np, kp, sl, ea, c->d_status);
+        oz_split_rows_kernel<<<(unsigned)(np / 32), 256, 0, st>>>(A, n, lda, np, kp, sl, ea, c->d_status);
     }
     note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
@@ -564,16 +768,15 @@ hodlr_status oz_matvec(hodlr_ctx *c, const void *abuf, int64_t n, int s, const d
     if (n == 0 || s == 0) return HODLR_OK;
     const int64_t np = oz_np(n), kp = oz_kp(n);
     const int sp = oz_sp(s);
-    if (np / TC_BM > 0x7fffffff || sp / TC_BN > 65535 || np > 0x7fffffff || kp > 0x7fffffff) {
+    if (sp / TC_BN > 65535 || np / TC_BM > 0x7fffffff / 2 || kp > 0x7fffffff) {
         set_error("oz_matvec: size out of range (n %lld, s %d)", (long long)n, s);
         return HODLR_RANGE;
     }
-    const auto *sl = reinterpret_cast<const __nv_bfloat16 *>(abuf);
-    const int *ea = reinterpret_cast<const int *>(reinterpret_cast<const char *>(abuf) +
-                                                  align256((size_t)S * np * kp * sizeof(__nv_bfloat16)));
+    const auto *sl = reinterpret_cast<const uint8_t *>(abuf);
+    const int *ea = reinterpret_cast<const int *>(reinterpret_cast<const char *>(abuf) + align256((size_t)S * np * kp));
     char *zp = reinterpret_cast<char *>(zbuf);
-    auto *zs = reinterpret_cast<__nv_bfloat16 *>(zp);
-    zp += align256((size_t)S * sp * kp * sizeof(__nv_bfloat16));
+    auto *zs = reinterpret_cast<__half *>(zp);
+    zp += align256((size_t)S * sp * kp * sizeof(__half));
     int *ez = reinterpret_cast<int *>(zp);
     zp += align256((size_t)sp * sizeof(int));
     auto *Phi = reinterpret_cast<unsigned long long *>(zp);
@@ -585,23 +788,20 @@ hodlr_status oz_matvec(hodlr_ctx *c, const void *abuf, int64_t n, int s, const d
     }
     note_launch();
     HODLR_TRY_CUDA(cudaMemsetAsync(Phi, 0, 2 * align256((size_t)sp * np * sizeof(unsigned long long)), st));
-    CUtensorMap mA, mZ;
-    HODLR_TRY(make_map(&mA, sl, np, kp, TC_BM));
-    HODLR_TRY(make_map(&mZ, zs, sp, kp, TC_BN));
-    // split k so that the grid holds about four CTAs per SM (one resident at a time)
-    const int tiles = (int)(np / TC_BM) * (sp / TC_BN);
+    // persistent: one CTA per SM over all (row tile, rhs tile, chunk) units
     const int nchunks = (int)(kp / TC_BK);
-    int ksplit = std::max(1, (4 * std::max(1, c->num_sms) + tiles - 1) / tiles);
-    ksplit = std::min(ksplit, std::max(1, nchunks / 8));
-    ksplit = std::min(ksplit, 65535);
-    const int per = (nchunks + ksplit - 1) / ksplit;
-    ksplit = (nchunks + per - 1) / per;
-    TcArgs ta{ea, ez, n, s, nchunks, per, Phi, Plo, np, c->d_status};
+    const long long tiles = (np / TC_BM) * (long long)(sp / TC_BN);
+    if (tiles > 0x7fffffffll) {
+        set_error("oz_matvec: size out of range (n %lld, s %d)", (long long)n, s);
+        return HODLR_RANGE;
+    }
+    const long long units = tiles * nchunks;
+    const int grid = (int)std::min<long long>(std::max(1, c->num_sms), units);
+    TcArgs ta{n, s, nchunks, sp / TC_BN, units, Phi, Plo, np, c->d_status};
     HODLR_TRY_CUDA(cudaFuncSetAttribute(oz_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    const dim3 grid((unsigned)(np / TC_BM), (unsigned)(sp / TC_BN), (unsigned)ksplit);
     {
         ProfScope ps("oz_tc_gemm_kernel", st);
-        oz_tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(mA, mZ, ta);
+        oz_tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(sl, zs, ta);
     }
     note_launch();
     HODLR_TRY_CUDA(cudaGetLastError());
