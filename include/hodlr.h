@@ -389,6 +389,18 @@ hodlr_status hodlr_profile_read(const char *kernel, double *ms_total, long long 
  * values it was recorded with). */
 hodlr_status hodlr_ctx_set_wait_test(hodlr_ctx *ctx, unsigned long long spin_limit, int unreachable);
 
+/* How the apply (Sec. 4.3 Solve, in hodlr_solve and every GMRES iteration) is
+ * launched; both compute the same result up to the rounding order of the node
+ * sums.  1: one cooperative launch for all levels, each CTA walking its row
+ * tiles and waiting per node for the tiles of the level below (the waits of
+ * hodlr_ctx_set_wait_test); 2: one launch per phase (the leaves, then each
+ * level) with one CTA per row tile, the launches ordering the levels; 0
+ * (default): 2 when the tiles outnumber twice the CTAs the single launch can
+ * hold, else 1.  Affects later calls on the context (a solve's recorded
+ * iteration keeps the path it was recorded with).  HODLR_INVALID_ARG for other
+ * values. */
+hodlr_status hodlr_ctx_set_apply_path(hodlr_ctx *ctx, int path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -350,6 +350,15 @@ hodlr_status hodlr_ctx_set_wait_test(hodlr_ctx *c, unsigned long long spin_limit
     return HODLR_OK;
 }
 
+hodlr_status hodlr_ctx_set_apply_path(hodlr_ctx *c, int path) {
+    if (!c || path < 0 || path > 2) {
+        set_error("hodlr_ctx_set_apply_path: invalid argument");
+        return HODLR_INVALID_ARG;
+    }
+    c->apply_path = path;
+    return HODLR_OK;
+}
+
 hodlr_status hodlr_profile_enable(int on) {
     hodlr::prof_clear();
     hodlr::g_prof_on.store(on ? 1 : 0);

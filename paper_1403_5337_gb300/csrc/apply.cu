@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -148,9 +149,21 @@ __device__ void fa_vtx(const FusedArgs<T, S> &a, int c, int child, int64_t row0,
         for (; col < rp; col += NW)
             sv[col * (TR + 1) + lane] = (lane < nrows) ? to_t<T>(Vc[row + (int64_t)col * a.ldn]) : T(0);
     }
-    for (int e = threadIdx.x; e < TR * RC; e += AP_THREADS) {
-        const int li = e % TR, q = e / TR;
-        xs[q * TR + li] = (li < nrows && q < rr) ? a.xt[row0 + li + (r0 + q) * a.ldn] : T(0);
+    {
+        // all of a thread's loads in flight before its stores (a store through
+        // a generic pointer between loads would serialise them)
+        constexpr int U = (TR * RC + AP_THREADS - 1) / AP_THREADS;
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = threadIdx.x + u * AP_THREADS, li = e % TR, q = e / TR;
+            v[u] = (e < TR * RC && li < nrows && q < rr) ? a.xt[row0 + li + (r0 + q) * a.ldn] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = threadIdx.x + u * AP_THREADS;
+            if (e < TR * RC) xs[e] = v[u];
+        }
     }
     __syncthreads();
     for (int cc = threadIdx.x; cc < rp; cc += AP_THREADS) {
@@ -260,9 +273,149 @@ __device__ __forceinline__ void store_x(const FusedArgs<T, S> &a, int64_t o, T v
     }
 }
 
+// One tile's share of the leaf phase: x = K_leaf^-1 x on the tile's rows,
+// then the leaf level's V^T x (partial sums added to w(L)).  Returns the leaf.
+template <typename T, typename S, int RC>
+__device__ __forceinline__ int leaf_tile(const FusedArgs<T, S> &a, int t, T *part, T *ws, T *sv, T *xs,
+                                         const unsigned char *stg) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = a.L;
+    const int4 tl = a.tiles[t];
+    const int leaf = tl.x, nrows = tl.z;
+    const int64_t row0 = tl.y;
+    const int64_t l0 = a.bounds[leaf];
+    const int b = (int)(a.bounds[leaf + 1] - l0);
+    const T *K = a.Kinv + (size_t)leaf * a.bmax * a.bmax;
+    const int il = (int)(row0 - l0) + lane;
+    const int kper = (b + 7) / 8, kb = warp * kper, ke = min(b, kb + kper);
+    for (int r0 = 0; r0 < a.s; r0 += RC) {
+        const int rr = min(RC, a.s - r0);
+        // the leaf's rows of X, converted once
+        // eight loads in flight per thread before their stores
+        for (int e0 = threadIdx.x; e0 < b * RC; e0 += 8 * AP_THREADS) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * AP_THREADS, k = e / RC, q = e % RC;
+                v[u] = (e < b * RC && q < rr) ? dev::from_double<T>(a.Xin[l0 + k + (int64_t)(r0 + q) * a.ldxin]) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * AP_THREADS;
+                if (e < b * RC) ws[e] = v[u];
+            }
+        }
+        __syncthreads();
+        T acc[RC];
+#pragma unroll
+        for (int q = 0; q < RC; ++q) acc[q] = T(0);
+        if (lane < nrows) {
+            if (stg)
+                stream_dot<T, T, RC>(reinterpret_cast<const T *>(stg) + lane, TR, ws, kb, ke, acc);
+            else
+                stream_dot<T, T, RC>(K + il, a.bmax, ws, kb, ke, acc);
+        }
+#pragma unroll
+        for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
+        __syncthreads();
+        for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
+            const int li = e % TR, q = e / TR;
+            if (li < nrows) {
+                const T v = warp_parts_sum<T, RC>(part, li, q);
+                a.xt[row0 + li + (r0 + q) * a.ldn] = v;
+                if (L == 0) store_x(a, row0 + li + (r0 + q) * a.ldx, v);
+            }
+        }
+        __syncthreads();
+        if (L >= 1) fa_vtx<T, S, RC>(a, L, leaf, row0, nrows, r0, rr, sv, xs, stg);
+    }
+    return leaf;
+}
+
+// One tile's share of level c: (FUSED: once every tile of its node has added
+// its part of w(c)) x -= E w(node) on the tile's rows, then the next level's
+// V^T x, or (c = 1) the store of x.  Returns the leaf.
+template <typename T, typename S, int RC, bool FUSED>
+__device__ __forceinline__ int level_tile(const FusedArgs<T, S> &a, int c, int t, T *part, T *ws, T *sv, T *xs,
+                                          const unsigned char *stg) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = a.L;
+    const int rp = a.rp[c];
+    const int s2 = 2 * rp;
+    const int shift = L - c + 1;   // leaf -> parent node of level c
+    const int4 tl = a.tiles[t];
+    const int leaf = tl.x, nrows = tl.z;
+    const int64_t row0 = tl.y;
+    const int node = leaf >> shift;
+    const int child = leaf >> (L - c);
+    if constexpr (FUSED) {
+        const unsigned target = (unsigned)(a.tile_first[(node + 1) << shift] - a.tile_first[node << shift]);
+        wait_node(a.cnt[c] + node, target + a.target_extra, a.status, a.spin_limit);
+    }
+    const T *wn = a.w[c] + (size_t)node * s2 * a.s;
+    const S *Ec = a.Eb + a.eoff[c];
+    const float *es = a.escale[c];
+    for (int r0 = 0; r0 < a.s; r0 += RC) {
+        const int rr = min(RC, a.s - r0);
+        if (rp > 0) {
+            // w of the node (complete: read past L1), times E's FP16 column factors
+            // (eight loads in flight per thread before their stores)
+            for (int e0 = threadIdx.x; e0 < s2 * RC; e0 += 8 * AP_THREADS) {
+                T v[8];
+                float f[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * AP_THREADS, k = e / RC, q = e % RC;
+                    v[u] = (e < s2 * RC && q < rr) ? __ldcg(wn + (size_t)k * a.s + r0 + q) : T(0);
+                    f[u] = (es && e < s2 * RC) ? es[(size_t)child * s2 + k] : 1.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * AP_THREADS;
+                    if (e < s2 * RC) ws[e] = v[u] * (T)f[u];
+                }
+            }
+            __syncthreads();
+            // x -= E w on the tile's rows: lanes over rows, warps split the 2 rp columns
+            const int uper = (s2 + 7) / 8, ub = warp * uper, ue = min(s2, ub + uper);
+            T acc[RC];
+#pragma unroll
+            for (int q = 0; q < RC; ++q) acc[q] = T(0);
+            if (lane < nrows) {
+                if (stg)
+                    stream_dot<T, S, RC>(reinterpret_cast<const S *>(stg + a.sofE[c]) + lane, TR, ws, ub, ue,
+                                         acc);
+                else
+                    stream_dot<T, S, RC>(Ec + row0 + lane, a.ldn, ws, ub, ue, acc);
+            }
+#pragma unroll
+            for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
+            __syncthreads();
+            for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
+                const int li = e % TR, q = e / TR;
+                if (li < nrows) {
+                    const int64_t o = row0 + li + (int64_t)(r0 + q) * a.ldn;
+                    const T v = a.xt[o] - warp_parts_sum<T, RC>(part, li, q);
+                    a.xt[o] = v;
+                    if (c == 1) store_x(a, row0 + li + (int64_t)(r0 + q) * a.ldx, v);
+                }
+            }
+            __syncthreads();
+        } else if (c == 1) {
+            for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
+                const int li = e % TR, q = e / TR;
+                if (li < nrows)
+                    store_x(a, row0 + li + (int64_t)(r0 + q) * a.ldx,
+                            a.xt[row0 + li + (int64_t)(r0 + q) * a.ldn]);
+            }
+        }
+        if (c > 1) fa_vtx<T, S, RC>(a, c - 1, leaf >> (L - c + 1), row0, nrows, r0, rr, sv, xs, stg);
+    }
+    return leaf;
+}
+
 template <typename T, typename S, int RC>
 __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs<T, S> a) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     T *part = reinterpret_cast<T *>(smem);                          // 8 warps x 32 rows x RC
     T *ws = part + (AP_THREADS / 32) * TR * RC;                     // w of the node: 2 rp x RC; the leaf's x
@@ -297,113 +450,208 @@ __global__ void __launch_bounds__(AP_THREADS) apply_fused_kernel(const FusedArgs
     }
     // ---- leaves: x = K_leaf^-1 x on the tile's rows, then the leaf level's V^T x
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const int4 tl = a.tiles[t];
-        const int leaf = tl.x, nrows = tl.z;
-        const int64_t row0 = tl.y;
-        const int64_t l0 = a.bounds[leaf];
-        const int b = (int)(a.bounds[leaf + 1] - l0);
-        const T *K = a.Kinv + (size_t)leaf * a.bmax * a.bmax;
-        const int il = (int)(row0 - l0) + lane;
-        const int kper = (b + 7) / 8, kb = warp * kper, ke = min(b, kb + kper);
-        for (int r0 = 0; r0 < a.s; r0 += RC) {
-            const int rr = min(RC, a.s - r0);
-            // the leaf's rows of X, converted once
-            for (int e = threadIdx.x; e < b * RC; e += AP_THREADS) {
-                const int k = e / RC, q = e % RC;
-                ws[k * RC + q] = (q < rr) ? dev::from_double<T>(a.Xin[l0 + k + (int64_t)(r0 + q) * a.ldxin]) : T(0);
-            }
-            __syncthreads();
-            T acc[RC];
-#pragma unroll
-            for (int q = 0; q < RC; ++q) acc[q] = T(0);
-            if (lane < nrows) {
-                if (stg)
-                    stream_dot<T, T, RC>(reinterpret_cast<const T *>(stg) + lane, TR, ws, kb, ke, acc);
-                else
-                    stream_dot<T, T, RC>(K + il, a.bmax, ws, kb, ke, acc);
-            }
-#pragma unroll
-            for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
-            __syncthreads();
-            for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
-                const int li = e % TR, q = e / TR;
-                if (li < nrows) {
-                    const T v = warp_parts_sum<T, RC>(part, li, q);
-                    a.xt[row0 + li + (r0 + q) * a.ldn] = v;
-                    if (L == 0) store_x(a, row0 + li + (r0 + q) * a.ldx, v);
-                }
-            }
-            __syncthreads();
-            if (L >= 1) fa_vtx<T, S, RC>(a, L, leaf, row0, nrows, r0, rr, sv, xs, stg);
-        }
+        const int leaf = leaf_tile<T, S, RC>(a, t, part, ws, sv, xs, stg);
         if (L >= 1) arrive(a.cnt[L] + (leaf >> 1));
     }
     // ---- levels c = L .. 1: x -= E w(node) on the tile's rows (E = d S^-1(half)
     // formed by the factorisation), then the next level's V^T x (or the store)
     for (int c = L; c >= 1; --c) {
-        const int rp = a.rp[c];
-        const int s2 = 2 * rp;
-        const int shift = L - c + 1;   // leaf -> parent node of level c
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-            const int4 tl = a.tiles[t];
-            const int leaf = tl.x, nrows = tl.z;
-            const int64_t row0 = tl.y;
-            const int node = leaf >> shift;
-            const int child = leaf >> (L - c);
-            const unsigned target =
-                (unsigned)(a.tile_first[(node + 1) << shift] - a.tile_first[node << shift]);
-            wait_node(a.cnt[c] + node, target + a.target_extra, a.status, a.spin_limit);
-            const T *wn = a.w[c] + (size_t)node * s2 * a.s;
-            const S *Ec = a.Eb + a.eoff[c];
-            const float *es = a.escale[c];
-            for (int r0 = 0; r0 < a.s; r0 += RC) {
-                const int rr = min(RC, a.s - r0);
-                if (rp > 0) {
-                    // w of the node (complete: read past L1), times E's FP16 column factors
-                    for (int e = threadIdx.x; e < s2 * RC; e += AP_THREADS) {
-                        const int k = e / RC, q = e % RC;
-                        T v = (q < rr) ? __ldcg(wn + (size_t)k * a.s + r0 + q) : T(0);
-                        if (es) v *= (T)es[(size_t)child * s2 + k];
-                        ws[k * RC + q] = v;
-                    }
-                    __syncthreads();
-                    // x -= E w on the tile's rows: lanes over rows, warps split the 2 rp columns
-                    const int uper = (s2 + 7) / 8, ub = warp * uper, ue = min(s2, ub + uper);
-                    T acc[RC];
-#pragma unroll
-                    for (int q = 0; q < RC; ++q) acc[q] = T(0);
-                    if (lane < nrows) {
-                        if (stg)
-                            stream_dot<T, S, RC>(reinterpret_cast<const S *>(stg + a.sofE[c]) + lane, TR, ws, ub, ue,
-                                                 acc);
-                        else
-                            stream_dot<T, S, RC>(Ec + row0 + lane, a.ldn, ws, ub, ue, acc);
-                    }
-#pragma unroll
-                    for (int q = 0; q < RC; ++q) part[(warp * TR + lane) * RC + q] = acc[q];
-                    __syncthreads();
-                    for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
-                        const int li = e % TR, q = e / TR;
-                        if (li < nrows) {
-                            const int64_t o = row0 + li + (int64_t)(r0 + q) * a.ldn;
-                            const T v = a.xt[o] - warp_parts_sum<T, RC>(part, li, q);
-                            a.xt[o] = v;
-                            if (c == 1) store_x(a, row0 + li + (int64_t)(r0 + q) * a.ldx, v);
-                        }
-                    }
-                    __syncthreads();
-                } else if (c == 1) {
-                    for (int e = threadIdx.x; e < TR * rr; e += AP_THREADS) {
-                        const int li = e % TR, q = e / TR;
-                        if (li < nrows)
-                            store_x(a, row0 + li + (int64_t)(r0 + q) * a.ldx,
-                                    a.xt[row0 + li + (int64_t)(r0 + q) * a.ldn]);
-                    }
-                }
-                if (c > 1) fa_vtx<T, S, RC>(a, c - 1, leaf >> (L - c + 1), row0, nrows, r0, rr, sv, xs, stg);
-            }
+            const int leaf = level_tile<T, S, RC, true>(a, c, t, part, ws, sv, xs, stg);
             if (c > 1) arrive(a.cnt[c - 1] + (leaf >> (L - c + 2)));
         }
+    }
+}
+
+// The apply phase by phase, one launch per phase (the leaves with level L's
+// V^T x, then each level c = L .. 1) and one CTA per tile: the kernel boundary
+// orders the phases, so no tile waits for another inside a launch.  Taken when
+// the tree has several tiles per resident CTA, where the single cooperative
+// launch would walk each CTA's tiles in series with a wait per node and level.
+template <typename T, typename S, int RC>
+__global__ void __launch_bounds__(AP_THREADS, 2) apply_phase_kernel(const FusedArgs<T, S> a, int c) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *part = reinterpret_cast<T *>(smem);                          // 8 warps x 32 rows x RC
+    T *ws = part + (AP_THREADS / 32) * TR * RC;                     // w of the node: 2 rp x RC; the leaf's x
+    T *sv = ws + (size_t)std::max(2 * a.rpmax, a.bmax) * RC;        // V tile: rp x (32 + 1)
+    T *xs = sv + (size_t)a.rpmax * (TR + 1);                        // x tile: RC x 32
+    if (c > a.L)
+        leaf_tile<T, S, RC>(a, blockIdx.x, part, ws, sv, xs, nullptr);
+    else
+        level_tile<T, S, RC, false>(a, c, blockIdx.x, part, ws, sv, xs, nullptr);
+}
+
+// The per-phase apply for FP32 arithmetic, one CTA per 32-row tile and up to
+// 32 right-hand sides per pass: lane = row of the tile, warp = 4 right-hand
+// sides.  Everything a tile reads in a phase is requested before any of it is
+// used -- E's (or the leaf inverse's) and the next level's V rows by
+// asynchronous copies into shared memory, the node's w and the tile's x by
+// batched loads -- so that a phase costs a few memory round trips per tile.  Then
+//   x -= E w          (k over 2 rp: one E element, four w values, four FMAs),
+//   w(next) += V^T x  (lane = column of V, warp = 4 right-hand sides, atomics),
+// or, at the top level, the store of x.  The leaf phase forms x = K_leaf^-1 x
+// from the tile's rows of the leaf inverse the same way.
+
+struct TileSmem {
+    size_t xs, vs, ws, es, total;
+};
+
+// Shared-memory layout of apply_tile_kernel (offsets in bytes).
+template <typename S>
+TileSmem tile_smem(int rpmax, int bmax) {
+    auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+    TileSmem m{};
+    m.xs = 0;                                                             // x: 32 rhs x 33 (padded rows)
+    m.vs = m.xs + al(32 * 33 * sizeof(float));                            // V: rp columns x 32 rows
+    m.ws = m.vs + al((size_t)32 * rpmax * sizeof(S));                     // w: 2 rp x 32, or the leaf's x: b x 32
+    m.es = m.ws + al((size_t)std::max(2 * rpmax, bmax) * 32 * sizeof(float));
+    m.total = m.es + al(std::max((size_t)2 * rpmax * 32 * sizeof(S), (size_t)bmax * 32 * sizeof(float)));
+    return m;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(AP_THREADS, 2) apply_tile_kernel(const FusedArgs<float, S> a, int c, TileSmem sm) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q0 = 4 * warp;
+    const int L = a.L;
+    const int4 tl = a.tiles[blockIdx.x];
+    const int leaf = tl.x, nrows = tl.z;
+    const int64_t row0 = tl.y;
+    const bool leafp = c > L;
+    const int cv = leafp ? L : c - 1;              // the level whose V^T x this phase adds (0: none)
+    const int rpv = cv >= 1 ? a.rp[cv] : 0;
+    const int childv = cv >= 1 ? leaf >> (L - cv) : 0;
+    float *xsP = reinterpret_cast<float *>(smem + sm.xs);   // x(row r, rhs q) at q * 33 + r
+    S *Vs = reinterpret_cast<S *>(smem + sm.vs);            // V(row r, column j) at j * 32 + r
+    float *ws = reinterpret_cast<float *>(smem + sm.ws);
+    unsigned char *es_raw = smem + sm.es;
+    // ---- E's (or the leaf inverse's) rows of the tile: asynchronous copies
+    int64_t l0 = 0;
+    int b = 0, rp = 0, s2 = 0, node = 0, child = 0;
+    if (leafp) {
+        l0 = a.bounds[leaf];
+        b = (int)(a.bounds[leaf + 1] - l0);
+        stage_cols<float>(reinterpret_cast<float *>(es_raw),
+                          a.Kinv + (size_t)leaf * a.bmax * a.bmax + (row0 - l0), a.bmax, b, nrows);
+    } else {
+        rp = a.rp[c];
+        s2 = 2 * rp;
+        node = leaf >> (L - c + 1);
+        child = leaf >> (L - c);
+        if (rp > 0) stage_cols<S>(reinterpret_cast<S *>(es_raw), a.Eb + a.eoff[c] + row0, a.ldn, s2, nrows);
+    }
+    // ---- the next level's V rows of the tile
+    if (rpv > 0) stage_cols<S>(Vs, a.Vb + a.voff[cv] + row0, a.ldn, rpv, nrows);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const float *vsc = cv >= 1 ? a.vscale[cv] : nullptr;
+    for (int r0 = 0; r0 < a.s; r0 += 32) {
+        const int rr = min(32, a.s - r0);
+        float x[4];
+        if (leafp) {
+            // the leaf's rows of X (FP64 -> FP32), sixteen loads in flight per thread
+            for (int e0 = threadIdx.x; e0 < b * 32; e0 += 16 * AP_THREADS) {
+                float v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int e = e0 + u * AP_THREADS, k = e >> 5, q = e & 31;
+                    v[u] = (e < b * 32 && q < rr) ? (float)a.Xin[l0 + k + (int64_t)(r0 + q) * a.ldxin] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int e = e0 + u * AP_THREADS;
+                    if (e < b * 32) ws[e] = v[u];
+                }
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            const float *Ks = reinterpret_cast<const float *>(es_raw);
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+            for (int k = 0; k < b; ++k) {
+                const float kv = Ks[k * 32 + lane];
+                const float4 y = *reinterpret_cast<const float4 *>(ws + k * 32 + q0);
+                acc[0] = fmaf(kv, y.x, acc[0]);
+                acc[1] = fmaf(kv, y.y, acc[1]);
+                acc[2] = fmaf(kv, y.z, acc[2]);
+                acc[3] = fmaf(kv, y.w, acc[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = acc[j];
+        } else {
+            // the tile's x and the node's w (times E's column factors), eight loads in flight
+            float xo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                xo[j] = (lane < nrows && q0 + j < rr) ? a.xt[row0 + lane + (int64_t)(r0 + q0 + j) * a.ldn] : 0.0f;
+            const float *wn = a.w[c] + (size_t)node * s2 * a.s;
+            const float *esc = a.escale[c];
+            for (int e0 = threadIdx.x; e0 < s2 * 32; e0 += 8 * AP_THREADS) {
+                float v[8], f[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * AP_THREADS, k = e >> 5, q = e & 31;
+                    v[u] = (e < s2 * 32 && q < rr) ? __ldcg(wn + (size_t)k * a.s + r0 + q) : 0.0f;
+                    f[u] = (esc && e < s2 * 32) ? esc[(size_t)child * s2 + k] : 1.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * AP_THREADS;
+                    if (e < s2 * 32) ws[e] = v[u] * f[u];
+                }
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            const S *Es = reinterpret_cast<const S *>(es_raw);
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+            for (int k = 0; k < s2; ++k) {
+                const float ev = to_t<float>(Es[k * 32 + lane]);
+                const float4 y = *reinterpret_cast<const float4 *>(ws + k * 32 + q0);
+                acc[0] = fmaf(ev, y.x, acc[0]);
+                acc[1] = fmaf(ev, y.y, acc[1]);
+                acc[2] = fmaf(ev, y.z, acc[2]);
+                acc[3] = fmaf(ev, y.w, acc[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = xo[j] - acc[j];
+        }
+        if (lane >= nrows) x[0] = x[1] = x[2] = x[3] = 0.0f;   // rows past a ragged tile
+        // ---- x: kept for the later phases, or (top level / single leaf) stored
+        if (lane < nrows) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (q0 + j < rr) {
+                    if (cv == 0)
+                        store_x(a, row0 + lane + (int64_t)(r0 + q0 + j) * a.ldx, x[j]);
+                    else
+                        a.xt[row0 + lane + (int64_t)(r0 + q0 + j) * a.ldn] = x[j];
+                }
+            }
+        }
+        if (cv >= 1) {
+            // ---- w(cv) += V^T x over the tile's rows: lane = column of V, warp =
+            // 4 right-hand sides; lane l reads row (r + l) mod 32 at step r, so
+            // that neither V (32 rows per column) nor x (33 per rhs) conflicts
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xsP[(q0 + j) * 33 + lane] = x[j];
+            __syncthreads();
+            for (int col = lane; col < rpv; col += 32) {
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) {
+                    const int rl = (r + lane) & 31;
+                    const float v = to_t<float>(Vs[col * 32 + rl]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[j] = fmaf(v, xsP[(q0 + j) * 33 + rl], acc[j]);
+                }
+                const float sc = vsc ? vsc[(size_t)childv * rpv + col] : 1.0f;
+                float *wd = a.w[cv] + ((size_t)childv * rpv + col) * a.s + r0 + q0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (q0 + j < rr) atomicAdd(wd + j, acc[j] * sc);
+            }
+        }
+        __syncthreads();   // the shared buffers are refilled by the next pass
     }
 }
 
@@ -526,6 +774,33 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a0, cudaStrea
     // staging needs one CTA per tile (ntiles <= SMs <= resident CTAs)
     const int grid = a.stage ? std::max(h->ntiles, 1)
                              : std::max(1, std::min(h->ctx->num_sms * std::min(per_sm, 2), std::max(h->ntiles, 1)));
+    const int path = h->ctx->apply_path ? h->ctx->apply_path : (!a.stage && h->ntiles >= 2 * grid ? 2 : 1);
+    if (path == 2 && a.L >= 1) {
+        // several tiles per CTA: one launch per phase, one CTA per tile
+        if constexpr (std::is_same<T, float>::value) {
+            const TileSmem tsm = tile_smem<S>(a.rpmax, a.bmax);
+            if (tsm.total <= (size_t)optin / 2) {   // two CTAs per SM
+                HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_tile_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)tsm.total));
+                ProfScope ps("apply_phase_kernel", st);
+                for (int c = a.L + 1; c >= 1; --c) {
+                    apply_tile_kernel<S><<<h->ntiles, AP_THREADS, tsm.total, st>>>(a, c, tsm);
+                    note_launch();
+                    HODLR_TRY_CUDA(cudaGetLastError());
+                }
+                return HODLR_OK;
+            }
+        }
+        HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_phase_kernel<T, S, RC>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+        ProfScope ps("apply_phase_kernel", st);
+        for (int c = a.L + 1; c >= 1; --c) {
+            apply_phase_kernel<T, S, RC><<<h->ntiles, AP_THREADS, sm0, st>>>(a, c);
+            note_launch();
+            HODLR_TRY_CUDA(cudaGetLastError());
+        }
+        return HODLR_OK;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(AP_THREADS);

@@ -111,6 +111,7 @@ struct hodlr_ctx {
     // to its arrival targets, set by hodlr_ctx_set_wait_test only
     unsigned long long wait_limit = 0;
     unsigned wait_extra = 0;
+    int apply_path = 0;   // 0: automatic, 1: one cooperative launch, 2: one launch per phase
 };
 #define HODLR_REPORT_BYTES 65536
 #define HODLR_CACHE_LIMIT (size_t(16) << 30)

@@ -80,7 +80,7 @@ SYMBOLS = ["hodlr_ctx_create", "hodlr_ctx_destroy", "hodlr_opts_default", "hodlr
            "hodlr_stats_get",
            "hodlr_export_level", "hodlr_export_core", "hodlr_export_core_cond", "hodlr_destroy", "hodlr_status_string",
            "hodlr_last_error", "hodlr_launch_count", "hodlr_build_batched", "hodlr_factor_batched",
-           "gmres_solve_batched", "hodlr_ctx_set_wait_test", "hodlr_profile_enable", "hodlr_profile_read",
+           "gmres_solve_batched", "hodlr_ctx_set_wait_test", "hodlr_ctx_set_apply_path", "hodlr_profile_enable", "hodlr_profile_read",
            "hodlr_build_diag", "hodlr_dense_lu_solve", "hodlr_save", "hodlr_load"]
 
 _lib = None
@@ -138,6 +138,7 @@ def load_library(path: str = _LIBPATH):
     lib.hodlr_destroy.argtypes = [vp]
     lib.hodlr_launch_count.argtypes = [C.POINTER(C.c_longlong)]
     lib.hodlr_ctx_set_wait_test.argtypes = [vp, C.c_ulonglong, ci]
+    lib.hodlr_ctx_set_apply_path.argtypes = [vp, ci]
     lib.hodlr_profile_enable.argtypes = [ci]
     lib.hodlr_profile_read.argtypes = [C.c_char_p, C.POINTER(cd), C.POINTER(C.c_longlong)]
     lib.hodlr_build_batched.argtypes = [vp, ci, C.POINTER(_Matrix), C.POINTER(ci), cd, ci, C.POINTER(_Opts), vp,
@@ -260,6 +261,11 @@ class Context:
     def set_wait_test(self, spin_limit: int = 0, unreachable: bool = False):
         """Test hook of the bounded device waits (see include/hodlr.h)."""
         _check(_lib.hodlr_ctx_set_wait_test(self.handle, int(spin_limit), 1 if unreachable else 0))
+
+    def set_apply_path(self, path: int = 0):
+        """0: automatic, 1: one cooperative launch, 2: one launch per phase
+        (include/hodlr.h, hodlr_ctx_set_apply_path)."""
+        _check(_lib.hodlr_ctx_set_apply_path(self.handle, int(path)))
 
     def close(self):
         if self.handle:

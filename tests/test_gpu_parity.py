@@ -892,3 +892,57 @@ def test_batched_octree_fronts(H, ctx):
         assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) < 1e-9
     for h in hs:
         h.close()
+
+
+@pytest.mark.parametrize("precision,nrhs", [("fp32", 4), ("fp16", 32), ("fp64", 3)])
+def test_apply_paths_agree(H, ctx, front4096, precision, nrhs):
+    """The apply launched once for all levels (per-node waits) and launched
+    once per phase (one CTA per row tile) compute the same K~^-1 X up to the
+    rounding order of the node sums, and GMRES on the per-phase path converges
+    to 1e-12 in the iterations of the single launch (+-1)."""
+    F = front4096
+    A = _dev(F.A)
+    B = fg.rhs(F.n, nrhs, seed=21)
+    h = H.hodlr_build(ctx, A, 128, 1e-4, "aca", precision=precision)
+    out = {}
+    try:
+        for path in (1, 2):
+            ctx.set_apply_path(path)
+            X = _dev(B.T)
+            H.hodlr_solve(h, X)
+            torch.cuda.synchronize()
+            Xg, info = H.gmres_solve(ctx, A, _dev(B.T), h, tol=1e-12)
+            out[path] = (X.cpu().numpy(), info)
+    finally:
+        ctx.set_apply_path(0)
+    x1, i1 = out[1]
+    x2, i2 = out[2]
+    assert np.all(np.isfinite(x2))
+    # FP32 (FP16-stored) arithmetic: node sums in another order differ by a few
+    # units of 2^-24 of the terms; FP64: of 2^-53
+    rtol = 1e-13 if precision == "fp64" else 2e-5
+    assert np.linalg.norm(x2 - x1) <= rtol * np.linalg.norm(x1)
+    assert i2.converged and np.all(i2.true_relres <= 1e-12)
+    assert np.abs(i1.iters - i2.iters).max() <= 1
+    h.close()
+
+
+def test_per_phase_apply_matches_oracle(H, ctx, front576):
+    """The per-phase apply against the oracle's recursive solve (FP64 factors,
+    ACA 1e-6), to the factor-and-solve tolerance."""
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    blocks = O.build(F.A, tree, "aca", 1e-6)
+    Fac = O.factor(F.A, tree, blocks)
+    h = H.hodlr_build(ctx, _dev(F.A), 64, 1e-6, "aca", precision="fp64")
+    b = fg.rhs(F.n, 5, seed=2)
+    X = _dev(b.T)
+    try:
+        ctx.set_apply_path(2)
+        H.hodlr_solve(h, X)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_apply_path(0)
+    ref = O.solve(Fac, b)
+    assert np.linalg.norm(X.cpu().numpy().T - ref) / np.linalg.norm(ref) < 1e-10
+    h.close()
