@@ -33,10 +33,10 @@
 // balanced to one unit.  Both operands are stored unit by unit (one unit of A
 // is 28 KB of bytes, one of Z 14 KB of FP16 already in the shared-memory
 // operand's 64-byte-swizzled order), so each arrives by one bulk copy.  Warp 0
-// streams A's units (3 stages); warps 2-3 convert them into the FP16 slices of
+// streams A's units (3 stages); warps 4-7 convert them into the FP16 slices of
 // one of 2 MMA stages and fetch Z's unit into it; warp 1 allocates TMEM
 // (two accumulator sets of 224 columns) and issues the MMAs (M = 128, N =
-// 32 (7 - p), K = 16, two k-steps per chunk); warps 4-11 drain the accumulators
+// 32 (7 - p), K = 16, two k-steps per chunk); warps 8-15 drain the accumulators
 // after every chunk (warp w reads the TMEM lanes of quarter w mod 4, i.e. 32
 // rows, and 16 of the 32 right-hand sides), adding each level's integer into a
 // 32-bit sum (exact for 512 chunks), and at the end of a tile's run of units
@@ -68,9 +68,15 @@ constexpr int TC_BN = 32;           // right-hand sides per unit
 constexpr int TC_BK = 32;           // k per unit: one exact flush of TMEM
 constexpr int TC_TSTAGES = 3;       // stages of A's bytes
 constexpr int TC_MSTAGES = 2;       // MMA stages (FP16 slices of A and Z)
-constexpr int TC_THREADS = 384;     // warp 0 loads, 1 MMA, 2-3 convert, 4-11 drain
-constexpr int TC_CONV_WARPS = 2;
-constexpr int TC_EPI_WARP0 = 4;
+constexpr int TC_THREADS = 512;     // warp 0 loads, 1 MMA, 4-7 convert, 8-15 drain (2-3 idle)
+constexpr int TC_CONV_WARP0 = 4;
+constexpr int TC_CONV_WARPS = 4;
+constexpr int TC_EPI_WARP0 = 8;
+// registers per thread: 128 at launch (65536 / 512); the first two warpgroups
+// (loads, MMA, converters) give up 48 each, the drain's two take 48 more each
+constexpr int TC_REGS_LAUNCH = 128, TC_REGS_LOW = 80, TC_REGS_HIGH = 176;
+static_assert(TC_REGS_LOW * 256 + TC_REGS_HIGH * 256 == TC_REGS_LAUNCH * TC_THREADS,
+              "the register split must add up to the CTA's allocation");
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_ACC_COLS = S * TC_BN;          // 224 TMEM columns per accumulator set
 constexpr int TC_TMEM_COLS = 512;
@@ -506,73 +512,81 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     volatile int *abort = &s_abort;
-
-    if (warp == 0) {
-        // ---------------- producer of A's digit bytes (bulk copies)
-        if (lane == 0 && nu > 0) {
-            int issued = 0;
-            Cursor cu = cursor_at(a, u0);
-            for (int i = 0; i < nu; ++i, cu.next(a.nchunks)) {
-                const int st = i % TC_TSTAGES;
-                const uint32_t ph = (uint32_t)((i / TC_TSTAGES) & 1);
-                if (!mbar_wait(tempty(st), ph ^ 1u, abort, a.status)) break;
-                const long long ua = (long long)(cu.tile / a.ntn) * a.nchunks + cu.chunk;
-                mbar_expect_tx(tfull(st), TC_AB_BYTES);
-                bulk_load(tbase + st * TC_AB_BYTES, Ab + ua * TC_AB_BYTES, TC_AB_BYTES, tfull(st));
-                ++issued;
-            }
-            // copies still in flight when the pipeline stopped early: wait for
-            // them (bounded) before the CTA may leave
-            if (*abort)
-                for (int i = max(0, issued - TC_TSTAGES); i < issued; ++i)
-                    mbar_drain(tfull(i % TC_TSTAGES), (uint32_t)((i / TC_TSTAGES) & 1), a.status);
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0 && nu > 0) {
-            for (int i = 0; i < nu; ++i) {
-                const int ms = i & 1;
-                const uint32_t ph = (uint32_t)((i >> 1) & 1);
-                if (!mbar_wait(cfull(ms), ph, abort, a.status)) break;
-                if (!mbar_wait(zfull(ms), ph, abort, a.status)) break;
-                if (!mbar_wait(acce(ms), ph ^ 1u, abort, a.status)) break;
-                tc_fence_after();
-                const uint32_t sa = mbase + ms * TC_MSTAGE_BYTES;
-                const uint32_t sz = sa + TC_AH_BYTES;
-                const uint32_t dcol = tmem + (uint32_t)(ms * TC_ACC_COLS);
-#pragma unroll
-                for (int ks = 0; ks < TC_BK / 16; ++ks) {
-#pragma unroll
-                    for (int p = 0; p < S; ++p) {
-                        const uint64_t ad = smem_desc(sa + p * (TC_BM * TC_BK * 2) + ks * 32);
-                        const uint64_t bd = smem_desc(sz + ks * 32);
-                        mma_f16(dcol + 32u * p, ad, bd, mma_idesc(TC_BM, TC_BN * (S - p)),
-                                (ks == 0 && p == 0) ? 0u : 1u);
-                    }
+    // Each warpgroup changes its registers at the top of its own branch (the
+    // host launches only when the kernel was compiled with TC_REGS_LAUNCH per
+    // thread): warpgroup 0 holds the loads and the MMA warp, 1 the converters,
+    // 2-3 the drain.
+    if (warp < TC_CONV_WARP0) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TC_REGS_LOW));
+        if (warp == 0) {
+            // ---------------- producer of A's digit bytes (bulk copies)
+            if (lane == 0 && nu > 0) {
+                int issued = 0;
+                Cursor cu = cursor_at(a, u0);
+                for (int i = 0; i < nu; ++i, cu.next(a.nchunks)) {
+                    const int st = i % TC_TSTAGES;
+                    const uint32_t ph = (uint32_t)((i / TC_TSTAGES) & 1);
+                    if (!mbar_wait(tempty(st), ph ^ 1u, abort, a.status)) break;
+                    const long long ua = (long long)(cu.tile / a.ntn) * a.nchunks + cu.chunk;
+                    mbar_expect_tx(tfull(st), TC_AB_BYTES);
+                    bulk_load(tbase + st * TC_AB_BYTES, Ab + ua * TC_AB_BYTES, TC_AB_BYTES, tfull(st));
+                    ++issued;
                 }
-                mma_commit(mempty(ms));   // the stage is free once these MMAs have read it
-                mma_commit(accf(ms));     // the accumulators are complete
+                // copies still in flight when the pipeline stopped early: wait for
+                // them (bounded) before the CTA may leave
+                if (*abort)
+                    for (int i = max(0, issued - TC_TSTAGES); i < issued; ++i)
+                        mbar_drain(tfull(i % TC_TSTAGES), (uint32_t)((i / TC_TSTAGES) & 1), a.status);
             }
-            // every MMA issued is complete before TMEM is released
-            mma_commit(drain);
-            mbar_drain(drain, 0, a.status);
+        } else if (warp == 1) {
+            // ---------------- MMA issuer
+            if (lane == 0 && nu > 0) {
+                for (int i = 0; i < nu; ++i) {
+                    const int ms = i & 1;
+                    const uint32_t ph = (uint32_t)((i >> 1) & 1);
+                    if (!mbar_wait(cfull(ms), ph, abort, a.status)) break;
+                    if (!mbar_wait(zfull(ms), ph, abort, a.status)) break;
+                    if (!mbar_wait(acce(ms), ph ^ 1u, abort, a.status)) break;
+                    tc_fence_after();
+                    const uint32_t sa = mbase + ms * TC_MSTAGE_BYTES;
+                    const uint32_t sz = sa + TC_AH_BYTES;
+                    const uint32_t dcol = tmem + (uint32_t)(ms * TC_ACC_COLS);
+    #pragma unroll
+                    for (int ks = 0; ks < TC_BK / 16; ++ks) {
+    #pragma unroll
+                        for (int p = 0; p < S; ++p) {
+                            const uint64_t ad = smem_desc(sa + p * (TC_BM * TC_BK * 2) + ks * 32);
+                            const uint64_t bd = smem_desc(sz + ks * 32);
+                            mma_f16(dcol + 32u * p, ad, bd, mma_idesc(TC_BM, TC_BN * (S - p)),
+                                    (ks == 0 && p == 0) ? 0u : 1u);
+                        }
+                    }
+                    mma_commit(mempty(ms));   // the stage is free once these MMAs have read it
+                    mma_commit(accf(ms));     // the accumulators are complete
+                }
+                // every MMA issued is complete before TMEM is released
+                mma_commit(drain);
+                mbar_drain(drain, 0, a.status);
+            }
         }
     } else if (warp < TC_EPI_WARP0) {
-        // ---------------- converters: warp wc turns rows 64 wc.. of every slice
-        // of A's byte unit into FP16 digits in the MMA stage; warp 2 also fetches
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TC_REGS_LOW));
+        // ---------------- converters: warp wc turns rows 32 wc.. of every slice
+        // of A's byte unit into FP16 digits in the MMA stage; warp 4 also fetches
         // Z's unit into that stage
-        const int wc = warp - 2;
+        const int wc = warp - TC_CONV_WARP0;
         int zissued = 0;
         Cursor cu = cursor_at(a, u0);
-        // 7 slices x 64 rows x 2 halves of 16 values of k: 28 pieces per lane;
-        // lane l takes row 64 wc + 16 jj + l / 2, half l mod 2, of every slice p
-        // and jj = 0..3, so that its offsets are constants plus a lane term, and
+        // 7 slices x 32 rows x 2 halves of 16 values of k: 14 pieces per lane;
+        // lane l takes row 32 wc + 16 jj + l / 2, half l mod 2, of every slice p
+        // and jj = 0..1, so that its offsets are constants plus a lane term, and
         // row r's 64-byte swizzle (r / 2) mod 4 = (l / 4) mod 4 is the lane's own
-        const uint32_t src_lane = (uint32_t)((wc * 64 + (lane >> 1)) * TC_BK + (lane & 1) * 16);
-        const uint32_t dst_lane = (uint32_t)((wc * 64 + (lane >> 1)) * (TC_BK * 2));
+        constexpr int JJ = TC_BM / TC_CONV_WARPS / 16;
+        const uint32_t src_lane = (uint32_t)((wc * (TC_BM / TC_CONV_WARPS) + (lane >> 1)) * TC_BK + (lane & 1) * 16);
+        const uint32_t dst_lane = (uint32_t)((wc * (TC_BM / TC_CONV_WARPS) + (lane >> 1)) * (TC_BK * 2));
         const int sw = (lane >> 2) & 3, hh = lane & 1;
         const uint32_t c0 = (uint32_t)(((2 * hh) ^ sw) << 4), c1 = (uint32_t)(((2 * hh + 1) ^ sw) << 4);
-        constexpr int NP = S * 4, G = NP / 2;   // pieces, and pieces loaded before any is converted
+        constexpr int NP = S * JJ, G = (NP + 1) / 2;   // pieces, and pieces loaded before any is converted
         for (int i = 0; i < nu; ++i, cu.next(a.nchunks)) {
             const int st = i % TC_TSTAGES;
             const uint32_t ph = (uint32_t)((i / TC_TSTAGES) & 1);
@@ -605,10 +619,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 uint4 b[G];
 #pragma unroll
                 for (int t = 0; t < G; ++t)
-                    b[t] = ld_shared_v4(src + ((g0 + t) >> 2) * (TC_BM * TC_BK) + ((g0 + t) & 3) * 16 * TC_BK);
+                    if (g0 + t < NP)
+                        b[t] = ld_shared_v4(src + ((g0 + t) / JJ) * (TC_BM * TC_BK) + ((g0 + t) % JJ) * 16 * TC_BK);
 #pragma unroll
                 for (int t = 0; t < G; ++t) {
-                    const int p = (g0 + t) >> 2, jj = (g0 + t) & 3;
+                    if (g0 + t >= NP) continue;
+                    const int p = (g0 + t) / JJ, jj = (g0 + t) % JJ;
                     uint32_t o[8];
                     bytes_to_half2(b[t].x, o[0], o[1]);
                     bytes_to_half2(b[t].y, o[2], o[3]);
@@ -630,6 +646,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int i = max(0, zissued - TC_MSTAGES); i < zissued; ++i)
                 mbar_drain(zfull(i & 1), (uint32_t)((i >> 1) & 1), a.status);
     } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(TC_REGS_HIGH));
         // ---------------- epilogue: warp w drains TMEM lanes 32 (w mod 4).., rhs 16 h..
         const int q = warp & 3, h = (warp - TC_EPI_WARP0) >> 2;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
@@ -799,6 +816,17 @@ hodlr_status oz_matvec(hodlr_ctx *c, const void *abuf, int64_t n, int s, const d
     const int grid = (int)std::min<long long>(std::max(1, c->num_sms), units);
     TcArgs ta{n, s, nchunks, sp / TC_BN, units, Phi, Plo, np, c->d_status};
     HODLR_TRY_CUDA(cudaFuncSetAttribute(oz_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    {
+        // the warpgroups' register changes assume this allocation per thread:
+        // with any other, the drain warps' increase could never be granted
+        cudaFuncAttributes fa;
+        HODLR_TRY_CUDA(cudaFuncGetAttributes(&fa, oz_tc_gemm_kernel));
+        if (fa.numRegs != TC_REGS_LAUNCH) {
+            set_error("oz_matvec: the product kernel was compiled with %d registers per thread, not %d", fa.numRegs,
+                      TC_REGS_LAUNCH);
+            return HODLR_CUDA_ERROR;
+        }
+    }
     {
         ProfScope ps("oz_tc_gemm_kernel", st);
         oz_tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(sl, zs, ta);
