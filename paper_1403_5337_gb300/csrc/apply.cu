@@ -496,21 +496,23 @@ struct TileSmem {
     size_t xs, vs, ws, es, total;
 };
 
-// Shared-memory layout of apply_tile_kernel (offsets in bytes).
+// Shared-memory layout of one phase of apply_tile_kernel (offsets in bytes):
+// kw rows of w (2 r_c of a level, the leaf size b of the leaf phase), rv
+// columns of the next level's V, and E's (or the leaf inverse's) rows.
 template <typename S>
-TileSmem tile_smem(int rpmax, int bmax) {
+TileSmem tile_smem(int kw, int rv, bool leafp) {
     auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
     TileSmem m{};
     m.xs = 0;                                                             // x: 32 rhs x 33 (padded rows)
-    m.vs = m.xs + al(32 * 33 * sizeof(float));                            // V: rp columns x 32 rows
-    m.ws = m.vs + al((size_t)32 * rpmax * sizeof(S));                     // w: 2 rp x 32, or the leaf's x: b x 32
-    m.es = m.ws + al((size_t)std::max(2 * rpmax, bmax) * 32 * sizeof(float));
-    m.total = m.es + al(std::max((size_t)2 * rpmax * 32 * sizeof(S), (size_t)bmax * 32 * sizeof(float)));
+    m.vs = m.xs + al(32 * 33 * sizeof(float));                            // V: rv columns x 32 rows
+    m.ws = m.vs + al((size_t)32 * rv * sizeof(S));                        // w: kw x 32 (the leaf's x: b x 32)
+    m.es = m.ws + al((size_t)kw * 32 * sizeof(float));
+    m.total = m.es + al((size_t)kw * 32 * (leafp ? sizeof(float) : sizeof(S)));
     return m;
 }
 
 template <typename S>
-__global__ void __launch_bounds__(AP_THREADS, 2) apply_tile_kernel(const FusedArgs<float, S> a, int c, TileSmem sm) {
+__global__ void __launch_bounds__(AP_THREADS, 3) apply_tile_kernel(const FusedArgs<float, S> a, int c, TileSmem sm) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q0 = 4 * warp;
     const int L = a.L;
@@ -778,13 +780,22 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a0, cudaStrea
     if (path == 2 && a.L >= 1) {
         // several tiles per CTA: one launch per phase, one CTA per tile
         if constexpr (std::is_same<T, float>::value) {
-            const TileSmem tsm = tile_smem<S>(a.rpmax, a.bmax);
-            if (tsm.total <= (size_t)optin / 2) {   // two CTAs per SM
+            // per phase: its own shared-memory layout (at most three CTAs' worth
+            // per SM on the largest)
+            std::vector<TileSmem> tsm(a.L + 2);
+            size_t most = 0;
+            for (int c = a.L + 1; c >= 1; --c) {
+                const bool leafp = c > a.L;
+                const int cv = leafp ? a.L : c - 1;
+                tsm[c] = tile_smem<S>(leafp ? a.bmax : 2 * a.rp[c], cv >= 1 ? a.rp[cv] : 0, leafp);
+                most = std::max(most, tsm[c].total);
+            }
+            if (most <= (size_t)optin / 2) {   // at least two CTAs per SM on every phase
                 HODLR_TRY_CUDA(cudaFuncSetAttribute(apply_tile_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)tsm.total));
+                                                    (int)most));
                 ProfScope ps("apply_phase_kernel", st);
                 for (int c = a.L + 1; c >= 1; --c) {
-                    apply_tile_kernel<S><<<h->ntiles, AP_THREADS, tsm.total, st>>>(a, c, tsm);
+                    apply_tile_kernel<S><<<h->ntiles, AP_THREADS, tsm[c].total, st>>>(a, c, tsm[c]);
                     note_launch();
                     HODLR_TRY_CUDA(cudaGetLastError());
                 }
