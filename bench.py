@@ -837,7 +837,8 @@ def main():
                               "fp64_oracle": oracle["precond_error_fp64_oracle"] if oracle else None},
             "x_vs_oracle": oracle,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": 8 * n * n + 8 * B.numel(),
+            "e2e": {"value": e2e_ms / world, "unit": "ms", "median_ms": statistics.median(e2e) / world,
+                    "h2d_bytes_per_step": 8 * n * n + 8 * B.numel(),
                     "d2h_bytes_per_step": 8 * B.numel()},
             "fp64_path": compare,
             "gpu_launches": n_launches, "gpu_launches_per_step": n_launches / args.steps,
