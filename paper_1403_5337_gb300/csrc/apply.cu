@@ -512,11 +512,11 @@ TileSmem tile_smem(int kw, int rv, bool leafp) {
 }
 
 template <typename S>
-__global__ void __launch_bounds__(AP_THREADS, 3) apply_tile_kernel(const FusedArgs<float, S> a, int c, TileSmem sm) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void tile_phase(const FusedArgs<float, S> &a, int c, const TileSmem &sm, int tile,
+                                           unsigned char *smem) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q0 = 4 * warp;
     const int L = a.L;
-    const int4 tl = a.tiles[blockIdx.x];
+    const int4 tl = a.tiles[tile];
     const int leaf = tl.x, nrows = tl.z;
     const int64_t row0 = tl.y;
     const bool leafp = c > L;
@@ -653,8 +653,16 @@ __global__ void __launch_bounds__(AP_THREADS, 3) apply_tile_kernel(const FusedAr
                     if (q0 + j < rr) atomicAdd(wd + j, acc[j] * sc);
             }
         }
-        __syncthreads();   // the shared buffers are refilled by the next pass
+        __syncthreads();   // the shared buffers are refilled by the next pass (or tile)
     }
+}
+
+// One phase over all tiles: CTAs resident together walk the tiles, so that no
+// partly filled last wave is left.
+template <typename S>
+__global__ void __launch_bounds__(AP_THREADS, 3) apply_tile_kernel(const FusedArgs<float, S> a, int c, TileSmem sm) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) tile_phase<S>(a, c, sm, t, smem);
 }
 
 template <typename T, typename S, int RC>
@@ -795,7 +803,11 @@ hodlr_status launch_fused(const hodlr_t *h, const FusedArgs<T, S> &a0, cudaStrea
                                                     (int)most));
                 ProfScope ps("apply_phase_kernel", st);
                 for (int c = a.L + 1; c >= 1; --c) {
-                    apply_tile_kernel<S><<<h->ntiles, AP_THREADS, tsm[c].total, st>>>(a, c, tsm[c]);
+                    int per = 0;
+                    HODLR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_tile_kernel<S>, AP_THREADS,
+                                                                                 tsm[c].total));
+                    const int g = std::max(1, std::min(h->ntiles, std::max(per, 1) * h->ctx->num_sms));
+                    apply_tile_kernel<S><<<g, AP_THREADS, tsm[c].total, st>>>(a, c, tsm[c]);
                     note_launch();
                     HODLR_TRY_CUDA(cudaGetLastError());
                 }
