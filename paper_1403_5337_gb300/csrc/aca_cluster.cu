@@ -339,39 +339,64 @@ __global__ void __launch_bounds__(CT, 1)
         // ---- row pass on own columns -> v_k (unscaled, kept in registers); U(i_k, :)
         // was gathered into pu at the end of the previous step
         const int kin = k < kcs ? k : kcs;
-        T ba = T(-1), bv = T(0);
-        int bi = INT_MAX;
+        // the NPT entries of a thread advance together through l (independent
+        // chains in flight; each entry's own terms still in the order l = 0..k-1)
         T rreg[NPT];
+        int64_t jl[NPT];
+        bool jok[NPT];
 #pragma unroll
         for (int t = 0; t < NPT; ++t) {
             const int64_t j = j0 + tid + (int64_t)t * CT;
-            T r = T(0);
-            if (j < j1) {
-                const int64_t jl = j - j0;
-                r = dev::from_double<T>(arow_pf[t]);
-                int l = 0;
-                if constexpr (sizeof(T) == 4) {   // U(i_k, l..l+3) in one 16-byte broadcast load
+            jok[t] = j < j1;
+            jl[t] = jok[t] ? j - j0 : 0;   // a slice entry that exists, for the idle lanes
+            rreg[t] = jok[t] ? dev::from_double<T>(arow_pf[t]) : T(0);
+        }
+        if (jok[0]) {   // (a thread that owns no column skips the pass)
+            int l = 0;
+            if constexpr (sizeof(T) == 4) {   // U(i_k, l..l+3) in one 16-byte broadcast load
 #pragma unroll 2
-                    for (; l + 4 <= kin; l += 4) {
-                        const float4 p4 = *reinterpret_cast<const float4 *>(pu + l);
-                        r = dev::sub_rn(r, dev::mul_rn(p4.x, Vs[(size_t)l * snr + jl]));
-                        r = dev::sub_rn(r, dev::mul_rn(p4.y, Vs[(size_t)(l + 1) * snr + jl]));
-                        r = dev::sub_rn(r, dev::mul_rn(p4.z, Vs[(size_t)(l + 2) * snr + jl]));
-                        r = dev::sub_rn(r, dev::mul_rn(p4.w, Vs[(size_t)(l + 3) * snr + jl]));
+                for (; l + 4 <= kin; l += 4) {
+                    const float4 p4 = *reinterpret_cast<const float4 *>(pu + l);
+#pragma unroll
+                    for (int t = 0; t < NPT; ++t) {
+                        const T *vs = Vs + (size_t)l * snr + jl[t];
+                        rreg[t] = dev::sub_rn(rreg[t], dev::mul_rn(p4.x, vs[0]));
+                        rreg[t] = dev::sub_rn(rreg[t], dev::mul_rn(p4.y, vs[snr]));
+                        rreg[t] = dev::sub_rn(rreg[t], dev::mul_rn(p4.z, vs[2 * snr]));
+                        rreg[t] = dev::sub_rn(rreg[t], dev::mul_rn(p4.w, vs[3 * snr]));
                     }
                 }
-#pragma unroll 8
-                for (; l < kin; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vs[(size_t)l * snr + jl]));
-                for (; l < k; ++l) r = dev::sub_rn(r, dev::mul_rn(pu[l], Vg[(int64_t)l * ld + j]));
+            }
+#pragma unroll(NPT == 1 ? 8 : (NPT >= 8 ? 2 : 4))
+            for (; l < kin; ++l) {
+                const T p = pu[l];
+#pragma unroll
+                for (int t = 0; t < NPT; ++t)
+                    rreg[t] = dev::sub_rn(rreg[t], dev::mul_rn(p, Vs[(size_t)l * snr + jl[t]]));
+            }
+#pragma unroll(NPT >= 8 ? 2 : 4)
+            for (; l < k; ++l) {
+                const T p = pu[l];
+                const T *vg = Vg + (int64_t)l * ld + j0;
+#pragma unroll
+                for (int t = 0; t < NPT; ++t)
+                    if (jok[t]) rreg[t] = dev::sub_rn(rreg[t], dev::mul_rn(p, vg[jl[t]]));
+            }
+        }
+        T ba = T(-1), bv = T(0);
+        int bi = INT_MAX;
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            if (jok[t]) {
+                const T r = rreg[t];
                 const T a = fabs(r);
                 if (a != a) atomicOr(status, ST_NONFINITE);
                 if (a > ba) {
                     ba = a;
-                    bi = (int)j;
+                    bi = (int)(j0 + jl[t]);
                     bv = r;
                 }
             }
-            rreg[t] = r;
         }
         const Cand<T> cr = cta_argmax(ba, bi, bv, red[0]);
         if (deferred) {   // the previous step's stop test, made meanwhile by the upper warps
@@ -424,32 +449,59 @@ __global__ void __launch_bounds__(CT, 1)
         greg_store(pv, k);
         __syncthreads();
         // ---- column pass on own rows -> u_k
+        T ureg[NPT];
+        int64_t ql[NPT];
+        bool qok[NPT];
+#pragma unroll
+        for (int t = 0; t < NPT; ++t) {
+            const int64_t q = i0 + tid + (int64_t)t * CT;
+            qok[t] = q < i1;
+            ql[t] = qok[t] ? q - i0 : 0;
+            ureg[t] = qok[t] ? dev::from_double<T>(acol_pf[t]) : T(0);
+        }
+        if (qok[0]) {
+            int l = 0;
+            if constexpr (sizeof(T) == 4) {   // V(j_k, l..l+3) in one 16-byte broadcast load
+#pragma unroll 2
+                for (; l + 4 <= kin; l += 4) {
+                    const float4 p4 = *reinterpret_cast<const float4 *>(pv + l);
+#pragma unroll
+                    for (int t = 0; t < NPT; ++t) {
+                        const T *us = Us + (size_t)l * smr + ql[t];
+                        ureg[t] = dev::sub_rn(ureg[t], dev::mul_rn(p4.x, us[0]));
+                        ureg[t] = dev::sub_rn(ureg[t], dev::mul_rn(p4.y, us[smr]));
+                        ureg[t] = dev::sub_rn(ureg[t], dev::mul_rn(p4.z, us[2 * smr]));
+                        ureg[t] = dev::sub_rn(ureg[t], dev::mul_rn(p4.w, us[3 * smr]));
+                    }
+                }
+            }
+#pragma unroll(NPT == 1 ? 8 : (NPT >= 8 ? 2 : 4))
+            for (; l < kin; ++l) {
+                const T p = pv[l];
+#pragma unroll
+                for (int t = 0; t < NPT; ++t)
+                    ureg[t] = dev::sub_rn(ureg[t], dev::mul_rn(p, Us[(size_t)l * smr + ql[t]]));
+            }
+#pragma unroll(NPT >= 8 ? 2 : 4)
+            for (; l < k; ++l) {
+                const T p = pv[l];
+                const T *ug = Ug + (int64_t)l * ld + i0;
+#pragma unroll
+                for (int t = 0; t < NPT; ++t)
+                    if (qok[t]) ureg[t] = dev::sub_rn(ureg[t], dev::mul_rn(p, ug[ql[t]]));
+            }
+        }
         T ca = T(-1), cvv = T(0);
         int ci = INT_MAX;
 #pragma unroll
         for (int t = 0; t < NPT; ++t) {
-            const int64_t q = i0 + tid + (int64_t)t * CT;
-            if (q < i1) {
-                const int64_t ql = q - i0;
-                T u = dev::from_double<T>(acol_pf[t]);
-                int l = 0;
-                if constexpr (sizeof(T) == 4) {   // V(j_k, l..l+3) in one 16-byte broadcast load
-#pragma unroll 2
-                    for (; l + 4 <= kin; l += 4) {
-                        const float4 p4 = *reinterpret_cast<const float4 *>(pv + l);
-                        u = dev::sub_rn(u, dev::mul_rn(p4.x, Us[(size_t)l * smr + ql]));
-                        u = dev::sub_rn(u, dev::mul_rn(p4.y, Us[(size_t)(l + 1) * smr + ql]));
-                        u = dev::sub_rn(u, dev::mul_rn(p4.z, Us[(size_t)(l + 2) * smr + ql]));
-                        u = dev::sub_rn(u, dev::mul_rn(p4.w, Us[(size_t)(l + 3) * smr + ql]));
-                    }
-                }
-#pragma unroll 8
-                for (; l < kin; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Us[(size_t)l * smr + ql]));
-                for (; l < k; ++l) u = dev::sub_rn(u, dev::mul_rn(pv[l], Ug[(int64_t)l * ld + q]));
-                if (k < kcs) Us[(size_t)k * smr + ql] = u;
+            if (qok[t]) {
+                const int64_t q = i0 + ql[t];
+                const T u = ureg[t];
+                if (k < kcs) Us[(size_t)k * smr + ql[t]] = u;
                 Ug[(int64_t)k * ld + q] = u;
                 if (u != u) atomicOr(status, ST_NONFINITE);
-                if (!used[ql]) {
+                if (!used[ql[t]]) {
                     const T a = fabs(u);
                     if (a > ca) {
                         ca = a;
@@ -473,15 +525,37 @@ __global__ void __launch_bounds__(CT, 1)
                 dp[(isu ? 0 : ACA_CAP + 1) + l] = d;
             }
         } else {
-            for (int l = warp; l <= k; l += CW) {
-                T su = T(0), sv = T(0);
-                for (int64_t q = i0 + lane; q < i1; q += 32) su = fma(Ug[(int64_t)l * ld + q], Ug[(int64_t)k * ld + q], su);
-                for (int64_t j = j0 + lane; j < j1; j += 32) sv = fma(Vg[(int64_t)l * ld + j], Vg[(int64_t)k * ld + j], sv);
-                su = warp_sum(su);
-                sv = warp_sum(sv);
-                if (lane == 0) {
-                    dp[l] = su;
-                    dp[ACA_CAP + 1 + l] = sv;
+            // LG columns l per warp at a time (independent chains; each dot
+            // still lane-strided in ascending q, then summed over the warp)
+            constexpr int LG = 4;
+            for (int l0 = warp * LG; l0 <= k; l0 += CW * LG) {
+                T su[LG], sv[LG];
+                const T *ul[LG], *vl[LG];
+#pragma unroll
+                for (int g = 0; g < LG; ++g) {
+                    su[g] = sv[g] = T(0);
+                    const int l = l0 + g <= k ? l0 + g : k;   // a column that exists, for the idle chains
+                    ul[g] = Ug + (int64_t)l * ld;
+                    vl[g] = Vg + (int64_t)l * ld;
+                }
+                const T *uk = Ug + (int64_t)k * ld, *vk = Vg + (int64_t)k * ld;
+                for (int64_t q = i0 + lane; q < i1; q += 32) {
+                    const T b = uk[q];
+#pragma unroll
+                    for (int g = 0; g < LG; ++g) su[g] = fma(ul[g][q], b, su[g]);
+                }
+                for (int64_t j = j0 + lane; j < j1; j += 32) {
+                    const T b = vk[j];
+#pragma unroll
+                    for (int g = 0; g < LG; ++g) sv[g] = fma(vl[g][j], b, sv[g]);
+                }
+#pragma unroll
+                for (int g = 0; g < LG; ++g) {
+                    const T tu = warp_sum(su[g]), tv = warp_sum(sv[g]);
+                    if (lane == 0 && l0 + g <= k) {
+                        dp[l0 + g] = tu;
+                        dp[ACA_CAP + 1 + l0 + g] = tv;
+                    }
                 }
             }
         }
@@ -636,7 +710,7 @@ hodlr_status launch_level(hodlr_ctx *c, const double *A, int64_t lda, int sym, c
 hodlr_status launch_aca_levels(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
                                const AcaBlockDesc *d_blocks, const std::vector<int> &level_first,
                                const std::vector<int64_t> &level_maxdim, double tol, cudaStream_t s,
-                               std::vector<cudaEvent_t> &done) {
+                               std::vector<cudaEvent_t> &done, const std::function<hodlr_status()> &after_first) {
     // level_first[l] .. level_first[l+1]: the blocks of level l + 1 (all of one size class)
     const int nlev = (int)level_first.size() - 1;
     done.assign(nlev, nullptr);
@@ -675,6 +749,7 @@ hodlr_status launch_aca_levels(hodlr_ctx *c, const double *A, int64_t lda, int s
         }
         cudaEventCreate(&done[l]);   // timed: the build reports the compression time
         cudaEventRecord(done[l], ls);
+        if (l == 0 && rs == HODLR_OK && after_first) rs = after_first();
     }
     cudaEventDestroy(fork);
     return rs;

@@ -720,6 +720,23 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
     // done[c - 1]: level c compressed; rstream[c]: the stream its ranks are read on
     std::vector<cudaEvent_t> done;
     std::vector<cudaStream_t> rstream(L + 1, st);
+    // The leaf inverses depend on A only and run on a side stream.  With ACA
+    // they are issued right after the top level's launch (one cluster per
+    // block, few SMs), so that their CTAs are dispatched before the lower
+    // levels' and every level's factor share, which waits for them, can start
+    // as soon as its level is compressed.
+    h->leafinv = mbase + o_leafinv;
+    cudaStream_t lstream = c->side[HODLR_SIDE_STREAMS - 1];
+    hodlr_status rleaf = HODLR_OK;
+    bool leaf_issued = false;
+    auto issue_leaf = [&]() -> hodlr_status {
+        cudaEventRecord(lfork, st);
+        cudaStreamWaitEvent(lstream, lfork, 0);
+        rleaf = leaf_inverses(h, lstream);
+        cudaEventRecord(ljoin, lstream);
+        leaf_issued = true;
+        return rleaf;
+    };
     if (method == HODLR_ACA) {
         AcaBlockDesc *db = (AcaBlockDesc *)(sbase + o_desc);
         cudaMemcpyAsync(db, blocks.data(), blocks.size() * sizeof(AcaBlockDesc), cudaMemcpyHostToDevice, st);
@@ -734,7 +751,7 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
             b0 += 1 << l;
         }
         first.push_back(b0);
-        rs = launch_aca_levels(c, A->data, A->ld, h->sym, cprec, db, first, maxdim, tol, st, done);
+        rs = launch_aca_levels(c, A->data, A->ld, h->sym, cprec, db, first, maxdim, tol, st, done, issue_leaf);
         for (int l = 1; l <= L; ++l) rstream[l] = c->side[(l - 1) % HODLR_SIDE_STREAMS];
     } else {
         // -2: the adaptive depth of Sec. 5.3 (run_bdlr grows it per block)
@@ -749,9 +766,8 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
     }
     // ---- what the compression does not need, issued after its launch: the
     // leaf bounds, the apply's row tiles (32 rows, never straddling a leaf) and
-    // the first tile of every leaf, and the leaf inverses, which depend on A
-    // only and run on a side stream while the off-diagonal blocks are
-    // compressed (they join the levels' streams and the caller's stream later)
+    // the first tile of every leaf, and (without ACA levels) the leaf inverses
+    // (they join the levels' streams and the caller's stream later)
     cudaMemcpyAsync(h->d_bounds, bounds.data(), bounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     h->d_tiles = (const int4 *)(mbase + o_tiles);
     h->d_tile_first = (int *)(mbase + o_tfirst);
@@ -759,12 +775,7 @@ static hodlr_status build_one(hodlr_ctx *c, const hodlr_matrix *A, int leaf, dou
     if (!tiles.empty())
         cudaMemcpyAsync((void *)h->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_tile_first, tfirst.data(), tfirst.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-    h->leafinv = mbase + o_leafinv;
-    cudaStream_t lstream = c->side[HODLR_SIDE_STREAMS - 1];
-    cudaEventRecord(lfork, st);
-    cudaStreamWaitEvent(lstream, lfork, 0);
-    const hodlr_status rleaf = leaf_inverses(h, lstream);
-    cudaEventRecord(ljoin, lstream);
+    if (!leaf_issued) issue_leaf();
     // share_done[l]: level l's compaction and (unless deferred) its share of the
     // factorisation are complete
     std::vector<cudaEvent_t> share_done(L + 1, nullptr);

@@ -6,6 +6,7 @@
 
 #include <string>
 #include <deque>
+#include <functional>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -246,11 +247,14 @@ struct AcaBlockDesc {
 // streams (forked from s; level l + 1 on side[l mod HODLR_SIDE_STREAMS]).  level_first: first block of
 // each level in d_blocks (size nlev + 1); level_maxdim: largest block side per level.
 // done[l] (created here, destroyed by the caller) completes with level l + 1's
-// compression; s itself does not wait for the levels.
+// compression; s itself does not wait for the levels.  after_first, if set, is
+// called once the first level is launched (work issued there is dispatched
+// before the other levels' CTAs); its error ends the launch.
 hodlr_status launch_aca_levels(hodlr_ctx *c, const double *A, int64_t lda, int sym, int cprec,
                                const AcaBlockDesc *d_blocks, const std::vector<int> &level_first,
                                const std::vector<int64_t> &level_maxdim, double tol, cudaStream_t s,
-                               std::vector<cudaEvent_t> &done);
+                               std::vector<cudaEvent_t> &done,
+                               const std::function<hodlr_status()> &after_first = {});
 
 struct BdlrHost;   // defined in bdlr.cu
 hodlr_status run_bdlr(hodlr_t *h, const hodlr_graph *g, int depth, cudaStream_t s,
