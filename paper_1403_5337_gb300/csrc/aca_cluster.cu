@@ -342,13 +342,13 @@ __global__ void __launch_bounds__(CT, 1)
         // the NPT entries of a thread advance together through l (independent
         // chains in flight; each entry's own terms still in the order l = 0..k-1)
         T rreg[NPT];
-        int64_t jl[NPT];
+        int jl[NPT];   // slice-local (below NPT CT)
         bool jok[NPT];
 #pragma unroll
         for (int t = 0; t < NPT; ++t) {
             const int64_t j = j0 + tid + (int64_t)t * CT;
             jok[t] = j < j1;
-            jl[t] = jok[t] ? j - j0 : 0;   // a slice entry that exists, for the idle lanes
+            jl[t] = jok[t] ? (int)(j - j0) : 0;   // a slice entry that exists, for the idle lanes
             rreg[t] = jok[t] ? dev::from_double<T>(arow_pf[t]) : T(0);
         }
         if (jok[0]) {   // (a thread that owns no column skips the pass)
@@ -450,13 +450,13 @@ __global__ void __launch_bounds__(CT, 1)
         __syncthreads();
         // ---- column pass on own rows -> u_k
         T ureg[NPT];
-        int64_t ql[NPT];
+        int ql[NPT];
         bool qok[NPT];
 #pragma unroll
         for (int t = 0; t < NPT; ++t) {
             const int64_t q = i0 + tid + (int64_t)t * CT;
             qok[t] = q < i1;
-            ql[t] = qok[t] ? q - i0 : 0;
+            ql[t] = qok[t] ? (int)(q - i0) : 0;
             ureg[t] = qok[t] ? dev::from_double<T>(acol_pf[t]) : T(0);
         }
         if (qok[0]) {

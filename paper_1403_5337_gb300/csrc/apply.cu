@@ -482,13 +482,17 @@ __global__ void __launch_bounds__(AP_THREADS, 2) apply_phase_kernel(const FusedA
 }
 
 // The per-phase apply for FP32 arithmetic, one CTA per 32-row tile and up to
-// 32 right-hand sides per pass: lane = row of the tile, warp = 4 right-hand
-// sides.  Everything a tile reads in a phase is requested before any of it is
-// used -- E's (or the leaf inverse's) and the next level's V rows by
-// asynchronous copies into shared memory, the node's w and the tile's x by
-// batched loads -- so that a phase costs a few memory round trips per tile.  Then
-//   x -= E w          (k over 2 rp: one E element, four w values, four FMAs),
-//   w(next) += V^T x  (lane = column of V, warp = 4 right-hand sides, atomics),
+// 32 right-hand sides per pass.  Everything a tile reads in a phase is requested
+// before any of it is used -- E's (or the leaf inverse's) and the next level's V
+// rows by asynchronous copies into shared memory, the node's w and the tile's x
+// by batched loads -- so that a phase costs a few memory round trips per tile.
+// Then
+//   x -= E w          thread = 2 rows x 8 right-hand sides over a quarter of
+//                     the k range (per k: one E pair, two broadcast w vectors,
+//                     16 FMAs); the four quarter sums added in shared memory,
+//   w(next) += V^T x  V transposed in shared memory, lane = 2 columns of V,
+//                     warp = 4 right-hand sides, x broadcast (per row: one V
+//                     pair, one x vector, 8 FMAs); atomics into w,
 // or, at the top level, the store of x.  The leaf phase forms x = K_leaf^-1 x
 // from the tile's rows of the leaf inverse the same way.
 
@@ -496,17 +500,56 @@ struct TileSmem {
     size_t xs, vs, ws, es, total;
 };
 
+// w (or the leaf's x) in shared memory: k rows of 32 right-hand sides, the
+// eight 4-wide groups of row k permuted by k mod 8, so that a warp storing one
+// right-hand side of 32 consecutive rows spreads over eight bank groups, and a
+// warp storing 32 right-hand sides of one row over all 32 banks.
+__device__ __forceinline__ int ws_at(int k, int q) { return k * 32 + ((((q >> 2) ^ k) & 7) << 2) + (q & 3); }
+__device__ __forceinline__ int ws_group(int k, int g) { return k * 32 + (((g ^ k) & 7) << 2); }
+
+// Row pitch (elements) of V transposed in shared memory: even, and an odd
+// number of 32-bit words for 16-bit V (a column's 32 rows over 32 banks).
+__host__ __device__ __forceinline__ int vt_pitch(int rv) { return (rv + 63) / 64 * 64 + 2; }
+
+constexpr int TP_KPARTS = 4;                                 // k-range quarters of x -= E w
+constexpr int TP_PART = 32 * 33;                             // one quarter's sums: x(row r, rhs q) at q 33 + r
+
+template <typename S>
+__device__ __forceinline__ float2 ld2f(const S *p) {
+    if constexpr (std::is_same<S, __half>::value)
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    else
+        return *reinterpret_cast<const float2 *>(p);
+}
+
+__device__ __forceinline__ void fma8(float *acc, float e, const float4 &y0, const float4 &y1) {
+    acc[0] = fmaf(e, y0.x, acc[0]);
+    acc[1] = fmaf(e, y0.y, acc[1]);
+    acc[2] = fmaf(e, y0.z, acc[2]);
+    acc[3] = fmaf(e, y0.w, acc[3]);
+    acc[4] = fmaf(e, y1.x, acc[4]);
+    acc[5] = fmaf(e, y1.y, acc[5]);
+    acc[6] = fmaf(e, y1.z, acc[6]);
+    acc[7] = fmaf(e, y1.w, acc[7]);
+}
+
 // Shared-memory layout of one phase of apply_tile_kernel (offsets in bytes):
-// kw rows of w (2 r_c of a level, the leaf size b of the leaf phase), rv
-// columns of the next level's V, and E's (or the leaf inverse's) rows.
+// x (32 rows x 32 rhs, row pitch 36), rv columns of the next level's V as
+// staged (32 rows each), the w region (kw rows of w -- 2 r_c of a level, the
+// leaf size b of the leaf phase -- later the quarter sums, then V transposed),
+// and E's (or the leaf inverse's) rows.
 template <typename S>
 TileSmem tile_smem(int kw, int rv, bool leafp) {
     auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
     TileSmem m{};
-    m.xs = 0;                                                             // x: 32 rhs x 33 (padded rows)
-    m.vs = m.xs + al(32 * 33 * sizeof(float));                            // V: rv columns x 32 rows
-    m.ws = m.vs + al((size_t)32 * rv * sizeof(S));                        // w: kw x 32 (the leaf's x: b x 32)
-    m.es = m.ws + al((size_t)kw * 32 * sizeof(float));
+    const size_t wbytes = std::max({(size_t)kw * 32 * sizeof(float), (size_t)TP_KPARTS * TP_PART * sizeof(float),
+                                    rv > 0 ? (size_t)32 * vt_pitch(rv) * sizeof(S) : size_t(0)});
+    m.xs = 0;
+    m.vs = m.xs + al(32 * 36 * sizeof(float));
+    m.ws = m.vs + al((size_t)32 * rv * sizeof(S));
+    m.es = m.ws + al(wbytes);
     m.total = m.es + al((size_t)kw * 32 * (leafp ? sizeof(float) : sizeof(S)));
     return m;
 }
@@ -523,8 +566,8 @@ __device__ __forceinline__ void tile_phase(const FusedArgs<float, S> &a, int c, 
     const int cv = leafp ? L : c - 1;              // the level whose V^T x this phase adds (0: none)
     const int rpv = cv >= 1 ? a.rp[cv] : 0;
     const int childv = cv >= 1 ? leaf >> (L - cv) : 0;
-    float *xsP = reinterpret_cast<float *>(smem + sm.xs);   // x(row r, rhs q) at q * 33 + r
-    S *Vs = reinterpret_cast<S *>(smem + sm.vs);            // V(row r, column j) at j * 32 + r
+    float *xT = reinterpret_cast<float *>(smem + sm.xs);    // x(row r, rhs q) at r * 36 + q
+    S *Vs = reinterpret_cast<S *>(smem + sm.vs);            // V(row r, column j) at j * 32 + r, as staged
     float *ws = reinterpret_cast<float *>(smem + sm.ws);
     unsigned char *es_raw = smem + sm.es;
     // ---- E's (or the leaf inverse's) rows of the tile: asynchronous copies
@@ -546,42 +589,35 @@ __device__ __forceinline__ void tile_phase(const FusedArgs<float, S> &a, int c, 
     if (rpv > 0) stage_cols<S>(Vs, a.Vb + a.voff[cv] + row0, a.ldn, rpv, nrows);
     asm volatile("cp.async.commit_group;" ::: "memory");
     const float *vsc = cv >= 1 ? a.vscale[cv] : nullptr;
+    // x -= E w: this thread's rows 2 rh, 2 rh + 1, right-hand sides 8 qb .. 8 qb + 7, k quarter kp
+    const int kp = warp >> 1, qb = ((warp & 1) << 1) | (lane >> 4), rh = lane & 15;
+    const int K = leafp ? b : s2;
+    const int kc = (K + TP_KPARTS - 1) / TP_KPARTS;
+    const int ka = min(K, kp * kc), kb = min(K, ka + kc);
     for (int r0 = 0; r0 < a.s; r0 += 32) {
         const int rr = min(32, a.s - r0);
-        float x[4];
+        float xo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (leafp) {
-            // the leaf's rows of X (FP64 -> FP32), sixteen loads in flight per thread
-            for (int e0 = threadIdx.x; e0 < b * 32; e0 += 16 * AP_THREADS) {
-                float v[16];
+            // the leaf's rows of X (FP64 -> FP32): a warp reads 32 consecutive
+            // rows of one right-hand side, sixteen loads in flight per thread
+            for (int k0 = 0; k0 < b; k0 += 256) {
+#pragma unroll 1
+                for (int qq = warp; qq < 32; qq += 16) {
+                    float v[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int e = e0 + u * AP_THREADS, k = e >> 5, q = e & 31;
-                    v[u] = (e < b * 32 && q < rr) ? (float)a.Xin[l0 + k + (int64_t)(r0 + q) * a.ldxin] : 0.0f;
-                }
+                    for (int u = 0; u < 16; ++u) {
+                        const int q = qq + 8 * (u >> 3), k = k0 + lane + 32 * (u & 7);
+                        v[u] = (k < b && q < rr) ? (float)a.Xin[l0 + k + (int64_t)(r0 + q) * a.ldxin] : 0.0f;
+                    }
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int e = e0 + u * AP_THREADS;
-                    if (e < b * 32) ws[e] = v[u];
+                    for (int u = 0; u < 16; ++u) {
+                        const int q = qq + 8 * (u >> 3), k = k0 + lane + 32 * (u & 7);
+                        if (k < b) ws[ws_at(k, q)] = v[u];
+                    }
                 }
             }
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncthreads();
-            const float *Ks = reinterpret_cast<const float *>(es_raw);
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 4
-            for (int k = 0; k < b; ++k) {
-                const float kv = Ks[k * 32 + lane];
-                const float4 y = *reinterpret_cast<const float4 *>(ws + k * 32 + q0);
-                acc[0] = fmaf(kv, y.x, acc[0]);
-                acc[1] = fmaf(kv, y.y, acc[1]);
-                acc[2] = fmaf(kv, y.z, acc[2]);
-                acc[3] = fmaf(kv, y.w, acc[3]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = acc[j];
         } else {
             // the tile's x and the node's w (times E's column factors), eight loads in flight
-            float xo[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 xo[j] = (lane < nrows && q0 + j < rr) ? a.xt[row0 + lane + (int64_t)(r0 + q0 + j) * a.ldn] : 0.0f;
@@ -598,24 +634,51 @@ __device__ __forceinline__ void tile_phase(const FusedArgs<float, S> &a, int c, 
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int e = e0 + u * AP_THREADS;
-                    if (e < s2 * 32) ws[e] = v[u] * f[u];
+                    if (e < s2 * 32) ws[ws_at(e >> 5, e & 31)] = v[u] * f[u];
                 }
             }
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncthreads();
-            const S *Es = reinterpret_cast<const S *>(es_raw);
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 4
-            for (int k = 0; k < s2; ++k) {
-                const float ev = to_t<float>(Es[k * 32 + lane]);
-                const float4 y = *reinterpret_cast<const float4 *>(ws + k * 32 + q0);
-                acc[0] = fmaf(ev, y.x, acc[0]);
-                acc[1] = fmaf(ev, y.y, acc[1]);
-                acc[2] = fmaf(ev, y.z, acc[2]);
-                acc[3] = fmaf(ev, y.w, acc[3]);
-            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        float acc[2][8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = xo[j] - acc[j];
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        if (leafp) {
+            const float *Ks = reinterpret_cast<const float *>(es_raw);
+#pragma unroll 4
+            for (int k = ka; k < kb; ++k) {
+                const float2 e = *reinterpret_cast<const float2 *>(Ks + k * 32 + 2 * rh);
+                const float4 y0 = *reinterpret_cast<const float4 *>(ws + ws_group(k, 2 * qb));
+                const float4 y1 = *reinterpret_cast<const float4 *>(ws + ws_group(k, 2 * qb + 1));
+                fma8(acc[0], e.x, y0, y1);
+                fma8(acc[1], e.y, y0, y1);
+            }
+        } else {
+            const S *Es = reinterpret_cast<const S *>(es_raw);
+#pragma unroll 4
+            for (int k = ka; k < kb; ++k) {
+                const float2 e = ld2f<S>(Es + k * 32 + 2 * rh);
+                const float4 y0 = *reinterpret_cast<const float4 *>(ws + ws_group(k, 2 * qb));
+                const float4 y1 = *reinterpret_cast<const float4 *>(ws + ws_group(k, 2 * qb + 1));
+                fma8(acc[0], e.x, y0, y1);
+                fma8(acc[1], e.y, y0, y1);
+            }
+        }
+        __syncthreads();   // every warp is done with w: its region takes the quarter sums
+        float *part = ws + kp * TP_PART;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part[(8 * qb + j) * 33 + 2 * rh + i] = acc[i][j];
+        __syncthreads();
+        float x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = (q0 + j) * 33 + lane;
+            const float sum = ((ws[o] + ws[TP_PART + o]) + ws[2 * TP_PART + o]) + ws[3 * TP_PART + o];
+            x[j] = leafp ? sum : xo[j] - sum;
         }
         if (lane >= nrows) x[0] = x[1] = x[2] = x[3] = 0.0f;   // rows past a ragged tile
         // ---- x: kept for the later phases, or (top level / single leaf) stored
@@ -631,26 +694,42 @@ __device__ __forceinline__ void tile_phase(const FusedArgs<float, S> &a, int c, 
             }
         }
         if (cv >= 1) {
-            // ---- w(cv) += V^T x over the tile's rows: lane = column of V, warp =
-            // 4 right-hand sides; lane l reads row (r + l) mod 32 at step r, so
-            // that neither V (32 rows per column) nor x (33 per rhs) conflicts
-#pragma unroll
-            for (int j = 0; j < 4; ++j) xsP[(q0 + j) * 33 + lane] = x[j];
+            // ---- w(cv) += V^T x over the tile's rows
+            __syncthreads();   // the quarter sums are read: the w region takes V transposed
+            *reinterpret_cast<float4 *>(xT + lane * 36 + q0) = make_float4(x[0], x[1], x[2], x[3]);
+            const int vp = vt_pitch(rpv);
+            S *Vt = reinterpret_cast<S *>(ws);   // V(row r, column j) at r * vp + j
+            for (int e = threadIdx.x; e < rpv * 32; e += AP_THREADS) {
+                const int col = e >> 5, r = e & 31;
+                if (r < nrows) Vt[r * vp + col] = Vs[col * 32 + r];
+            }
             __syncthreads();
-            for (int col = lane; col < rpv; col += 32) {
-                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 8
-                for (int r = 0; r < 32; ++r) {
-                    const int rl = (r + lane) & 31;
-                    const float v = to_t<float>(Vs[col * 32 + rl]);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[j] = fmaf(v, xsP[(q0 + j) * 33 + rl], acc[j]);
+            for (int j0 = 2 * lane; j0 < rpv; j0 += 64) {
+                float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+                for (int r = 0; r < nrows; ++r) {
+                    const float2 v = ld2f<S>(Vt + r * vp + j0);
+                    const float4 y = *reinterpret_cast<const float4 *>(xT + r * 36 + q0);
+                    a0[0] = fmaf(v.x, y.x, a0[0]);
+                    a0[1] = fmaf(v.x, y.y, a0[1]);
+                    a0[2] = fmaf(v.x, y.z, a0[2]);
+                    a0[3] = fmaf(v.x, y.w, a0[3]);
+                    a1[0] = fmaf(v.y, y.x, a1[0]);
+                    a1[1] = fmaf(v.y, y.y, a1[1]);
+                    a1[2] = fmaf(v.y, y.z, a1[2]);
+                    a1[3] = fmaf(v.y, y.w, a1[3]);
                 }
-                const float sc = vsc ? vsc[(size_t)childv * rpv + col] : 1.0f;
-                float *wd = a.w[cv] + ((size_t)childv * rpv + col) * a.s + r0 + q0;
+                const bool two = j0 + 1 < rpv;
+                const float sc0 = vsc ? vsc[(size_t)childv * rpv + j0] : 1.0f;
+                const float sc1 = (vsc && two) ? vsc[(size_t)childv * rpv + j0 + 1] : 1.0f;
+                float *wd = a.w[cv] + ((size_t)childv * rpv + j0) * a.s + r0 + q0;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (q0 + j < rr) atomicAdd(wd + j, acc[j] * sc);
+                for (int j = 0; j < 4; ++j) {
+                    if (q0 + j < rr) {
+                        atomicAdd(wd + j, a0[j] * sc0);
+                        if (two) atomicAdd(wd + a.s + j, a1[j] * sc1);
+                    }
+                }
             }
         }
         __syncthreads();   // the shared buffers are refilled by the next pass (or tile)

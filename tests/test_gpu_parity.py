@@ -927,6 +927,36 @@ def test_apply_paths_agree(H, ctx, front4096, precision, nrhs):
     h.close()
 
 
+@pytest.mark.parametrize("precision,nrhs", [("fp32", 5), ("fp16", 40), ("bf16", 33)])
+def test_per_phase_apply_ragged_tiles(H, ctx, front576, precision, nrhs):
+    """FP32-arithmetic per-phase apply on leaves of 72 rows (row tiles of 32, 32
+    and 8) and, past 32 right-hand sides, in two passes: the same K~^-1 X as
+    the single launch up to the rounding order of the sums, and the same as the
+    oracle's solve with the FP64 factors to the storage's rounding."""
+    F = front576
+    tree = O.make_tree(F.n, 64, F.bounds)
+    Fac = O.factor(F.A, tree, O.build(F.A, tree, "aca", 1e-6))
+    h = H.hodlr_build(ctx, _dev(F.A), 64, 1e-6, "aca", precision=precision)
+    b = fg.rhs(F.n, nrhs, seed=7)
+    out = {}
+    try:
+        for path in (1, 2):
+            ctx.set_apply_path(path)
+            X = _dev(b.T)
+            H.hodlr_solve(h, X)
+            torch.cuda.synchronize()
+            out[path] = X.cpu().numpy().T
+    finally:
+        ctx.set_apply_path(0)
+    x1, x2 = out[1], out[2]
+    assert np.all(np.isfinite(x2))
+    assert np.linalg.norm(x2 - x1) <= 2e-5 * np.linalg.norm(x1)
+    ref = O.solve(Fac, b)
+    tol = {"fp32": 1e-4, "fp16": 1e-2, "bf16": 5e-2}[precision]
+    assert np.linalg.norm(x2 - ref) <= tol * np.linalg.norm(ref)
+    h.close()
+
+
 def test_per_phase_apply_matches_oracle(H, ctx, front576):
     """The per-phase apply against the oracle's recursive solve (FP64 factors,
     ACA 1e-6), to the factor-and-solve tolerance."""
